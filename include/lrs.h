@@ -1,0 +1,213 @@
+/*
+ * lrs.h - C-ABI of the GB300 local real-space screening library (liblrs.so).
+ *
+ * The library computes, for atom-centred site grids, the static RPA
+ * polarizability chi0(r, r') and the screened interaction W = v + v chi0 W of
+ * Vinson & Shirley, "Fast, efficient, and accurate dielectric screening using
+ * a local, real-space approach", and the adjoint of that map.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: LRS_OK (0) or one of the
+ *     LRS_ERR_* codes below.  No function aborts, throws or traps.  After a
+ *     failure lrs_last_error() returns a human-readable message for the
+ *     calling thread (valid until that thread's next call).
+ *   - Host pointers passed in are read during the call only and stay owned by
+ *     the caller; the library copies what it needs into device memory that it
+ *     allocates and owns until lrs_destroy().  Host output buffers are
+ *     written before the call returns.  Device pointers ("_dev" entry points)
+ *     are caller-owned, must be on the context's device and are accessed in
+ *     stream order on the context's stream.
+ *   - Matrices are row-major.  Complex numbers are interleaved (re, im)
+ *     float64 pairs.  Site grids index points p = 0 .. npts-1 and, for
+ *     product grids, p = radial_shell * nang + angular_point.
+ *   - Orbital columns are ordered (k outer, band inner); within each k the
+ *     nocc[k] occupied bands come first.
+ *   - Units: Hartree atomic units (bohr, Hartree).
+ *   - A context is not thread-safe; distinct contexts may be used from
+ *     distinct threads.
+ */
+#ifndef LRS_H
+#define LRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LRS_OK            0
+#define LRS_ERR_ARG       1   /* invalid argument (null pointer, size, range) */
+#define LRS_ERR_OOM       2   /* device allocation failed */
+#define LRS_ERR_CUDA      3   /* a CUDA runtime/driver call failed */
+#define LRS_ERR_STATE     4   /* call made out of order (e.g. build before load) */
+#define LRS_ERR_TIMEOUT   5   /* a bounded device-side wait gave up */
+#define LRS_ERR_NUMERIC   6   /* non-finite value or exactly zero pivot */
+#define LRS_ERR_UNSUPPORTED 7 /* mode not available on this device/build */
+
+/* arithmetic of the Green's-function contractions (chi0, adjoint, projection) */
+#define LRS_FP64          0   /* float64 throughout */
+#define LRS_MIXED_BF16X3  1   /* bf16 hi+lo split operands, 3 products, fp32 accumulation */
+#define LRS_MIXED_FP16X3  2   /* fp16 hi+lo split operands (power-of-two scaled), fp32 accumulation */
+
+/* projection modes */
+#define LRS_PROJ_EXACT    0   /* direct Fourier sum, Sec. VI.B method 1 */
+
+typedef struct lrs_ctx lrs_ctx;
+
+typedef struct lrs_stats_t {
+  double ms_project;      /* device time of the last lrs_project call */
+  double ms_chi0;         /* device time of the last lrs_build_chi0 call */
+  double ms_w;            /* device time of the last lrs_solve_w call */
+  double ms_backward;     /* device time of the last lrs_backward call */
+  double ms_chi0_main;    /* device time of the main contraction kernel(s) of the last lrs_build_chi0 */
+  double flop_chi0;       /* algorithmic flop of the last lrs_build_chi0: sum 8 npts^2 K nfreq */
+  double flop_w;          /* algorithmic flop of the last lrs_solve_w: sum 14/3 npts^3 */
+  int64_t kernel_launches;/* kernels launched by this context since creation */
+  int64_t device_bytes;   /* device memory currently held by the context */
+  int64_t device_bytes_peak;
+  int status_word;        /* last device-side status (0 = ok) */
+} lrs_stats_t;
+
+/* Last error message of the calling thread ("" if none). */
+const char* lrs_last_error(void);
+
+/* Library version string. */
+const char* lrs_version(void);
+
+/*
+ * Create a context on CUDA device `device`.  `precision` is LRS_FP64,
+ * LRS_MIXED_BF16X3 or LRS_MIXED_FP16X3 and selects the arithmetic of the
+ * projection, chi0 and adjoint contractions; energy denominators, frequency
+ * accumulation, the Coulomb operator and the Dyson LU are float64 in every
+ * mode.  `stream` is a cudaStream_t (NULL = legacy default stream) on which
+ * all work of the context is issued.
+ * Errors: LRS_ERR_ARG (null ctx, bad precision), LRS_ERR_CUDA.
+ */
+int lrs_create(lrs_ctx** ctx, int device, int precision, void* stream);
+
+/* Free every device buffer and the context (NULL is accepted). */
+int lrs_destroy(lrs_ctx* ctx);
+
+/* Change the stream of an existing context (same device). */
+int lrs_set_stream(lrs_ctx* ctx, void* stream);
+
+/*
+ * Load Bloch coefficients and band energies (Eq. (bloch), Sec. VI.A-B).
+ *   cell[9]          lattice vectors a1, a2, a3 as rows (bohr)
+ *   nk, kpts[nk*3]   k-points, cartesian (bohr^-1)
+ *   kweights[nk]     k-point weights w_k of the Brillouin-zone sum (Sec. VI.D), sum 1
+ *   ng, gvec[ng*3]   plane waves as integer multiples of the reciprocal vectors
+ *   nbands, nocc[nk] bands per k and how many of them are occupied (0 < nocc < nbands)
+ *   coeff            [nk][ng][nbands] complex C_kb(G); psi_kb(r) =
+ *                    Omega^-1/2 sum_G C_kb(G) exp(i (k+G).r)
+ *   energies         [nk][nbands] band energies (occupied first)
+ * Replaces any previous orbitals and invalidates projected site orbitals.
+ * Errors: LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA.
+ */
+int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kpts,
+                      const double* kweights, int ng, const int* gvec, int nbands,
+                      const int* nocc, const double* coeff, const double* energies);
+
+/*
+ * Define the site grids (Sec. VI.A, App. D.1).
+ *   centers[nsites*3]  site centres tau (bohr)
+ *   npts[nsites]       points per site
+ *   pts                concatenation over sites of [npts][3] offsets r - tau (bohr, nonzero)
+ *   wts                concatenation over sites of [npts] integration weights (include r^2,
+ *                      angular weights summing to 4 pi)
+ *   lmax[nsites]       multipole cutoff L of the Coulomb operator (Sec. VI.E), 0..64
+ * Replaces any previous sites.
+ * Errors: LRS_ERR_ARG (npts < 1, point at the origin, lmax out of range), LRS_ERR_OOM.
+ */
+int lrs_set_sites(lrs_ctx* ctx, int nsites, const double* centers, const int* npts,
+                  const double* pts, const double* wts, const int* lmax);
+
+/*
+ * Imaginary-frequency quadrature of Eq. (chi1) (App. D.1, single-grid map):
+ * nf Gauss-Legendre points a_i, weights w_i on [0,1], t_i = zeta a_i/(1-a_i),
+ * W_i = zeta w_i/(1-a_i)^2.  mu: chemical potential (NaN = mid-gap over all k).
+ * zeta <= 0 selects the rule of App. D.1: geometric mean of the smallest and
+ * largest |mu - eps| with 0.5 eV added in quadrature to the smallest.
+ * mu_out/zeta_out (may be NULL) receive the values used.  nf in 1..128.
+ * Requires orbitals.  Errors: LRS_ERR_ARG, LRS_ERR_STATE.
+ */
+int lrs_set_frequency_quadrature(lrs_ctx* ctx, int nf, double mu, double zeta,
+                                 double* mu_out, double* zeta_out);
+
+/* Read back the quadrature nodes t[nf] and weights W[nf] (host, may be NULL). */
+int lrs_get_frequency_quadrature(lrs_ctx* ctx, double* t, double* w);
+
+/*
+ * Project the orbitals onto the grids of `nsite` sites (`sites` = NULL means
+ * all): psi_kb(tau + r_p) by the direct Fourier sum (Eq. (bloch), Sec. VI.B
+ * method 1), as a complex contraction over G in the context's precision.
+ * Errors: LRS_ERR_STATE (no orbitals/sites), LRS_ERR_ARG, LRS_ERR_OOM.
+ */
+int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode);
+
+/*
+ * Set / get the site-grid orbitals directly (bypassing lrs_project).
+ * psi: host [npts][nk*nbands] complex in the column order above.
+ */
+int lrs_set_site_orbitals(lrs_ctx* ctx, int site, const double* psi);
+int lrs_get_site_orbitals(lrs_ctx* ctx, int site, double* psi);
+
+/*
+ * Build chi0 on the grids of `nsite` sites (NULL = all), Eq. (chi1) with the
+ * Green's functions of Sec. VI.D: per frequency t_i the occupied and
+ * unoccupied parts
+ *   Go(p,p')  = sum_{kv} conj psi_kv(p) d_kv psi_kv(p'),
+ *   Gu^T(p,p')= sum_{kc} psi_kc(p) d_kc conj psi_kc(p'),  d = w_k/(mu + i t - eps),
+ * and chi0 = (2/pi)(S + S^T), S = sum_i W_i Re[Go o Gu^T].
+ * Requires projected (or set) orbitals and a quadrature.  Asynchronous on the
+ * context stream.  Errors: LRS_ERR_STATE, LRS_ERR_ARG, LRS_ERR_OOM.
+ */
+int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites);
+
+/*
+ * Solve the Dyson equation for W (Eq. (eq-reducible), (eq-W), Sec. VI.E) on
+ * the full site grid: v = sum_{l<=L} r_<^l/r_>^(l+1) P_l(cos gamma),
+ * Q = diag(wts), (I - v Q chi0 Q) W = v by float64 LU with partial pivoting.
+ * Requires chi0 of those sites.  Errors: LRS_ERR_STATE, LRS_ERR_NUMERIC
+ * (zero pivot or non-finite value), LRS_ERR_OOM.
+ */
+int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites);
+
+/* Copy chi0, W or v of one site ([npts][npts] float64) to host memory. */
+int lrs_get_chi0(lrs_ctx* ctx, int site, double* out);
+int lrs_get_w(lrs_ctx* ctx, int site, double* out);
+int lrs_get_v(lrs_ctx* ctx, int site, double* out);
+/* Same into caller-owned device memory, asynchronously on the context stream. */
+int lrs_get_chi0_dev(lrs_ctx* ctx, int site, double* out_dev);
+int lrs_get_w_dev(lrs_ctx* ctx, int site, double* out_dev);
+
+/*
+ * Adjoint of (energies, site orbitals) -> chi0 -> W for one site (the paper
+ * has no gradients).  Given dL/dW (grad_w, [npts][npts], may be NULL) and
+ * dL/dchi0 (grad_chi0, may be NULL), writes
+ *   grad_energies [nk][nbands]            dL/d eps_kb
+ *   grad_psi      [npts][nk*nbands] complex dL/dRe psi + i dL/dIm psi
+ * at fixed mu and quadrature.  The Green's functions are recomputed per
+ * frequency, never stored across frequencies.  Host buffers; the _dev variant
+ * takes device pointers.  Requires a prior lrs_solve_w of the site (or
+ * lrs_build_chi0 when grad_w is NULL).
+ * Errors: LRS_ERR_STATE, LRS_ERR_ARG, LRS_ERR_OOM.
+ */
+int lrs_backward(lrs_ctx* ctx, int site, const double* grad_w, const double* grad_chi0,
+                 double* grad_energies, double* grad_psi);
+int lrs_backward_dev(lrs_ctx* ctx, int site, const double* grad_w_dev,
+                     const double* grad_chi0_dev, double* grad_energies_dev,
+                     double* grad_psi_dev);
+
+/* Wait for the context stream; fold device timings into the stats. */
+int lrs_synchronize(lrs_ctx* ctx);
+
+/* Statistics of the context (synchronises the stream first). */
+int lrs_stats(lrs_ctx* ctx, lrs_stats_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRS_H */

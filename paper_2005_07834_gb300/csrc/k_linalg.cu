@@ -1,0 +1,313 @@
+// Float64 dense linear algebra of the Dyson step (Sec. VI.E; Eq. (eq-reducible)
+// and (eq-W) give (I - v Q chi0 Q) W = v on the grid):
+//   dgemm         C = alpha op(A) diag(ks) op(B) diag(cs) + beta C
+//   lu_panel      unblocked LU with partial pivoting of a column panel
+//   laswp         row interchanges outside the panel
+//   trsm          triangular solves with a jb x jb diagonal block
+// and the right-looking blocked LU plus forward/backward substitution that
+// solve for W with all npts right-hand sides.  The FP64 pipe of GB300 retires
+// about two DFMA per SM clock, so every kernel here is bound by DFMA issue;
+// the tiling only has to keep all SMs busy.
+#include <cmath>
+
+#include "lrs_internal.h"
+
+namespace lrs {
+
+constexpr int GT = 64;   // dgemm tile edge
+constexpr int GKC = 16;  // dgemm k chunk
+constexpr int NB = 32;   // LU panel width
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double alpha,
+                                                    const double* __restrict__ A, int lda,
+                                                    const double* __restrict__ ks,
+                                                    const double* __restrict__ B, int ldb,
+                                                    const double* __restrict__ cs, double beta,
+                                                    double* __restrict__ C, int ldc) {
+  __shared__ double As[GKC][GT + 1];
+  __shared__ double Bs[GKC][GT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < k; k0 += GKC) {
+    for (int idx = threadIdx.x; idx < GKC * GT; idx += 256) {
+      int r, kk;
+      if (TA) { kk = idx / GT; r = idx % GT; } else { r = idx / GKC; kk = idx % GKC; }
+      int gi = i0 + r, gk = k0 + kk;
+      double a = 0.0;
+      if (gi < m && gk < k) {
+        a = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+        if (ks) a *= ks[gk];
+      }
+      As[kk][r] = a;
+    }
+    for (int idx = threadIdx.x; idx < GKC * GT; idx += 256) {
+      int c, kk;
+      if (TB) { c = idx / GKC; kk = idx % GKC; } else { kk = idx / GT; c = idx % GT; }
+      int gj = j0 + c, gk = k0 + kk;
+      double b = 0.0;
+      if (gj < n && gk < k) b = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+      Bs[kk][c] = b;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GKC; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gi = i0 + ty + 16 * i;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gj = j0 + tx + 16 * j;
+      if (gj >= n) continue;
+      double v = alpha * acc[i][j];
+      if (cs) v *= cs[gj];
+      double* c = &C[(size_t)gi * ldc + gj];
+      *c = (beta == 0.0) ? v : fma(beta, *c, v);
+    }
+  }
+}
+
+int dgemm_t(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+            const double* ks, const double* b, int ldb, const double* cs, double beta, double* c, int ldc) {
+  if (m <= 0 || n <= 0) return LRS_OK;
+  dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT);
+  if (k <= 0) k = 0;
+  if (!ta && !tb)
+    dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
+  else if (ta && !tb)
+    dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
+  else if (!ta && tb)
+    dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
+  else
+    dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
+  return after_launch(ctx, "dgemm_kernel");
+}
+
+int dgemm(lrs_ctx* ctx, int m, int n, int k, double alpha, const double* a, int lda, const double* kscale,
+          const double* b, int ldb, const double* cscale, double beta, double* c, int ldc) {
+  return dgemm_t(ctx, false, false, m, n, k, alpha, a, lda, kscale, b, ldb, cscale, beta, c, ldc);
+}
+
+__global__ void add_identity_kernel(double* __restrict__ a, int n, int lda, double s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[(size_t)i * lda + i] += s;
+}
+
+// Unblocked LU with partial pivoting of rows [j0, n) x columns [j0, j0+jb).
+// One CTA; the panel stays in L2.  status[0] = 1 on a zero or non-finite
+// pivot column (status[1] = that column), left for the host to report.
+__global__ void __launch_bounds__(1024) lu_panel_kernel(double* __restrict__ A, int lda, int n, int j0, int jb,
+                                                        int* __restrict__ ipiv, int* __restrict__ status) {
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_bad[32];
+  __shared__ double urow[NB];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int c = 0; c < jb; ++c) {
+    const int col = j0 + c;
+    double best = -1.0;
+    int bi = n;
+    int bad = 0;
+    for (int r = col + tid; r < n; r += blockDim.x) {
+      double a = A[(size_t)r * lda + col];
+      if (!isfinite(a)) bad = 1;
+      double m = fabs(a);
+      if (m > best) { best = m; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      bad |= __shfl_down_sync(0xffffffffu, bad, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; s_bad[warp] = bad; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? s_val[lane] : -1.0;
+      bi = lane < nwarp ? s_idx[lane] : n;
+      bad = lane < nwarp ? s_bad[lane] : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        bad |= __shfl_down_sync(0xffffffffu, bad, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (bi >= n) bi = col;
+        s_piv = bi;
+        ipiv[col] = bi;
+        if ((bad || !(best > 0.0)) && atomicCAS(&status[0], 0, 1) == 0) status[1] = col;
+      }
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != col) {
+      for (int j = tid; j < jb; j += blockDim.x) {
+        double t = A[(size_t)col * lda + j0 + j];
+        A[(size_t)col * lda + j0 + j] = A[(size_t)piv * lda + j0 + j];
+        A[(size_t)piv * lda + j0 + j] = t;
+      }
+    }
+    __syncthreads();
+    if (tid < jb) urow[tid] = A[(size_t)col * lda + j0 + tid];
+    __syncthreads();
+    const double d = urow[c];
+    const double inv = (d != 0.0) ? 1.0 / d : 0.0;
+    for (int r = col + 1 + tid; r < n; r += blockDim.x) {
+      double* row = A + (size_t)r * lda + j0;
+      double l = row[c] * inv;
+      row[c] = l;
+      for (int j = c + 1; j < jb; ++j) row[j] = fma(-l, urow[j], row[j]);
+    }
+    __syncthreads();
+  }
+}
+
+// Applies the interchanges ipiv[r0 .. r0+cnt) (in order) to every column
+// except [skip0, skip0+skipn).  One thread per column.
+__global__ void laswp_kernel(double* __restrict__ A, int lda, int ncols, const int* __restrict__ ipiv, int r0,
+                             int cnt, int skip0, int skipn) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int col = t < skip0 ? t : t + skipn;
+  if (t >= ncols - skipn || col >= ncols) return;
+  for (int i = r0; i < r0 + cnt; ++i) {
+    int p = ipiv[i];
+    if (p != i) {
+      double a = A[(size_t)i * lda + col];
+      A[(size_t)i * lda + col] = A[(size_t)p * lda + col];
+      A[(size_t)p * lda + col] = a;
+    }
+  }
+}
+
+// X = T^-1 B for a jb x jb triangular block T (lower unit or upper non-unit)
+// and a jb x ncols block B, in place.  One thread per column of B.
+template <bool kLowerUnit>
+__global__ void trsm_kernel(const double* __restrict__ T, int ldt, int jb, double* __restrict__ B, int ldb,
+                            int ncols) {
+  __shared__ double Ts[NB][NB + 1];
+  for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x) {
+    int i = idx / jb, j = idx % jb;
+    Ts[i][j] = T[(size_t)i * ldt + j];
+  }
+  __syncthreads();
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncols) return;
+  double x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) x[i] = (i < jb) ? B[(size_t)i * ldb + col] : 0.0;
+  if (kLowerUnit) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      if (i >= jb) break;
+      double s = x[i];
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < i) s = fma(-Ts[i][k], x[k], s);
+      x[i] = s;
+    }
+  } else {
+#pragma unroll
+    for (int ii = NB - 1; ii >= 0; --ii) {
+      if (ii >= jb) continue;
+      double s = x[ii];
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k > ii && k < jb) s = fma(-Ts[ii][k], x[k], s);
+      x[ii] = s / Ts[ii][ii];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < jb) B[(size_t)i * ldb + col] = x[i];
+}
+
+// In-place LU with partial pivoting of the n x n matrix A (row-major).
+int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status) {
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    int jb = std::min(NB, n - j0);
+    lu_panel_kernel<<<1, 1024, 0, ctx->stream>>>(A, n, n, j0, jb, ipiv, status);
+    LRS_TRY(after_launch(ctx, "lu_panel_kernel"));
+    if (n - jb > 0) {
+      laswp_kernel<<<(n - jb + 255) / 256, 256, 0, ctx->stream>>>(A, n, n, ipiv, j0, jb, j0, jb);
+      LRS_TRY(after_launch(ctx, "laswp_kernel"));
+    }
+    int rest = n - j0 - jb;
+    if (rest > 0) {
+      trsm_kernel<true><<<(rest + 127) / 128, 128, 0, ctx->stream>>>(A + (size_t)j0 * n + j0, n, jb,
+                                                                      A + (size_t)j0 * n + j0 + jb, n, rest);
+      LRS_TRY(after_launch(ctx, "trsm_kernel"));
+      LRS_TRY(dgemm_t(ctx, false, false, rest, rest, jb, -1.0, A + (size_t)(j0 + jb) * n + j0, n, nullptr,
+                      A + (size_t)j0 * n + j0 + jb, n, nullptr, 1.0, A + (size_t)(j0 + jb) * n + j0 + jb, n));
+    }
+  }
+  return LRS_OK;
+}
+
+// Solves (LU) X = P B for the n x nrhs matrix B in place (row-major, ldb).
+int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb) {
+  laswp_kernel<<<(nrhs + 255) / 256, 256, 0, ctx->stream>>>(B, ldb, nrhs, ipiv, 0, n, nrhs, 0);
+  LRS_TRY(after_launch(ctx, "laswp_kernel"));
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    int jb = std::min(NB, n - j0);
+    trsm_kernel<true><<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(LU + (size_t)j0 * n + j0, n, jb,
+                                                                    B + (size_t)j0 * ldb, ldb, nrhs);
+    LRS_TRY(after_launch(ctx, "trsm_kernel"));
+    int rest = n - j0 - jb;
+    if (rest > 0)
+      LRS_TRY(dgemm_t(ctx, false, false, rest, nrhs, jb, -1.0, LU + (size_t)(j0 + jb) * n + j0, n, nullptr,
+                      B + (size_t)j0 * ldb, ldb, nullptr, 1.0, B + (size_t)(j0 + jb) * ldb, ldb));
+  }
+  int last = ((n - 1) / NB) * NB;
+  for (int j0 = last; j0 >= 0; j0 -= NB) {
+    int jb = std::min(NB, n - j0);
+    trsm_kernel<false><<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(LU + (size_t)j0 * n + j0, n, jb,
+                                                                     B + (size_t)j0 * ldb, ldb, nrhs);
+    LRS_TRY(after_launch(ctx, "trsm_kernel"));
+    if (j0 > 0)
+      LRS_TRY(dgemm_t(ctx, false, false, j0, nrhs, jb, -1.0, LU + j0, n, nullptr, B + (size_t)j0 * ldb, ldb,
+                      nullptr, 1.0, B, ldb));
+  }
+  return LRS_OK;
+}
+
+int dyson_solve(lrs_ctx* ctx, Site& s) {
+  const int n = s.npts;
+  const size_t nn = (size_t)n * n;
+  LRS_TRY(ensure(ctx, s.v, nn));
+  LRS_TRY(ensure(ctx, s.w, nn));
+  LRS_TRY(ensure(ctx, ctx->ws.dyson_a, nn));
+  LRS_TRY(ensure(ctx, ctx->ws.ipiv, n));
+  LRS_TRY(coulomb_build(ctx, s, s.v.ptr));
+  double* A = ctx->ws.dyson_a.ptr;
+  // A = I - (v Q)(chi0 Q)
+  LRS_TRY(dgemm_t(ctx, false, false, n, n, n, -1.0, s.v.ptr, n, s.wts.ptr, s.chi0.ptr, n, s.wts.ptr, 0.0, A, n));
+  add_identity_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(A, n, n, 1.0);
+  LRS_TRY(after_launch(ctx, "add_identity_kernel"));
+  LRS_TRY(lu_factor(ctx, A, n, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));
+  LRS_CUDA_TRY(cudaMemcpyAsync(s.w.ptr, s.v.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return lu_solve(ctx, A, n, ctx->ws.ipiv.ptr, s.w.ptr, n, n);
+}
+
+}  // namespace lrs

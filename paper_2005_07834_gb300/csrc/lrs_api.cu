@@ -1,0 +1,669 @@
+// C-ABI entry points of liblrs (declared in include/lrs.h): argument checks,
+// device-memory ownership, the frequency quadrature of App. D.1 and the
+// dispatch of each stage to the kernels of the k_*.cu translation units.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+
+#include "lrs_internal.h"
+
+namespace lrs {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int after_launch(lrs_ctx* ctx, const char* what, int n) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_error(LRS_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  ctx->stats.kernel_launches += n;
+  return LRS_OK;
+}
+
+int dev_alloc_bytes(lrs_ctx* ctx, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return set_error(LRS_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->stats.device_bytes += (int64_t)bytes;
+  ctx->stats.device_bytes_peak = std::max(ctx->stats.device_bytes_peak, ctx->stats.device_bytes);
+  return LRS_OK;
+}
+
+void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->stats.device_bytes -= (int64_t)bytes;
+}
+
+int stage_begin(lrs_ctx* ctx, Stage s) {
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev[s][0], ctx->stream));
+  return LRS_OK;
+}
+
+int stage_end(lrs_ctx* ctx, Stage s) {
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev[s][1], ctx->stream));
+  ctx->ev_pending[s] = true;
+  return LRS_OK;
+}
+
+// Switches to the context's device for the duration of an API call.
+struct DeviceGuard {
+  int prev = -1;
+  int rc = LRS_OK;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) rc = set_error(LRS_ERR_CUDA, "cudaSetDevice(%d): %s", dev, cudaGetErrorString(e));
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1] by Newton iteration
+// on the three-term recurrence (l+1) P_{l+1} = (2l+1) x P_l - l P_{l-1}.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int l = 1; l < n; ++l) {
+        double p2 = ((2.0 * l + 1.0) * z * p1 - l * p0) / (l + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      // P_n = p1, P_{n-1} = p0;  P_n' = n (z P_n - P_{n-1}) / (z^2 - 1)
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        // one more evaluation of the derivative at the converged node
+        p0 = 1.0; p1 = z;
+        for (int l = 1; l < n; ++l) {
+          double p2 = ((2.0 * l + 1.0) * z * p1 - l * p0) / (l + 1.0);
+          p0 = p1;
+          p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = wi;
+    w[n - 1 - i] = wi;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+static bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+static int check_site(lrs_ctx* ctx, int site) {
+  if (site < 0 || site >= (int)ctx->sites.size())
+    return set_error(LRS_ERR_ARG, "site %d out of range (have %zu)", site, ctx->sites.size());
+  return LRS_OK;
+}
+
+static int site_list(lrs_ctx* ctx, int nsite, const int* sites, std::vector<int>& out) {
+  out.clear();
+  if (ctx->sites.empty()) return set_error(LRS_ERR_STATE, "no sites defined");
+  if (sites == nullptr) {
+    for (int i = 0; i < (int)ctx->sites.size(); ++i) out.push_back(i);
+    return LRS_OK;
+  }
+  if (nsite < 0) return set_error(LRS_ERR_ARG, "nsite < 0");
+  for (int i = 0; i < nsite; ++i) {
+    LRS_TRY(check_site(ctx, sites[i]));
+    out.push_back(sites[i]);
+  }
+  return LRS_OK;
+}
+
+static void free_site(lrs_ctx* ctx, Site& s) {
+  release(ctx, s.pts);
+  release(ctx, s.wts);
+  release(ctx, s.psi_o);
+  release(ctx, s.psi_u);
+  release(ctx, s.chi0);
+  release(ctx, s.w);
+  release(ctx, s.v);
+  s.has_psi = s.has_chi0 = s.has_w = false;
+}
+
+static void free_workspace(lrs_ctx* ctx) {
+  Workspace& w = ctx->ws;
+  release(ctx, w.denom_o); release(ctx, w.denom_u); release(ctx, w.dyson_a); release(ctx, w.ipiv);
+  release(ctx, w.status); release(ctx, w.phase_tab); release(ctx, w.kphase); release(ctx, w.ru);
+  release(ctx, w.gamma_s); release(ctx, w.gbuf_o); release(ctx, w.gbuf_u); release(ctx, w.ybuf);
+  release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
+  release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.s_acc); release(ctx, w.psi32);
+}
+
+}  // namespace lrs
+
+using namespace lrs;
+
+extern "C" {
+
+const char* lrs_last_error(void) { return g_last_error.c_str(); }
+
+const char* lrs_version(void) { return "lrs 0.1 (sm_103a)"; }
+
+int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
+  clear_error();
+  if (!out) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  *out = nullptr;
+  if (precision != LRS_FP64 && precision != LRS_MIXED_BF16X3 && precision != LRS_MIXED_FP16X3)
+    return set_error(LRS_ERR_ARG, "unknown precision %d", precision);
+  int ndev = 0;
+  LRS_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(LRS_ERR_ARG, "device %d out of range (%d)", device, ndev);
+  DeviceGuard g(device);
+  if (g.rc) return g.rc;
+  cudaDeviceProp prop;
+  LRS_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  if (precision != LRS_FP64 && prop.major * 10 + prop.minor < 100)
+    return set_error(LRS_ERR_UNSUPPORTED, "mixed precision needs tcgen05 (sm_100 family), device is sm_%d%d",
+                     prop.major, prop.minor);
+  lrs_ctx* ctx = new lrs_ctx();
+  ctx->device = device;
+  ctx->precision = precision;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->num_sms = prop.multiProcessorCount;
+  for (int s = 0; s < 6; ++s)
+    for (int j = 0; j < 2; ++j)
+      if (cudaEventCreate(&ctx->ev[s][j]) != cudaSuccess) {
+        delete ctx;
+        return set_error(LRS_ERR_CUDA, "cudaEventCreate failed");
+      }
+  int rc = ensure(ctx, ctx->ws.status, 64);
+  if (rc) { delete ctx; return rc; }
+  cudaMemsetAsync(ctx->ws.status.ptr, 0, 64 * sizeof(int), ctx->stream);
+  *out = ctx;
+  return LRS_OK;
+}
+
+int lrs_destroy(lrs_ctx* ctx) {
+  clear_error();
+  if (!ctx) return LRS_OK;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& s : ctx->sites) free_site(ctx, s);
+  release(ctx, ctx->coeff);
+  release(ctx, ctx->d_gvec);
+  release(ctx, ctx->d_kpts);
+  release(ctx, ctx->d_t);
+  release(ctx, ctx->d_W);
+  release(ctx, ctx->e_o); release(ctx, ctx->e_u); release(ctx, ctx->w_o); release(ctx, ctx->w_u);
+  release(ctx, ctx->d_col_o); release(ctx, ctx->d_col_u);
+  free_workspace(ctx);
+  for (int s = 0; s < 6; ++s)
+    for (int j = 0; j < 2; ++j)
+      if (ctx->ev[s][j]) cudaEventDestroy(ctx->ev[s][j]);
+  delete ctx;
+  return LRS_OK;
+}
+
+int lrs_set_stream(lrs_ctx* ctx, void* stream) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return LRS_OK;
+}
+
+int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kpts,
+                      const double* kweights, int ng, const int* gvec, int nbands,
+                      const int* nocc, const double* coeff, const double* energies) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!cell || !kpts || !kweights || !gvec || !nocc || !coeff || !energies)
+    return set_error(LRS_ERR_ARG, "null input pointer");
+  if (nk < 1 || ng < 1 || nbands < 2) return set_error(LRS_ERR_ARG, "nk, ng >= 1 and nbands >= 2 required");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  double det = cell[0] * (cell[4] * cell[8] - cell[5] * cell[7]) -
+               cell[1] * (cell[3] * cell[8] - cell[5] * cell[6]) +
+               cell[2] * (cell[3] * cell[7] - cell[4] * cell[6]);
+  if (!std::isfinite(det) || std::fabs(det) < 1e-12) return set_error(LRS_ERR_ARG, "singular cell");
+  if (!finite_all(kpts, 3 * (size_t)nk) || !finite_all(kweights, nk) ||
+      !finite_all(energies, (size_t)nk * nbands))
+    return set_error(LRS_ERR_ARG, "non-finite k-point, weight or energy");
+  int Ko = 0, Ku = 0;
+  for (int k = 0; k < nk; ++k) {
+    if (nocc[k] < 1 || nocc[k] >= nbands)
+      return set_error(LRS_ERR_ARG, "nocc[%d] = %d must be in [1, nbands-1]", k, nocc[k]);
+    Ko += nocc[k];
+    Ku += nbands - nocc[k];
+  }
+  // reciprocal rows b_i = 2 pi (cell^-1)^T rows
+  double inv[9];
+  inv[0] = (cell[4] * cell[8] - cell[5] * cell[7]) / det;
+  inv[1] = (cell[2] * cell[7] - cell[1] * cell[8]) / det;
+  inv[2] = (cell[1] * cell[5] - cell[2] * cell[4]) / det;
+  inv[3] = (cell[5] * cell[6] - cell[3] * cell[8]) / det;
+  inv[4] = (cell[0] * cell[8] - cell[2] * cell[6]) / det;
+  inv[5] = (cell[2] * cell[3] - cell[0] * cell[5]) / det;
+  inv[6] = (cell[3] * cell[7] - cell[4] * cell[6]) / det;
+  inv[7] = (cell[1] * cell[6] - cell[0] * cell[7]) / det;
+  inv[8] = (cell[0] * cell[4] - cell[1] * cell[3]) / det;
+  const double two_pi = 6.283185307179586476925;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) ctx->recip[3 * i + j] = two_pi * inv[3 * j + i];
+  std::memcpy(ctx->cell, cell, 9 * sizeof(double));
+  ctx->omega = std::fabs(det);
+  ctx->nk = nk; ctx->ng = ng; ctx->nb = nbands; ctx->Ko = Ko; ctx->Ku = Ku;
+  ctx->nocc.assign(nocc, nocc + nk);
+  ctx->kpts.assign(kpts, kpts + 3 * nk);
+  ctx->kw.assign(kweights, kweights + nk);
+  ctx->energies.assign(energies, energies + (size_t)nk * nbands);
+  ctx->gvec.assign(gvec, gvec + 3 * (size_t)ng);
+  for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = 0;
+  for (int gi = 0; gi < ng; ++gi)
+    for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = std::max(ctx->gmax_idx[i], std::abs(gvec[3 * gi + i]));
+  // column maps and per-column energies / k-weights
+  ctx->col_o.clear(); ctx->col_u.clear();
+  std::vector<double> eo, eu, wo, wu;
+  for (int k = 0; k < nk; ++k)
+    for (int b = 0; b < nbands; ++b) {
+      double e = energies[(size_t)k * nbands + b];
+      if (b < nocc[k]) { ctx->col_o.push_back(k * nbands + b); eo.push_back(e); wo.push_back(kweights[k]); }
+      else { ctx->col_u.push_back(k * nbands + b); eu.push_back(e); wu.push_back(kweights[k]); }
+    }
+  size_t ncoef = (size_t)nk * ng * nbands;
+  LRS_TRY(ensure(ctx, ctx->coeff, ncoef));
+  LRS_TRY(ensure(ctx, ctx->d_gvec, 3 * (size_t)ng));
+  LRS_TRY(ensure(ctx, ctx->d_kpts, 3 * (size_t)nk));
+  LRS_TRY(ensure(ctx, ctx->e_o, Ko)); LRS_TRY(ensure(ctx, ctx->e_u, Ku));
+  LRS_TRY(ensure(ctx, ctx->w_o, Ko)); LRS_TRY(ensure(ctx, ctx->w_u, Ku));
+  LRS_TRY(ensure(ctx, ctx->d_col_o, Ko)); LRS_TRY(ensure(ctx, ctx->d_col_u, Ku));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->coeff.ptr, coeff, ncoef * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->d_gvec.ptr, gvec, 3 * (size_t)ng * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->d_kpts.ptr, kpts, 3 * (size_t)nk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->e_o.ptr, eo.data(), Ko * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->e_u.ptr, eu.data(), Ku * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->w_o.ptr, wo.data(), Ko * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->w_u.ptr, wu.data(), Ku * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->d_col_o.ptr, ctx->col_o.data(), Ko * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(ctx->d_col_u.ptr, ctx->col_u.data(), Ku * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  // the host vectors above go out of scope: wait for the copies
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->has_orb = true;
+  ctx->nf = 0;
+  for (auto& s : ctx->sites) s.has_psi = s.has_chi0 = s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_set_sites(lrs_ctx* ctx, int nsites, const double* centers, const int* npts,
+                  const double* pts, const double* wts, const int* lmax) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (nsites < 1 || !centers || !npts || !pts || !wts || !lmax)
+    return set_error(LRS_ERR_ARG, "nsites >= 1 and non-null arrays required");
+  size_t off = 0;
+  for (int i = 0; i < nsites; ++i) {
+    if (npts[i] < 1) return set_error(LRS_ERR_ARG, "npts[%d] = %d", i, npts[i]);
+    if (lmax[i] < 0 || lmax[i] > 64) return set_error(LRS_ERR_ARG, "lmax[%d] = %d out of [0,64]", i, lmax[i]);
+    for (int p = 0; p < npts[i]; ++p) {
+      const double* r = pts + 3 * (off + p);
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (!(rr > 0.0) || !std::isfinite(rr) || !std::isfinite(wts[off + p]))
+        return set_error(LRS_ERR_ARG, "site %d point %d at the origin or non-finite", i, p);
+    }
+    off += npts[i];
+  }
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& s : ctx->sites) free_site(ctx, s);
+  ctx->sites.clear();
+  ctx->sites.resize(nsites);
+  off = 0;
+  for (int i = 0; i < nsites; ++i) {
+    Site& s = ctx->sites[i];
+    s.npts = npts[i];
+    s.lmax = lmax[i];
+    std::memcpy(s.center, centers + 3 * i, 3 * sizeof(double));
+    LRS_TRY(ensure(ctx, s.pts, 3 * (size_t)s.npts));
+    LRS_TRY(ensure(ctx, s.wts, s.npts));
+    LRS_CUDA_TRY(cudaMemcpy(s.pts.ptr, pts + 3 * off, 3 * (size_t)s.npts * sizeof(double), cudaMemcpyHostToDevice));
+    LRS_CUDA_TRY(cudaMemcpy(s.wts.ptr, wts + off, (size_t)s.npts * sizeof(double), cudaMemcpyHostToDevice));
+    off += npts[i];
+  }
+  return LRS_OK;
+}
+
+int lrs_set_frequency_quadrature(lrs_ctx* ctx, int nf, double mu, double zeta, double* mu_out,
+                                 double* zeta_out) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  if (nf < 1 || nf > 128) return set_error(LRS_ERR_ARG, "nf = %d out of [1,128]", nf);
+  if (std::isnan(mu)) {
+    double top = -1e300, bottom = 1e300;
+    for (int k = 0; k < ctx->nk; ++k)
+      for (int b = 0; b < ctx->nb; ++b) {
+        double e = ctx->energies[(size_t)k * ctx->nb + b];
+        if (b < ctx->nocc[k]) top = std::max(top, e);
+        else bottom = std::min(bottom, e);
+      }
+    mu = 0.5 * (top + bottom);
+  }
+  if (!std::isfinite(mu)) return set_error(LRS_ERR_ARG, "non-finite mu");
+  double dmin = 1e300, dmax = 0.0;
+  for (double e : ctx->energies) {
+    double d = std::fabs(mu - e);
+    dmin = std::min(dmin, d);
+    dmax = std::max(dmax, d);
+  }
+  // every occupied level must lie below mu and every unoccupied one above it
+  for (int k = 0; k < ctx->nk; ++k)
+    for (int b = 0; b < ctx->nb; ++b) {
+      double e = ctx->energies[(size_t)k * ctx->nb + b];
+      if ((b < ctx->nocc[k] && !(e < mu)) || (b >= ctx->nocc[k] && !(e > mu)))
+        return set_error(LRS_ERR_ARG, "mu = %g does not separate occupied and unoccupied levels", mu);
+    }
+  if (!(zeta > 0.0)) {
+    const double floor_ha = 0.5 / 27.211386245988;  // 0.5 eV added in quadrature
+    zeta = std::sqrt(std::sqrt(dmin * dmin + floor_ha * floor_ha) * dmax);
+  }
+  if (!std::isfinite(zeta)) return set_error(LRS_ERR_ARG, "non-finite zeta");
+  std::vector<double> x, w;
+  gauss_legendre(nf, x, w);
+  ctx->t.resize(nf);
+  ctx->W.resize(nf);
+  for (int i = 0; i < nf; ++i) {
+    double a = 0.5 * (x[i] + 1.0), wa = 0.5 * w[i];
+    ctx->t[i] = zeta * a / (1.0 - a);
+    ctx->W[i] = zeta * wa / ((1.0 - a) * (1.0 - a));
+  }
+  LRS_TRY(ensure(ctx, ctx->d_t, nf));
+  LRS_TRY(ensure(ctx, ctx->d_W, nf));
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpy(ctx->d_t.ptr, ctx->t.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
+  LRS_CUDA_TRY(cudaMemcpy(ctx->d_W.ptr, ctx->W.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
+  ctx->nf = nf;
+  ctx->mu = mu;
+  ctx->zeta = zeta;
+  if (mu_out) *mu_out = mu;
+  if (zeta_out) *zeta_out = zeta;
+  for (auto& s : ctx->sites) s.has_chi0 = s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_get_frequency_quadrature(lrs_ctx* ctx, double* t, double* w) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (ctx->nf == 0) return set_error(LRS_ERR_STATE, "no quadrature set");
+  if (t) std::memcpy(t, ctx->t.data(), ctx->nf * sizeof(double));
+  if (w) std::memcpy(w, ctx->W.data(), ctx->nf * sizeof(double));
+  return LRS_OK;
+}
+
+static int alloc_psi(lrs_ctx* ctx, Site& s) {
+  LRS_TRY(ensure(ctx, s.psi_o, (size_t)s.npts * ctx->Ko));
+  LRS_TRY(ensure(ctx, s.psi_u, (size_t)s.npts * ctx->Ku));
+  return LRS_OK;
+}
+
+int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  if (mode != LRS_PROJ_EXACT) return set_error(LRS_ERR_UNSUPPORTED, "projection mode %d not available", mode);
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  std::vector<int> list;
+  LRS_TRY(site_list(ctx, nsite, sites, list));
+  for (int i : list) LRS_TRY(alloc_psi(ctx, ctx->sites[i]));
+  LRS_TRY(stage_begin(ctx, ST_PROJECT));
+  for (int i : list) {
+    Site& s = ctx->sites[i];
+    if (ctx->precision == LRS_FP64) LRS_TRY(project_fp64(ctx, s));
+    else LRS_TRY(project_mixed(ctx, s));
+    s.has_psi = true;
+    s.has_chi0 = s.has_w = false;
+  }
+  LRS_TRY(stage_end(ctx, ST_PROJECT));
+  return LRS_OK;
+}
+
+int lrs_set_site_orbitals(lrs_ctx* ctx, int site, const double* psi) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  LRS_TRY(check_site(ctx, site));
+  if (!psi) return set_error(LRS_ERR_ARG, "psi is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  Site& s = ctx->sites[site];
+  LRS_TRY(alloc_psi(ctx, s));
+  const size_t ncol = (size_t)ctx->nk * ctx->nb;
+  std::vector<double2> o((size_t)s.npts * ctx->Ko), u((size_t)s.npts * ctx->Ku);
+  for (int p = 0; p < s.npts; ++p) {
+    const double2* row = reinterpret_cast<const double2*>(psi) + p * ncol;
+    for (int j = 0; j < ctx->Ko; ++j) o[(size_t)p * ctx->Ko + j] = row[ctx->col_o[j]];
+    for (int j = 0; j < ctx->Ku; ++j) u[(size_t)p * ctx->Ku + j] = row[ctx->col_u[j]];
+  }
+  LRS_CUDA_TRY(cudaMemcpyAsync(s.psi_o.ptr, o.data(), o.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(s.psi_u.ptr, u.data(), u.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  s.has_psi = true;
+  s.has_chi0 = s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_get_site_orbitals(lrs_ctx* ctx, int site, double* psi) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  LRS_TRY(check_site(ctx, site));
+  if (!psi) return set_error(LRS_ERR_ARG, "psi is NULL");
+  Site& s = ctx->sites[site];
+  if (!s.has_psi) return set_error(LRS_ERR_STATE, "site %d has no orbitals", site);
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  const size_t ncol = (size_t)ctx->nk * ctx->nb;
+  std::vector<double2> o((size_t)s.npts * ctx->Ko), u((size_t)s.npts * ctx->Ku);
+  LRS_CUDA_TRY(cudaMemcpyAsync(o.data(), s.psi_o.ptr, o.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(u.data(), s.psi_u.ptr, u.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  for (int p = 0; p < s.npts; ++p) {
+    double2* row = reinterpret_cast<double2*>(psi) + p * ncol;
+    for (int j = 0; j < ctx->Ko; ++j) row[ctx->col_o[j]] = o[(size_t)p * ctx->Ko + j];
+    for (int j = 0; j < ctx->Ku; ++j) row[ctx->col_u[j]] = u[(size_t)p * ctx->Ku + j];
+  }
+  return LRS_OK;
+}
+
+int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (ctx->nf == 0) return set_error(LRS_ERR_STATE, "set the frequency quadrature first");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  std::vector<int> list;
+  LRS_TRY(site_list(ctx, nsite, sites, list));
+  for (int i : list)
+    if (!ctx->sites[i].has_psi) return set_error(LRS_ERR_STATE, "site %d has no orbitals", i);
+  for (int i : list) LRS_TRY(ensure(ctx, ctx->sites[i].chi0, (size_t)ctx->sites[i].npts * ctx->sites[i].npts));
+  LRS_TRY(stage_begin(ctx, ST_CHI0));
+  LRS_TRY(build_denominators(ctx));
+  double flop = 0;
+  for (int i : list) {
+    Site& s = ctx->sites[i];
+    if (ctx->precision == LRS_FP64) LRS_TRY(chi0_fp64(ctx, s));
+    else LRS_TRY(chi0_mixed(ctx, s));
+    s.has_chi0 = true;
+    s.has_w = false;
+    flop += 8.0 * s.npts * (double)s.npts * (ctx->Ko + ctx->Ku) * ctx->nf;
+  }
+  LRS_TRY(stage_end(ctx, ST_CHI0));
+  ctx->stats.flop_chi0 = flop;
+  return LRS_OK;
+}
+
+int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  std::vector<int> list;
+  LRS_TRY(site_list(ctx, nsite, sites, list));
+  for (int i : list)
+    if (!ctx->sites[i].has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", i);
+  LRS_TRY(stage_begin(ctx, ST_W));
+  double flop = 0;
+  for (int i : list) {
+    Site& s = ctx->sites[i];
+    LRS_TRY(dyson_solve(ctx, s));
+    s.has_w = true;
+    flop += 14.0 / 3.0 * (double)s.npts * s.npts * s.npts;
+  }
+  LRS_TRY(stage_end(ctx, ST_W));
+  ctx->stats.flop_w = flop;
+  // zero pivots / non-finite values are reported through the status word
+  int status[4] = {0, 0, 0, 0};
+  LRS_CUDA_TRY(cudaMemcpyAsync(status, ctx->ws.status.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->stats.status_word = status[0];
+  if (status[0] != 0) {
+    cudaMemsetAsync(ctx->ws.status.ptr, 0, 4 * sizeof(int), ctx->stream);
+    for (int i : list) ctx->sites[i].has_w = false;
+    return set_error(LRS_ERR_NUMERIC, "Dyson LU: zero or non-finite pivot (status %d, column %d)", status[0], status[1]);
+  }
+  return LRS_OK;
+}
+
+static int get_matrix(lrs_ctx* ctx, int site, double* out, int which, bool device_out) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  LRS_TRY(check_site(ctx, site));
+  if (!out) return set_error(LRS_ERR_ARG, "out is NULL");
+  Site& s = ctx->sites[site];
+  const double* src = nullptr;
+  if (which == 0) { if (!s.has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", site); src = s.chi0.ptr; }
+  if (which == 1) { if (!s.has_w) return set_error(LRS_ERR_STATE, "site %d has no W", site); src = s.w.ptr; }
+  if (which == 2) { if (!s.has_w) return set_error(LRS_ERR_STATE, "site %d has no v (solve W first)", site); src = s.v.ptr; }
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  size_t bytes = (size_t)s.npts * s.npts * sizeof(double);
+  LRS_CUDA_TRY(cudaMemcpyAsync(out, src, bytes, device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  if (!device_out) LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
+int lrs_get_chi0(lrs_ctx* ctx, int site, double* out) { return get_matrix(ctx, site, out, 0, false); }
+int lrs_get_w(lrs_ctx* ctx, int site, double* out) { return get_matrix(ctx, site, out, 1, false); }
+int lrs_get_v(lrs_ctx* ctx, int site, double* out) { return get_matrix(ctx, site, out, 2, false); }
+int lrs_get_chi0_dev(lrs_ctx* ctx, int site, double* out) { return get_matrix(ctx, site, out, 0, true); }
+int lrs_get_w_dev(lrs_ctx* ctx, int site, double* out) { return get_matrix(ctx, site, out, 1, true); }
+
+int lrs_backward_dev(lrs_ctx* ctx, int site, const double* grad_w_dev, const double* grad_chi0_dev,
+                     double* grad_energies_dev, double* grad_psi_dev) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  LRS_TRY(check_site(ctx, site));
+  if (!grad_energies_dev || !grad_psi_dev) return set_error(LRS_ERR_ARG, "null output pointer");
+  if (!grad_w_dev && !grad_chi0_dev) return set_error(LRS_ERR_ARG, "grad_w and grad_chi0 are both NULL");
+  Site& s = ctx->sites[site];
+  if (!s.has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", site);
+  if (grad_w_dev && !s.has_w) return set_error(LRS_ERR_STATE, "site %d has no W", site);
+  if (ctx->nf == 0) return set_error(LRS_ERR_STATE, "no quadrature");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_TRY(stage_begin(ctx, ST_BACKWARD));
+  LRS_TRY(backward_site(ctx, s, grad_w_dev, grad_chi0_dev, grad_energies_dev,
+                        reinterpret_cast<double2*>(grad_psi_dev)));
+  LRS_TRY(stage_end(ctx, ST_BACKWARD));
+  return LRS_OK;
+}
+
+int lrs_backward(lrs_ctx* ctx, int site, const double* grad_w, const double* grad_chi0,
+                 double* grad_energies, double* grad_psi) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  LRS_TRY(check_site(ctx, site));
+  if (!grad_energies || !grad_psi) return set_error(LRS_ERR_ARG, "null output pointer");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  Site& s = ctx->sites[site];
+  size_t nn = (size_t)s.npts * s.npts;
+  size_t ne = (size_t)ctx->nk * ctx->nb;
+  double *gw = nullptr, *gc = nullptr, *ge = nullptr, *gp = nullptr;
+  int rc = LRS_OK;
+  if (grad_w) rc = dev_alloc_bytes(ctx, (void**)&gw, nn * sizeof(double));
+  if (!rc && grad_chi0) rc = dev_alloc_bytes(ctx, (void**)&gc, nn * sizeof(double));
+  if (!rc) rc = dev_alloc_bytes(ctx, (void**)&ge, ne * sizeof(double));
+  if (!rc) rc = dev_alloc_bytes(ctx, (void**)&gp, ne * s.npts * sizeof(double2));
+  if (!rc && gw && cudaMemcpyAsync(gw, grad_w, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    rc = set_error(LRS_ERR_CUDA, "copy of grad_w failed");
+  if (!rc && gc && cudaMemcpyAsync(gc, grad_chi0, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    rc = set_error(LRS_ERR_CUDA, "copy of grad_chi0 failed");
+  if (!rc) rc = lrs_backward_dev(ctx, site, gw, gc, ge, gp);
+  if (!rc && cudaMemcpyAsync(grad_energies, ge, ne * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    rc = set_error(LRS_ERR_CUDA, "copy of grad_energies failed");
+  if (!rc && cudaMemcpyAsync(grad_psi, gp, ne * s.npts * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    rc = set_error(LRS_ERR_CUDA, "copy of grad_psi failed");
+  cudaStreamSynchronize(ctx->stream);
+  if (gw) dev_free_bytes(ctx, gw, nn * sizeof(double));
+  if (gc) dev_free_bytes(ctx, gc, nn * sizeof(double));
+  if (ge) dev_free_bytes(ctx, ge, ne * sizeof(double));
+  if (gp) dev_free_bytes(ctx, gp, ne * s.npts * sizeof(double2));
+  return rc;
+}
+
+int lrs_synchronize(lrs_ctx* ctx) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  for (int s = 0; s < 6; ++s)
+    if (ctx->ev_pending[s]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->ev[s][0], ctx->ev[s][1]) == cudaSuccess) ctx->ms_acc[s] = ms;
+      ctx->ev_pending[s] = false;
+    }
+  ctx->stats.ms_project = ctx->ms_acc[ST_PROJECT];
+  ctx->stats.ms_chi0 = ctx->ms_acc[ST_CHI0];
+  ctx->stats.ms_w = ctx->ms_acc[ST_W];
+  ctx->stats.ms_backward = ctx->ms_acc[ST_BACKWARD];
+  ctx->stats.ms_chi0_main = ctx->ms_acc[ST_CHI0_MAIN];
+  return LRS_OK;
+}
+
+int lrs_stats(lrs_ctx* ctx, lrs_stats_t* out) {
+  LRS_TRY(lrs_synchronize(ctx));
+  if (!out) return set_error(LRS_ERR_ARG, "out is NULL");
+  *out = ctx->stats;
+  return LRS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal declarations of liblrs: context layout, error helpers and the
+// kernel launchers implemented in the k_*.cu translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lrs.h"
+
+namespace lrs {
+
+// ---------------------------------------------------------------- errors
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+#define LRS_CUDA_TRY(call)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return ::lrs::set_error(LRS_ERR_CUDA, "%s failed: %s (%s:%d)", #call,        \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);        \
+  } while (0)
+
+#define LRS_TRY(call)            \
+  do {                           \
+    int rc_ = (call);            \
+    if (rc_ != LRS_OK) return rc_; \
+  } while (0)
+
+// Checks the launch that was just issued and counts it.
+int after_launch(lrs_ctx* ctx, const char* what, int n = 1);
+
+// ---------------------------------------------------------------- device memory
+template <typename T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t count = 0;
+};
+
+int dev_alloc_bytes(lrs_ctx* ctx, void** p, size_t bytes);
+void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes);
+
+template <typename T>
+int ensure(lrs_ctx* ctx, DevBuf<T>& b, size_t count) {
+  if (b.count >= count && b.ptr) return LRS_OK;
+  if (b.ptr) dev_free_bytes(ctx, b.ptr, b.count * sizeof(T));
+  b.ptr = nullptr;
+  b.count = 0;
+  if (count == 0) return LRS_OK;
+  void* p = nullptr;
+  int rc = dev_alloc_bytes(ctx, &p, count * sizeof(T));
+  if (rc != LRS_OK) return rc;
+  b.ptr = static_cast<T*>(p);
+  b.count = count;
+  return LRS_OK;
+}
+
+template <typename T>
+void release(lrs_ctx* ctx, DevBuf<T>& b) {
+  if (b.ptr) dev_free_bytes(ctx, b.ptr, b.count * sizeof(T));
+  b.ptr = nullptr;
+  b.count = 0;
+}
+
+// ---------------------------------------------------------------- state
+struct Site {
+  int npts = 0, lmax = 0;
+  double center[3] = {0, 0, 0};
+  DevBuf<double> pts, wts;          // [npts][3], [npts]
+  DevBuf<double2> psi_o, psi_u;     // [npts][Ko], [npts][Ku]
+  DevBuf<double> chi0, w, v;        // [npts][npts]
+  bool has_psi = false, has_chi0 = false, has_w = false;
+};
+
+// Split-precision operand planes of one matrix [rows_pad][k_pad] (4 planes:
+// re_hi, re_lo, im_hi, im_lo), 16-bit elements.
+struct Planes {
+  DevBuf<uint16_t> data;
+  int rows_pad = 0, k_pad = 0;
+  size_t plane_elems() const { return (size_t)rows_pad * k_pad; }
+};
+
+// Unit direction and radius of a grid point.
+struct __align__(32) RadialUnit {
+  double x, y, z, r;
+};
+
+struct Workspace {
+  DevBuf<double2> denom_o, denom_u;   // [nf][Ko], [nf][Ku]
+  DevBuf<double> dyson_a;             // [n][n]
+  DevBuf<int> ipiv;                   // [n]
+  DevBuf<int> status;                 // device status words
+  DevBuf<double2> phase_tab;          // projection phase tables
+  DevBuf<double2> kphase;             // [nk][npts]
+  DevBuf<RadialUnit> ru;              // [npts] unit vector and radius
+  // adjoint
+  DevBuf<double> gamma_s;             // [n][n]
+  DevBuf<double2> gbuf_o, gbuf_u;     // [n][n] per-frequency Green's functions
+  DevBuf<double2> ybuf;               // [n][K]
+  DevBuf<double> ge;                  // [K]
+  DevBuf<double2> gpsi;               // [n][K]
+  DevBuf<double> tmp_nn;              // [n][n]
+  // mixed precision
+  DevBuf<uint16_t> planes_a, planes_b;
+  DevBuf<double> s_acc;               // tile-blocked fp64 accumulator
+  DevBuf<float2> psi32;
+};
+
+}  // namespace lrs
+
+struct lrs_ctx {
+  int device = 0;
+  int precision = LRS_FP64;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+
+  // orbitals
+  bool has_orb = false;
+  int nk = 0, ng = 0, nb = 0, Ko = 0, Ku = 0;
+  std::vector<int> nocc;
+  double cell[9], recip[9], omega = 0;
+  std::vector<double> kpts, kw, energies;
+  std::vector<int> gvec;
+  int gmax_idx[3] = {0, 0, 0};
+  lrs::DevBuf<double2> coeff;          // [nk][ng][nb]
+  lrs::DevBuf<int> d_gvec;             // [ng][3]
+  lrs::DevBuf<double> d_kpts;          // [nk][3]
+  lrs::DevBuf<double> e_o, e_u, w_o, w_u;  // per internal column
+  std::vector<int> col_o, col_u;       // internal column -> public column (k*nb + b)
+  lrs::DevBuf<int> d_col_o, d_col_u;
+
+  // quadrature
+  int nf = 0;
+  double mu = 0, zeta = 0;
+  std::vector<double> t, W;
+  lrs::DevBuf<double> d_t, d_W;        // [nf] on the device
+
+  std::vector<lrs::Site> sites;
+  lrs::Workspace ws;
+
+  lrs_stats_t stats{};
+  // stage timing events: [stage][0=start,1=end]
+  cudaEvent_t ev[6][2] = {};
+  bool ev_pending[6] = {};
+  double ms_acc[6] = {};
+};
+
+namespace lrs {
+
+enum Stage { ST_PROJECT = 0, ST_CHI0 = 1, ST_W = 2, ST_BACKWARD = 3, ST_CHI0_MAIN = 4 };
+int stage_begin(lrs_ctx* ctx, Stage s);
+int stage_end(lrs_ctx* ctx, Stage s);
+
+// ---------------------------------------------------------------- launchers
+// Projection (k_project.cu)
+int project_fp64(lrs_ctx* ctx, Site& s);
+int project_mixed(lrs_ctx* ctx, Site& s);
+
+// Denominators d[f][col] = w/(mu + i t_f - eps) (k_chi0_fp64.cu)
+int build_denominators(lrs_ctx* ctx);
+
+// FP64 chi0 (k_chi0_fp64.cu): S accumulated into s.chi0, then symmetrised.
+int chi0_fp64(lrs_ctx* ctx, Site& s);
+int symmetrize_chi0(lrs_ctx* ctx, double* chi0, int n);
+
+// Mixed chi0 on tcgen05 (k_chi0_tc.cu)
+int chi0_mixed(lrs_ctx* ctx, Site& s);
+
+// Coulomb operator (k_coulomb.cu)
+int coulomb_build(lrs_ctx* ctx, Site& s, double* v);
+
+// FP64 linear algebra (k_linalg.cu)
+int dgemm(lrs_ctx* ctx, int m, int n, int k, double alpha, const double* a, int lda,
+          const double* kscale, const double* b, int ldb, const double* cscale, double beta,
+          double* c, int ldc);
+int dyson_solve(lrs_ctx* ctx, Site& s);
+
+// Adjoint (k_adjoint.cu)
+int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev,
+                  double* grad_e_dev, double2* grad_psi_dev);
+
+}  // namespace lrs

@@ -1,0 +1,249 @@
+"""ctypes binding of liblrs (include/lrs.h).
+
+Two layers:
+  * the raw entry points under their C names (``lrs_create``, ``lrs_build_chi0``
+    ...), exported from the loaded library with argument types attached;
+  * ``Screening``, a small owner of one context that marshals NumPy arrays and
+    torch tensors to those entry points and raises ``LrsError`` on a non-zero
+    status.
+Every step of the computation runs inside the library.  If liblrs.so is
+missing the import of this module fails: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("LRS_LIBRARY", os.path.join(_HERE, "liblrs.so"))
+
+LRS_OK, LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA, LRS_ERR_STATE = 0, 1, 2, 3, 4
+LRS_ERR_TIMEOUT, LRS_ERR_NUMERIC, LRS_ERR_UNSUPPORTED = 5, 6, 7
+LRS_FP64, LRS_MIXED_BF16X3, LRS_MIXED_FP16X3 = 0, 1, 2
+LRS_PROJ_EXACT = 0
+PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
+
+
+class lrs_stats_t(C.Structure):
+    _fields_ = [("ms_project", C.c_double), ("ms_chi0", C.c_double), ("ms_w", C.c_double),
+                ("ms_backward", C.c_double), ("ms_chi0_main", C.c_double), ("flop_chi0", C.c_double),
+                ("flop_w", C.c_double), ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
+                ("device_bytes_peak", C.c_int64), ("status_word", C.c_int)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"liblrs.so not found at {LIB_PATH}: run __graft_entry__.build() "
+                      "(python -m paper_2005_07834_gb300.build)")
+lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+_SIGS = {
+    "lrs_last_error": (C.c_char_p, []),
+    "lrs_version": (C.c_char_p, []),
+    "lrs_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, _P]),
+    "lrs_destroy": (C.c_int, [_P]),
+    "lrs_set_stream": (C.c_int, [_P, _P]),
+    "lrs_load_orbitals": (C.c_int, [_P, _DP, C.c_int, _DP, _DP, C.c_int, _IP, C.c_int, _IP, _DP, _DP]),
+    "lrs_set_sites": (C.c_int, [_P, C.c_int, _DP, _IP, _DP, _DP, _IP]),
+    "lrs_set_frequency_quadrature": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _DP, _DP]),
+    "lrs_get_frequency_quadrature": (C.c_int, [_P, _DP, _DP]),
+    "lrs_project": (C.c_int, [_P, C.c_int, _IP, C.c_int]),
+    "lrs_set_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_get_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_build_chi0": (C.c_int, [_P, C.c_int, _IP]),
+    "lrs_solve_w": (C.c_int, [_P, C.c_int, _IP]),
+    "lrs_get_chi0": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_get_w": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_get_v": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_get_chi0_dev": (C.c_int, [_P, C.c_int, _P]),
+    "lrs_get_w_dev": (C.c_int, [_P, C.c_int, _P]),
+    "lrs_backward": (C.c_int, [_P, C.c_int, _DP, _DP, _DP, _DP]),
+    "lrs_backward_dev": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "lrs_synchronize": (C.c_int, [_P]),
+    "lrs_stats": (C.c_int, [_P, C.POINTER(lrs_stats_t)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class LrsError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what} failed with status {code}: {lrs_last_error().decode()}")
+        self.code = code
+
+
+def _check(code, what):
+    if code != LRS_OK:
+        raise LrsError(code, what)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_IP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128_view(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a, a.view(np.float64)
+
+
+class Screening:
+    """One library context: orbitals, site grids, quadrature and results on one device."""
+
+    def __init__(self, device=0, precision="fp64", stream=None):
+        self.ctx = _P()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lrs_create(C.byref(self.ctx), int(device), prec, _P(stream or 0)), "lrs_create")
+        self.precision = prec
+        self.npts = []
+        self.nk = self.nb = 0
+
+    # -- lifetime
+    def close(self):
+        if self.ctx:
+            lrs_destroy(self.ctx)
+            self.ctx = _P()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lrs_set_stream(self.ctx, _P(stream or 0)), "lrs_set_stream")
+
+    # -- inputs
+    def load_orbitals(self, cell, kpts, kweights, gvec, coeff, energies, nocc):
+        coeff, cview = _c128_view(coeff)
+        nk, ng, nb = coeff.shape
+        cell, kpts, kw, en = _f64(cell), _f64(kpts), _f64(kweights), _f64(energies)
+        g = np.ascontiguousarray(gvec, dtype=np.int32)
+        no = np.ascontiguousarray(nocc, dtype=np.int32)
+        _check(lrs_load_orbitals(self.ctx, _dp(cell), nk, _dp(kpts), _dp(kw), ng, _ip(g), nb, _ip(no),
+                                 _dp(cview), _dp(en)), "lrs_load_orbitals")
+        self.nk, self.nb = nk, nb
+
+    def load(self, orbitals):
+        o = orbitals
+        self.load_orbitals(o.cell, o.kpts, o.kweights, o.gvec, o.coeff, o.energies, o.nocc)
+
+    def set_sites(self, sites):
+        centers = _f64(np.stack([s.center for s in sites]))
+        npts = np.array([s.npts for s in sites], np.int32)
+        pts = _f64(np.concatenate([s.pts for s in sites]))
+        wts = _f64(np.concatenate([s.wts for s in sites]))
+        lmax = np.array([s.lmax for s in sites], np.int32)
+        _check(lrs_set_sites(self.ctx, len(sites), _dp(centers), _ip(npts), _dp(pts), _dp(wts), _ip(lmax)),
+               "lrs_set_sites")
+        self.npts = [int(n) for n in npts]
+
+    def set_frequency_quadrature(self, nf, mu=float("nan"), zeta=0.0):
+        mo, zo = C.c_double(), C.c_double()
+        _check(lrs_set_frequency_quadrature(self.ctx, int(nf), float(mu), float(zeta), C.byref(mo), C.byref(zo)),
+               "lrs_set_frequency_quadrature")
+        self.nf = int(nf)
+        return mo.value, zo.value
+
+    def get_frequency_quadrature(self):
+        t = np.empty(self.nf)
+        w = np.empty(self.nf)
+        _check(lrs_get_frequency_quadrature(self.ctx, _dp(t), _dp(w)), "lrs_get_frequency_quadrature")
+        return t, w
+
+    # -- stages
+    @staticmethod
+    def _sites(sites):
+        if sites is None:
+            return 0, None, None
+        arr = np.ascontiguousarray(np.atleast_1d(sites), dtype=np.int32)
+        return len(arr), _ip(arr), arr
+
+    def project(self, sites=None, mode=LRS_PROJ_EXACT):
+        n, p, _keep = self._sites(sites)
+        _check(lrs_project(self.ctx, n, p, mode), "lrs_project")
+
+    def set_site_orbitals(self, site, psi):
+        psi, view = _c128_view(psi)
+        assert psi.shape == (self.npts[site], self.nk * self.nb)
+        _check(lrs_set_site_orbitals(self.ctx, int(site), _dp(view)), "lrs_set_site_orbitals")
+
+    def get_site_orbitals(self, site):
+        out = np.empty((self.npts[site], self.nk * self.nb), np.complex128)
+        _check(lrs_get_site_orbitals(self.ctx, int(site), _dp(out.view(np.float64))), "lrs_get_site_orbitals")
+        return out
+
+    def build_chi0(self, sites=None):
+        n, p, _keep = self._sites(sites)
+        _check(lrs_build_chi0(self.ctx, n, p), "lrs_build_chi0")
+
+    def solve_w(self, sites=None):
+        n, p, _keep = self._sites(sites)
+        _check(lrs_solve_w(self.ctx, n, p), "lrs_solve_w")
+
+    def _get(self, fn, site, name):
+        n = self.npts[site]
+        out = np.empty((n, n))
+        _check(fn(self.ctx, int(site), _dp(out)), name)
+        return out
+
+    def get_chi0(self, site=0):
+        return self._get(lrs_get_chi0, site, "lrs_get_chi0")
+
+    def get_w(self, site=0):
+        return self._get(lrs_get_w, site, "lrs_get_w")
+
+    def get_v(self, site=0):
+        return self._get(lrs_get_v, site, "lrs_get_v")
+
+    def get_chi0_dev(self, site, out_ptr):
+        _check(lrs_get_chi0_dev(self.ctx, int(site), _P(out_ptr)), "lrs_get_chi0_dev")
+
+    def get_w_dev(self, site, out_ptr):
+        _check(lrs_get_w_dev(self.ctx, int(site), _P(out_ptr)), "lrs_get_w_dev")
+
+    def backward(self, site, grad_w=None, grad_chi0=None):
+        n = self.npts[site]
+        gw = None if grad_w is None else _f64(grad_w)
+        gc = None if grad_chi0 is None else _f64(grad_chi0)
+        ge = np.empty((self.nk, self.nb))
+        gp = np.empty((n, self.nk * self.nb), np.complex128)
+        _check(lrs_backward(self.ctx, int(site), None if gw is None else _dp(gw), None if gc is None else _dp(gc),
+                            _dp(ge), _dp(gp.view(np.float64))), "lrs_backward")
+        return ge, gp
+
+    def backward_dev(self, site, grad_w_ptr, grad_chi0_ptr, grad_e_ptr, grad_psi_ptr):
+        _check(lrs_backward_dev(self.ctx, int(site), _P(grad_w_ptr or 0), _P(grad_chi0_ptr or 0),
+                                _P(grad_e_ptr), _P(grad_psi_ptr)), "lrs_backward_dev")
+
+    def synchronize(self):
+        _check(lrs_synchronize(self.ctx), "lrs_synchronize")
+
+    def stats(self):
+        s = lrs_stats_t()
+        _check(lrs_stats(self.ctx, C.byref(s)), "lrs_stats")
+        return {name: getattr(s, name) for name, _ in lrs_stats_t._fields_}
+
+
+def exported_symbols():
+    return sorted(_SIGS)

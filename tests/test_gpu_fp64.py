@@ -1,0 +1,123 @@
+"""FP64 CUDA path vs the FP64 oracle through the C-ABI (tolerance 1e-10 relative Frobenius)."""
+import numpy as np
+import pytest
+
+from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys
+from paper_2005_07834_gb300 import synth
+from tests.gpu_util import Reference, public_psi, rel_fro
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lrs():
+    from paper_2005_07834_gb300 import lrs as _lrs
+    return _lrs
+
+
+@pytest.fixture(scope="module")
+def cfg_260():
+    return Reference(synth.single_site_260())
+
+
+def run_fp64(lrs, workload, nfreq):
+    scr = lrs.Screening(0, "fp64")
+    scr.load(workload.orbitals)
+    scr.set_sites(workload.sites)
+    mu, zeta = scr.set_frequency_quadrature(nfreq)
+    scr.project()
+    scr.build_chi0()
+    scr.solve_w()
+    return scr, mu, zeta
+
+
+def test_single_site_260_forward(lrs, cfg_260):
+    ref = cfg_260
+    scr, mu, zeta = run_fp64(lrs, synth.single_site_260(), 12)
+    pr = ref.pr
+    assert mu == pytest.approx(pr.mu, abs=1e-15) and zeta == pytest.approx(pr.zeta, rel=1e-14)
+    t, W = scr.get_frequency_quadrature()
+    assert np.max(np.abs(t / pr.t - 1)) < 1e-13 and np.max(np.abs(W / pr.W - 1)) < 1e-13
+    psi = scr.get_site_orbitals(0)
+    assert rel_fro(psi, public_psi(pr)) < 1e-12
+    assert rel_fro(scr.get_v(0), ref.v) < 1e-13
+    chi = scr.get_chi0(0)
+    assert rel_fro(chi, ref.chi0) < TOL
+    assert np.max(np.abs(chi - ref.chi0)) < TOL * np.max(np.abs(ref.chi0))
+    assert np.array_equal(chi, chi.T)
+    w = scr.get_w(0)
+    assert rel_fro(w, ref.w) < TOL
+    assert rel_fro(w - ref.v, ref.w - ref.v) < 1e-8
+    st = scr.stats()
+    assert st["kernel_launches"] > 0 and st["status_word"] == 0
+    scr.close()
+
+
+def test_ragged_multisite(lrs):
+    """Two sites whose sizes are not multiples of the tiles, odd band counts."""
+    wl = synth.tiny(nk=8, nocc=3, nunocc=5)
+    extra = synth.site_grid(np.array([1.0, 2.0, 0.5]), 5, 14, 2.5)      # 70 points
+    wl.sites.append(extra)
+    scr, mu, zeta = run_fp64(lrs, wl, 12)
+    for i in range(2):
+        ref = Reference(wl, site=i)
+        assert rel_fro(scr.get_chi0(i), ref.chi0) < TOL
+        assert rel_fro(scr.get_w(i), ref.w) < TOL
+    scr.close()
+
+
+def test_set_site_orbitals_bypasses_projection(lrs, cfg_260):
+    ref = cfg_260
+    wl = synth.single_site_260()
+    scr = lrs.Screening(0, "fp64")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(12)
+    scr.set_site_orbitals(0, public_psi(ref.pr))
+    scr.build_chi0([0])
+    scr.solve_w([0])
+    assert rel_fro(scr.get_chi0(0), ref.chi0) < TOL
+    assert rel_fro(scr.get_w(0), ref.w) < TOL
+    scr.close()
+
+
+def test_zeta_override_and_more_frequencies(lrs):
+    wl = synth.tiny(nk=1, nocc=2, nunocc=6)
+    ref_pr = Reference(wl, nfreq=24).pr
+    scr = lrs.Screening(0, "fp64")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    mu, zeta = scr.set_frequency_quadrature(24, mu=ref_pr.mu, zeta=0.3)
+    assert zeta == 0.3
+    scr.project()
+    scr.build_chi0()
+    from oracle import quadrature as oq
+    t, W = oq.frequency_grid(24, 0.3)
+    chi = ochi0.chi0_pairs(*ref_pr.args(), t, W)
+    assert rel_fro(scr.get_chi0(0), chi) < TOL
+    scr.close()
+
+
+def test_state_and_argument_errors(lrs):
+    wl = synth.tiny()
+    scr = lrs.Screening(0, "fp64")
+    with pytest.raises(lrs.LrsError) as e:
+        scr.set_frequency_quadrature(12)
+    assert e.value.code == lrs.LRS_ERR_STATE
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(8)
+    with pytest.raises(lrs.LrsError) as e:
+        scr.build_chi0()
+    assert e.value.code == lrs.LRS_ERR_STATE
+    with pytest.raises(lrs.LrsError) as e:
+        scr.solve_w()
+    assert e.value.code == lrs.LRS_ERR_STATE
+    with pytest.raises(lrs.LrsError) as e:
+        scr.set_frequency_quadrature(8, mu=5.0)      # mu above every level
+    assert e.value.code == lrs.LRS_ERR_ARG
+    with pytest.raises(lrs.LrsError) as e:
+        scr.build_chi0([7])
+    assert e.value.code == lrs.LRS_ERR_ARG
+    scr.close()
