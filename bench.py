@@ -1,0 +1,315 @@
+"""Throughput of site chi0 + W builds on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole hot path over one site with the orbitals
+resident in HBM: projection of the Bloch coefficients onto the site grid,
+frequency denominators, the Green's-function contraction for chi0 with its
+FP64 frequency accumulation, the Coulomb operator and the FP64 LU Dyson solve
+for W.  `value` is site builds per second over all ranks; `e2e` measures the
+same through the C-ABI with host buffers (host->device copy of the
+coefficients and device->host copy of W inside the timed region).
+
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0
+only), on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP64 FMA: 2 per SM per clock (1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz) = 3.97 flop/clk/SM).
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "single-site-3520": "single_site_3520",
+    "single-site-260": "single_site_260",
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["source"] = "fallback"
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(name):
+    from paper_2005_07834_gb300 import synth
+    return getattr(synth, WORKLOADS[name])()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def oracle_build_sample(wl, kfrac_k=1, nfreq_sample=2):
+    """Times the FP64 oracle on one site: projection on `kfrac_k` of the k-points,
+    chi0 by the Green's-function route on `nfreq_sample` of the frequencies, and
+    the full Dyson solve; returns the time of one whole build scaled from it."""
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
+    o, s = wl.orbitals, wl.sites[0]
+    t0 = time.perf_counter()
+    psi_k = oproj.project_direct(o.cell, o.kpts[:kfrac_k], o.gvec, o.coeff[:kfrac_k], s.center, s.pts)
+    t_proj = (time.perf_counter() - t0) * o.nk / kfrac_k
+    # orbitals of the remaining k-points are not timed: reuse the sampled ones
+    psi = np.concatenate([psi_k] * (o.nk // kfrac_k), axis=1)
+    po, pu, eo, eu, wo, wu = oproj.split_occupied(psi, o.energies, o.nocc, o.kweights)
+    mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
+    t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
+    t0 = time.perf_counter()
+    chi = ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t[:nfreq_sample], W[:nfreq_sample])
+    t_chi = (time.perf_counter() - t0) * wl.nfreq / nfreq_sample
+    t0 = time.perf_counter()
+    v = ocoul.coulomb_multipole(s.pts, s.lmax)
+    odys.screened_interaction(v, chi, s.wts)
+    t_w = time.perf_counter() - t0
+    return t_proj + t_chi + t_w, {"t_project_s": t_proj, "t_chi0_s": t_chi, "t_w_s": t_w}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    cores = os.cpu_count()
+    sample = (f"one site of {args.workload}: projection timed on 1 of {wl.orbitals.nk} k-points, chi0 "
+              f"(Green's-function route) on 2 of {wl.nfreq} frequencies, full Dyson LU; scaled to one build")
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_build_sample(wl)
+    times = []
+    parts = None
+    for _ in range(args.steps):
+        t, parts = oracle_build_sample(wl)
+        times.append(t)
+    ms = 1e3 * statistics.mean(times)
+    value = 1e3 / ms
+    line = {"impl": "reference", "metric": "site chi0+W builds/s", "value": value, "unit": "builds/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": args.workload, "precision": "fp64-oracle-cpu"},
+            "cpu_baseline": {"value": value, "unit": "builds/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "parts_s": parts}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2005_07834_gb300 import lrs
+
+    wl = make_workload(args.workload)
+    o, s = wl.orbitals, wl.sites[0]
+    stream = torch.cuda.current_stream()
+    scr = lrs.Screening(local, args.precision, stream.cuda_stream)
+    scr.load(o)
+    scr.set_sites([s])
+    scr.set_frequency_quadrature(wl.nfreq)
+
+    def step():
+        scr.project()
+        scr.build_chi0()
+        scr.solve_w()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = scr.stats()["kernel_launches"]
+    sampler = ClockSampler(local)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    chi_main_ms, chi_ms, w_ms, proj_ms = [], [], [], []
+    barrier()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        # per-stage device times are read after the timed region (events inside the library)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    # stage times of the last timed step, event-timed inside the library on the same stream
+    st = scr.stats()
+    launches = st["kernel_launches"] - launches0
+    ms = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1e3 / ms
+
+    # end to end through the C-ABI with host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        scr2 = lrs.Screening(local, args.precision, stream.cuda_stream)
+        h2d = o.coeff.nbytes + o.energies.nbytes + o.kpts.nbytes + o.kweights.nbytes + o.gvec.nbytes + \
+            s.pts.nbytes + s.wts.nbytes
+        d2h = s.npts * s.npts * 8
+        reps = 1 if args.precision == "fp64" else max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            scr2.load(o)
+            scr2.set_sites([s])
+            scr2.set_frequency_quadrature(wl.nfreq)
+            scr2.project()
+            scr2.build_chi0()
+            scr2.solve_w()
+            scr2.get_w(0)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / reps
+        scr2.close()
+        e2e = {"value": 1.0 / e2e_s, "unit": "builds/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    peaks = load_peaks()
+    n, K, nf = s.npts, o.nk * o.nbands, wl.nfreq
+    flop_chi0 = 8.0 * n * n * K * nf
+    main_ms = st["ms_chi0_main"]
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    else:
+        pk = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": pk,
+                "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {peaks['source']}",
+                "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "chi0_fp64_kernel" if args.precision == "fp64" else "chi0_tc_kernel"
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            t_cpu, parts = oracle_build_sample(wl)
+            cpu = {"value": 1.0 / t_cpu, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"one site: projection on 1 of {o.nk} k-points, chi0 (Green's-function route) on 2 "
+                             f"of {nf} frequencies, full Dyson LU; scaled to one build", "parts_s": parts}
+        line = {
+            "metric": "site chi0+W builds/s", "value": value, "unit": "builds/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x3": "bf16x3/f32acc/f64", "fp16x3": "fp16x3/f32acc/f64"}[args.precision],
+            "data": "synthetic (seeded generator; no DFT orbitals)",
+            "config": {"workload": args.workload, "npts": n, "K": K, "nfreq": nf, "ng": o.ng,
+                       "precision": args.precision, "replicas_per_gpu": 1,
+                       "l2": "inputs larger than L2 (coefficients %d MB, orbitals %d MB)" % (
+                           o.coeff.nbytes >> 20, (n * K * 16) >> 20)},
+            "tflops": (flop_chi0 + 14.0 / 3.0 * n ** 3) / (ms * 1e-3) / 1e12,
+            "stage_ms": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
+                         "w": st["ms_w"]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "device_bytes_peak": st["device_bytes_peak"],
+        }
+        print(json.dumps(line), flush=True)
+    scr.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "fp16x3"])
+    ap.add_argument("--workload", default="single-site-3520", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
