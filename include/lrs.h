@@ -201,6 +201,35 @@ int lrs_backward_dev(lrs_ctx* ctx, int site, const double* grad_w_dev,
                      const double* grad_chi0_dev, double* grad_energies_dev,
                      double* grad_psi_dev);
 
+/*
+ * W for one site without any device allocation (the paper has no counterpart;
+ * this is a service to callers that cannot allocate device memory: a plugin
+ * inside a program whose caching allocator already holds the GPU's memory, a
+ * latency-critical loop that cannot take the device synchronisation of
+ * cudaMalloc/cudaFree, or a caller with a memory budget fixed at start-up).
+ * Same arithmetic as lrs_solve_w: v of the multipole form, then
+ * (I - v Q chi0 Q) W = v by float64 LU with partial pivoting.
+ *   npts                1 .. LRS_STATIC_MAX_NPTS (larger sizes: LRS_ERR_ARG, no work done)
+ *   lmax                multipole cutoff, 0..64
+ *   pts_dev [npts][3]   point offsets from the site centre (device, nonzero)
+ *   wts_dev [npts]      integration weights (device)
+ *   chi0_dev [npts][npts] chi0 of the site (device, e.g. from lrs_get_chi0_dev)
+ *   w_dev [npts][npts]  output W (device, caller-owned)
+ *   stream              cudaStream_t of the work (NULL = legacy default stream)
+ * Runs on the current device.  Scratch lives in one statically reserved
+ * device array of about 2.1 MB (LRS_STATIC_MAX_NPTS^2 doubles plus pivots)
+ * that every GPU loading the library holds until exit.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU race, so serialise them.
+ * The call waits for its stream to read the pivot status.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * Errors: LRS_ERR_ARG, LRS_ERR_CUDA, LRS_ERR_NUMERIC (zero/non-finite pivot).
+ */
+#define LRS_STATIC_MAX_NPTS 512
+int lrs_solve_w_static(int npts, int lmax, const double* pts_dev, const double* wts_dev,
+                       const double* chi0_dev, double* w_dev, void* stream);
+
 /* Wait for the context stream; fold device timings into the stats. */
 int lrs_synchronize(lrs_ctx* ctx);
 

@@ -63,6 +63,7 @@ _SIGS = {
     "lrs_get_w_dev": (C.c_int, [_P, C.c_int, _P]),
     "lrs_backward": (C.c_int, [_P, C.c_int, _DP, _DP, _DP, _DP]),
     "lrs_backward_dev": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "lrs_solve_w_static": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "lrs_synchronize": (C.c_int, [_P]),
     "lrs_stats": (C.c_int, [_P, C.POINTER(lrs_stats_t)]),
 }
