@@ -263,7 +263,34 @@ def run_ours(args):
                 "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel"] = "chi0_fp64_kernel" if args.precision == "fp64" else "chi0_tc_kernel"
+    roof["kernel"] = "chi0_fp64_kernel" if args.precision == "fp64" else "zgemm_tc_kernel<chi0>"
+
+    # the plain FP64 path on the same workload, one untimed-warm step (for "mixed vs FP64 plain")
+    plain = None
+    if rank == 0 and args.precision != "fp64" and not args.no_fp64_compare:
+        scr3 = lrs.Screening(local, "fp64", stream.cuda_stream)
+        scr3.load(o)
+        scr3.set_sites([s])
+        scr3.set_frequency_quadrature(wl.nfreq)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        scr3.project()
+        scr3.build_chi0()
+        scr3.solve_w()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        st3 = scr3.stats()
+        plain_ms = p0.elapsed_time(p1)
+        chi_plain, w_plain = scr3.get_chi0(0), scr3.get_w(0)
+        scr3.close()
+        chi_mixed, w_mixed = scr.get_chi0(0), scr.get_w(0)
+        plain = {"builds_per_s": 1e3 / plain_ms, "ms_per_step": plain_ms,
+                 "stage_ms": {"project": st3["ms_project"], "chi0": st3["ms_chi0"], "w": st3["ms_w"]},
+                 "mixed_vs_plain_speedup": plain_ms / ms,
+                 "mixed_rel_err_chi0": float(np.linalg.norm(chi_mixed - chi_plain) / np.linalg.norm(chi_plain)),
+                 "mixed_rel_err_w": float(np.linalg.norm(w_mixed - w_plain) / np.linalg.norm(w_plain))}
 
     if rank == 0:
         cpu = None
@@ -286,7 +313,7 @@ def run_ours(args):
             "stage_ms": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
                          "w": st["ms_w"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "device_bytes_peak": st["device_bytes_peak"],
+            "clocks": clocks, "device_bytes_peak": st["device_bytes_peak"], "plain_fp64": plain,
         }
         print(json.dumps(line), flush=True)
     scr.close()
@@ -297,10 +324,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "fp16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "fp16x3"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the one-step timing of the plain FP64 path on the same workload")
     ap.add_argument("--workload", default="single-site-3520", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -1,0 +1,371 @@
+// Mixed-precision projection and chi0 on the tcgen05 tensor cores.
+//
+// Projection (Sec. VI.B method 1): psi_k = e^{ik.R}/sqrt(Omega) (P C_k) with
+// the k-independent phase operand P(p, G) = e^{i G.R_p} and the coefficient
+// operand C_k(G, b), both of modulus <= 1.  It is always computed with fp16
+// hi/lo planes (11-bit significands, scaled by powers of two into the normal
+// fp16 range), whose split residual is 2^-22.
+//
+// chi0 (Sec. VI.D, Eq. (chi1), single-grid quadrature of App. D.1): per
+// frequency t_f the tensor cores form
+//   Go(p,p')   = sum_v [conj psi_v(p) d_v] psi_v(p'),
+//   Gu^T(p,p') = sum_c [psi_c(p) d_c] conj psi_c(p'),
+// (A planes per frequency, B planes shared), the epilogue writes the fp32
+// product X_f = Re[Go o Gu^T] of each frequency to its own slab, and the
+// reduction forms chi0 = (2/pi) sum_f W_f (X_f + X_f^T) in float64.  The
+// denominators d = w_k/(mu + i t - eps) are float64 (k_chi0_fp64.cu); the
+// split is bf16 (LRS_MIXED_BF16X3) or scaled fp16 (LRS_MIXED_FP16X3).
+#include <cmath>
+
+#include "tc_gemm.cuh"
+
+namespace lrs {
+
+int make_operand_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return set_error(LRS_ERR_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (cols * 2) % 16 != 0 || cols % 64 != 0 || rows % 128 != 0)
+    return set_error(LRS_ERR_ARG, "operand map: misaligned base or shape (%llu x %llu)",
+                     (unsigned long long)rows, (unsigned long long)cols);
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(LRS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return LRS_OK;
+}
+
+// ---------------------------------------------------------------- operand preparation
+template <uint32_t FMT>
+__device__ __forceinline__ void put_split(uint16_t* plane_row, int k, float x) {
+  uint16_t h, l;
+  split16<FMT>(x, h, l);
+  const int col = (k >> 5) * 64 + (k & 31);
+  plane_row[col] = h;
+  plane_row[col + 32] = l;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned int* dst, float v) {
+  atomicMax(dst, __float_as_uint(v));   // non-negative floats order like their bit patterns
+}
+
+// max |z| over a complex float64 array (result as float bits, pre-zeroed).
+__global__ void max_abs_kernel(const double2* __restrict__ a, size_t n, unsigned int* __restrict__ out) {
+  float m = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = a[i];
+    m = fmaxf(m, (float)sqrt(v.x * v.x + v.y * v.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+// scales[f] for the A planes of frequency f (|conj psi d_f| <= max|psi| max|d_f|),
+// scales[nf] for the B planes.  One block per frequency.
+__global__ void chi0_scales_kernel(const double2* __restrict__ d_o, int Ko, const double2* __restrict__ d_u, int Ku,
+                                   int nf, const unsigned int* __restrict__ psi_max_bits, float* __restrict__ scales) {
+  const int f = blockIdx.x;
+  float m = 0.f;
+  for (int k = threadIdx.x; k < Ko + Ku; k += blockDim.x) {
+    const double2 d = k < Ko ? d_o[(size_t)f * Ko + k] : d_u[(size_t)f * Ku + (k - Ko)];
+    m = fmaxf(m, (float)sqrt(d.x * d.x + d.y * d.y));
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    const float pm = __uint_as_float(*psi_max_bits);
+    scales[f] = pow2_scale(pm * m);
+    if (f == 0) scales[nf] = pow2_scale(pm);
+  }
+}
+
+// B planes (frequency independent):  occupied columns psi, unoccupied conj(psi).
+// A planes per frequency:            occupied conj(psi) d_f, unoccupied psi d_f.
+// Planes: [2 (re, im)][rows][2*Kp] with rows = Np (B) or nf*Np (A).  `scales`
+// (NULL = 1) multiplies the A planes of frequency f by scales[f] and the B
+// planes by scales[nf].
+template <uint32_t FMT>
+__global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, const double2* __restrict__ psi_u,
+                                 int Ku, int n, int Np, int Kop, int Kp, const double2* __restrict__ d_o,
+                                 const double2* __restrict__ d_u, int nf, const float* __restrict__ scales,
+                                 uint16_t* __restrict__ A, uint16_t* __restrict__ B) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (k >= Kp || p >= Np) return;
+  const bool occ = k < Kop;
+  const int kk = occ ? k : k - Kop;
+  const bool live = p < n && (occ ? kk < Ko : kk < Ku);
+  float xr = 0.f, xi = 0.f;
+  if (live) {
+    double2 v = occ ? psi_o[(size_t)p * Ko + kk] : psi_u[(size_t)p * Ku + kk];
+    xr = (float)v.x;
+    xi = (float)v.y;
+  }
+  const size_t ld = 2 * (size_t)Kp;
+  const size_t bplane = (size_t)Np * ld;
+  const float sb = scales ? scales[nf] : 1.f;
+  put_split<FMT>(B + (size_t)p * ld, k, sb * xr);
+  put_split<FMT>(B + bplane + (size_t)p * ld, k, sb * (occ ? xi : -xi));
+  const size_t aplane = (size_t)nf * Np * ld;
+  const float cr = xr, ci = occ ? -xi : xi;   // conj for occupied
+  for (int f = 0; f < nf; ++f) {
+    float ar = 0.f, ai = 0.f;
+    if (live) {
+      const double2 d = occ ? d_o[(size_t)f * Ko + kk] : d_u[(size_t)f * Ku + kk];
+      const float sa = scales ? scales[f] : 1.f;
+      const float dr = (float)d.x * sa, di = (float)d.y * sa;
+      ar = cr * dr - ci * di;
+      ai = cr * di + ci * dr;
+    }
+    const size_t row = (size_t)f * Np + p;
+    put_split<FMT>(A + row * ld, k, ar);
+    put_split<FMT>(A + aplane + row * ld, k, ai);
+  }
+}
+
+// chi0 = (2/pi) sum_f W_f (X_f + X_f^T) / (scales[f] scales[nf])^2, float64 accumulation.
+__global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf, const double* __restrict__ Wf,
+                                   const float* __restrict__ scales, int n, double* __restrict__ chi0) {
+  __shared__ float t[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int f = 0; f < nf; ++f) {
+    const float* s = slab + (size_t)f * Np * Np;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
+    __syncthreads();
+    double w = Wf[f];
+    if (scales) {
+      const double sc = (double)scales[f] * (double)scales[nf];
+      w /= sc * sc;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float direct = s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
+      acc[i] = fma(w, (double)(direct + t[tx][ty + 8 * i]), acc[i]);
+    }
+    __syncthreads();
+  }
+  const double c = 0.63661977236758134308;   // 2/pi
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 8 * i, q = c0 + tx;
+    if (r < n && q < n) chi0[(size_t)r * n + q] = c * acc[i];
+  }
+}
+
+// Projection B operand: C_k(G, b) * scale -> planes [2][nk*nbp][2*NGp] (rows = k*nbp + b, K = G).
+template <uint32_t FMT>
+__global__ void coeff_prep_kernel(const double2* __restrict__ coeff, int ng, int nb, int NGp, int nbp,
+                                  const float* __restrict__ scale, uint16_t* __restrict__ B, size_t im_off) {
+  __shared__ float2 t[32][33];
+  const int k = blockIdx.z;
+  const int g0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const float sc = *scale;
+  for (int i = ty; i < 32; i += 8) {
+    const int g = g0 + i, b = b0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (g < ng && b < nb) {
+      const double2 c = coeff[((size_t)k * ng + g) * nb + b];
+      v = make_float2((float)c.x * sc, (float)c.y * sc);
+    }
+    t[i][tx] = v;
+  }
+  __syncthreads();
+  const size_t ld = 2 * (size_t)NGp;
+  for (int i = ty; i < 32; i += 8) {
+    const int b = b0 + i, g = g0 + tx;
+    if (b >= nbp || g >= NGp) continue;
+    const float2 v = t[tx][i];
+    uint16_t* row = B + ((size_t)k * nbp + b) * ld;
+    put_split<FMT>(row, g, v.x);
+    put_split<FMT>(row + im_off, g, v.y);
+  }
+}
+
+// Projection A operand: e^{i G.R_p} = T1 T2 T3 (times `scale`) -> planes [2][Np][2*NGp].
+template <uint32_t FMT>
+__global__ void phase_prep_kernel(const double2* __restrict__ tab, int npts, int3 nmax, int off1, int off2,
+                                  const int* __restrict__ gvec, int ng, int Np, int NGp, float scale,
+                                  uint16_t* __restrict__ A, size_t im_off) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (g >= NGp || p >= Np) return;
+  float re = 0.f, im = 0.f;
+  if (g < ng && p < npts) {
+    const int w1 = 2 * nmax.x + 1, w2 = 2 * nmax.y + 1, w3 = 2 * nmax.z + 1;
+    const double2 t1 = tab[(size_t)p * w1 + gvec[3 * g] + nmax.x];
+    const double2 t2 = tab[off1 + (size_t)p * w2 + gvec[3 * g + 1] + nmax.y];
+    const double2 t3 = tab[off2 + (size_t)p * w3 + gvec[3 * g + 2] + nmax.z];
+    const float ar = (float)t1.x, ai = (float)t1.y, br = (float)t2.x, bi = (float)t2.y;
+    const float cr = ar * br - ai * bi, ci = ar * bi + ai * br;
+    const float dr = (float)t3.x, di = (float)t3.y;
+    re = (cr * dr - ci * di) * scale;
+    im = (cr * di + ci * dr) * scale;
+  }
+  uint16_t* row = A + (size_t)p * 2 * NGp;
+  put_split<FMT>(row, g, re);
+  put_split<FMT>(row + im_off, g, im);
+}
+
+// unscale = 1 / (phase_scale * coefficient scale), the coefficient scale from max |C|.
+__global__ void coeff_scale_kernel(const unsigned int* __restrict__ cmax_bits, float phase_scale,
+                                   float* __restrict__ scale, float* __restrict__ unscale) {
+  const float s = pow2_scale(__uint_as_float(*cmax_bits));
+  *scale = s;
+  *unscale = 1.f / (s * phase_scale);
+}
+
+static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+constexpr int CHI0_TN = 128;   // chi0 tile columns
+constexpr int PROJ_TN = 128;   // projection tile columns
+
+int phase_setup(lrs_ctx* ctx, Site& s, int* off1, int* off2);
+
+template <uint32_t FMT>
+static int chi0_mixed_t(lrs_ctx* ctx, Site& s) {
+  const int n = s.npts, nf = ctx->nf;
+  const int Np = round_up(n, TILE_M);
+  const int Kop = round_up(ctx->Ko, 32), Kup = round_up(ctx->Ku, 32), Kp = Kop + Kup;
+  const size_t ld = 2 * (size_t)Kp;
+  LRS_TRY(ensure(ctx, ctx->ws.planes_a, 2 * (size_t)nf * Np * ld));
+  LRS_TRY(ensure(ctx, ctx->ws.planes_b, 2 * (size_t)Np * ld));
+  LRS_TRY(ensure(ctx, ctx->ws.slab, (size_t)nf * Np * Np));
+  const float* scales = nullptr;
+  if (FMT == 0) {
+    LRS_TRY(ensure(ctx, ctx->ws.scales, (size_t)nf + 8));
+    unsigned int* pmax = reinterpret_cast<unsigned int*>(ctx->ws.scales.ptr + nf + 4);
+    LRS_CUDA_TRY(cudaMemsetAsync(pmax, 0, sizeof(unsigned int), ctx->stream));
+    max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(s.psi_o.ptr, (size_t)n * ctx->Ko, pmax);
+    LRS_TRY(after_launch(ctx, "max_abs_kernel"));
+    max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(s.psi_u.ptr, (size_t)n * ctx->Ku, pmax);
+    LRS_TRY(after_launch(ctx, "max_abs_kernel"));
+    chi0_scales_kernel<<<nf, 256, 0, ctx->stream>>>(ctx->ws.denom_o.ptr, ctx->Ko, ctx->ws.denom_u.ptr, ctx->Ku, nf,
+                                                     pmax, ctx->ws.scales.ptr);
+    LRS_TRY(after_launch(ctx, "chi0_scales_kernel"));
+    scales = ctx->ws.scales.ptr;
+  }
+  dim3 pg((Kp + 127) / 128, Np);
+  chi0_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku, n, Np, Kop, Kp,
+                                                      ctx->ws.denom_o.ptr, ctx->ws.denom_u.ptr, nf, scales,
+                                                      ctx->ws.planes_a.ptr, ctx->ws.planes_b.ptr);
+  LRS_TRY(after_launch(ctx, "chi0_prep_kernel"));
+  CUtensorMap ma, mb;
+  LRS_TRY(make_operand_map(&ma, ctx->ws.planes_a.ptr, ld, 2 * (uint64_t)nf * Np, TILE_M));
+  LRS_TRY(make_operand_map(&mb, ctx->ws.planes_b.ptr, ld, 2 * (uint64_t)Np, CHI0_TN));
+  TcShape sh;
+  sh.m_tiles = Np / TILE_M;
+  sh.n_tiles = Np / CHI0_TN;
+  sh.batches = nf;
+  sh.nchunk = Kp / 32;
+  sh.nchunk0 = Kop / 32;
+  sh.seg = ctx->seg_chunks;
+  sh.a_batch_rows = Np;
+  sh.b_batch_rows = 0;
+  sh.a_im_rows = nf * Np;
+  sh.b_im_rows = Np;
+  LRS_TRY(ensure(ctx, ctx->ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * CHI0_TN));
+  Chi0Store epi{ctx->ws.slab.ptr, ctx->ws.tc_scratch.ptr, Np, CHI0_TN};
+  LRS_TRY(stage_begin(ctx, ST_CHI0_MAIN));
+  LRS_TRY((launch_tc<CHI0_TN, 2, FMT, Chi0Store>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0>")));
+  LRS_TRY(stage_end(ctx, ST_CHI0_MAIN));
+  dim3 rg(Np / 32, Np / 32);
+  chi0_reduce_kernel<<<rg, dim3(32, 8), 0, ctx->stream>>>(ctx->ws.slab.ptr, Np, nf, ctx->d_W.ptr, scales, n,
+                                                          s.chi0.ptr);
+  return after_launch(ctx, "chi0_reduce_kernel");
+}
+
+int chi0_mixed(lrs_ctx* ctx, Site& s) {
+  if (ctx->precision == LRS_MIXED_FP16X3) return chi0_mixed_t<0>(ctx, s);
+  return chi0_mixed_t<1>(ctx, s);
+}
+
+int project_mixed(lrs_ctx* ctx, Site& s) {
+  constexpr uint32_t FMT = 0;               // fp16 hi/lo: operands are bounded by 1
+  constexpr float PHASE_SCALE = 16384.f;    // |e^{iG.R}| = 1
+  if (ctx->nk > MAX_K_POINTS)
+    return set_error(LRS_ERR_UNSUPPORTED, "mixed projection supports at most %d k-points", MAX_K_POINTS);
+  const int n = s.npts;
+  const int Np = round_up(n, TILE_M);
+  const int NGp = round_up(ctx->ng, 32);
+  const int nbp = round_up(ctx->nb, PROJ_TN);
+  const size_t ld = 2 * (size_t)NGp;
+  LRS_TRY(ensure(ctx, ctx->ws.proj_scale, 4));
+  float* cscale = ctx->ws.proj_scale.ptr;      // [0] coefficient scale, [1] unscale, [2] max bits
+  // coefficient planes depend only on the orbitals: rebuilt when they change
+  const size_t bsz = 2 * (size_t)ctx->nk * nbp * ld;
+  if (!ctx->ws.coeff_planes_valid || ctx->ws.proj_b.count < bsz) {
+    LRS_TRY(ensure(ctx, ctx->ws.proj_b, bsz));
+    unsigned int* cmax = reinterpret_cast<unsigned int*>(cscale + 2);
+    LRS_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(unsigned int), ctx->stream));
+    max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->coeff.ptr, (size_t)ctx->nk * ctx->ng * ctx->nb,
+                                                               cmax);
+    LRS_TRY(after_launch(ctx, "max_abs_kernel"));
+    coeff_scale_kernel<<<1, 1, 0, ctx->stream>>>(cmax, PHASE_SCALE, cscale, cscale + 1);
+    LRS_TRY(after_launch(ctx, "coeff_scale_kernel"));
+    dim3 cg((NGp + 31) / 32, (nbp + 31) / 32, ctx->nk);
+    coeff_prep_kernel<FMT><<<cg, dim3(32, 8), 0, ctx->stream>>>(ctx->coeff.ptr, ctx->ng, ctx->nb, NGp, nbp, cscale,
+                                                                  ctx->ws.proj_b.ptr, (size_t)ctx->nk * nbp * ld);
+    LRS_TRY(after_launch(ctx, "coeff_prep_kernel"));
+    ctx->ws.coeff_planes_valid = true;
+  }
+  int off1, off2;
+  LRS_TRY(phase_setup(ctx, s, &off1, &off2));
+  LRS_TRY(ensure(ctx, ctx->ws.proj_a, 2 * (size_t)Np * ld));
+  const int* nm = ctx->gmax_idx;
+  dim3 pg((NGp + 127) / 128, Np);
+  phase_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(ctx->ws.phase_tab.ptr, n, make_int3(nm[0], nm[1], nm[2]),
+                                                       off1, off2, ctx->d_gvec.ptr, ctx->ng, Np, NGp, PHASE_SCALE,
+                                                       ctx->ws.proj_a.ptr, (size_t)Np * ld);
+  LRS_TRY(after_launch(ctx, "phase_prep_kernel"));
+  CUtensorMap ma, mb;
+  LRS_TRY(make_operand_map(&ma, ctx->ws.proj_a.ptr, ld, 2 * (uint64_t)Np, TILE_M));
+  LRS_TRY(make_operand_map(&mb, ctx->ws.proj_b.ptr, ld, 2 * (uint64_t)ctx->nk * nbp, PROJ_TN));
+  TcShape sh;
+  sh.m_tiles = Np / TILE_M;
+  sh.n_tiles = nbp / PROJ_TN;
+  sh.batches = ctx->nk;
+  sh.nchunk = NGp / 32;
+  sh.nchunk0 = sh.nchunk;
+  sh.seg = ctx->proj_seg_chunks;
+  sh.a_batch_rows = 0;
+  sh.b_batch_rows = nbp;
+  sh.a_im_rows = Np;
+  sh.b_im_rows = ctx->nk * nbp;
+  ProjStore epi;
+  epi.kph = ctx->ws.kphase.ptr;
+  epi.unscale = cscale + 1;
+  epi.npts = n;
+  epi.nb = ctx->nb;
+  epi.psi_o = s.psi_o.ptr;
+  epi.psi_u = s.psi_u.ptr;
+  epi.Ko = ctx->Ko;
+  epi.Ku = ctx->Ku;
+  int oo = 0, uo = 0;
+  for (int k = 0; k < ctx->nk; ++k) {
+    epi.nocc[k] = ctx->nocc[k];
+    epi.oofs[k] = oo;
+    epi.uofs[k] = uo;
+    oo += ctx->nocc[k];
+    uo += ctx->nb - ctx->nocc[k];
+  }
+  return launch_tc<PROJ_TN, 1, FMT, ProjStore>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<project>");
+}
+
+}  // namespace lrs

@@ -162,7 +162,8 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.status); release(ctx, w.phase_tab); release(ctx, w.kphase); release(ctx, w.ru);
   release(ctx, w.gamma_s); release(ctx, w.gbuf_o); release(ctx, w.gbuf_u); release(ctx, w.ybuf);
   release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
-  release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.s_acc); release(ctx, w.psi32);
+  release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.tc_scratch);
+  release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
 
 }  // namespace lrs
@@ -196,6 +197,10 @@ int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   ctx->precision = precision;
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->num_sms = prop.multiProcessorCount;
+  if (const char* seg = getenv("LRS_SEG_CHUNKS")) {
+    int v = atoi(seg);
+    if (v >= 1 && v <= 1024) ctx->seg_chunks = v;
+  }
   for (int s = 0; s < 6; ++s)
     for (int j = 0; j < 2; ++j)
       if (cudaEventCreate(&ctx->ev[s][j]) != cudaSuccess) {
@@ -314,6 +319,7 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   // the host vectors above go out of scope: wait for the copies
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->has_orb = true;
+  ctx->ws.coeff_planes_valid = false;
   ctx->nf = 0;
   for (auto& s : ctx->sites) s.has_psi = s.has_chi0 = s.has_w = false;
   return LRS_OK;
@@ -549,10 +555,14 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   LRS_TRY(stage_end(ctx, ST_W));
   ctx->stats.flop_w = flop;
   // zero pivots / non-finite values are reported through the status word
-  int status[4] = {0, 0, 0, 0};
-  LRS_CUDA_TRY(cudaMemcpyAsync(status, ctx->ws.status.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int status[16] = {0};
+  LRS_CUDA_TRY(cudaMemcpyAsync(status, ctx->ws.status.ptr, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  ctx->stats.status_word = status[0];
+  ctx->stats.status_word = status[0] ? status[0] : status[8];
+  if (status[8] != 0) {
+    cudaMemsetAsync(ctx->ws.status.ptr + 8, 0, sizeof(int), ctx->stream);
+    return set_error(LRS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code %d)", status[8]);
+  }
   if (status[0] != 0) {
     cudaMemsetAsync(ctx->ws.status.ptr, 0, 4 * sizeof(int), ctx->stream);
     for (int i : list) ctx->sites[i].has_w = false;
@@ -645,6 +655,13 @@ int lrs_synchronize(lrs_ctx* ctx) {
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  int tc_status = 0;
+  LRS_CUDA_TRY(cudaMemcpy(&tc_status, ctx->ws.status.ptr + 8, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tc_status != 0) {
+    ctx->stats.status_word = tc_status;
+    cudaMemset(ctx->ws.status.ptr + 8, 0, sizeof(int));
+    return set_error(LRS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code %d)", tc_status);
+  }
   for (int s = 0; s < 6; ++s)
     if (ctx->ev_pending[s]) {
       float ms = 0.f;

@@ -104,10 +104,14 @@ struct Workspace {
   DevBuf<double> ge;                  // [K]
   DevBuf<double2> gpsi;               // [n][K]
   DevBuf<double> tmp_nn;              // [n][n]
-  // mixed precision
-  DevBuf<uint16_t> planes_a, planes_b;
-  DevBuf<double> s_acc;               // tile-blocked fp64 accumulator
-  DevBuf<float2> psi32;
+  // mixed precision (bf16 hi/lo operand planes)
+  DevBuf<uint16_t> planes_a, planes_b;  // chi0: per-frequency A, frequency-independent B
+  DevBuf<float> slab;                   // chi0: [nf][Np][Np] fp32 Re[Go o Gu^T] per frequency
+  DevBuf<float> tc_scratch;             // chi0: per-CTA parked occupied sums
+  DevBuf<uint16_t> proj_a, proj_b;      // projection: phase planes, coefficient planes
+  DevBuf<float> scales;                 // chi0: fp16 operand scales per frequency
+  DevBuf<float> proj_scale;             // projection: coefficient scale and unscale
+  bool coeff_planes_valid = false;
 };
 
 }  // namespace lrs
@@ -117,6 +121,8 @@ struct lrs_ctx {
   int precision = LRS_FP64;
   cudaStream_t stream = nullptr;
   int num_sms = 0;
+  int seg_chunks = 4;                  // chi0 tensor-core accumulation segment (K chunks of 32)
+  int proj_seg_chunks = 2;             // projection accumulation segment (K chunks of 32)
 
   // orbitals
   bool has_orb = false;

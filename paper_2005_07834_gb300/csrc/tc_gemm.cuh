@@ -1,0 +1,398 @@
+// Generic split-precision complex GEMM on tcgen05 (sm_103a): D = A B^T with
+// A [M][K], B [N][K] stored as 16-bit hi/lo planes (re and im separately).
+//   Re D = Ar Br - Ai Bi,  Im D = Ar Bi + Ai Br,
+// each real product as hi*hi + hi*lo + lo*hi (12 MMAs of 128 x TN x 16 per
+// 16-wide K step).  Tiles are staged by TMA with the 128-byte swizzle through
+// an mbarrier pipeline.
+//
+// Segmented accumulation.  The tensor cores add every MMA result into their
+// fp32 accumulator with a rounding that is biased toward zero, so the error of
+// one long accumulation grows linearly with K (measured: relative 4.5e-5 at
+// K = 5120).  The K loop is therefore cut into segments of `seg` chunks of 32:
+// each segment is accumulated from zero into one of two TMEM buffers, and the
+// epilogue warps fold the finished buffer into fp32 register sums with
+// round-to-nearest additions while the tensor cores fill the other buffer.
+// The tensor-core error is then bounded by one segment.
+//
+// NPHASE = 2 (chi0) splits K into two contractions with separate sums: the
+// first `nchunk0` chunks (occupied bands, Go) and the rest (unoccupied, Gu^T).
+//
+// Roles (320 threads, one CTA per SM, persistent over work units):
+//   warp 0      TMA producer (one lane)
+//   warp 1      TMEM allocation and MMA issue (one lane)
+//   warps 2..9  epilogue: two warps per TMEM lane quarter, each owning TN/2
+//               columns of its 32 rows
+// Every wait is bounded in time; a timeout raises a status code and the CTA
+// drains and frees its TMEM before returning.
+#pragma once
+
+#include "lrs_internal.h"
+#include "tc_common.cuh"
+
+namespace lrs {
+
+using namespace tc;
+
+constexpr int TC_THREADS = 320;
+constexpr int TC_EPI_WARPS = 8;
+constexpr int MAX_K_POINTS = 64;
+
+struct TcShape {
+  int m_tiles, n_tiles, batches;
+  int nchunk;        // K chunks of 32
+  int nchunk0;       // chunks of the first contraction (NPHASE = 2)
+  int seg;           // chunks per accumulation segment
+  int a_batch_rows;  // row offset of batch b in A (0 = shared)
+  int b_batch_rows;  // row offset of batch b in B (0 = shared)
+  int a_im_rows;     // row offset of the imaginary planes in A
+  int b_im_rows;     // row offset of the imaginary planes in B
+};
+
+__device__ __forceinline__ void decode_unit(const TcShape& sh, int u, int& tm, int& tn, int& b) {
+  b = u % sh.batches;
+  int t = u / sh.batches;
+  tm = t / sh.n_tiles;
+  tn = t % sh.n_tiles;
+}
+
+// Segments of a unit: phase 0 covers chunks [0, c0), phase 1 [c0, nchunk).
+template <int NPHASE>
+struct SegPlan {
+  int c0, nchunk, seg;
+  __device__ __forceinline__ int count() const {
+    if (NPHASE == 1) return (nchunk + seg - 1) / seg;
+    return (c0 + seg - 1) / seg + (nchunk - c0 + seg - 1) / seg;
+  }
+  __device__ __forceinline__ int count_phase0() const { return (c0 + seg - 1) / seg; }
+  // first chunk, chunk count and phase of segment i
+  __device__ __forceinline__ void get(int i, int& first, int& len, int& phase) const {
+    const int n0 = (NPHASE == 1) ? count() : (c0 + seg - 1) / seg;
+    if (i < n0) {
+      phase = 0;
+      first = i * seg;
+      const int end = (NPHASE == 1) ? nchunk : c0;
+      len = min(seg, end - first);
+    } else {
+      phase = 1;
+      first = c0 + (i - n0) * seg;
+      len = min(seg, nchunk - first);
+    }
+  }
+};
+
+template <int TN>
+__host__ __device__ constexpr int tc_stage_bytes() {
+  return 2 * TILE_BYTES + 2 * (TN * 128);   // A re, A im (128 rows) + B re, B im (TN rows)
+}
+
+template <int TN>
+__host__ __device__ constexpr int tc_stages() {
+  return (200 * 1024) / tc_stage_bytes<TN>() > 6 ? 6 : (200 * 1024) / tc_stage_bytes<TN>();
+}
+
+template <int TN>
+__host__ __device__ constexpr int tc_smem_bytes() {
+  return tc_stages<TN>() * tc_stage_bytes<TN>() + 1024;
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int TN, int NPHASE, uint32_t FMT, class Epi>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    zgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const TcShape sh, const Epi epi, int* status) {
+  constexpr int STAGES = tc_stages<TN>();
+  constexpr int STAGE_BYTES = tc_stage_bytes<TN>();
+  constexpr int B_TILE = TN * 128;
+  constexpr uint32_t SET_COLS = 2 * TN;             // re + im of one complex accumulator
+  constexpr uint32_t TMEM_COLS = 2 * SET_COLS < 32 ? 32 : 2 * SET_COLS;
+  constexpr int COLS = TN / 2;                       // columns per epilogue thread
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = sh.m_tiles * sh.n_tiles * sh.batches;
+  const SegPlan<NPHASE> plan{sh.nchunk0, sh.nchunk, sh.seg};
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], TC_EPI_WARPS);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_map(&tmA);
+    tma_prefetch_map(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        int tm, tn, b;
+        decode_unit(sh, u, tm, tn, b);
+        const int ya = b * sh.a_batch_rows + tm * TILE_M;
+        const int yb = b * sh.b_batch_rows + tn * TN;
+        for (int c = 0; c < sh.nchunk; ++c) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_PRODUCER);
+            goto producer_done;
+          }
+          mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
+          const uint32_t s = smem_base + stage * STAGE_BYTES;
+          tma_load_2d(s, &tmA, &full_bar[stage], c * 64, ya);
+          tma_load_2d(s + TILE_BYTES, &tmA, &full_bar[stage], c * 64, ya + sh.a_im_rows);
+          tma_load_2d(s + 2 * TILE_BYTES, &tmB, &full_bar[stage], c * 64, yb);
+          tma_load_2d(s + 2 * TILE_BYTES + B_TILE, &tmB, &full_bar[stage], c * 64, yb + sh.b_im_rows);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+    producer_done:;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t ID_POS = idesc_f16(TILE_M, TN, FMT, false);
+      constexpr uint32_t ID_NEG = idesc_f16(TILE_M, TN, FMT, true);
+      int stage = 0, set = 0;
+      uint32_t phase = 0, set_phase = 0;
+      const int nseg = plan.count();
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        for (int sg = 0; sg < nseg && ok; ++sg) {
+          int first, len, ph;
+          plan.get(sg, first, len, ph);
+          (void)first;
+          (void)ph;
+          if (!mbar_wait(&acce_bar[set], set_phase ^ 1u, &abort_flag)) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_MMA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dre = tbase + set * SET_COLS, dim = dre + TN;
+          for (int c = 0; c < len; ++c) {
+            if (!mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+              abort_flag = 1;
+              atomicCAS(status, 0, TC_TIMEOUT_MMA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t s = smem_base + stage * STAGE_BYTES;
+            const uint32_t aR = s, aI = s + TILE_BYTES, bR = s + 2 * TILE_BYTES, bI = bR + B_TILE;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;
+              const uint32_t a0 = (c == 0 && ks == 0) ? 0u : 1u;
+              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
+              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
+              mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
+              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + hi), ID_NEG, 1u);
+              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + lo), ID_NEG, 1u);
+              mma_f16(dre, sw128_desc(aI + lo), sw128_desc(bI + hi), ID_NEG, 1u);
+              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + hi), ID_POS, a0);
+              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + lo), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aR + lo), sw128_desc(bI + hi), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
+            }
+            mma_commit(&empty_bar[stage]);
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          }
+          if (!ok) break;
+          mma_commit(&accf_bar[set]);
+          set ^= 1;
+          if (set == 0) set_phase ^= 1u;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..9)
+    const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+    const int half = (warp - 2) >> 2;             // column half of the tile
+    const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+    // Register sums (re, im) of the contraction in progress.  For NPHASE = 2 the
+    // occupied sums are parked in the epilogue's scratch at the phase switch.
+    float sum[2][COLS];
+    int set = 0;
+    uint32_t set_phase = 0;
+    const int nseg = plan.count();
+    const int lrow = quarter * 32 + lane, lcol0 = half * COLS;
+    bool ok = true;
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      int tm, tn, b;
+      decode_unit(sh, u, tm, tn, b);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int i = 0; i < COLS; ++i) sum[q][i] = 0.f;
+      for (int sg = 0; sg < nseg; ++sg) {
+        int first, len, ph;
+        plan.get(sg, first, len, ph);
+        (void)first;
+        (void)len;
+        if (NPHASE == 2 && ph == 1 && (sg == 0 || sg == plan.count_phase0())) {
+          epi.template save_phase0<COLS>(sum, lrow, lcol0);
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int i = 0; i < COLS; ++i) sum[q][i] = 0.f;
+        }
+        int got = 1;
+        if (lane == 0) got = mbar_wait(&accf_bar[set], set_phase, &abort_flag) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        if (!got) {
+          if (lane == 0) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_EPILOGUE);
+          }
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = tbase + lane_off + set * SET_COLS + half * COLS;
+#pragma unroll
+        for (int j = 0; j < COLS / 16; ++j) {
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {   // re, then im: 16 registers in flight
+            float v[16];
+            tmem_ld16(tb + part * TN + 16 * j, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sum[part][16 * j + i] += v[i];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[set]);
+        set ^= 1;
+        if (set == 0) set_phase ^= 1u;
+      }
+      if (!ok) break;
+      epi.template store<COLS>(sum, tm * TILE_M + lrow, lrow, tn * TN + lcol0, lcol0, b);
+    }
+  }
+
+  __syncthreads();
+  if (abort_flag) {
+    // let copies and MMAs already issued land before the shared memory and TMEM go away
+    const uint64_t t0 = global_timer_ns();
+    while (global_timer_ns() - t0 < 200000ull) {
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, TMEM_COLS);
+  }
+}
+
+template <int TN, int NPHASE, uint32_t FMT, class Epi>
+int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const TcShape& sh, const Epi& epi,
+              const char* name) {
+  constexpr int smem = tc_smem_bytes<TN>();
+  LRS_CUDA_TRY(cudaFuncSetAttribute(zgemm_tc_kernel<TN, NPHASE, FMT, Epi>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int units = sh.m_tiles * sh.n_tiles * sh.batches;
+  const int grid = std::min(units, ctx->num_sms);
+  zgemm_tc_kernel<TN, NPHASE, FMT, Epi><<<grid, TC_THREADS, smem, ctx->stream>>>(ma, mb, sh, epi,
+                                                                                 ctx->ws.status.ptr + 8);
+  return after_launch(ctx, name);
+}
+
+// ---------------------------------------------------------------- epilogue stores
+// chi0: X = Re[Go o Gu^T] of one frequency into its fp32 slab.
+// The occupied sums Go of a unit are parked in `scratch` (per CTA
+// [2][128][tile_n] fp32, L2 resident) while the unoccupied sums accumulate in
+// registers; each thread reads back only what it wrote.
+struct Chi0Store {
+  float* slab;      // [batches][ld][ld]
+  float* scratch;   // [gridDim.x][2][128][tile_n]
+  int ld, tile_n;
+  template <int COLS>
+  __device__ void save_phase0(const float (&s)[2][COLS], int lrow, int lcol0) const {
+    float* base = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
+#pragma unroll
+    for (int part = 0; part < 2; ++part)
+#pragma unroll
+      for (int i = 0; i < COLS; i += 4)
+        *reinterpret_cast<float4*>(base + (size_t)part * 128 * tile_n + i) =
+            make_float4(s[part][i], s[part][i + 1], s[part][i + 2], s[part][i + 3]);
+  }
+  template <int COLS>
+  __device__ void store(const float (&s)[2][COLS], int row, int lrow, int col0, int lcol0, int b) const {
+    const float* go = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
+    float* dst = slab + ((size_t)b * ld + row) * ld + col0;
+#pragma unroll
+    for (int i = 0; i < COLS; i += 4) {
+      const float4 r = *reinterpret_cast<const float4*>(go + i);
+      const float4 m = *reinterpret_cast<const float4*>(go + (size_t)128 * tile_n + i);
+      float4 v;
+      v.x = fmaf(-m.x, s[1][i + 0], r.x * s[0][i + 0]);
+      v.y = fmaf(-m.y, s[1][i + 1], r.y * s[0][i + 1]);
+      v.z = fmaf(-m.z, s[1][i + 2], r.z * s[0][i + 2]);
+      v.w = fmaf(-m.w, s[1][i + 3], r.w * s[0][i + 3]);
+      *reinterpret_cast<float4*>(dst + i) = v;
+    }
+  }
+};
+
+// projection: psi(p, b) = e^{ik.R_p}/sqrt(Omega) * unscale * D(p, b), scattered
+// into the occupied / unoccupied orbital blocks.
+struct ProjStore {
+  const double2* kph;     // [nk][npts]
+  const float* unscale;   // device scalar
+  int npts, nb;
+  double2* psi_o;
+  double2* psi_u;
+  int Ko, Ku;
+  int nocc[MAX_K_POINTS], oofs[MAX_K_POINTS], uofs[MAX_K_POINTS];
+  template <int COLS>
+  __device__ void save_phase0(const float (&)[2][COLS], int, int) const {}
+  template <int COLS>
+  __device__ void store(const float (&s)[2][COLS], int row, int lrow, int col0, int lcol0, int k) const {
+    (void)lrow;
+    (void)lcol0;
+    if (row >= npts) return;
+    const double us = (double)*unscale;
+    const double2 ph = kph[(size_t)k * npts + row];
+    const float pr = (float)(ph.x * us), pi = (float)(ph.y * us);
+    const int no = nocc[k];
+#pragma unroll
+    for (int i = 0; i < COLS; ++i) {
+      const int band = col0 + i;
+      if (band >= nb) continue;
+      const float a = s[0][i], c = s[1][i];
+      const double2 v = make_double2((double)(pr * a - pi * c), (double)(pr * c + pi * a));
+      if (band < no) psi_o[(size_t)row * Ko + oofs[k] + band] = v;
+      else psi_u[(size_t)row * Ku + uofs[k] + band - no] = v;
+    }
+  }
+};
+
+}  // namespace lrs
