@@ -54,6 +54,14 @@ extern "C" {
 /* projection modes */
 #define LRS_PROJ_EXACT    0   /* direct Fourier sum, Sec. VI.B method 1 */
 
+/* options (lrs_set_option) */
+#define LRS_OPT_DYSON_BASIS      1  /* value: LRS_DYSON_AUTO, LRS_DYSON_FULL or LRS_DYSON_LM */
+#define LRS_OPT_CHI0_SEGMENT     2  /* value: K chunks of 32 per tensor-core accumulation segment (1..1024) */
+#define LRS_OPT_PROJ_SEGMENT     3  /* same for the mixed-precision projection */
+#define LRS_DYSON_AUTO    0   /* lm basis when the site grid is a radial x angular product that it shrinks */
+#define LRS_DYSON_FULL    1   /* LU on the full npts x npts grid matrix */
+#define LRS_DYSON_LM      2   /* LU in the (radial shell, l, m) basis (product grids only) */
+
 typedef struct lrs_ctx lrs_ctx;
 
 typedef struct lrs_stats_t {
@@ -92,6 +100,16 @@ int lrs_destroy(lrs_ctx* ctx);
 
 /* Change the stream of an existing context (same device). */
 int lrs_set_stream(lrs_ctx* ctx, void* stream);
+
+/*
+ * Tuning and algorithm options (LRS_OPT_*).  LRS_OPT_DYSON_BASIS selects how
+ * the Dyson equation is solved: on the full grid, or - for product grids
+ * p = shell * nang + angular point with the same angular set on every shell -
+ * in the basis of radial shells x real spherical harmonics l <= L where the
+ * multipole Coulomb operator is block diagonal (Sec. VI.E).  Both give the
+ * same W up to rounding.  Errors: LRS_ERR_ARG (unknown option or value).
+ */
+int lrs_set_option(lrs_ctx* ctx, int option, int value);
 
 /*
  * Load Bloch coefficients and band energies (Eq. (bloch), Sec. VI.A-B).
@@ -168,8 +186,11 @@ int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites);
 
 /*
  * Solve the Dyson equation for W (Eq. (eq-reducible), (eq-W), Sec. VI.E) on
- * the full site grid: v = sum_{l<=L} r_<^l/r_>^(l+1) P_l(cos gamma),
+ * the site grid: v = sum_{l<=L} r_<^l/r_>^(l+1) P_l(cos gamma),
  * Q = diag(wts), (I - v Q chi0 Q) W = v by float64 LU with partial pivoting.
+ * On product grids (see lrs_set_option) the same equation is solved in the
+ * (shell, l, m) basis: with v = Y C Y^T and X = Y^T Q chi0 Q Y,
+ * W = Y (I - C X)^-1 C Y^T, the LU being of size nrad (L+1)^2.
  * Requires chi0 of those sites.  Errors: LRS_ERR_STATE, LRS_ERR_NUMERIC
  * (zero pivot or non-finite value), LRS_ERR_OOM.
  */

@@ -1,0 +1,167 @@
+// Dyson equation in the (radial shell, l, m) basis on product grids (Sec. VI.E).
+//
+// On a grid p = j * nang + a (shell radius r_j, direction Omega_a, the same
+// angular set on every shell) the multipole Coulomb operator factorises
+// exactly through the addition theorem P_l(u.u') = 4pi/(2l+1) sum_m Y_lm(u) Y_lm(u'):
+//   v = Y C Y^T,  Y[(j,a),(j',lm)] = delta_jj' Y_lm(Omega_a),
+//   C[(j,lm),(j',l'm')] = delta_{lm,l'm'} 4pi/(2l+1) r_<^l / r_>^(l+1),
+// so (I - v Q chi0 Q) W = v becomes, with X = Y^T Q chi0 Q Y and the
+// push-through identity (I - U V)^-1 U = U (I - V U)^-1,
+//   W = Y Z Y^T,   (I - C X) Z = C,
+// an LU of size r = nrad (L+1)^2 instead of npts.  This is the basis in which
+// the paper forms chi = S^-1 chi0; here it is used to obtain the full-grid W.
+#include <cmath>
+#include <vector>
+
+#include "lrs_internal.h"
+
+namespace lrs {
+
+// Real spherical harmonics Y_lm (orthonormal on the sphere) at unit vector u,
+// l = 0..L, ordered l*l + l + m for m = -l..l.  Associated Legendre functions
+// by the standard upward recurrences in l at fixed m.
+static void real_sph_harm(int L, double x, double y, double z, double* out) {
+  const double pi = 3.14159265358979323846;
+  const double ct = std::max(-1.0, std::min(1.0, z));
+  const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+  const double phi = std::atan2(y, x);
+  std::vector<double> P((L + 1) * (L + 1), 0.0);   // P[l][m], m >= 0
+  auto Pl = [&](int l, int m) -> double& { return P[l * (L + 1) + m]; };
+  Pl(0, 0) = 1.0;
+  for (int m = 1; m <= L; ++m) Pl(m, m) = -(2.0 * m - 1.0) * st * Pl(m - 1, m - 1);
+  for (int m = 0; m < L; ++m) Pl(m + 1, m) = (2.0 * m + 1.0) * ct * Pl(m, m);
+  for (int m = 0; m <= L; ++m)
+    for (int l = m + 2; l <= L; ++l)
+      Pl(l, m) = ((2.0 * l - 1.0) * ct * Pl(l - 1, m) - (l + m - 1.0) * Pl(l - 2, m)) / (l - m);
+  for (int l = 0; l <= L; ++l) {
+    for (int m = 0; m <= l; ++m) {
+      double ratio = 1.0;   // (l-m)!/(l+m)!
+      for (int k = l - m + 1; k <= l + m; ++k) ratio /= k;
+      const double norm = std::sqrt((2.0 * l + 1.0) / (4.0 * pi) * ratio);
+      if (m == 0) {
+        out[l * l + l] = norm * Pl(l, 0);
+      } else {
+        out[l * l + l + m] = std::sqrt(2.0) * norm * Pl(l, m) * std::cos(m * phi);
+        out[l * l + l - m] = std::sqrt(2.0) * norm * Pl(l, m) * std::sin(m * phi);
+      }
+    }
+  }
+}
+
+int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts) {
+  s.product = false;
+  const int n = s.npts;
+  auto radius = [&](int p) {
+    return std::sqrt(pts[3 * p] * pts[3 * p] + pts[3 * p + 1] * pts[3 * p + 1] + pts[3 * p + 2] * pts[3 * p + 2]);
+  };
+  const double r0 = radius(0);
+  int nang = 1;
+  while (nang < n && std::fabs(radius(nang) - r0) <= 1e-12 * r0) ++nang;
+  if (n % nang != 0 || nang < 2) return LRS_OK;
+  const int nrad = n / nang;
+  std::vector<double> rad(nrad);
+  for (int j = 0; j < nrad; ++j) {
+    const double rj = radius(j * nang);
+    rad[j] = rj;
+    for (int a = 0; a < nang; ++a) {
+      const int p = j * nang + a;
+      const double rp = radius(p);
+      if (std::fabs(rp - rj) > 1e-12 * rj) return LRS_OK;
+      for (int d = 0; d < 3; ++d)
+        if (std::fabs(pts[3 * p + d] / rp - pts[3 * a + d] / r0) > 1e-12) return LRS_OK;
+    }
+  }
+  const int L = s.lmax, L2 = (L + 1) * (L + 1);
+  std::vector<double> yang((size_t)nang * L2);
+  for (int a = 0; a < nang; ++a)
+    real_sph_harm(L, pts[3 * a] / r0, pts[3 * a + 1] / r0, pts[3 * a + 2] / r0, &yang[(size_t)a * L2]);
+  const double pi = 3.14159265358979323846;
+  std::vector<double> rl((size_t)(L + 1) * nrad * nrad);
+  for (int l = 0; l <= L; ++l)
+    for (int j = 0; j < nrad; ++j)
+      for (int k = 0; k < nrad; ++k) {
+        const double lo = std::min(rad[j], rad[k]), hi = std::max(rad[j], rad[k]);
+        rl[((size_t)l * nrad + j) * nrad + k] = 4.0 * pi / (2.0 * l + 1.0) * std::pow(lo / hi, l) / hi;
+      }
+  LRS_TRY(ensure(ctx, s.yang, yang.size()));
+  LRS_TRY(ensure(ctx, s.rl, rl.size()));
+  LRS_CUDA_TRY(cudaMemcpy(s.yang.ptr, yang.data(), yang.size() * sizeof(double), cudaMemcpyHostToDevice));
+  LRS_CUDA_TRY(cudaMemcpy(s.rl.ptr, rl.data(), rl.size() * sizeof(double), cudaMemcpyHostToDevice));
+  s.product = true;
+  s.nrad = nrad;
+  s.nang = nang;
+  return LRS_OK;
+}
+
+// B = I - C X on the (j, lm) index: b[(j,lm), c] = delta - sum_j' rl[l][j][j'] X[(j',lm), c].
+__global__ void lm_dyson_matrix_kernel(const double* __restrict__ X, const double* __restrict__ rl, int nrad,
+                                       int L2, double* __restrict__ B) {
+  const int r = nrad * L2;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;            // (j, lm)
+  if (col >= r || row >= r) return;
+  const int j = row / L2, lm = row % L2;
+  int l = 0;
+  while ((l + 1) * (l + 1) <= lm) ++l;
+  const double* rlj = rl + ((size_t)l * nrad + j) * nrad;
+  double s = 0.0;
+  for (int jp = 0; jp < nrad; ++jp) s = fma(rlj[jp], X[(size_t)(jp * L2 + lm) * r + col], s);
+  B[(size_t)row * r + col] = (row == col ? 1.0 : 0.0) - s;
+}
+
+// Dense C (right-hand side of (I - C X) Z = C).
+__global__ void lm_coulomb_kernel(const double* __restrict__ rl, int nrad, int L2, double* __restrict__ Cm) {
+  const int r = nrad * L2;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (col >= r || row >= r) return;
+  const int j = row / L2, lm = row % L2, jp = col / L2, lmp = col % L2;
+  double v = 0.0;
+  if (lm == lmp) {
+    int l = 0;
+    while ((l + 1) * (l + 1) <= lm) ++l;
+    v = rl[((size_t)l * nrad + j) * nrad + jp];
+  }
+  Cm[(size_t)row * r + col] = v;
+}
+
+int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
+  const int n = s.npts, nrad = s.nrad, nang = s.nang;
+  const int L2 = (s.lmax + 1) * (s.lmax + 1), r = nrad * L2;
+  const size_t nn = (size_t)n * n, rr = (size_t)r * r;
+  // workspace: T / U [n][r], X, B, Z [r][r]
+  LRS_TRY(ensure(ctx, ctx->ws.dyson_a, std::max(nn, 3 * rr + (size_t)n * r)));
+  LRS_TRY(ensure(ctx, ctx->ws.ipiv, std::max(n, r)));
+  double* T = ctx->ws.dyson_a.ptr;        // [n][r]
+  double* X = T + (size_t)n * r;          // [r][r]
+  double* B = X + rr;                     // [r][r]
+  double* Z = B + rr;                     // [r][r]
+  const double* Yang = s.yang.ptr;        // [nang][L2]
+  // T[:, j' block] = chi0[:, shell j'] diag(Q_j') Yang
+  for (int jp = 0; jp < nrad; ++jp)
+    LRS_TRY(dgemm_t(ctx, false, false, n, L2, nang, 1.0, s.chi0.ptr + (size_t)jp * nang, n,
+                    s.wts.ptr + (size_t)jp * nang, Yang, L2, nullptr, 0.0, T + (size_t)jp * L2, r));
+  // X[j block, :] = Yang^T diag(Q_j) T[shell j, :]
+  for (int j = 0; j < nrad; ++j)
+    LRS_TRY(dgemm_t(ctx, true, false, L2, r, nang, 1.0, Yang, L2, s.wts.ptr + (size_t)j * nang,
+                    T + (size_t)j * nang * r, r, nullptr, 0.0, X + (size_t)j * L2 * r, r));
+  dim3 g((r + 127) / 128, r);
+  lm_dyson_matrix_kernel<<<g, 128, 0, ctx->stream>>>(X, s.rl.ptr, nrad, L2, B);
+  LRS_TRY(after_launch(ctx, "lm_dyson_matrix_kernel"));
+  lm_coulomb_kernel<<<g, 128, 0, ctx->stream>>>(s.rl.ptr, nrad, L2, Z);
+  LRS_TRY(after_launch(ctx, "lm_coulomb_kernel"));
+  LRS_TRY(lu_factor(ctx, B, r, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));
+  LRS_TRY(lu_solve(ctx, B, r, ctx->ws.ipiv.ptr, Z, r, r));
+  // U[shell j, :] = Yang Z[j block, :]   (reuses T)
+  double* U = T;
+  for (int j = 0; j < nrad; ++j)
+    LRS_TRY(dgemm_t(ctx, false, false, nang, r, L2, 1.0, Yang, L2, nullptr, Z + (size_t)j * L2 * r, r, nullptr,
+                    0.0, U + (size_t)j * nang * r, r));
+  // W[:, shell j'] = U[:, j' block] Yang^T
+  for (int jp = 0; jp < nrad; ++jp)
+    LRS_TRY(dgemm_t(ctx, false, true, n, nang, L2, 1.0, U + (size_t)jp * L2, r, nullptr, Yang, L2, nullptr, 0.0,
+                    s.w.ptr + (size_t)jp * nang, n));
+  return LRS_OK;
+}
+
+}  // namespace lrs

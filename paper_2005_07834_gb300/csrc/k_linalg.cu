@@ -8,6 +8,8 @@
 // solve for W with all npts right-hand sides.  The FP64 pipe of GB300 retires
 // about two DFMA per SM clock, so every kernel here is bound by DFMA issue;
 // the tiling only has to keep all SMs busy.
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "lrs_internal.h"
@@ -243,12 +245,181 @@ __global__ void trsm_kernel(const double* __restrict__ T, int ldt, int jb, doubl
     if (i < jb) B[(size_t)i * ldb + col] = x[i];
 }
 
+// Panel LU held in the shared memory of one thread-block cluster.  The rows
+// [j0, n) of the jb-wide panel are split into CS contiguous chunks, one per
+// CTA.  Per column: each CTA finds its local pivot candidate; after a cluster
+// barrier every CTA reads all candidates through distributed shared memory
+// and agrees on the pivot (largest |a|, lowest row on ties); the owners of
+// the pivot row and of the diagonal row publish them; after a second barrier
+// the rows are exchanged and every CTA applies the rank-1 update to its rows.
+// Same arithmetic and pivot choice as lu_panel_kernel, on-chip.
+constexpr int PANEL_CS = 16;         // CTAs per cluster
+constexpr int PANEL_THREADS = 512;
+
+__global__ void __launch_bounds__(PANEL_THREADS) lu_panel_cluster_kernel(double* __restrict__ A, int lda, int n,
+                                                                         int j0, int jb, int rows_per_cta,
+                                                                         int* __restrict__ ipiv,
+                                                                         int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ double panel[];                 // [rows_per_cta][NB]
+  __shared__ double cand_val;
+  __shared__ int cand_idx, cand_bad;
+  __shared__ double prow[NB], crow[NB], urow[NB];
+  __shared__ double w_val[PANEL_THREADS / 32];
+  __shared__ int w_idx[PANEL_THREADS / 32], w_bad[PANEL_THREADS / 32];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = j0 + rank * rows_per_cta;                       // first global row of this CTA
+  const int nloc = max(0, min(rows_per_cta, n - r0));            // rows held here
+  for (int i = tid; i < nloc * NB; i += PANEL_THREADS) {
+    const int r = i / NB, c = i % NB;
+    panel[i] = c < jb ? A[(size_t)(r0 + r) * lda + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    const int col = j0 + c;
+    // 1. local candidate over rows >= col
+    double best = -1.0;
+    int bi = n, bad = 0;
+    for (int r = tid; r < nloc; r += PANEL_THREADS) {
+      if (r0 + r < col) continue;
+      const double a = panel[r * NB + c];
+      if (!isfinite(a)) bad = 1;
+      const double m = fabs(a);
+      if (m > best) { best = m; bi = r0 + r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      bad |= __shfl_down_sync(0xffffffffu, bad, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { w_val[warp] = best; w_idx[warp] = bi; w_bad[warp] = bad; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < PANEL_THREADS / 32; ++w) {
+        if (w_val[w] > best || (w_val[w] == best && w_idx[w] < bi)) { best = w_val[w]; bi = w_idx[w]; }
+        bad |= w_bad[w];
+      }
+      cand_val = best;
+      cand_idx = bi;
+      cand_bad = bad;
+    }
+    cluster.sync();
+    // 2. agree on the pivot
+    if (warp == 0) {
+      double v = -1.0;
+      int ix = n, bd = 0;
+      if (lane < PANEL_CS) {
+        v = *cluster.map_shared_rank(&cand_val, lane);
+        ix = *cluster.map_shared_rank(&cand_idx, lane);
+        bd = *cluster.map_shared_rank(&cand_bad, lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, o);
+        const int oi = __shfl_down_sync(0xffffffffu, ix, o);
+        bd |= __shfl_down_sync(0xffffffffu, bd, o);
+        if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
+      }
+      if (lane == 0) {
+        if (ix >= n) ix = col;
+        s_piv = ix;
+        if (rank == 0) {
+          ipiv[col] = ix;
+          if ((bd || !(v > 0.0)) && atomicCAS(&status[0], 0, 1) == 0) status[1] = col;
+        }
+      }
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    const int own_p = (piv - j0) / rows_per_cta, own_c = (col - j0) / rows_per_cta;
+    // 3. publish the pivot row and the diagonal row
+    if (rank == own_p && tid < NB) prow[tid] = panel[(piv - r0) * NB + tid];
+    if (rank == own_c && tid < NB) crow[tid] = panel[(col - r0) * NB + tid];
+    cluster.sync();
+    // 4. exchange and take the pivot row as the U row of this column
+    if (tid < NB) {
+      const double u = *cluster.map_shared_rank(&prow[tid], own_p);
+      urow[tid] = u;
+      if (rank == own_c) panel[(col - r0) * NB + tid] = u;
+      if (rank == own_p && piv != col) panel[(piv - r0) * NB + tid] = *cluster.map_shared_rank(&crow[tid], own_c);
+    }
+    __syncthreads();
+    // 5. rank-1 update of this CTA's rows below the diagonal
+    const double d = urow[c];
+    const double inv = (d != 0.0) ? 1.0 / d : 0.0;
+    const int rbeg = max(0, col + 1 - r0);
+    for (int r = rbeg + tid; r < nloc; r += PANEL_THREADS) panel[r * NB + c] *= inv;
+    __syncthreads();
+    const int w = jb - c - 1;
+    for (int i = tid; i < (nloc - rbeg) * w; i += PANEL_THREADS) {
+      const int r = rbeg + i / w, cc = c + 1 + i % w;
+      panel[r * NB + cc] = fma(-panel[r * NB + c], urow[cc], panel[r * NB + cc]);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nloc * NB; i += PANEL_THREADS) {
+    const int r = i / NB, c = i % NB;
+    if (c < jb) A[(size_t)(r0 + r) * lda + j0 + c] = panel[i];
+  }
+  cluster.sync();   // no CTA leaves while others may still read its shared memory
+}
+
+static int launch_panel_cluster(lrs_ctx* ctx, double* A, int n, int j0, int jb, int* ipiv, int* status,
+                                bool* used) {
+  *used = false;
+  const int m = n - j0;
+  const int rows = (m + PANEL_CS - 1) / PANEL_CS;
+  const size_t smem = (size_t)rows * NB * sizeof(double);
+  if (smem > 200 * 1024) return LRS_OK;   // taller panels: single-CTA kernel
+  static bool configured = false, usable = true;
+  if (!configured) {
+    configured = true;
+    if (cudaFuncSetAttribute(lu_panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(lu_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      usable = false;
+    }
+  }
+  if (!usable) return LRS_OK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(PANEL_CS);
+  cfg.blockDim = dim3(PANEL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = PANEL_CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel, A, n, n, j0, jb, rows, ipiv, status);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    usable = false;   // e.g. cluster size not supported: fall back for good
+    return LRS_OK;
+  }
+  *used = true;
+  return after_launch(ctx, "lu_panel_cluster_kernel");
+}
+
 // In-place LU with partial pivoting of the n x n matrix A (row-major).
 int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status) {
   for (int j0 = 0; j0 < n; j0 += NB) {
     int jb = std::min(NB, n - j0);
-    lu_panel_kernel<<<1, 1024, 0, ctx->stream>>>(A, n, n, j0, jb, ipiv, status);
-    LRS_TRY(after_launch(ctx, "lu_panel_kernel"));
+    bool used = false;
+    LRS_TRY(launch_panel_cluster(ctx, A, n, j0, jb, ipiv, status, &used));
+    if (!used) {
+      lu_panel_kernel<<<1, 1024, 0, ctx->stream>>>(A, n, n, j0, jb, ipiv, status);
+      LRS_TRY(after_launch(ctx, "lu_panel_kernel"));
+    }
     if (n - jb > 0) {
       laswp_kernel<<<(n - jb + 255) / 256, 256, 0, ctx->stream>>>(A, n, n, ipiv, j0, jb, j0, jb);
       LRS_TRY(after_launch(ctx, "laswp_kernel"));
@@ -299,7 +470,14 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
   LRS_TRY(ensure(ctx, s.w, nn));
   LRS_TRY(ensure(ctx, ctx->ws.dyson_a, nn));
   LRS_TRY(ensure(ctx, ctx->ws.ipiv, n));
+  const int L2 = (s.lmax + 1) * (s.lmax + 1);
+  if (ctx->dyson_basis == LRS_DYSON_LM && !s.product)
+    return set_error(LRS_ERR_ARG, "lm-basis Dyson solve needs a radial x angular product grid");
+  if (s.product && (ctx->dyson_basis == LRS_DYSON_LM ||
+                    (ctx->dyson_basis == LRS_DYSON_AUTO && (long long)s.nrad * L2 < n)))
+    return dyson_solve_lm(ctx, s);   // the full-grid v is built only on request
   LRS_TRY(coulomb_build(ctx, s, s.v.ptr));
+  s.has_v = true;
   double* A = ctx->ws.dyson_a.ptr;
   // A = I - (v Q)(chi0 Q)
   LRS_TRY(dgemm_t(ctx, false, false, n, n, n, -1.0, s.v.ptr, n, s.wts.ptr, s.chi0.ptr, n, s.wts.ptr, 0.0, A, n));

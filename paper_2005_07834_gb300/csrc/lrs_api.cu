@@ -148,11 +148,15 @@ static int site_list(lrs_ctx* ctx, int nsite, const int* sites, std::vector<int>
 static void free_site(lrs_ctx* ctx, Site& s) {
   release(ctx, s.pts);
   release(ctx, s.wts);
+  s.has_v = false;
   release(ctx, s.psi_o);
   release(ctx, s.psi_u);
   release(ctx, s.chi0);
   release(ctx, s.w);
   release(ctx, s.v);
+  release(ctx, s.yang);
+  release(ctx, s.rl);
+  s.product = false;
   s.has_psi = s.has_chi0 = s.has_w = false;
 }
 
@@ -233,6 +237,25 @@ int lrs_destroy(lrs_ctx* ctx) {
       if (ctx->ev[s][j]) cudaEventDestroy(ctx->ev[s][j]);
   delete ctx;
   return LRS_OK;
+}
+
+int lrs_set_option(lrs_ctx* ctx, int option, int value) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  switch (option) {
+    case LRS_OPT_DYSON_BASIS:
+      if (value != LRS_DYSON_AUTO && value != LRS_DYSON_FULL && value != LRS_DYSON_LM)
+        return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
+      ctx->dyson_basis = value;
+      return LRS_OK;
+    case LRS_OPT_CHI0_SEGMENT:
+    case LRS_OPT_PROJ_SEGMENT:
+      if (value < 1 || value > 1024) return set_error(LRS_ERR_ARG, "segment %d out of [1,1024]", value);
+      (option == LRS_OPT_CHI0_SEGMENT ? ctx->seg_chunks : ctx->proj_seg_chunks) = value;
+      return LRS_OK;
+    default:
+      return set_error(LRS_ERR_ARG, "unknown option %d", option);
+  }
 }
 
 int lrs_set_stream(lrs_ctx* ctx, void* stream) {
@@ -359,6 +382,7 @@ int lrs_set_sites(lrs_ctx* ctx, int nsites, const double* centers, const int* np
     LRS_TRY(ensure(ctx, s.wts, s.npts));
     LRS_CUDA_TRY(cudaMemcpy(s.pts.ptr, pts + 3 * off, 3 * (size_t)s.npts * sizeof(double), cudaMemcpyHostToDevice));
     LRS_CUDA_TRY(cudaMemcpy(s.wts.ptr, wts + off, (size_t)s.npts * sizeof(double), cudaMemcpyHostToDevice));
+    LRS_TRY(site_detect_product(ctx, s, pts + 3 * off));
     off += npts[i];
   }
   return LRS_OK;
@@ -580,7 +604,16 @@ static int get_matrix(lrs_ctx* ctx, int site, double* out, int which, bool devic
   const double* src = nullptr;
   if (which == 0) { if (!s.has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", site); src = s.chi0.ptr; }
   if (which == 1) { if (!s.has_w) return set_error(LRS_ERR_STATE, "site %d has no W", site); src = s.w.ptr; }
-  if (which == 2) { if (!s.has_w) return set_error(LRS_ERR_STATE, "site %d has no v (solve W first)", site); src = s.v.ptr; }
+  if (which == 2) {
+    if (!s.has_v) {
+      DeviceGuard g0(ctx->device);
+      if (g0.rc) return g0.rc;
+      LRS_TRY(ensure(ctx, s.v, (size_t)s.npts * s.npts));
+      LRS_TRY(coulomb_build(ctx, s, s.v.ptr));
+      s.has_v = true;
+    }
+    src = s.v.ptr;
+  }
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
   size_t bytes = (size_t)s.npts * s.npts * sizeof(double);

@@ -73,7 +73,12 @@ struct Site {
   DevBuf<double> pts, wts;          // [npts][3], [npts]
   DevBuf<double2> psi_o, psi_u;     // [npts][Ko], [npts][Ku]
   DevBuf<double> chi0, w, v;        // [npts][npts]
-  bool has_psi = false, has_chi0 = false, has_w = false;
+  bool has_psi = false, has_chi0 = false, has_w = false, has_v = false;
+  // product grid p = j * nang + a (radial shell j, angular point a), if detected
+  bool product = false;
+  int nrad = 0, nang = 0;
+  DevBuf<double> yang;              // [nang][(lmax+1)^2] real spherical harmonics
+  DevBuf<double> rl;                // [lmax+1][nrad][nrad] 4pi/(2l+1) r<^l / r>^(l+1)
 };
 
 // Split-precision operand planes of one matrix [rows_pad][k_pad] (4 planes:
@@ -123,6 +128,7 @@ struct lrs_ctx {
   int num_sms = 0;
   int seg_chunks = 4;                  // chi0 tensor-core accumulation segment (K chunks of 32)
   int proj_seg_chunks = 2;             // projection accumulation segment (K chunks of 32)
+  int dyson_basis = LRS_DYSON_AUTO;    // full grid or lm basis
 
   // orbitals
   bool has_orb = false;
@@ -184,6 +190,14 @@ int dgemm(lrs_ctx* ctx, int m, int n, int k, double alpha, const double* a, int 
           const double* kscale, const double* b, int ldb, const double* cscale, double beta,
           double* c, int ldc);
 int dyson_solve(lrs_ctx* ctx, Site& s);
+int dgemm_t(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+            const double* ks, const double* b, int ldb, const double* cs, double beta, double* c, int ldc);
+int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status);
+int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb);
+
+// lm-basis Dyson on product grids (k_dyson_lm.cu)
+int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);
+int dyson_solve_lm(lrs_ctx* ctx, Site& s);
 
 // Adjoint (k_adjoint.cu)
 int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev,

@@ -23,6 +23,8 @@ LRS_OK, LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA, LRS_ERR_STATE = 0, 1, 2, 3, 4
 LRS_ERR_TIMEOUT, LRS_ERR_NUMERIC, LRS_ERR_UNSUPPORTED = 5, 6, 7
 LRS_FP64, LRS_MIXED_BF16X3, LRS_MIXED_FP16X3 = 0, 1, 2
 LRS_PROJ_EXACT = 0
+LRS_OPT_DYSON_BASIS, LRS_OPT_CHI0_SEGMENT, LRS_OPT_PROJ_SEGMENT = 1, 2, 3
+LRS_DYSON_AUTO, LRS_DYSON_FULL, LRS_DYSON_LM = 0, 1, 2
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
 
@@ -47,6 +49,7 @@ _SIGS = {
     "lrs_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, _P]),
     "lrs_destroy": (C.c_int, [_P]),
     "lrs_set_stream": (C.c_int, [_P, _P]),
+    "lrs_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
     "lrs_load_orbitals": (C.c_int, [_P, _DP, C.c_int, _DP, _DP, C.c_int, _IP, C.c_int, _IP, _DP, _DP]),
     "lrs_set_sites": (C.c_int, [_P, C.c_int, _DP, _IP, _DP, _DP, _IP]),
     "lrs_set_frequency_quadrature": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _DP, _DP]),
@@ -133,6 +136,9 @@ class Screening:
 
     def set_stream(self, stream):
         _check(lrs_set_stream(self.ctx, _P(stream or 0)), "lrs_set_stream")
+
+    def set_option(self, option, value):
+        _check(lrs_set_option(self.ctx, int(option), int(value)), "lrs_set_option")
 
     # -- inputs
     def load_orbitals(self, cell, kpts, kweights, gvec, coeff, energies, nocc):

@@ -121,3 +121,36 @@ def test_state_and_argument_errors(lrs):
         scr.build_chi0([7])
     assert e.value.code == lrs.LRS_ERR_ARG
     scr.close()
+
+
+@pytest.mark.parametrize("basis", ["full", "lm"])
+def test_dyson_bases_match_oracle(lrs, cfg_260, basis):
+    ref = cfg_260
+    wl = synth.single_site_260()
+    scr = lrs.Screening(0, "fp64")
+    scr.set_option(lrs.LRS_OPT_DYSON_BASIS, lrs.LRS_DYSON_FULL if basis == "full" else lrs.LRS_DYSON_LM)
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(12)
+    scr.project()
+    scr.build_chi0()
+    scr.solve_w()
+    w = scr.get_w(0)
+    assert rel_fro(w, ref.w) < TOL
+    assert rel_fro(w - ref.v, ref.w - ref.v) < 1e-8
+    scr.close()
+
+
+def test_non_product_grid_uses_full_basis(lrs):
+    wl = synth.tiny(nk=8, nocc=3, nunocc=5)
+    s = wl.sites[0]
+    s.pts = s.pts.copy()
+    s.pts[5] *= 1.01                       # breaks the radial x angular product structure
+    ref = Reference(wl)
+    scr, mu, zeta = run_fp64(lrs, wl, 12)  # automatic basis: full grid
+    assert rel_fro(scr.get_w(0), ref.w) < TOL
+    scr.set_option(lrs.LRS_OPT_DYSON_BASIS, lrs.LRS_DYSON_LM)
+    with pytest.raises(lrs.LrsError) as e:
+        scr.solve_w()
+    assert e.value.code == lrs.LRS_ERR_ARG
+    scr.close()
