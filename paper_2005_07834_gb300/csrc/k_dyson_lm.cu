@@ -137,31 +137,27 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   double* B = X + rr;                     // [r][r]
   double* Z = B + rr;                     // [r][r]
   const double* Yang = s.yang.ptr;        // [nang][L2]
-  // T[:, j' block] = chi0[:, shell j'] diag(Q_j') Yang
-  for (int jp = 0; jp < nrad; ++jp)
-    LRS_TRY(dgemm_t(ctx, false, false, n, L2, nang, 1.0, s.chi0.ptr + (size_t)jp * nang, n,
-                    s.wts.ptr + (size_t)jp * nang, Yang, L2, nullptr, 0.0, T + (size_t)jp * L2, r));
+  // T[:, j' block] = chi0[:, shell j'] diag(Q_j') Yang        (one launch, batch = shell)
+  LRS_TRY(dgemm_batched(ctx, false, false, n, L2, nang, 1.0, s.chi0.ptr, n, nang, s.wts.ptr, nang, Yang, L2, 0,
+                        nullptr, 0.0, T, r, L2, nrad));
   // X[j block, :] = Yang^T diag(Q_j) T[shell j, :]
-  for (int j = 0; j < nrad; ++j)
-    LRS_TRY(dgemm_t(ctx, true, false, L2, r, nang, 1.0, Yang, L2, s.wts.ptr + (size_t)j * nang,
-                    T + (size_t)j * nang * r, r, nullptr, 0.0, X + (size_t)j * L2 * r, r));
+  LRS_TRY(dgemm_batched(ctx, true, false, L2, r, nang, 1.0, Yang, L2, 0, s.wts.ptr, nang, T, r,
+                        (long long)nang * r, nullptr, 0.0, X, r, (long long)L2 * r, nrad));
   dim3 g((r + 127) / 128, r);
   lm_dyson_matrix_kernel<<<g, 128, 0, ctx->stream>>>(X, s.rl.ptr, nrad, L2, B);
   LRS_TRY(after_launch(ctx, "lm_dyson_matrix_kernel"));
   lm_coulomb_kernel<<<g, 128, 0, ctx->stream>>>(s.rl.ptr, nrad, L2, Z);
   LRS_TRY(after_launch(ctx, "lm_coulomb_kernel"));
   LRS_TRY(lu_factor(ctx, B, r, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));
-  LRS_TRY(lu_solve(ctx, B, r, ctx->ws.ipiv.ptr, Z, r, r));
+  LRS_TRY(ensure(ctx, ctx->ws.tinv, 2 * (size_t)((r + 31) / 32) * 32 * 32));
+  LRS_TRY(lu_solve_inv(ctx, B, r, ctx->ws.ipiv.ptr, Z, r, r, ctx->ws.tinv.ptr));
   // U[shell j, :] = Yang Z[j block, :]   (reuses T)
   double* U = T;
-  for (int j = 0; j < nrad; ++j)
-    LRS_TRY(dgemm_t(ctx, false, false, nang, r, L2, 1.0, Yang, L2, nullptr, Z + (size_t)j * L2 * r, r, nullptr,
-                    0.0, U + (size_t)j * nang * r, r));
+  LRS_TRY(dgemm_batched(ctx, false, false, nang, r, L2, 1.0, Yang, L2, 0, nullptr, 0, Z, r, (long long)L2 * r,
+                        nullptr, 0.0, U, r, (long long)nang * r, nrad));
   // W[:, shell j'] = U[:, j' block] Yang^T
-  for (int jp = 0; jp < nrad; ++jp)
-    LRS_TRY(dgemm_t(ctx, false, true, n, nang, L2, 1.0, U + (size_t)jp * L2, r, nullptr, Yang, L2, nullptr, 0.0,
-                    s.w.ptr + (size_t)jp * nang, n));
-  return LRS_OK;
+  return dgemm_batched(ctx, false, true, n, nang, L2, 1.0, U, r, L2, nullptr, 0, Yang, L2, 0, nullptr, 0.0, s.w.ptr,
+                       n, nang, nrad);
 }
 
 }  // namespace lrs

@@ -20,15 +20,24 @@ constexpr int GT = 64;   // dgemm tile edge
 constexpr int GKC = 16;  // dgemm k chunk
 constexpr int NB = 32;   // LU panel width
 
+// Element offsets between the matrices of consecutive batch entries (blockIdx.z).
+struct BatchStrides {
+  long long a = 0, ks = 0, b = 0, c = 0;
+};
+
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double alpha,
                                                     const double* __restrict__ A, int lda,
                                                     const double* __restrict__ ks,
                                                     const double* __restrict__ B, int ldb,
                                                     const double* __restrict__ cs, double beta,
-                                                    double* __restrict__ C, int ldc) {
+                                                    double* __restrict__ C, int ldc, BatchStrides bs) {
   __shared__ double As[GKC][GT + 1];
   __shared__ double Bs[GKC][GT + 1];
+  A += bs.a * blockIdx.z;
+  B += bs.b * blockIdx.z;
+  C += bs.c * blockIdx.z;
+  if (ks) ks += bs.ks * blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
   double acc[4][4];
@@ -87,20 +96,32 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
   }
 }
 
+int dgemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+                  long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                  long long stride_b, const double* cs, double beta, double* c, int ldc, long long stride_c,
+                  int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
+  dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch);
+  if (k <= 0) k = 0;
+  BatchStrides bs;
+  bs.a = stride_a;
+  bs.ks = stride_ks;
+  bs.b = stride_b;
+  bs.c = stride_c;
+  if (!ta && !tb)
+    dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else if (ta && !tb)
+    dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else if (!ta && tb)
+    dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else
+    dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  return after_launch(ctx, "dgemm_kernel");
+}
+
 int dgemm_t(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
             const double* ks, const double* b, int ldb, const double* cs, double beta, double* c, int ldc) {
-  if (m <= 0 || n <= 0) return LRS_OK;
-  dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT);
-  if (k <= 0) k = 0;
-  if (!ta && !tb)
-    dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
-  else if (ta && !tb)
-    dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
-  else if (!ta && tb)
-    dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
-  else
-    dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc);
-  return after_launch(ctx, "dgemm_kernel");
+  return dgemm_batched(ctx, ta, tb, m, n, k, alpha, a, lda, 0, ks, 0, b, ldb, 0, cs, beta, c, ldc, 0, 1);
 }
 
 int dgemm(lrs_ctx* ctx, int m, int n, int k, double alpha, const double* a, int lda, const double* kscale,
@@ -463,6 +484,111 @@ int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, 
   return LRS_OK;
 }
 
+// Inverses of the jb x jb diagonal blocks of an LU factor (unit lower or
+// upper), one CTA per block, thread c solving for column c.  out: [blocks][NB][NB].
+template <bool kLowerUnit>
+__global__ void invert_diag_blocks_kernel(const double* __restrict__ LU, int n, double* __restrict__ out) {
+  __shared__ double T[NB][NB + 1];
+  const int b = blockIdx.x, j0 = b * NB, jb = min(NB, n - j0);
+  for (int i = threadIdx.x; i < jb * jb; i += blockDim.x) T[i / jb][i % jb] = LU[(size_t)(j0 + i / jb) * n + j0 + i % jb];
+  __syncthreads();
+  const int c = threadIdx.x;
+  double x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) x[i] = 0.0;
+  if (c < jb) {
+    if (kLowerUnit) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (i >= jb) break;
+        double s = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          if (k < i) s = fma(-T[i][k], x[k], s);
+        x[i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int ii = NB - 1; ii >= 0; --ii) {
+        if (ii >= jb) continue;
+        double s = (ii == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          if (k > ii && k < jb) s = fma(-T[ii][k], x[k], s);
+        x[ii] = s / T[ii][ii];
+      }
+    }
+  }
+  double* o = out + (size_t)b * NB * NB;
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (c < NB) o[i * NB + c] = (c < jb && i < jb) ? x[i] : 0.0;
+}
+
+// B[0:jb, :] <- Tinv B[0:jb, :] in place, 16 columns per CTA (all of a CTA's
+// columns are read before any is written, and no other CTA touches them).
+constexpr int TA_COLS = 16;
+__global__ void __launch_bounds__(256) trsm_apply_kernel(const double* __restrict__ Tinv, int jb,
+                                                         double* __restrict__ B, int ldb, int ncols) {
+  __shared__ double Ts[NB][NB + 1];
+  __shared__ double Bs[NB][TA_COLS + 1];
+  const int c0 = blockIdx.x * TA_COLS;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) Ts[i / NB][i % NB] = Tinv[i];
+  for (int i = threadIdx.x; i < NB * TA_COLS; i += blockDim.x) {
+    const int r = i / TA_COLS, c = i % TA_COLS;
+    Bs[r][c] = (r < jb && c0 + c < ncols) ? B[(size_t)r * ldb + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  // 256 threads: row r = tid / 8, columns (tid % 8) and (tid % 8) + 8
+  const int r = threadIdx.x >> 3, ca = threadIdx.x & 7;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const double t = Ts[r][k];
+    s0 = fma(t, Bs[k][ca], s0);
+    s1 = fma(t, Bs[k][ca + 8], s1);
+  }
+  if (r < jb) {
+    if (c0 + ca < ncols) B[(size_t)r * ldb + c0 + ca] = s0;
+    if (c0 + ca + 8 < ncols) B[(size_t)r * ldb + c0 + ca + 8] = s1;
+  }
+}
+
+// lu_solve with the diagonal blocks inverted once (tinv: 2 * ceil(n/NB) * NB * NB doubles).
+int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb,
+                 double* tinv) {
+  const int nblk = (n + NB - 1) / NB;
+  double* linv = tinv;
+  double* uinv = tinv + (size_t)nblk * NB * NB;
+  invert_diag_blocks_kernel<true><<<nblk, NB, 0, ctx->stream>>>(LU, n, linv);
+  LRS_TRY(after_launch(ctx, "invert_diag_blocks_kernel"));
+  invert_diag_blocks_kernel<false><<<nblk, NB, 0, ctx->stream>>>(LU, n, uinv);
+  LRS_TRY(after_launch(ctx, "invert_diag_blocks_kernel"));
+  laswp_kernel<<<(nrhs + 255) / 256, 256, 0, ctx->stream>>>(B, ldb, nrhs, ipiv, 0, n, nrhs, 0);
+  LRS_TRY(after_launch(ctx, "laswp_kernel"));
+  const int tgrid = (nrhs + TA_COLS - 1) / TA_COLS;
+  for (int b = 0; b < nblk; ++b) {
+    const int j0 = b * NB, jb = std::min(NB, n - j0);
+    trsm_apply_kernel<<<tgrid, 256, 0, ctx->stream>>>(linv + (size_t)b * NB * NB, jb, B + (size_t)j0 * ldb, ldb,
+                                                       nrhs);
+    LRS_TRY(after_launch(ctx, "trsm_apply_kernel"));
+    const int rest = n - j0 - jb;
+    if (rest > 0)
+      LRS_TRY(dgemm_t(ctx, false, false, rest, nrhs, jb, -1.0, LU + (size_t)(j0 + jb) * n + j0, n, nullptr,
+                      B + (size_t)j0 * ldb, ldb, nullptr, 1.0, B + (size_t)(j0 + jb) * ldb, ldb));
+  }
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int j0 = b * NB, jb = std::min(NB, n - j0);
+    trsm_apply_kernel<<<tgrid, 256, 0, ctx->stream>>>(uinv + (size_t)b * NB * NB, jb, B + (size_t)j0 * ldb, ldb,
+                                                       nrhs);
+    LRS_TRY(after_launch(ctx, "trsm_apply_kernel"));
+    if (j0 > 0)
+      LRS_TRY(dgemm_t(ctx, false, false, j0, nrhs, jb, -1.0, LU + j0, n, nullptr, B + (size_t)j0 * ldb, ldb,
+                      nullptr, 1.0, B, ldb));
+  }
+  return LRS_OK;
+}
+
 int dyson_solve(lrs_ctx* ctx, Site& s) {
   const int n = s.npts;
   const size_t nn = (size_t)n * n;
@@ -485,7 +611,8 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
   LRS_TRY(after_launch(ctx, "add_identity_kernel"));
   LRS_TRY(lu_factor(ctx, A, n, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));
   LRS_CUDA_TRY(cudaMemcpyAsync(s.w.ptr, s.v.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  return lu_solve(ctx, A, n, ctx->ws.ipiv.ptr, s.w.ptr, n, n);
+  LRS_TRY(ensure(ctx, ctx->ws.tinv, 2 * (size_t)((n + NB - 1) / NB) * NB * NB));
+  return lu_solve_inv(ctx, A, n, ctx->ws.ipiv.ptr, s.w.ptr, n, n, ctx->ws.tinv.ptr);
 }
 
 }  // namespace lrs

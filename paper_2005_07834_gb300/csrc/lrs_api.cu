@@ -162,7 +162,7 @@ static void free_site(lrs_ctx* ctx, Site& s) {
 
 static void free_workspace(lrs_ctx* ctx) {
   Workspace& w = ctx->ws;
-  release(ctx, w.denom_o); release(ctx, w.denom_u); release(ctx, w.dyson_a); release(ctx, w.ipiv);
+  release(ctx, w.denom_o); release(ctx, w.denom_u); release(ctx, w.dyson_a); release(ctx, w.ipiv); release(ctx, w.tinv);
   release(ctx, w.status); release(ctx, w.phase_tab); release(ctx, w.kphase); release(ctx, w.ru);
   release(ctx, w.gamma_s); release(ctx, w.gbuf_o); release(ctx, w.gbuf_u); release(ctx, w.ybuf);
   release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
@@ -201,10 +201,6 @@ int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   ctx->precision = precision;
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->num_sms = prop.multiProcessorCount;
-  if (const char* seg = getenv("LRS_SEG_CHUNKS")) {
-    int v = atoi(seg);
-    if (v >= 1 && v <= 1024) ctx->seg_chunks = v;
-  }
   for (int s = 0; s < 6; ++s)
     for (int j = 0; j < 2; ++j)
       if (cudaEventCreate(&ctx->ev[s][j]) != cudaSuccess) {

@@ -98,6 +98,7 @@ struct Workspace {
   DevBuf<double2> denom_o, denom_u;   // [nf][Ko], [nf][Ku]
   DevBuf<double> dyson_a;             // [n][n]
   DevBuf<int> ipiv;                   // [n]
+  DevBuf<double> tinv;                // inverted diagonal blocks of the LU factors
   DevBuf<int> status;                 // device status words
   DevBuf<double2> phase_tab;          // projection phase tables
   DevBuf<double2> kphase;             // [nk][npts]
@@ -192,8 +193,14 @@ int dgemm(lrs_ctx* ctx, int m, int n, int k, double alpha, const double* a, int 
 int dyson_solve(lrs_ctx* ctx, Site& s);
 int dgemm_t(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
             const double* ks, const double* b, int ldb, const double* cs, double beta, double* c, int ldc);
+int dgemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+                  long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                  long long stride_b, const double* cs, double beta, double* c, int ldc, long long stride_c,
+                  int batch);
 int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status);
 int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb);
+int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb,
+                 double* tinv);
 
 // lm-basis Dyson on product grids (k_dyson_lm.cu)
 int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);
