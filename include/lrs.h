@@ -129,6 +129,14 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
                       const int* nocc, const double* coeff, const double* energies);
 
 /*
+ * Replace the band energies [nk][nbands] (same layout as in lrs_load_orbitals)
+ * without touching coefficients or projected orbitals, e.g. for a scissor
+ * shift.  The frequency quadrature (mu, t_i, W_i) is kept as it is; chi0 and
+ * W of every site become stale.  Errors: LRS_ERR_STATE, LRS_ERR_ARG.
+ */
+int lrs_set_energies(lrs_ctx* ctx, const double* energies);
+
+/*
  * Define the site grids (Sec. VI.A, App. D.1).
  *   centers[nsites*3]  site centres tau (bohr)
  *   npts[nsites]       points per site

@@ -1,0 +1,270 @@
+// Adjoint of (band energies, site-grid orbitals) -> chi0 -> W for one site.
+// The paper has no gradients; this is the derivative of the computation it
+// defines (Eq. (chi1) with the single-grid quadrature, Eq. (eq-W)).
+//
+// With A = I - v Q chi0 Q and W = A^-1 v,  dW = W Q dchi0 Q W, so
+//   dL/dchi0 = Q W^T G_W W^T Q (+ any direct dL/dchi0),
+// and with chi0 = (2/pi)(S + S^T), dL/dS = G_S = (2/pi)(G + G^T).
+// Per frequency t_f (mu and the quadrature held fixed) the Green's functions
+//   Go(p,p')   = sum_b conj psi(p,b) d_b psi(p',b)     (occupied)
+//   GuT(p,p')  = sum_c psi(p,c) d_c conj psi(p',c)     (unoccupied)
+// are recomputed (never stored across frequencies), S_f = W_f Re[Go o GuT],
+// and with Ho = W_f G_S o GuT, Hu = W_f G_S o Go:
+//   Yo = Ho psi_o,  Zo = Ho^T conj psi_o,  Yu = Hu conj psi_u,  Zu = Hu^T psi_u,
+//   dL/dpsi_o += d Yo + conj(d Zo),        dL/dpsi_u += conj(d Yu) + d Zu,
+//   dL/deps_b += Re[(d_b^2 / w_b) sum_p conj psi(p,b) Yo(p,b)]   (occupied)
+//   dL/deps_c += Re[(d_c^2 / w_c) sum_p psi(p,c) Yu(p,c)]        (unoccupied)
+// in the dL/dRe + i dL/dIm convention.  All arithmetic is float64.
+#include "lrs_internal.h"
+
+namespace lrs {
+
+constexpr int ZT = 64;    // tile edge
+constexpr int ZK = 16;    // k chunk
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// C[m][n] = sum_k opA(m,k) s_k opB(k,n)  (+ beta C), complex float64, row-major.
+// opA(m,k) = (TA ? A[k][m] : A[m][k]), conjugated if CA; opB likewise.
+template <bool TA, bool CA, bool TB, bool CB>
+__global__ void __launch_bounds__(256) zgemm64_kernel(int m, int n, int k, const double2* __restrict__ A, int lda,
+                                                      const double2* __restrict__ s, const double2* __restrict__ B,
+                                                      int ldb, double beta, double2* __restrict__ C, int ldc) {
+  __shared__ double2 As[ZK][ZT + 1];
+  __shared__ double2 Bs[ZK][ZT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < k; k0 += ZK) {
+    for (int idx = threadIdx.x; idx < ZK * ZT; idx += 256) {
+      int r, kk;
+      if (TA) { kk = idx / ZT; r = idx % ZT; } else { r = idx / ZK; kk = idx % ZK; }
+      const int gi = i0 + r, gk = k0 + kk;
+      double2 a = make_double2(0.0, 0.0);
+      if (gi < m && gk < k) {
+        a = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+        if (CA) a = zconj(a);
+        if (s) a = zmul(a, s[gk]);
+      }
+      As[kk][r] = a;
+    }
+    for (int idx = threadIdx.x; idx < ZK * ZT; idx += 256) {
+      int c, kk;
+      if (TB) { c = idx / ZK; kk = idx % ZK; } else { kk = idx / ZT; c = idx % ZT; }
+      const int gj = j0 + c, gk = k0 + kk;
+      double2 b = make_double2(0.0, 0.0);
+      if (gj < n && gk < k) {
+        b = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+        if (CB) b = zconj(b);
+      }
+      Bs[kk][c] = b;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < ZK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + ty + 16 * i;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tx + 16 * j;
+      if (gj >= n) continue;
+      double2* c = &C[(size_t)gi * ldc + gj];
+      if (beta == 0.0) {
+        *c = acc[i][j];
+      } else {
+        const double2 o = *c;
+        *c = make_double2(fma(beta, o.x, acc[i][j].x), fma(beta, o.y, acc[i][j].y));
+      }
+    }
+  }
+}
+
+template <bool TA, bool CA, bool TB, bool CB>
+static int zgemm64(lrs_ctx* ctx, int m, int n, int k, const double2* A, int lda, const double2* s,
+                   const double2* B, int ldb, double beta, double2* C, int ldc) {
+  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
+  zgemm64_kernel<TA, CA, TB, CB><<<grid, 256, 0, ctx->stream>>>(m, n, k, A, lda, s, B, ldb, beta, C, ldc);
+  return after_launch(ctx, "zgemm64_kernel");
+}
+
+// G_S = (2/pi) [Q_p Q_q (T[p][q] + T[q][p]) + gc[p][q] + gc[q][p]]
+__global__ void gamma_s_kernel(const double* __restrict__ T, const double* __restrict__ gc,
+                               const double* __restrict__ q, int n, double* __restrict__ G) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (c >= n || r >= n) return;
+  double v = 0.0;
+  if (T) v = q[r] * q[c] * (T[(size_t)r * n + c] + T[(size_t)c * n + r]);
+  if (gc) v += gc[(size_t)r * n + c] + gc[(size_t)c * n + r];
+  G[(size_t)r * n + c] = 0.63661977236758134308 * v;
+}
+
+// In place: go <- W_f G_S o gu (= Ho), gu <- W_f G_S o go (= Hu).
+__global__ void hadamard_kernel(const double* __restrict__ G, double wf, size_t nn, double2* __restrict__ go,
+                                double2* __restrict__ gu) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const double g = wf * G[i];
+  const double2 a = go[i], b = gu[i];
+  go[i] = make_double2(g * b.x, g * b.y);
+  gu[i] = make_double2(g * a.x, g * a.y);
+}
+
+// Accumulates the orbital and energy gradients of one column set and frequency.
+// occupied: gpsi += d Y + conj(d Z),  e_b = sum_p conj psi(p,b) Y(p,b)
+// unoccupied: gpsi += conj(d Y) + d Z, e_c = sum_p psi(p,c) Y(p,c)
+// ge[b] += Re[e_b d_b^2 / w_b].  One block per column, threads over points.
+template <bool kOcc>
+__global__ void grad_accum_kernel(const double2* __restrict__ psi, const double2* __restrict__ Y,
+                                  const double2* __restrict__ Z, const double2* __restrict__ d,
+                                  const double* __restrict__ w, int n, int K, double2* __restrict__ gpsi,
+                                  double* __restrict__ ge) {
+  const int b = blockIdx.x;
+  const double2 db = d[b];
+  double er = 0.0, ei = 0.0;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const size_t ix = (size_t)p * K + b;
+    const double2 y = Y[ix], z = Z[ix], ps = psi[ix];
+    const double2 dy = zmul(db, y), dz = zmul(db, z);
+    double2 g = gpsi[ix];
+    if (kOcc) {
+      g.x += dy.x + dz.x;
+      g.y += dy.y - dz.y;
+      const double2 t = zmul(zconj(ps), y);
+      er += t.x;
+      ei += t.y;
+    } else {
+      g.x += dy.x + dz.x;
+      g.y += -dy.y + dz.y;
+      const double2 t = zmul(ps, y);
+      er += t.x;
+      ei += t.y;
+    }
+    gpsi[ix] = g;
+  }
+  __shared__ double sr[32], si[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    er += __shfl_down_sync(0xffffffffu, er, o);
+    ei += __shfl_down_sync(0xffffffffu, ei, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = er; si[threadIdx.x >> 5] = ei; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { er += sr[i]; ei += si[i]; }
+    const double2 d2 = zmul(db, db);
+    // Re[e d^2 / w]
+    ge[b] += (er * d2.x - ei * d2.y) / w[b];
+  }
+}
+
+// Scatter of the internal (occupied | unoccupied) columns to the public (k, band) order.
+__global__ void scatter_grad_kernel(const double2* __restrict__ go, const double2* __restrict__ gu, int n, int Ko,
+                                    int Ku, const int* __restrict__ col_o, const int* __restrict__ col_u, int ncol,
+                                    double2* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (p >= n || j >= Ko + Ku) return;
+  if (j < Ko) out[(size_t)p * ncol + col_o[j]] = go[(size_t)p * Ko + j];
+  else out[(size_t)p * ncol + col_u[j - Ko]] = gu[(size_t)p * Ku + (j - Ko)];
+}
+
+__global__ void scatter_energy_kernel(const double* __restrict__ ge, int Ko, int Ku, const int* __restrict__ col_o,
+                                      const int* __restrict__ col_u, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Ko + Ku) return;
+  if (j < Ko) out[col_o[j]] = ge[j];
+  else out[col_u[j - Ko]] = ge[j];
+}
+
+int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w, const double* grad_chi0, double* grad_e,
+                  double2* grad_psi) {
+  const int n = s.npts, Ko = ctx->Ko, Ku = ctx->Ku, K = Ko + Ku, nf = ctx->nf;
+  const size_t nn = (size_t)n * n;
+  Workspace& ws = ctx->ws;
+  LRS_TRY(ensure(ctx, ws.gamma_s, nn));
+  LRS_TRY(ensure(ctx, ws.gbuf_o, nn));
+  LRS_TRY(ensure(ctx, ws.gbuf_u, nn));
+  LRS_TRY(ensure(ctx, ws.ybuf, 2 * (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.gpsi, (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.ge, (size_t)K));
+  LRS_TRY(ensure(ctx, ws.tmp_nn, 2 * nn));
+  // denominators of the current quadrature (held fixed)
+  LRS_TRY(build_denominators(ctx));
+  // G_S
+  double* T = nullptr;
+  if (grad_w) {
+    double* T1 = ws.tmp_nn.ptr;
+    T = ws.tmp_nn.ptr + nn;
+    LRS_TRY(dgemm_t(ctx, false, true, n, n, n, 1.0, grad_w, n, nullptr, s.w.ptr, n, nullptr, 0.0, T1, n));
+    LRS_TRY(dgemm_t(ctx, true, false, n, n, n, 1.0, s.w.ptr, n, nullptr, T1, n, nullptr, 0.0, T, n));
+  }
+  dim3 g2((n + 127) / 128, n);
+  gamma_s_kernel<<<g2, 128, 0, ctx->stream>>>(T, grad_chi0, s.wts.ptr, n, ws.gamma_s.ptr);
+  LRS_TRY(after_launch(ctx, "gamma_s_kernel"));
+  LRS_CUDA_TRY(cudaMemsetAsync(ws.gpsi.ptr, 0, (size_t)n * K * sizeof(double2), ctx->stream));
+  LRS_CUDA_TRY(cudaMemsetAsync(ws.ge.ptr, 0, (size_t)K * sizeof(double), ctx->stream));
+  double2* go = ws.gbuf_o.ptr;
+  double2* gu = ws.gbuf_u.ptr;
+  double2* Y = ws.ybuf.ptr;             // [n][K] (occupied block then unoccupied block, each [n][Kx])
+  double2* Z = ws.ybuf.ptr + (size_t)n * K;
+  double2* Yo = Y;
+  double2* Yu = Y + (size_t)n * Ko;
+  double2* Zo = Z;
+  double2* Zu = Z + (size_t)n * Ko;
+  double2* gpo = ws.gpsi.ptr;
+  double2* gpu = ws.gpsi.ptr + (size_t)n * Ko;
+  for (int f = 0; f < nf; ++f) {
+    const double2* dof = ws.denom_o.ptr + (size_t)f * Ko;
+    const double2* duf = ws.denom_u.ptr + (size_t)f * Ku;
+    // Go = (conj psi_o d) psi_o^T,  GuT = (psi_u d) conj(psi_u)^T
+    LRS_TRY((zgemm64<false, true, true, false>(ctx, n, n, Ko, s.psi_o.ptr, Ko, dof, s.psi_o.ptr, Ko, 0.0, go, n)));
+    LRS_TRY((zgemm64<false, false, true, true>(ctx, n, n, Ku, s.psi_u.ptr, Ku, duf, s.psi_u.ptr, Ku, 0.0, gu, n)));
+    hadamard_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(ws.gamma_s.ptr, ctx->W[f], nn, go, gu);
+    LRS_TRY(after_launch(ctx, "hadamard_kernel"));
+    // now go = Ho, gu = Hu
+    LRS_TRY((zgemm64<false, false, false, false>(ctx, n, Ko, n, go, n, nullptr, s.psi_o.ptr, Ko, 0.0, Yo, Ko)));
+    LRS_TRY((zgemm64<true, false, false, true>(ctx, n, Ko, n, go, n, nullptr, s.psi_o.ptr, Ko, 0.0, Zo, Ko)));
+    LRS_TRY((zgemm64<false, false, false, true>(ctx, n, Ku, n, gu, n, nullptr, s.psi_u.ptr, Ku, 0.0, Yu, Ku)));
+    LRS_TRY((zgemm64<true, false, false, false>(ctx, n, Ku, n, gu, n, nullptr, s.psi_u.ptr, Ku, 0.0, Zu, Ku)));
+    grad_accum_kernel<true><<<Ko, 256, 0, ctx->stream>>>(s.psi_o.ptr, Yo, Zo, dof, ctx->w_o.ptr, n, Ko, gpo,
+                                                         ws.ge.ptr);
+    LRS_TRY(after_launch(ctx, "grad_accum_kernel"));
+    grad_accum_kernel<false><<<Ku, 256, 0, ctx->stream>>>(s.psi_u.ptr, Yu, Zu, duf, ctx->w_u.ptr, n, Ku, gpu,
+                                                          ws.ge.ptr + Ko);
+    LRS_TRY(after_launch(ctx, "grad_accum_kernel"));
+  }
+  const int ncol = ctx->nk * ctx->nb;
+  dim3 gs((K + 255) / 256, n);
+  scatter_grad_kernel<<<gs, 256, 0, ctx->stream>>>(gpo, gpu, n, Ko, Ku, ctx->d_col_o.ptr, ctx->d_col_u.ptr, ncol,
+                                                   grad_psi);
+  LRS_TRY(after_launch(ctx, "scatter_grad_kernel"));
+  scatter_energy_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ws.ge.ptr, Ko, Ku, ctx->d_col_o.ptr,
+                                                                   ctx->d_col_u.ptr, grad_e);
+  return after_launch(ctx, "scatter_energy_kernel");
+}
+
+}  // namespace lrs

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) chi0_fp64_kernel(
       int q = j0 + tx + 16 * j;
       if (q >= n) continue;
       double re = go[i][j].x * gu[i][j].x - go[i][j].y * gu[i][j].y;
-      atomicAdd(&S[(size_t)p * n + q], wf * re);
+      S[((size_t)f * n + p) * n + q] = wf * re;   // this frequency's slab: no atomics, fixed sum order
     }
   }
 }
@@ -142,17 +142,48 @@ int symmetrize_chi0(lrs_ctx* ctx, double* chi0, int n) {
   return after_launch(ctx, "symmetrize_kernel");
 }
 
+// chi0 = (2/pi) sum_f (S_f + S_f^T), frequencies summed in order (deterministic).
+__global__ void reduce_slabs_kernel(const double* __restrict__ slab, int n, int nf, double* __restrict__ chi0) {
+  __shared__ double t[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int f = 0; f < nf; ++f) {
+    const double* s = slab + (size_t)f * n * n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = c0 + ty + 8 * i, c = r0 + tx;
+      t[ty + 8 * i][tx] = (r < n && c < n) ? s[(size_t)r * n + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty + 8 * i, c = c0 + tx;
+      const double direct = (r < n && c < n) ? s[(size_t)r * n + c] : 0.0;
+      acc[i] += direct + t[tx][ty + 8 * i];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 8 * i, c = c0 + tx;
+    if (r < n && c < n) chi0[(size_t)r * n + c] = 0.63661977236758134308 * acc[i];
+  }
+}
+
 int chi0_fp64(lrs_ctx* ctx, Site& s) {
   const int n = s.npts;
-  LRS_CUDA_TRY(cudaMemsetAsync(s.chi0.ptr, 0, (size_t)n * n * sizeof(double), ctx->stream));
+  LRS_TRY(ensure(ctx, ctx->ws.slab64, (size_t)ctx->nf * n * n));
   LRS_TRY(stage_begin(ctx, ST_CHI0_MAIN));
   dim3 grid((n + TT - 1) / TT, (n + TT - 1) / TT, ctx->nf);
   chi0_fp64_kernel<<<grid, 256, 0, ctx->stream>>>(s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku,
                                                    ctx->ws.denom_o.ptr, ctx->ws.denom_u.ptr, ctx->d_W.ptr, n,
-                                                   s.chi0.ptr);
+                                                   ctx->ws.slab64.ptr);
   LRS_TRY(after_launch(ctx, "chi0_fp64_kernel"));
   LRS_TRY(stage_end(ctx, ST_CHI0_MAIN));
-  return symmetrize_chi0(ctx, s.chi0.ptr, n);
+  dim3 rg((n + 31) / 32, (n + 31) / 32);
+  reduce_slabs_kernel<<<rg, dim3(32, 8), 0, ctx->stream>>>(ctx->ws.slab64.ptr, n, ctx->nf, s.chi0.ptr);
+  return after_launch(ctx, "reduce_slabs_kernel");
 }
 
 }  // namespace lrs

@@ -166,7 +166,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.status); release(ctx, w.phase_tab); release(ctx, w.kphase); release(ctx, w.ru);
   release(ctx, w.gamma_s); release(ctx, w.gbuf_o); release(ctx, w.gbuf_u); release(ctx, w.ybuf);
   release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
-  release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.tc_scratch);
+  release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.tc_scratch); release(ctx, w.slab64);
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
 
@@ -478,6 +478,26 @@ int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode) {
     s.has_chi0 = s.has_w = false;
   }
   LRS_TRY(stage_end(ctx, ST_PROJECT));
+  return LRS_OK;
+}
+
+int lrs_set_energies(lrs_ctx* ctx, const double* energies) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  if (!energies) return set_error(LRS_ERR_ARG, "energies is NULL");
+  const size_t ne = (size_t)ctx->nk * ctx->nb;
+  if (!finite_all(energies, ne)) return set_error(LRS_ERR_ARG, "non-finite energy");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  ctx->energies.assign(energies, energies + ne);
+  std::vector<double> eo(ctx->Ko), eu(ctx->Ku);
+  for (int j = 0; j < ctx->Ko; ++j) eo[j] = energies[ctx->col_o[j]];
+  for (int j = 0; j < ctx->Ku; ++j) eu[j] = energies[ctx->col_u[j]];
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpy(ctx->e_o.ptr, eo.data(), ctx->Ko * sizeof(double), cudaMemcpyHostToDevice));
+  LRS_CUDA_TRY(cudaMemcpy(ctx->e_u.ptr, eu.data(), ctx->Ku * sizeof(double), cudaMemcpyHostToDevice));
+  for (auto& s : ctx->sites) s.has_chi0 = s.has_w = false;
   return LRS_OK;
 }
 

@@ -114,6 +114,7 @@ struct Workspace {
   DevBuf<uint16_t> planes_a, planes_b;  // chi0: per-frequency A, frequency-independent B
   DevBuf<float> slab;                   // chi0: [nf][Np][Np] fp32 Re[Go o Gu^T] per frequency
   DevBuf<float> tc_scratch;             // chi0: per-CTA parked occupied sums
+  DevBuf<double> slab64;                // FP64 chi0: [nf][n][n] per-frequency W_f Re[Go o Gu^T]
   DevBuf<uint16_t> proj_a, proj_b;      // projection: phase planes, coefficient planes
   DevBuf<float> scales;                 // chi0: fp16 operand scales per frequency
   DevBuf<float> proj_scale;             // projection: coefficient scale and unscale

@@ -52,6 +52,7 @@ _SIGS = {
     "lrs_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
     "lrs_load_orbitals": (C.c_int, [_P, _DP, C.c_int, _DP, _DP, C.c_int, _IP, C.c_int, _IP, _DP, _DP]),
     "lrs_set_sites": (C.c_int, [_P, C.c_int, _DP, _IP, _DP, _DP, _IP]),
+    "lrs_set_energies": (C.c_int, [_P, _DP]),
     "lrs_set_frequency_quadrature": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _DP, _DP]),
     "lrs_get_frequency_quadrature": (C.c_int, [_P, _DP, _DP]),
     "lrs_project": (C.c_int, [_P, C.c_int, _IP, C.c_int]),
@@ -154,6 +155,11 @@ class Screening:
     def load(self, orbitals):
         o = orbitals
         self.load_orbitals(o.cell, o.kpts, o.kweights, o.gvec, o.coeff, o.energies, o.nocc)
+
+    def set_energies(self, energies):
+        e = _f64(energies)
+        assert e.size == self.nk * self.nb
+        _check(lrs_set_energies(self.ctx, _dp(e)), "lrs_set_energies")
 
     def set_sites(self, sites):
         centers = _f64(np.stack([s.center for s in sites]))
