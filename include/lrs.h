@@ -58,6 +58,7 @@ extern "C" {
 #define LRS_OPT_DYSON_BASIS      1  /* value: LRS_DYSON_AUTO, LRS_DYSON_FULL or LRS_DYSON_LM */
 #define LRS_OPT_CHI0_SEGMENT     2  /* value: K chunks of 32 per tensor-core accumulation segment (1..1024) */
 #define LRS_OPT_PROJ_SEGMENT     3  /* same for the mixed-precision projection */
+#define LRS_OPT_CHI0_TILE_N      4  /* value: 64 or 128 grid points per tensor-core tile column */
 #define LRS_DYSON_AUTO    0   /* lm basis when the site grid is a radial x angular product that it shrinks */
 #define LRS_DYSON_FULL    1   /* LU on the full npts x npts grid matrix */
 #define LRS_DYSON_LM      2   /* LU in the (radial shell, l, m) basis (product grids only) */
@@ -258,6 +259,29 @@ int lrs_backward_dev(lrs_ctx* ctx, int site, const double* grad_w_dev,
 #define LRS_STATIC_MAX_NPTS 512
 int lrs_solve_w_static(int npts, int lmax, const double* pts_dev, const double* wts_dev,
                        const double* chi0_dev, double* w_dev, void* stream);
+
+/*
+ * Record the whole build of `nsite` sites (NULL = all) - projection, chi0 in
+ * one persistent tensor-core launch over every (site, tile, tile, frequency)
+ * unit, and the Dyson solves - as a CUDA graph on the context stream, which
+ * must not be the legacy default stream.  The call first runs the build once
+ * eagerly (allocating every buffer and checking the status words), then
+ * records it.  lrs_graph_launch replays it asynchronously on the context
+ * stream, recomputing chi0 and W of those sites from the resident orbitals;
+ * status words are not read during replays (call lrs_synchronize).
+ * Errors: LRS_ERR_STATE, plus those of the stages.
+ */
+int lrs_graph_capture(lrs_ctx* ctx, int nsite, const int* sites);
+int lrs_graph_launch(lrs_ctx* ctx);
+
+/*
+ * Tile shape tuning of the chi0 tensor-core launch for `nsite` sites: times
+ * tile widths {128, 64} x accumulation segments {4, 2} chunks of 32 (short
+ * segments bound the tensor cores' accumulation error) and keeps the fastest
+ * on the context.  Outputs (may be NULL): tile_n, segment, ms_best.
+ * Requires mixed precision and orbitals on the sites.
+ */
+int lrs_autotune(lrs_ctx* ctx, int nsite, const int* sites, int* tile_n, int* segment, double* ms_best);
 
 /* Wait for the context stream; fold device timings into the stats. */
 int lrs_synchronize(lrs_ctx* ctx);

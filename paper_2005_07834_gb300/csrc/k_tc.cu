@@ -16,6 +16,7 @@
 // denominators d = w_k/(mu + i t - eps) are float64 (k_chi0_fp64.cu); the
 // split is bf16 (LRS_MIXED_BF16X3) or scaled fp16 (LRS_MIXED_FP16X3).
 #include <cmath>
+#include <cstring>
 
 #include "tc_gemm.cuh"
 
@@ -101,7 +102,8 @@ template <uint32_t FMT>
 __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, const double2* __restrict__ psi_u,
                                  int Ku, int n, int Np, int Kop, int Kp, const double2* __restrict__ d_o,
                                  const double2* __restrict__ d_u, int nf, const float* __restrict__ scales,
-                                 uint16_t* __restrict__ A, uint16_t* __restrict__ B) {
+                                 uint16_t* __restrict__ A, size_t aplane, uint16_t* __restrict__ B,
+                                 size_t bplane) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (k >= Kp || p >= Np) return;
@@ -115,11 +117,9 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
     xi = (float)v.y;
   }
   const size_t ld = 2 * (size_t)Kp;
-  const size_t bplane = (size_t)Np * ld;
   const float sb = scales ? scales[nf] : 1.f;
   put_split<FMT>(B + (size_t)p * ld, k, sb * xr);
   put_split<FMT>(B + bplane + (size_t)p * ld, k, sb * (occ ? xi : -xi));
-  const size_t aplane = (size_t)nf * Np * ld;
   const float cr = xr, ci = occ ? -xi : xi;   // conj for occupied
   for (int f = 0; f < nf; ++f) {
     float ar = 0.f, ai = 0.f;
@@ -238,62 +238,110 @@ constexpr int PROJ_TN = 128;   // projection tile columns
 
 int phase_setup(lrs_ctx* ctx, Site& s, int* off1, int* off2);
 
-template <uint32_t FMT>
-static int chi0_mixed_t(lrs_ctx* ctx, Site& s) {
-  const int n = s.npts, nf = ctx->nf;
-  const int Np = round_up(n, TILE_M);
+// chi0 of several sites in one persistent tensor-core launch.  The operand
+// planes of all sites are stacked (A: [2][sum_s nf Np_s][2Kp], B: [2][sum_s
+// Np_s][2Kp]) so that one pair of tensor maps covers every unit; a site table
+// maps the global unit index to (site, tile, tile, frequency).
+template <uint32_t FMT, int TN>
+static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list) {
+  const int nf = ctx->nf;
   const int Kop = round_up(ctx->Ko, 32), Kup = round_up(ctx->Ku, 32), Kp = Kop + Kup;
   const size_t ld = 2 * (size_t)Kp;
-  LRS_TRY(ensure(ctx, ctx->ws.planes_a, 2 * (size_t)nf * Np * ld));
-  LRS_TRY(ensure(ctx, ctx->ws.planes_b, 2 * (size_t)Np * ld));
-  LRS_TRY(ensure(ctx, ctx->ws.slab, (size_t)nf * Np * Np));
-  const float* scales = nullptr;
-  if (FMT == 0) {
-    LRS_TRY(ensure(ctx, ctx->ws.scales, (size_t)nf + 8));
-    unsigned int* pmax = reinterpret_cast<unsigned int*>(ctx->ws.scales.ptr + nf + 4);
-    LRS_CUDA_TRY(cudaMemsetAsync(pmax, 0, sizeof(unsigned int), ctx->stream));
-    max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(s.psi_o.ptr, (size_t)n * ctx->Ko, pmax);
-    LRS_TRY(after_launch(ctx, "max_abs_kernel"));
-    max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(s.psi_u.ptr, (size_t)n * ctx->Ku, pmax);
-    LRS_TRY(after_launch(ctx, "max_abs_kernel"));
-    chi0_scales_kernel<<<nf, 256, 0, ctx->stream>>>(ctx->ws.denom_o.ptr, ctx->Ko, ctx->ws.denom_u.ptr, ctx->Ku, nf,
-                                                     pmax, ctx->ws.scales.ptr);
-    LRS_TRY(after_launch(ctx, "chi0_scales_kernel"));
-    scales = ctx->ws.scales.ptr;
+  const int ns = (int)list.size();
+  std::vector<SiteTile>& table = ctx->site_tiles_host;
+  table.resize(ns);
+  long long ra = 0, rb = 0, slab = 0, units = 0;
+  for (int i = 0; i < ns; ++i) {
+    const int np = round_up(ctx->sites[list[i]].npts, TILE_M);
+    SiteTile& t = table[i];
+    t.unit0 = (int)units;
+    t.m_tiles = np / TILE_M;
+    t.n_tiles = np / TN;
+    t.np = np;
+    t.a_row0 = (int)ra;
+    t.b_row0 = (int)rb;
+    t.slab0 = slab;
+    units += (long long)t.m_tiles * t.n_tiles * nf;
+    ra += (long long)nf * np;
+    rb += np;
+    slab += (long long)nf * np * np;
   }
-  dim3 pg((Kp + 127) / 128, Np);
-  chi0_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku, n, Np, Kop, Kp,
-                                                      ctx->ws.denom_o.ptr, ctx->ws.denom_u.ptr, nf, scales,
-                                                      ctx->ws.planes_a.ptr, ctx->ws.planes_b.ptr);
-  LRS_TRY(after_launch(ctx, "chi0_prep_kernel"));
+  if (2 * ra > INT32_MAX || units > INT32_MAX) return set_error(LRS_ERR_ARG, "too many sites for one launch");
+  LRS_TRY(ensure(ctx, ctx->ws.planes_a, 2 * (size_t)ra * ld));
+  LRS_TRY(ensure(ctx, ctx->ws.planes_b, 2 * (size_t)rb * ld));
+  LRS_TRY(ensure(ctx, ctx->ws.slab, (size_t)slab));
+  LRS_TRY(ensure(ctx, ctx->ws.site_tiles, (size_t)ns));
+  LRS_TRY(ensure(ctx, ctx->ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * TN));
+  const size_t sstride = (size_t)nf + 8;    // fp16 operand scales of one site
+  if (FMT == 0) LRS_TRY(ensure(ctx, ctx->ws.scales, sstride * ns));
+  // the unit table goes to the device only when it changes (never while a graph is recorded)
+  const bool same = ctx->site_tiles_dev_ptr == ctx->ws.site_tiles.ptr && ctx->site_tiles_dev.size() == table.size() &&
+                    std::memcmp(ctx->site_tiles_dev.data(), table.data(), ns * sizeof(SiteTile)) == 0;
+  if (!same) {
+    if (ctx->capturing) return set_error(LRS_ERR_STATE, "site table changed during graph capture");
+    LRS_CUDA_TRY(cudaMemcpyAsync(ctx->ws.site_tiles.ptr, table.data(), ns * sizeof(SiteTile),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->site_tiles_dev = table;
+    ctx->site_tiles_dev_ptr = ctx->ws.site_tiles.ptr;
+  }
+  for (int i = 0; i < ns; ++i) {
+    Site& s = ctx->sites[list[i]];
+    const SiteTile& t = table[i];
+    const int n = s.npts;
+    float* scales = nullptr;
+    if (FMT == 0) {
+      scales = ctx->ws.scales.ptr + sstride * i;
+      unsigned int* pmax = reinterpret_cast<unsigned int*>(scales + nf + 4);
+      LRS_CUDA_TRY(cudaMemsetAsync(pmax, 0, sizeof(unsigned int), ctx->stream));
+      max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(s.psi_o.ptr, (size_t)n * ctx->Ko, pmax);
+      LRS_TRY(after_launch(ctx, "max_abs_kernel"));
+      max_abs_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(s.psi_u.ptr, (size_t)n * ctx->Ku, pmax);
+      LRS_TRY(after_launch(ctx, "max_abs_kernel"));
+      chi0_scales_kernel<<<nf, 256, 0, ctx->stream>>>(ctx->ws.denom_o.ptr, ctx->Ko, ctx->ws.denom_u.ptr, ctx->Ku,
+                                                       nf, pmax, scales);
+      LRS_TRY(after_launch(ctx, "chi0_scales_kernel"));
+    }
+    dim3 pg((Kp + 127) / 128, t.np);
+    chi0_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(
+        s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku, n, t.np, Kop, Kp, ctx->ws.denom_o.ptr, ctx->ws.denom_u.ptr, nf,
+        scales, ctx->ws.planes_a.ptr + (size_t)t.a_row0 * ld, (size_t)ra * ld,
+        ctx->ws.planes_b.ptr + (size_t)t.b_row0 * ld, (size_t)rb * ld);
+    LRS_TRY(after_launch(ctx, "chi0_prep_kernel"));
+  }
   CUtensorMap ma, mb;
-  LRS_TRY(make_operand_map(&ma, ctx->ws.planes_a.ptr, ld, 2 * (uint64_t)nf * Np, TILE_M));
-  LRS_TRY(make_operand_map(&mb, ctx->ws.planes_b.ptr, ld, 2 * (uint64_t)Np, CHI0_TN));
-  TcShape sh;
-  sh.m_tiles = Np / TILE_M;
-  sh.n_tiles = Np / CHI0_TN;
+  LRS_TRY(make_operand_map(&ma, ctx->ws.planes_a.ptr, ld, 2 * (uint64_t)ra, TILE_M));
+  LRS_TRY(make_operand_map(&mb, ctx->ws.planes_b.ptr, ld, 2 * (uint64_t)rb, TN));
+  TcShape sh{};
   sh.batches = nf;
   sh.nchunk = Kp / 32;
   sh.nchunk0 = Kop / 32;
   sh.seg = ctx->seg_chunks;
-  sh.a_batch_rows = Np;
-  sh.b_batch_rows = 0;
-  sh.a_im_rows = nf * Np;
-  sh.b_im_rows = Np;
-  LRS_TRY(ensure(ctx, ctx->ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * CHI0_TN));
-  Chi0Store epi{ctx->ws.slab.ptr, ctx->ws.tc_scratch.ptr, Np, CHI0_TN};
+  sh.a_im_rows = (int)ra;
+  sh.b_im_rows = (int)rb;
+  sh.units = (int)units;
+  sh.sites = ctx->ws.site_tiles.ptr;
+  sh.nsites = ns;
+  Chi0Store epi{ctx->ws.slab.ptr, ctx->ws.tc_scratch.ptr, 0, TN};
   LRS_TRY(stage_begin(ctx, ST_CHI0_MAIN));
-  LRS_TRY((launch_tc<CHI0_TN, 2, FMT, Chi0Store>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0>")));
+  LRS_TRY((launch_tc<TN, 2, FMT, Chi0Store>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0>")));
   LRS_TRY(stage_end(ctx, ST_CHI0_MAIN));
-  dim3 rg(Np / 32, Np / 32);
-  chi0_reduce_kernel<<<rg, dim3(32, 8), 0, ctx->stream>>>(ctx->ws.slab.ptr, Np, nf, ctx->d_W.ptr, scales, n,
-                                                          s.chi0.ptr);
-  return after_launch(ctx, "chi0_reduce_kernel");
+  for (int i = 0; i < ns; ++i) {
+    Site& s = ctx->sites[list[i]];
+    const SiteTile& t = table[i];
+    dim3 rg(t.np / 32, t.np / 32);
+    chi0_reduce_kernel<<<rg, dim3(32, 8), 0, ctx->stream>>>(ctx->ws.slab.ptr + t.slab0, t.np, nf, ctx->d_W.ptr,
+                                                            FMT == 0 ? ctx->ws.scales.ptr + sstride * i : nullptr,
+                                                            s.npts, s.chi0.ptr);
+    LRS_TRY(after_launch(ctx, "chi0_reduce_kernel"));
+  }
+  return LRS_OK;
 }
 
-int chi0_mixed(lrs_ctx* ctx, Site& s) {
-  if (ctx->precision == LRS_MIXED_FP16X3) return chi0_mixed_t<0>(ctx, s);
-  return chi0_mixed_t<1>(ctx, s);
+int chi0_mixed(lrs_ctx* ctx, const std::vector<int>& list) {
+  const bool fp16 = ctx->precision == LRS_MIXED_FP16X3;
+  if (ctx->chi0_tn == 64) return fp16 ? chi0_mixed_t<0, 64>(ctx, list) : chi0_mixed_t<1, 64>(ctx, list);
+  return fp16 ? chi0_mixed_t<0, 128>(ctx, list) : chi0_mixed_t<1, 128>(ctx, list);
 }
 
 int project_mixed(lrs_ctx* ctx, Site& s) {
@@ -348,6 +396,9 @@ int project_mixed(lrs_ctx* ctx, Site& s) {
   sh.b_batch_rows = nbp;
   sh.a_im_rows = Np;
   sh.b_im_rows = ctx->nk * nbp;
+  sh.units = sh.m_tiles * sh.n_tiles * sh.batches;
+  sh.sites = nullptr;
+  sh.nsites = 0;
   ProjStore epi;
   epi.kph = ctx->ws.kphase.ptr;
   epi.unscale = cscale + 1;

@@ -51,11 +51,13 @@ void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes) {
 }
 
 int stage_begin(lrs_ctx* ctx, Stage s) {
+  if (ctx->capturing) return LRS_OK;   // stage timings are not part of a recorded graph
   LRS_CUDA_TRY(cudaEventRecord(ctx->ev[s][0], ctx->stream));
   return LRS_OK;
 }
 
 int stage_end(lrs_ctx* ctx, Stage s) {
+  if (ctx->capturing) return LRS_OK;
   LRS_CUDA_TRY(cudaEventRecord(ctx->ev[s][1], ctx->stream));
   ctx->ev_pending[s] = true;
   return LRS_OK;
@@ -167,6 +169,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.gamma_s); release(ctx, w.gbuf_o); release(ctx, w.gbuf_u); release(ctx, w.ybuf);
   release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
   release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.tc_scratch); release(ctx, w.slab64);
+  release(ctx, w.site_tiles);
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
 
@@ -228,6 +231,7 @@ int lrs_destroy(lrs_ctx* ctx) {
   release(ctx, ctx->e_o); release(ctx, ctx->e_u); release(ctx, ctx->w_o); release(ctx, ctx->w_u);
   release(ctx, ctx->d_col_o); release(ctx, ctx->d_col_u);
   free_workspace(ctx);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   for (int s = 0; s < 6; ++s)
     for (int j = 0; j < 2; ++j)
       if (ctx->ev[s][j]) cudaEventDestroy(ctx->ev[s][j]);
@@ -243,6 +247,10 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
       if (value != LRS_DYSON_AUTO && value != LRS_DYSON_FULL && value != LRS_DYSON_LM)
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
+      return LRS_OK;
+    case LRS_OPT_CHI0_TILE_N:
+      if (value != 64 && value != 128) return set_error(LRS_ERR_ARG, "chi0 tile width %d not in {64, 128}", value);
+      ctx->chi0_tn = value;
       return LRS_OK;
     case LRS_OPT_CHI0_SEGMENT:
     case LRS_OPT_PROJ_SEGMENT:
@@ -562,10 +570,10 @@ int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites) {
   LRS_TRY(stage_begin(ctx, ST_CHI0));
   LRS_TRY(build_denominators(ctx));
   double flop = 0;
+  if (ctx->precision != LRS_FP64) LRS_TRY(chi0_mixed(ctx, list));   // all sites in one launch
   for (int i : list) {
     Site& s = ctx->sites[i];
     if (ctx->precision == LRS_FP64) LRS_TRY(chi0_fp64(ctx, s));
-    else LRS_TRY(chi0_mixed(ctx, s));
     s.has_chi0 = true;
     s.has_w = false;
     flop += 8.0 * s.npts * (double)s.npts * (ctx->Ko + ctx->Ku) * ctx->nf;
@@ -594,6 +602,7 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   }
   LRS_TRY(stage_end(ctx, ST_W));
   ctx->stats.flop_w = flop;
+  if (ctx->capturing) return LRS_OK;   // checked after each replay by lrs_graph_launch's caller
   // zero pivots / non-finite values are reported through the status word
   int status[16] = {0};
   LRS_CUDA_TRY(cudaMemcpyAsync(status, ctx->ws.status.ptr, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -696,6 +705,100 @@ int lrs_backward(lrs_ctx* ctx, int site, const double* grad_w, const double* gra
   if (ge) dev_free_bytes(ctx, ge, ne * sizeof(double));
   if (gp) dev_free_bytes(ctx, gp, ne * s.npts * sizeof(double2));
   return rc;
+}
+
+int lrs_graph_capture(lrs_ctx* ctx, int nsite, const int* sites) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (ctx->stream == nullptr)
+    return set_error(LRS_ERR_STATE, "graph capture needs a non-default stream (lrs_create/lrs_set_stream)");
+  // one eager build allocates every buffer, builds cached operands and checks the status words
+  LRS_TRY(lrs_project(ctx, nsite, sites, LRS_PROJ_EXACT));
+  LRS_TRY(lrs_build_chi0(ctx, nsite, sites));
+  LRS_TRY(lrs_solve_w(ctx, nsite, sites));
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  LRS_CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = true;
+  int rc = lrs_project(ctx, nsite, sites, LRS_PROJ_EXACT);
+  if (rc == LRS_OK) rc = lrs_build_chi0(ctx, nsite, sites);
+  if (rc == LRS_OK) rc = lrs_solve_w(ctx, nsite, sites);
+  ctx->capturing = false;
+  std::string err = lrs_last_error();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (rc != LRS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return set_error(rc, "while recording the graph: %s", err.c_str());
+  }
+  if (e != cudaSuccess) return set_error(LRS_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    ctx->graph_exec = nullptr;
+    return set_error(LRS_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  return LRS_OK;
+}
+
+int lrs_graph_launch(lrs_ctx* ctx) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->graph_exec) return set_error(LRS_ERR_STATE, "no recorded graph (lrs_graph_capture)");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_CUDA_TRY(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+  return LRS_OK;
+}
+
+int lrs_autotune(lrs_ctx* ctx, int nsite, const int* sites, int* tile_n, int* segment, double* ms_best) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (ctx->precision == LRS_FP64) return set_error(LRS_ERR_STATE, "autotuning applies to the mixed precisions");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  const int tns[2] = {128, 64};
+  const int segs[2] = {4, 2};   // segments of at most 128 K keep the accumulation error below 1e-5
+  double best = 1e300;
+  int btn = ctx->chi0_tn, bseg = ctx->seg_chunks;
+  cudaEvent_t e0, e1;
+  LRS_CUDA_TRY(cudaEventCreate(&e0));
+  LRS_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = LRS_OK;
+  for (int tn : tns)
+    for (int sg : segs) {
+      ctx->chi0_tn = tn;
+      ctx->seg_chunks = sg;
+      rc = lrs_build_chi0(ctx, nsite, sites);   // warm-up (and allocation)
+      if (rc) break;
+      cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < 2 && rc == LRS_OK; ++r) rc = lrs_build_chi0(ctx, nsite, sites);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc) break;
+      if (ms / 2 < best) {
+        best = ms / 2;
+        btn = tn;
+        bseg = sg;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->chi0_tn = btn;
+  ctx->seg_chunks = bseg;
+  if (rc) return rc;
+  if (tile_n) *tile_n = btn;
+  if (segment) *segment = bseg;
+  if (ms_best) *ms_best = best;
+  return LRS_OK;
 }
 
 int lrs_synchronize(lrs_ctx* ctx) {

@@ -89,6 +89,18 @@ struct Planes {
   size_t plane_elems() const { return (size_t)rows_pad * k_pad; }
 };
 
+// One site of a multi-site tensor-core launch: its work units are
+// [unit0, unit0 + m_tiles^2 * batches).
+struct SiteTile {
+  int unit0;         // first global unit of the site
+  int m_tiles;       // np / 128
+  int n_tiles;       // np / tile width
+  int np;            // padded points (rows of one A batch, leading dimension of the slab)
+  int a_row0;        // first row of the site's A planes
+  int b_row0;        // first row of the site's B planes
+  long long slab0;   // first element of the site's output slab
+};
+
 // Unit direction and radius of a grid point.
 struct __align__(32) RadialUnit {
   double x, y, z, r;
@@ -115,6 +127,7 @@ struct Workspace {
   DevBuf<float> slab;                   // chi0: [nf][Np][Np] fp32 Re[Go o Gu^T] per frequency
   DevBuf<float> tc_scratch;             // chi0: per-CTA parked occupied sums
   DevBuf<double> slab64;                // FP64 chi0: [nf][n][n] per-frequency W_f Re[Go o Gu^T]
+  DevBuf<SiteTile> site_tiles;          // multi-site chi0 unit table
   DevBuf<uint16_t> proj_a, proj_b;      // projection: phase planes, coefficient planes
   DevBuf<float> scales;                 // chi0: fp16 operand scales per frequency
   DevBuf<float> proj_scale;             // projection: coefficient scale and unscale
@@ -131,6 +144,8 @@ struct lrs_ctx {
   int seg_chunks = 4;                  // chi0 tensor-core accumulation segment (K chunks of 32)
   int proj_seg_chunks = 2;             // projection accumulation segment (K chunks of 32)
   int dyson_basis = LRS_DYSON_AUTO;    // full grid or lm basis
+  int chi0_tn = 128;                   // chi0 tensor-core tile width (64 or 128)
+  bool capturing = false;              // a CUDA graph is being recorded on the stream
 
   // orbitals
   bool has_orb = false;
@@ -155,6 +170,10 @@ struct lrs_ctx {
 
   std::vector<lrs::Site> sites;
   lrs::Workspace ws;
+  std::vector<lrs::SiteTile> site_tiles_host;
+  std::vector<lrs::SiteTile> site_tiles_dev;   // copy of the table last uploaded
+  const lrs::SiteTile* site_tiles_dev_ptr = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;        // recorded multi-site build
 
   lrs_stats_t stats{};
   // stage timing events: [stage][0=start,1=end]
@@ -182,7 +201,7 @@ int chi0_fp64(lrs_ctx* ctx, Site& s);
 int symmetrize_chi0(lrs_ctx* ctx, double* chi0, int n);
 
 // Mixed chi0 on tcgen05 (k_chi0_tc.cu)
-int chi0_mixed(lrs_ctx* ctx, Site& s);
+int chi0_mixed(lrs_ctx* ctx, const std::vector<int>& sites);   // one launch for all listed sites
 
 // Coulomb operator (k_coulomb.cu)
 int coulomb_build(lrs_ctx* ctx, Site& s, double* v);

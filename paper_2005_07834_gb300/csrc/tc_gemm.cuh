@@ -46,13 +46,56 @@ struct TcShape {
   int b_batch_rows;  // row offset of batch b in B (0 = shared)
   int a_im_rows;     // row offset of the imaginary planes in A
   int b_im_rows;     // row offset of the imaginary planes in B
+  int units;         // total work units
+  const struct SiteTile* sites;   // multi-site table (NULL: one problem)
+  int nsites;
 };
 
-__device__ __forceinline__ void decode_unit(const TcShape& sh, int u, int& tm, int& tn, int& b) {
-  b = u % sh.batches;
-  int t = u / sh.batches;
-  tm = t / sh.n_tiles;
-  tn = t % sh.n_tiles;
+struct Unit {
+  int tm, tn, b;     // row tile, column tile, batch (frequency or k-point)
+  int ya, yb;        // first operand rows of the unit in A and B
+  int site;
+  long long slab0;   // output offset of the site (multi-site launches)
+  int ld;            // output leading dimension (multi-site launches)
+};
+
+// Units of a launch.  With a site table the units of all sites are numbered
+// site after site (every unit has the same K, hence the same cost, so the
+// static round-robin over CTAs stays balanced for uneven sites).
+template <int TN>
+__device__ __forceinline__ Unit decode_unit(const TcShape& sh, const SiteTile* __restrict__ sites, int nsites,
+                                            int u) {
+  Unit x;
+  if (sites) {
+    int lo = 0, hi = nsites - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sites[mid].unit0 <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    const SiteTile st = sites[lo];
+    const int lu = u - st.unit0;
+    x.b = lu % sh.batches;
+    const int t = lu / sh.batches;
+    x.tm = t / st.n_tiles;
+    x.tn = t % st.n_tiles;
+    x.ya = st.a_row0 + x.b * st.np + x.tm * TILE_M;
+    x.yb = st.b_row0 + x.tn * TN;
+    x.site = lo;
+    x.slab0 = st.slab0;
+    x.ld = st.np;
+  } else {
+    x.b = u % sh.batches;
+    const int t = u / sh.batches;
+    x.tm = t / sh.n_tiles;
+    x.tn = t % sh.n_tiles;
+    x.ya = x.b * sh.a_batch_rows + x.tm * TILE_M;
+    x.yb = x.b * sh.b_batch_rows + x.tn * TN;
+    x.site = 0;
+    x.slab0 = 0;
+    x.ld = sh.m_tiles * TILE_M;
+  }
+  return x;
 }
 
 // Segments of a unit: phase 0 covers chunks [0, c0), phase 1 [c0, nchunk).
@@ -116,7 +159,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int units = sh.m_tiles * sh.n_tiles * sh.batches;
+  const int units = sh.units;
   const SegPlan<NPHASE> plan{sh.nchunk0, sh.nchunk, sh.seg};
 
   if (threadIdx.x == 0) {
@@ -150,10 +193,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        int tm, tn, b;
-        decode_unit(sh, u, tm, tn, b);
-        const int ya = b * sh.a_batch_rows + tm * TILE_M;
-        const int yb = b * sh.b_batch_rows + tn * TN;
+        const Unit x = decode_unit<TN>(sh, sh.sites, sh.nsites, u);
+        const int ya = x.ya, yb = x.yb;
         for (int c = 0; c < sh.nchunk; ++c) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) {
             abort_flag = 1;
@@ -245,8 +286,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int lrow = quarter * 32 + lane, lcol0 = half * COLS;
     bool ok = true;
     for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-      int tm, tn, b;
-      decode_unit(sh, u, tm, tn, b);
+      const Unit x = decode_unit<TN>(sh, sh.sites, sh.nsites, u);
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -295,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (set == 0) set_phase ^= 1u;
       }
       if (!ok) break;
-      epi.template store<COLS>(sum, tm * TILE_M + lrow, lrow, tn * TN + lcol0, lcol0, b);
+      epi.template store<COLS>(sum, x, x.tm * TILE_M + lrow, lrow, x.tn * TN + lcol0, lcol0);
     }
   }
 
@@ -316,10 +356,11 @@ template <int TN, int NPHASE, uint32_t FMT, class Epi>
 int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const TcShape& sh, const Epi& epi,
               const char* name) {
   constexpr int smem = tc_smem_bytes<TN>();
-  LRS_CUDA_TRY(cudaFuncSetAttribute(zgemm_tc_kernel<TN, NPHASE, FMT, Epi>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const int units = sh.m_tiles * sh.n_tiles * sh.batches;
-  const int grid = std::min(units, ctx->num_sms);
+  if (!ctx->capturing)
+    LRS_CUDA_TRY(cudaFuncSetAttribute(zgemm_tc_kernel<TN, NPHASE, FMT, Epi>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int grid = std::min(sh.units, ctx->num_sms);
+  if (grid <= 0) return LRS_OK;
   zgemm_tc_kernel<TN, NPHASE, FMT, Epi><<<grid, TC_THREADS, smem, ctx->stream>>>(ma, mb, sh, epi,
                                                                                  ctx->ws.status.ptr + 8);
   return after_launch(ctx, name);
@@ -345,9 +386,9 @@ struct Chi0Store {
             make_float4(s[part][i], s[part][i + 1], s[part][i + 2], s[part][i + 3]);
   }
   template <int COLS>
-  __device__ void store(const float (&s)[2][COLS], int row, int lrow, int col0, int lcol0, int b) const {
+  __device__ void store(const float (&s)[2][COLS], const Unit& x, int row, int lrow, int col0, int lcol0) const {
     const float* go = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
-    float* dst = slab + ((size_t)b * ld + row) * ld + col0;
+    float* dst = slab + x.slab0 + ((size_t)x.b * x.ld + row) * x.ld + col0;
 #pragma unroll
     for (int i = 0; i < COLS; i += 4) {
       const float4 r = *reinterpret_cast<const float4*>(go + i);
@@ -375,9 +416,10 @@ struct ProjStore {
   template <int COLS>
   __device__ void save_phase0(const float (&)[2][COLS], int, int) const {}
   template <int COLS>
-  __device__ void store(const float (&s)[2][COLS], int row, int lrow, int col0, int lcol0, int k) const {
+  __device__ void store(const float (&s)[2][COLS], const Unit& x, int row, int lrow, int col0, int lcol0) const {
     (void)lrow;
     (void)lcol0;
+    const int k = x.b;
     if (row >= npts) return;
     const double us = (double)*unscale;
     const double2 ph = kph[(size_t)k * npts + row];

@@ -23,7 +23,7 @@ LRS_OK, LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA, LRS_ERR_STATE = 0, 1, 2, 3, 4
 LRS_ERR_TIMEOUT, LRS_ERR_NUMERIC, LRS_ERR_UNSUPPORTED = 5, 6, 7
 LRS_FP64, LRS_MIXED_BF16X3, LRS_MIXED_FP16X3 = 0, 1, 2
 LRS_PROJ_EXACT = 0
-LRS_OPT_DYSON_BASIS, LRS_OPT_CHI0_SEGMENT, LRS_OPT_PROJ_SEGMENT = 1, 2, 3
+LRS_OPT_DYSON_BASIS, LRS_OPT_CHI0_SEGMENT, LRS_OPT_PROJ_SEGMENT, LRS_OPT_CHI0_TILE_N = 1, 2, 3, 4
 LRS_DYSON_AUTO, LRS_DYSON_FULL, LRS_DYSON_LM = 0, 1, 2
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
@@ -68,6 +68,9 @@ _SIGS = {
     "lrs_backward": (C.c_int, [_P, C.c_int, _DP, _DP, _DP, _DP]),
     "lrs_backward_dev": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "lrs_solve_w_static": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _P]),
+    "lrs_graph_capture": (C.c_int, [_P, C.c_int, _IP]),
+    "lrs_graph_launch": (C.c_int, [_P]),
+    "lrs_autotune": (C.c_int, [_P, C.c_int, _IP, _IP, _IP, _DP]),
     "lrs_synchronize": (C.c_int, [_P]),
     "lrs_stats": (C.c_int, [_P, C.POINTER(lrs_stats_t)]),
 }
@@ -248,6 +251,19 @@ class Screening:
     def backward_dev(self, site, grad_w_ptr, grad_chi0_ptr, grad_e_ptr, grad_psi_ptr):
         _check(lrs_backward_dev(self.ctx, int(site), _P(grad_w_ptr or 0), _P(grad_chi0_ptr or 0),
                                 _P(grad_e_ptr), _P(grad_psi_ptr)), "lrs_backward_dev")
+
+    def graph_capture(self, sites=None):
+        n, p, _keep = self._sites(sites)
+        _check(lrs_graph_capture(self.ctx, n, p), "lrs_graph_capture")
+
+    def graph_launch(self):
+        _check(lrs_graph_launch(self.ctx), "lrs_graph_launch")
+
+    def autotune(self, sites=None):
+        n, p, _keep = self._sites(sites)
+        tn, seg, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(lrs_autotune(self.ctx, n, p, C.byref(tn), C.byref(seg), C.byref(ms)), "lrs_autotune")
+        return {"tile_n": tn.value, "segment": seg.value, "ms_chi0": ms.value}
 
     def synchronize(self):
         _check(lrs_synchronize(self.ctx), "lrs_synchronize")
