@@ -59,6 +59,7 @@ extern "C" {
 #define LRS_OPT_CHI0_SEGMENT     2  /* value: K chunks of 32 per tensor-core accumulation segment (1..1024) */
 #define LRS_OPT_PROJ_SEGMENT     3  /* same for the mixed-precision projection */
 #define LRS_OPT_CHI0_TILE_N      4  /* value: 64 or 128 grid points per tensor-core tile column */
+#define LRS_OPT_WORKSPACE_GB     5  /* value: GB of chi0 operand planes per launch (sites are grouped; default 48) */
 #define LRS_DYSON_AUTO    0   /* lm basis when the site grid is a radial x angular product that it shrinks */
 #define LRS_DYSON_FULL    1   /* LU on the full npts x npts grid matrix */
 #define LRS_DYSON_LM      2   /* LU in the (radial shell, l, m) basis (product grids only) */

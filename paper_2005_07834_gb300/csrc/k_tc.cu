@@ -243,13 +243,12 @@ int phase_setup(lrs_ctx* ctx, Site& s, int* off1, int* off2);
 // Np_s][2Kp]) so that one pair of tensor maps covers every unit; a site table
 // maps the global unit index to (site, tile, tile, frequency).
 template <uint32_t FMT, int TN>
-static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list) {
+static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
   const int nf = ctx->nf;
   const int Kop = round_up(ctx->Ko, 32), Kup = round_up(ctx->Ku, 32), Kp = Kop + Kup;
   const size_t ld = 2 * (size_t)Kp;
   const int ns = (int)list.size();
-  std::vector<SiteTile>& table = ctx->site_tiles_host;
-  table.resize(ns);
+  std::vector<SiteTile> table(ns);
   long long ra = 0, rb = 0, slab = 0, units = 0;
   for (int i = 0; i < ns; ++i) {
     const int np = round_up(ctx->sites[list[i]].npts, TILE_M);
@@ -270,19 +269,21 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list) {
   LRS_TRY(ensure(ctx, ctx->ws.planes_a, 2 * (size_t)ra * ld));
   LRS_TRY(ensure(ctx, ctx->ws.planes_b, 2 * (size_t)rb * ld));
   LRS_TRY(ensure(ctx, ctx->ws.slab, (size_t)slab));
-  LRS_TRY(ensure(ctx, ctx->ws.site_tiles, (size_t)ns));
+  LRS_TRY(ensure(ctx, ctx->ws.site_tiles, (size_t)toff + ns));
   LRS_TRY(ensure(ctx, ctx->ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * TN));
   const size_t sstride = (size_t)nf + 8;    // fp16 operand scales of one site
   if (FMT == 0) LRS_TRY(ensure(ctx, ctx->ws.scales, sstride * ns));
   // the unit table goes to the device only when it changes (never while a graph is recorded)
-  const bool same = ctx->site_tiles_dev_ptr == ctx->ws.site_tiles.ptr && ctx->site_tiles_dev.size() == table.size() &&
-                    std::memcmp(ctx->site_tiles_dev.data(), table.data(), ns * sizeof(SiteTile)) == 0;
+  if (ctx->site_tiles_dev_ptr != ctx->ws.site_tiles.ptr) ctx->site_tiles_dev.clear();   // buffer was replaced
+  const bool same = ctx->site_tiles_dev.size() >= (size_t)toff + ns &&
+                    std::memcmp(ctx->site_tiles_dev.data() + toff, table.data(), ns * sizeof(SiteTile)) == 0;
   if (!same) {
     if (ctx->capturing) return set_error(LRS_ERR_STATE, "site table changed during graph capture");
-    LRS_CUDA_TRY(cudaMemcpyAsync(ctx->ws.site_tiles.ptr, table.data(), ns * sizeof(SiteTile),
+    LRS_CUDA_TRY(cudaMemcpyAsync(ctx->ws.site_tiles.ptr + toff, table.data(), ns * sizeof(SiteTile),
                                  cudaMemcpyHostToDevice, ctx->stream));
     LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    ctx->site_tiles_dev = table;
+    if (ctx->site_tiles_dev.size() < (size_t)toff + ns) ctx->site_tiles_dev.resize((size_t)toff + ns);
+    std::memcpy(ctx->site_tiles_dev.data() + toff, table.data(), ns * sizeof(SiteTile));
     ctx->site_tiles_dev_ptr = ctx->ws.site_tiles.ptr;
   }
   for (int i = 0; i < ns; ++i) {
@@ -320,7 +321,7 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list) {
   sh.a_im_rows = (int)ra;
   sh.b_im_rows = (int)rb;
   sh.units = (int)units;
-  sh.sites = ctx->ws.site_tiles.ptr;
+  sh.sites = ctx->ws.site_tiles.ptr + toff;
   sh.nsites = ns;
   Chi0Store epi{ctx->ws.slab.ptr, ctx->ws.tc_scratch.ptr, 0, TN};
   LRS_TRY(stage_begin(ctx, ST_CHI0_MAIN));
@@ -338,10 +339,10 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list) {
   return LRS_OK;
 }
 
-int chi0_mixed(lrs_ctx* ctx, const std::vector<int>& list) {
+int chi0_mixed(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
   const bool fp16 = ctx->precision == LRS_MIXED_FP16X3;
-  if (ctx->chi0_tn == 64) return fp16 ? chi0_mixed_t<0, 64>(ctx, list) : chi0_mixed_t<1, 64>(ctx, list);
-  return fp16 ? chi0_mixed_t<0, 128>(ctx, list) : chi0_mixed_t<1, 128>(ctx, list);
+  if (ctx->chi0_tn == 64) return fp16 ? chi0_mixed_t<0, 64>(ctx, list, toff) : chi0_mixed_t<1, 64>(ctx, list, toff);
+  return fp16 ? chi0_mixed_t<0, 128>(ctx, list, toff) : chi0_mixed_t<1, 128>(ctx, list, toff);
 }
 
 int project_mixed(lrs_ctx* ctx, Site& s) {

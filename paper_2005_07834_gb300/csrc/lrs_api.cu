@@ -248,6 +248,10 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
       return LRS_OK;
+    case LRS_OPT_WORKSPACE_GB:
+      if (value < 1 || value > 4096) return set_error(LRS_ERR_ARG, "workspace budget %d GB out of range", value);
+      ctx->workspace_budget = 1e9 * value;
+      return LRS_OK;
     case LRS_OPT_CHI0_TILE_N:
       if (value != 64 && value != 128) return set_error(LRS_ERR_ARG, "chi0 tile width %d not in {64, 128}", value);
       ctx->chi0_tn = value;
@@ -570,7 +574,27 @@ int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites) {
   LRS_TRY(stage_begin(ctx, ST_CHI0));
   LRS_TRY(build_denominators(ctx));
   double flop = 0;
-  if (ctx->precision != LRS_FP64) LRS_TRY(chi0_mixed(ctx, list));   // all sites in one launch
+  if (ctx->precision != LRS_FP64) {
+    // as many sites per persistent launch as the operand workspace budget allows
+    const double kp = 2.0 * (((ctx->Ko + 31) / 32 + (ctx->Ku + 31) / 32) * 32);
+    LRS_TRY(ensure(ctx, ctx->ws.site_tiles, list.size()));   // one table slot per site, all groups
+    std::vector<int> group;
+    double bytes = 0;
+    int toff = 0;
+    for (size_t i = 0; i < list.size(); ++i) {
+      const double np = (double)((ctx->sites[list[i]].npts + 127) / 128 * 128);
+      const double b = 2.0 * (ctx->nf + 1) * np * kp * 2.0 + (double)ctx->nf * np * np * 4.0;
+      if (!group.empty() && bytes + b > ctx->workspace_budget) {
+        LRS_TRY(chi0_mixed(ctx, group, toff));
+        toff += (int)group.size();
+        group.clear();
+        bytes = 0;
+      }
+      group.push_back(list[i]);
+      bytes += b;
+    }
+    if (!group.empty()) LRS_TRY(chi0_mixed(ctx, group, toff));
+  }
   for (int i : list) {
     Site& s = ctx->sites[i];
     if (ctx->precision == LRS_FP64) LRS_TRY(chi0_fp64(ctx, s));

@@ -145,6 +145,7 @@ struct lrs_ctx {
   int proj_seg_chunks = 2;             // projection accumulation segment (K chunks of 32)
   int dyson_basis = LRS_DYSON_AUTO;    // full grid or lm basis
   int chi0_tn = 128;                   // chi0 tensor-core tile width (64 or 128)
+  double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
 
   // orbitals
@@ -201,7 +202,8 @@ int chi0_fp64(lrs_ctx* ctx, Site& s);
 int symmetrize_chi0(lrs_ctx* ctx, double* chi0, int n);
 
 // Mixed chi0 on tcgen05 (k_chi0_tc.cu)
-int chi0_mixed(lrs_ctx* ctx, const std::vector<int>& sites);   // one launch for all listed sites
+// One launch for all listed sites; `toff` is the group's offset in the device site table.
+int chi0_mixed(lrs_ctx* ctx, const std::vector<int>& sites, int toff);
 
 // Coulomb operator (k_coulomb.cu)
 int coulomb_build(lrs_ctx* ctx, Site& s, double* v);
