@@ -78,6 +78,7 @@ typedef struct lrs_stats_t {
   int64_t device_bytes;   /* device memory currently held by the context */
   int64_t device_bytes_peak;
   int status_word;        /* last device-side status (0 = ok) */
+  double flop_w_executed; /* float64 flop actually executed by the last lrs_solve_w (GEMM, TRSM, LU) */
 } lrs_stats_t;
 
 /* Last error message of the calling thread ("" if none). */

@@ -101,6 +101,7 @@ int dgemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double al
                   long long stride_b, const double* cs, double beta, double* c, int ldc, long long stride_c,
                   int batch) {
   if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
+  ctx->fp64_flops += 2.0 * m * (double)n * (k > 0 ? k : 0) * batch;
   dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch);
   if (k <= 0) k = 0;
   BatchStrides bs;
@@ -436,6 +437,8 @@ int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status) {
   for (int j0 = 0; j0 < n; j0 += NB) {
     int jb = std::min(NB, n - j0);
     bool used = false;
+    // panel rank-1 updates plus the triangular solve of the U row block
+    ctx->fp64_flops += (double)(n - j0) * jb * jb + (double)jb * jb * (n - j0 - jb);
     LRS_TRY(launch_panel_cluster(ctx, A, n, j0, jb, ipiv, status, &used));
     if (!used) {
       lu_panel_kernel<<<1, 1024, 0, ctx->stream>>>(A, n, n, j0, jb, ipiv, status);
@@ -567,6 +570,7 @@ int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double*
   laswp_kernel<<<(nrhs + 255) / 256, 256, 0, ctx->stream>>>(B, ldb, nrhs, ipiv, 0, n, nrhs, 0);
   LRS_TRY(after_launch(ctx, "laswp_kernel"));
   const int tgrid = (nrhs + TA_COLS - 1) / TA_COLS;
+  ctx->fp64_flops += 2.0 * 2.0 * NB * (double)n * nrhs;   // diagonal-block products, both sweeps
   for (int b = 0; b < nblk; ++b) {
     const int j0 = b * NB, jb = std::min(NB, n - j0);
     trsm_apply_kernel<<<tgrid, 256, 0, ctx->stream>>>(linv + (size_t)b * NB * NB, jb, B + (size_t)j0 * ldb, ldb,

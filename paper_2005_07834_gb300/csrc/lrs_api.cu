@@ -181,7 +181,9 @@ extern "C" {
 
 const char* lrs_last_error(void) { return g_last_error.c_str(); }
 
-const char* lrs_version(void) { return "lrs 0.1 (sm_103a)"; }
+// The chi0 tensor-core kernel revision lets measurements quote profiler
+// counters only for the kernel version they were taken on.
+const char* lrs_version(void) { return "lrs 0.2 (sm_103a) chi0-tc r1"; }
 
 int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   clear_error();
@@ -618,6 +620,7 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
     if (!ctx->sites[i].has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", i);
   LRS_TRY(stage_begin(ctx, ST_W));
   double flop = 0;
+  const double fp64_before = ctx->fp64_flops;
   for (int i : list) {
     Site& s = ctx->sites[i];
     LRS_TRY(dyson_solve(ctx, s));
@@ -626,6 +629,7 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   }
   LRS_TRY(stage_end(ctx, ST_W));
   ctx->stats.flop_w = flop;
+  ctx->stats.flop_w_executed = ctx->fp64_flops - fp64_before;
   if (ctx->capturing) return LRS_OK;   // checked after each replay by lrs_graph_launch's caller
   // zero pivots / non-finite values are reported through the status word
   int status[16] = {0};

@@ -177,6 +177,7 @@ struct lrs_ctx {
   cudaGraphExec_t graph_exec = nullptr;        // recorded multi-site build
 
   lrs_stats_t stats{};
+  double fp64_flops = 0;               // running count of FP64 flop issued by the linear algebra
   // stage timing events: [stage][0=start,1=end]
   cudaEvent_t ev[6][2] = {};
   bool ev_pending[6] = {};
