@@ -270,7 +270,10 @@ int lrs_solve_w_static(int npts, int lmax, const double* pts_dev, const double* 
  * eagerly (allocating every buffer and checking the status words), then
  * records it.  lrs_graph_launch replays it asynchronously on the context
  * stream, recomputing chi0 and W of those sites from the resident orbitals;
- * status words are not read during replays (call lrs_synchronize).
+ * status words are not read during replays (call lrs_synchronize).  The
+ * recording is dropped (lrs_graph_launch then fails with LRS_ERR_STATE) when
+ * a later call frees or replaces workspace memory it reads, or changes the
+ * multi-site unit table; capture again after such calls.
  * Errors: LRS_ERR_STATE, plus those of the stages.
  */
 int lrs_graph_capture(lrs_ctx* ctx, int nsite, const int* sites);

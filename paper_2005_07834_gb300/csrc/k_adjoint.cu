@@ -200,23 +200,15 @@ __global__ void scatter_energy_kernel(const double* __restrict__ ge, int Ko, int
   else out[col_u[j - Ko]] = ge[j];
 }
 
-int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w, const double* grad_chi0, double* grad_e,
-                  double2* grad_psi) {
-  const int n = s.npts, Ko = ctx->Ko, Ku = ctx->Ku, K = Ko + Ku, nf = ctx->nf;
+// G_S = (2/pi)(G + G^T), G = Q W^T G_W W^T Q + dL/dchi0, into ws.gamma_s.
+int gamma_s_build(lrs_ctx* ctx, Site& s, const double* grad_w, const double* grad_chi0) {
+  const int n = s.npts;
   const size_t nn = (size_t)n * n;
   Workspace& ws = ctx->ws;
   LRS_TRY(ensure(ctx, ws.gamma_s, nn));
-  LRS_TRY(ensure(ctx, ws.gbuf_o, nn));
-  LRS_TRY(ensure(ctx, ws.gbuf_u, nn));
-  LRS_TRY(ensure(ctx, ws.ybuf, 2 * (size_t)n * K));
-  LRS_TRY(ensure(ctx, ws.gpsi, (size_t)n * K));
-  LRS_TRY(ensure(ctx, ws.ge, (size_t)K));
-  LRS_TRY(ensure(ctx, ws.tmp_nn, 2 * nn));
-  // denominators of the current quadrature (held fixed)
-  LRS_TRY(build_denominators(ctx));
-  // G_S
   double* T = nullptr;
   if (grad_w) {
+    LRS_TRY(ensure(ctx, ws.tmp_nn, 2 * nn));
     double* T1 = ws.tmp_nn.ptr;
     T = ws.tmp_nn.ptr + nn;
     LRS_TRY(dgemm_t(ctx, false, true, n, n, n, 1.0, grad_w, n, nullptr, s.w.ptr, n, nullptr, 0.0, T1, n));
@@ -224,7 +216,23 @@ int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w, const double* gra
   }
   dim3 g2((n + 127) / 128, n);
   gamma_s_kernel<<<g2, 128, 0, ctx->stream>>>(T, grad_chi0, s.wts.ptr, n, ws.gamma_s.ptr);
-  LRS_TRY(after_launch(ctx, "gamma_s_kernel"));
+  return after_launch(ctx, "gamma_s_kernel");
+}
+
+int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w, const double* grad_chi0, double* grad_e,
+                  double2* grad_psi) {
+  if (ctx->precision != LRS_FP64) return backward_site_mixed(ctx, s, grad_w, grad_chi0, grad_e, grad_psi);
+  const int n = s.npts, Ko = ctx->Ko, Ku = ctx->Ku, K = Ko + Ku, nf = ctx->nf;
+  const size_t nn = (size_t)n * n;
+  Workspace& ws = ctx->ws;
+  LRS_TRY(ensure(ctx, ws.gbuf_o, nn));
+  LRS_TRY(ensure(ctx, ws.gbuf_u, nn));
+  LRS_TRY(ensure(ctx, ws.ybuf, 2 * (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.gpsi, (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.ge, (size_t)K));
+  // denominators of the current quadrature (held fixed)
+  LRS_TRY(build_denominators(ctx));
+  LRS_TRY(gamma_s_build(ctx, s, grad_w, grad_chi0));
   LRS_CUDA_TRY(cudaMemsetAsync(ws.gpsi.ptr, 0, (size_t)n * K * sizeof(double2), ctx->stream));
   LRS_CUDA_TRY(cudaMemsetAsync(ws.ge.ptr, 0, (size_t)K * sizeof(double), ctx->stream));
   double2* go = ws.gbuf_o.ptr;
@@ -257,13 +265,20 @@ int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w, const double* gra
                                                           ws.ge.ptr + Ko);
     LRS_TRY(after_launch(ctx, "grad_accum_kernel"));
   }
+  return scatter_gradients(ctx, n, gpo, gpu, ws.ge.ptr, grad_e, grad_psi);
+}
+
+// Internal (occupied | unoccupied) gradient columns to the public (k, band) order.
+int scatter_gradients(lrs_ctx* ctx, int n, const double2* gpo, const double2* gpu, const double* ge,
+                      double* grad_e, double2* grad_psi) {
+  const int Ko = ctx->Ko, Ku = ctx->Ku, K = Ko + Ku;
   const int ncol = ctx->nk * ctx->nb;
   dim3 gs((K + 255) / 256, n);
   scatter_grad_kernel<<<gs, 256, 0, ctx->stream>>>(gpo, gpu, n, Ko, Ku, ctx->d_col_o.ptr, ctx->d_col_u.ptr, ncol,
                                                    grad_psi);
   LRS_TRY(after_launch(ctx, "scatter_grad_kernel"));
-  scatter_energy_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ws.ge.ptr, Ko, Ku, ctx->d_col_o.ptr,
-                                                                   ctx->d_col_u.ptr, grad_e);
+  scatter_energy_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ge, Ko, Ku, ctx->d_col_o.ptr, ctx->d_col_u.ptr,
+                                                                   grad_e);
   return after_launch(ctx, "scatter_energy_kernel");
 }
 

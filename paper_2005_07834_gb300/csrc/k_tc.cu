@@ -256,6 +256,9 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
     t.unit0 = (int)units;
     t.m_tiles = np / TILE_M;
     t.n_tiles = np / TN;
+    t.ldc = np;
+    t.m_valid = np;
+    t.n_valid = np;
     t.np = np;
     t.a_row0 = (int)ra;
     t.b_row0 = (int)rb;
@@ -279,6 +282,7 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
                     std::memcmp(ctx->site_tiles_dev.data() + toff, table.data(), ns * sizeof(SiteTile)) == 0;
   if (!same) {
     if (ctx->capturing) return set_error(LRS_ERR_STATE, "site table changed during graph capture");
+    drop_graph(ctx);   // a recorded build reads this table
     LRS_CUDA_TRY(cudaMemcpyAsync(ctx->ws.site_tiles.ptr + toff, table.data(), ns * sizeof(SiteTile),
                                  cudaMemcpyHostToDevice, ctx->stream));
     LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -418,6 +422,257 @@ int project_mixed(lrs_ctx* ctx, Site& s) {
     uo += ctx->nb - ctx->nocc[k];
   }
   return launch_tc<PROJ_TN, 1, FMT, ProjStore>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<project>");
+}
+
+}  // namespace lrs
+
+// ============================================================================
+// Adjoint on the tensor cores (mixed precisions).  Same mathematics as the
+// float64 adjoint (k_adjoint.cu): per frequency the Green's functions are
+// recomputed with the chi0 operand planes and stored as fp32 (GStore), then
+//   Ho = W_f G_S o Gu^T,  Hu = W_f G_S o Go   (bf16 hi/lo planes, and their transposes)
+//   Yo = Ho psi_o, Zo = Ho^T conj psi_o, Yu = Hu conj psi_u, Zu = Hu^T psi_u
+// run as one tensor-core launch with four problems (ZStore), and the
+// gradients accumulate over frequencies in float64.
+// ============================================================================
+namespace lrs {
+
+// Transposed orbital planes for the B operand of the Y/Z products.  Rows:
+// [psi_o^T | conj psi_o^T | conj psi_u^T | psi_u^T] (band rows, padded to
+// 128 per block), K = grid point.  blockIdx.z: 0 occupied, 1 unoccupied.
+__global__ void psiT_prep_kernel(const double2* __restrict__ psi_o, int Ko, const double2* __restrict__ psi_u,
+                                 int Ku, int n, int Np, int Ko128, int Ku128, uint16_t* __restrict__ T,
+                                 size_t im_off) {
+  __shared__ float2 tile[32][33];
+  const bool occ = blockIdx.z == 0;
+  const int Kx = occ ? Ko : Ku, Kx128 = occ ? Ko128 : Ku128;
+  const double2* psi = occ ? psi_o : psi_u;
+  const int p0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  if (b0 >= Kx128) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    const int p = p0 + i, b = b0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (p < n && b < Kx) {
+      const double2 d = psi[(size_t)p * Kx + b];
+      v = make_float2((float)d.x, (float)d.y);
+    }
+    tile[i][tx] = v;
+  }
+  __syncthreads();
+  const size_t ld = 2 * (size_t)Np;
+  const int rplain = occ ? 0 : 2 * Ko128 + Ku128;
+  const int rconj = occ ? Ko128 : 2 * Ko128;
+  for (int i = ty; i < 32; i += 8) {
+    const int b = b0 + i, p = p0 + tx;
+    if (p >= Np) continue;
+    const float2 v = tile[tx][i];
+    uint16_t* rp = T + (size_t)(rplain + b) * ld;
+    uint16_t* rc = T + (size_t)(rconj + b) * ld;
+    put_split<1>(rp, p, v.x);
+    put_split<1>(rp + im_off, p, v.y);
+    put_split<1>(rc, p, v.x);
+    put_split<1>(rc + im_off, p, -v.y);
+  }
+}
+
+// H planes for one frequency: rows [Ho | Ho^T | Hu | Hu^T] (Np each), K = grid point.
+__global__ void hprep_kernel(const float2* __restrict__ go, const float2* __restrict__ gu,
+                             const double* __restrict__ gs, int n, int Np, double wf, uint16_t* __restrict__ H,
+                             size_t im_off) {
+  __shared__ float2 to[32][33], tu[32][33];
+  const int q0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const size_t ld = 2 * (size_t)Np;
+  for (int i = ty; i < 32; i += 8) {
+    const int p = p0 + i, q = q0 + tx;
+    float2 ho = make_float2(0.f, 0.f), hu = make_float2(0.f, 0.f);
+    if (p < n && q < n) {
+      const float g = (float)(wf * gs[(size_t)p * n + q]);
+      const float2 a = go[(size_t)p * Np + q], b = gu[(size_t)p * Np + q];
+      ho = make_float2(g * b.x, g * b.y);
+      hu = make_float2(g * a.x, g * a.y);
+    }
+    to[i][tx] = ho;
+    tu[i][tx] = hu;
+    uint16_t* r0 = H + (size_t)p * ld;                    // Ho row p, K = q
+    uint16_t* r2 = H + (size_t)(2 * Np + p) * ld;         // Hu row p
+    put_split<1>(r0, q, ho.x);
+    put_split<1>(r0 + im_off, q, ho.y);
+    put_split<1>(r2, q, hu.x);
+    put_split<1>(r2 + im_off, q, hu.y);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int q = q0 + i, p = p0 + tx;                    // transposed: row q, K = p
+    const float2 ho = to[tx][i], hu = tu[tx][i];
+    uint16_t* r1 = H + (size_t)(Np + q) * ld;
+    uint16_t* r3 = H + (size_t)(3 * Np + q) * ld;
+    put_split<1>(r1, p, ho.x);
+    put_split<1>(r1 + im_off, p, ho.y);
+    put_split<1>(r3, p, hu.x);
+    put_split<1>(r3 + im_off, p, hu.y);
+  }
+}
+
+__device__ __forceinline__ double2 zmul64(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Same update as the float64 adjoint's grad_accum_kernel, from fp32 Y, Z.
+template <bool kOcc>
+__global__ void grad_accum32_kernel(const double2* __restrict__ psi, const float2* __restrict__ Y,
+                                    const float2* __restrict__ Z, const double2* __restrict__ d,
+                                    const double* __restrict__ w, int n, int K, double2* __restrict__ gpsi,
+                                    double* __restrict__ ge) {
+  const int b = blockIdx.x;
+  const double2 db = d[b];
+  double er = 0.0, ei = 0.0;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const size_t ix = (size_t)p * K + b;
+    const float2 yf = Y[ix], zf = Z[ix];
+    const double2 y = make_double2(yf.x, yf.y), z = make_double2(zf.x, zf.y), ps = psi[ix];
+    const double2 dy = zmul64(db, y), dz = zmul64(db, z);
+    double2 g = gpsi[ix];
+    g.x += dy.x + dz.x;
+    g.y += kOcc ? (dy.y - dz.y) : (-dy.y + dz.y);
+    gpsi[ix] = g;
+    const double2 t = kOcc ? zmul64(make_double2(ps.x, -ps.y), y) : zmul64(ps, y);
+    er += t.x;
+    ei += t.y;
+  }
+  __shared__ double sr[32], si[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    er += __shfl_down_sync(0xffffffffu, er, o);
+    ei += __shfl_down_sync(0xffffffffu, ei, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = er; si[threadIdx.x >> 5] = ei; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { er += sr[i]; ei += si[i]; }
+    const double2 d2 = zmul64(db, db);
+    ge[b] += (er * d2.x - ei * d2.y) / w[b];
+  }
+}
+
+int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w, const double* grad_chi0, double* grad_e,
+                        double2* grad_psi) {
+  const int n = s.npts, nf = ctx->nf, Ko = ctx->Ko, Ku = ctx->Ku, K = Ko + Ku;
+  const int Np = round_up(n, TILE_M);
+  const int Kop = round_up(Ko, 32), Kup = round_up(Ku, 32), Kp = Kop + Kup;
+  const int Ko128 = round_up(Ko, 128), Ku128 = round_up(Ku, 128);
+  const int RB = 2 * Ko128 + 2 * Ku128;
+  const size_t ldg = 2 * (size_t)Kp, ldn = 2 * (size_t)Np;
+  Workspace& ws = ctx->ws;
+  if (ctx->capturing) return set_error(LRS_ERR_STATE, "the adjoint cannot be recorded in a graph");
+  LRS_TRY(build_denominators(ctx));
+  LRS_TRY(gamma_s_build(ctx, s, grad_w, grad_chi0));
+  LRS_TRY(ensure(ctx, ws.planes_a, 2 * (size_t)nf * Np * ldg));
+  LRS_TRY(ensure(ctx, ws.planes_b, 2 * (size_t)Np * ldg));
+  LRS_TRY(ensure(ctx, ws.planes_t, 2 * (size_t)RB * ldn));
+  LRS_TRY(ensure(ctx, ws.planes_h, 2 * (size_t)4 * Np * ldn));
+  LRS_TRY(ensure(ctx, ws.g32, 2 * (size_t)Np * Np));
+  LRS_TRY(ensure(ctx, ws.yz32, 2 * (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.gpsi, (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.ge, (size_t)K));
+  LRS_TRY(ensure(ctx, ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * 128));
+  LRS_TRY(ensure(ctx, ws.adj_tiles, (size_t)nf + 4));
+  LRS_CUDA_TRY(cudaMemsetAsync(ws.gpsi.ptr, 0, (size_t)n * K * sizeof(double2), ctx->stream));
+  LRS_CUDA_TRY(cudaMemsetAsync(ws.ge.ptr, 0, (size_t)K * sizeof(double), ctx->stream));
+  // operands of the Green's functions (all frequencies) and of the Y/Z products
+  dim3 pg((Kp + 127) / 128, Np);
+  chi0_prep_kernel<1><<<pg, 128, 0, ctx->stream>>>(s.psi_o.ptr, Ko, s.psi_u.ptr, Ku, n, Np, Kop, Kp,
+                                                    ws.denom_o.ptr, ws.denom_u.ptr, nf, nullptr, ws.planes_a.ptr,
+                                                    (size_t)nf * Np * ldg, ws.planes_b.ptr, (size_t)Np * ldg);
+  LRS_TRY(after_launch(ctx, "chi0_prep_kernel"));
+  dim3 tg(Np / 32, std::max(Ko128, Ku128) / 32, 2);
+  psiT_prep_kernel<<<tg, dim3(32, 8), 0, ctx->stream>>>(s.psi_o.ptr, Ko, s.psi_u.ptr, Ku, n, Np, Ko128, Ku128,
+                                                        ws.planes_t.ptr, (size_t)RB * ldn);
+  LRS_TRY(after_launch(ctx, "psiT_prep_kernel"));
+  // unit tables: nf single-frequency Green's-function problems, then the four Y/Z products
+  std::vector<SiteTile> tbl(nf + 4);
+  for (int f = 0; f < nf; ++f) {
+    SiteTile& t = tbl[f];
+    t.unit0 = 0;
+    t.m_tiles = Np / TILE_M;
+    t.n_tiles = Np / 128;
+    t.np = Np;
+    t.a_row0 = f * Np;
+    t.b_row0 = 0;
+    t.slab0 = 0;
+    t.ldc = Np;
+    t.m_valid = Np;
+    t.n_valid = Np;
+  }
+  const int kx[4] = {Ko, Ko, Ku, Ku}, kx128[4] = {Ko128, Ko128, Ku128, Ku128};
+  const int brow[4] = {0, Ko128, 2 * Ko128, 2 * Ko128 + Ku128};
+  const long long yoff[4] = {0, (long long)n * Ko, 2LL * n * Ko, 2LL * n * Ko + (long long)n * Ku};
+  int units = 0;
+  for (int j = 0; j < 4; ++j) {
+    SiteTile& t = tbl[nf + j];
+    t.unit0 = units;
+    t.m_tiles = Np / TILE_M;
+    t.n_tiles = kx128[j] / 128;
+    t.np = Np;
+    t.a_row0 = j * Np;
+    t.b_row0 = brow[j];
+    t.slab0 = yoff[j];
+    t.ldc = kx[j];
+    t.m_valid = n;
+    t.n_valid = kx[j];
+    units += t.m_tiles * t.n_tiles;
+  }
+  LRS_CUDA_TRY(cudaMemcpyAsync(ws.adj_tiles.ptr, tbl.data(), tbl.size() * sizeof(SiteTile), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  CUtensorMap ma_g, mb_g, ma_h, mb_t;
+  LRS_TRY(make_operand_map(&ma_g, ws.planes_a.ptr, ldg, 2 * (uint64_t)nf * Np, TILE_M));
+  LRS_TRY(make_operand_map(&mb_g, ws.planes_b.ptr, ldg, 2 * (uint64_t)Np, 128));
+  LRS_TRY(make_operand_map(&ma_h, ws.planes_h.ptr, ldn, 2 * (uint64_t)4 * Np, TILE_M));
+  LRS_TRY(make_operand_map(&mb_t, ws.planes_t.ptr, ldn, 2 * (uint64_t)RB, 128));
+  float2* go = ws.g32.ptr;
+  float2* gu = ws.g32.ptr + (size_t)Np * Np;
+  float2* Y = ws.yz32.ptr;
+  GStore gst{go, gu, ws.tc_scratch.ptr, 128};
+  ZStore zst{Y};
+  for (int f = 0; f < nf; ++f) {
+    TcShape sg{};
+    sg.batches = 1;
+    sg.nchunk = Kp / 32;
+    sg.nchunk0 = Kop / 32;
+    sg.seg = ctx->seg_chunks;
+    sg.a_im_rows = nf * Np;
+    sg.b_im_rows = Np;
+    sg.units = (Np / TILE_M) * (Np / 128);
+    sg.sites = ws.adj_tiles.ptr + f;
+    sg.nsites = 1;
+    LRS_TRY((launch_tc<128, 2, 1, GStore>(ctx, ma_g, mb_g, sg, gst, "zgemm_tc_kernel<green>")));
+    dim3 hg(Np / 32, Np / 32);
+    hprep_kernel<<<hg, dim3(32, 8), 0, ctx->stream>>>(go, gu, ws.gamma_s.ptr, n, Np, ctx->W[f], ws.planes_h.ptr,
+                                                      (size_t)4 * Np * ldn);
+    LRS_TRY(after_launch(ctx, "hprep_kernel"));
+    TcShape sy{};
+    sy.batches = 1;
+    sy.nchunk = Np / 32;
+    sy.nchunk0 = sy.nchunk;
+    sy.seg = ctx->seg_chunks;
+    sy.a_im_rows = 4 * Np;
+    sy.b_im_rows = RB;
+    sy.units = units;
+    sy.sites = ws.adj_tiles.ptr + nf;
+    sy.nsites = 4;
+    LRS_TRY((launch_tc<128, 1, 1, ZStore>(ctx, ma_h, mb_t, sy, zst, "zgemm_tc_kernel<adjoint>")));
+    const double2* dof = ws.denom_o.ptr + (size_t)f * Ko;
+    const double2* duf = ws.denom_u.ptr + (size_t)f * Ku;
+    grad_accum32_kernel<true><<<Ko, 256, 0, ctx->stream>>>(s.psi_o.ptr, Y + yoff[0], Y + yoff[1], dof, ctx->w_o.ptr,
+                                                           n, Ko, ws.gpsi.ptr, ws.ge.ptr);
+    LRS_TRY(after_launch(ctx, "grad_accum32_kernel"));
+    grad_accum32_kernel<false><<<Ku, 256, 0, ctx->stream>>>(s.psi_u.ptr, Y + yoff[2], Y + yoff[3], duf,
+                                                            ctx->w_u.ptr, n, Ku, ws.gpsi.ptr + (size_t)n * Ko,
+                                                            ws.ge.ptr + Ko);
+    LRS_TRY(after_launch(ctx, "grad_accum32_kernel"));
+  }
+  return scatter_gradients(ctx, n, ws.gpsi.ptr, ws.gpsi.ptr + (size_t)n * Ko, ws.ge.ptr, grad_e, grad_psi);
 }
 
 }  // namespace lrs

@@ -44,21 +44,45 @@ int dev_alloc_bytes(lrs_ctx* ctx, void** p, size_t bytes) {
   return LRS_OK;
 }
 
+void drop_graph(lrs_ctx* ctx) {
+  if (!ctx->graph_exec) return;
+  cudaGraphExecDestroy(ctx->graph_exec);
+  ctx->graph_exec = nullptr;
+}
+
 void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes) {
   if (!p) return;
+  drop_graph(ctx);
   cudaFree(p);
   ctx->stats.device_bytes -= (int64_t)bytes;
 }
 
+// A top-level stage starts a new measurement; ST_CHI0_MAIN intervals add up
+// until the next ST_CHI0 begins.
 int stage_begin(lrs_ctx* ctx, Stage s) {
   if (ctx->capturing) return LRS_OK;   // stage timings are not part of a recorded graph
-  LRS_CUDA_TRY(cudaEventRecord(ctx->ev[s][0], ctx->stream));
+  if (s != ST_CHI0_MAIN) ctx->ev_used[s] = 0;
+  if (s == ST_CHI0) ctx->ev_used[ST_CHI0_MAIN] = 0;
+  const size_t i = ctx->ev_used[s];
+  if (i >= ctx->ev_begin[s].size()) {
+    cudaEvent_t b = nullptr, e = nullptr;
+    LRS_CUDA_TRY(cudaEventCreate(&b));
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) {
+      cudaEventDestroy(b);
+      return set_error(LRS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(err));
+    }
+    ctx->ev_begin[s].push_back(b);
+    ctx->ev_end[s].push_back(e);
+  }
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_begin[s][i], ctx->stream));
   return LRS_OK;
 }
 
 int stage_end(lrs_ctx* ctx, Stage s) {
   if (ctx->capturing) return LRS_OK;
-  LRS_CUDA_TRY(cudaEventRecord(ctx->ev[s][1], ctx->stream));
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_end[s][ctx->ev_used[s]], ctx->stream));
+  ++ctx->ev_used[s];
   ctx->ev_pending[s] = true;
   return LRS_OK;
 }
@@ -170,6 +194,8 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
   release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.tc_scratch); release(ctx, w.slab64);
   release(ctx, w.site_tiles);
+  release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
+  release(ctx, w.adj_tiles);
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
 
@@ -206,12 +232,6 @@ int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   ctx->precision = precision;
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->num_sms = prop.multiProcessorCount;
-  for (int s = 0; s < 6; ++s)
-    for (int j = 0; j < 2; ++j)
-      if (cudaEventCreate(&ctx->ev[s][j]) != cudaSuccess) {
-        delete ctx;
-        return set_error(LRS_ERR_CUDA, "cudaEventCreate failed");
-      }
   int rc = ensure(ctx, ctx->ws.status, 64);
   if (rc) { delete ctx; return rc; }
   cudaMemsetAsync(ctx->ws.status.ptr, 0, 64 * sizeof(int), ctx->stream);
@@ -234,9 +254,10 @@ int lrs_destroy(lrs_ctx* ctx) {
   release(ctx, ctx->d_col_o); release(ctx, ctx->d_col_u);
   free_workspace(ctx);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
-  for (int s = 0; s < 6; ++s)
-    for (int j = 0; j < 2; ++j)
-      if (ctx->ev[s][j]) cudaEventDestroy(ctx->ev[s][j]);
+  for (int s = 0; s < 6; ++s) {
+    for (cudaEvent_t e : ctx->ev_begin[s]) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->ev_end[s]) cudaEventDestroy(e);
+  }
   delete ctx;
   return LRS_OK;
 }
@@ -844,8 +865,12 @@ int lrs_synchronize(lrs_ctx* ctx) {
   }
   for (int s = 0; s < 6; ++s)
     if (ctx->ev_pending[s]) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ctx->ev[s][0], ctx->ev[s][1]) == cudaSuccess) ctx->ms_acc[s] = ms;
+      double sum = 0.0;
+      for (int i = 0; i < ctx->ev_used[s]; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_begin[s][i], ctx->ev_end[s][i]) == cudaSuccess) sum += ms;
+      }
+      ctx->ms_acc[s] = sum;
       ctx->ev_pending[s] = false;
     }
   ctx->stats.ms_project = ctx->ms_acc[ST_PROJECT];

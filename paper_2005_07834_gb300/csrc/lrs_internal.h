@@ -42,7 +42,10 @@ struct DevBuf {
 };
 
 int dev_alloc_bytes(lrs_ctx* ctx, void** p, size_t bytes);
+// Frees workspace memory; a recorded graph (which may read it) is dropped.
 void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes);
+// Drops the recorded multi-site graph, if any.
+void drop_graph(lrs_ctx* ctx);
 
 template <typename T>
 int ensure(lrs_ctx* ctx, DevBuf<T>& b, size_t count) {
@@ -99,6 +102,9 @@ struct SiteTile {
   int a_row0;        // first row of the site's A planes
   int b_row0;        // first row of the site's B planes
   long long slab0;   // first element of the site's output slab
+  int ldc;           // leading dimension of the output (np for chi0 slabs)
+  int m_valid;       // rows of the output that exist (stores beyond are skipped)
+  int n_valid;       // columns of the output that exist
 };
 
 // Unit direction and radius of a grid point.
@@ -128,6 +134,12 @@ struct Workspace {
   DevBuf<float> tc_scratch;             // chi0: per-CTA parked occupied sums
   DevBuf<double> slab64;                // FP64 chi0: [nf][n][n] per-frequency W_f Re[Go o Gu^T]
   DevBuf<SiteTile> site_tiles;          // multi-site chi0 unit table
+  // tensor-core adjoint
+  DevBuf<uint16_t> planes_t;            // transposed orbital planes (B of the Y/Z products)
+  DevBuf<uint16_t> planes_h;            // H, H^T planes of one frequency (A of the Y/Z products)
+  DevBuf<float2> g32;                   // Go, Gu^T of one frequency
+  DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
+  DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<uint16_t> proj_a, proj_b;      // projection: phase planes, coefficient planes
   DevBuf<float> scales;                 // chi0: fp16 operand scales per frequency
   DevBuf<float> proj_scale;             // projection: coefficient scale and unscale
@@ -178,8 +190,10 @@ struct lrs_ctx {
 
   lrs_stats_t stats{};
   double fp64_flops = 0;               // running count of FP64 flop issued by the linear algebra
-  // stage timing events: [stage][0=start,1=end]
-  cudaEvent_t ev[6][2] = {};
+  // stage timing: event pairs of the stage's intervals since its last reset
+  // (the main chi0 kernel runs once per workspace group of one build)
+  std::vector<cudaEvent_t> ev_begin[6], ev_end[6];
+  int ev_used[6] = {};
   bool ev_pending[6] = {};
   double ms_acc[6] = {};
 };
@@ -229,8 +243,13 @@ int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double*
 int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);
 int dyson_solve_lm(lrs_ctx* ctx, Site& s);
 
-// Adjoint (k_adjoint.cu)
+// Adjoint (k_adjoint.cu: float64; k_tc.cu: tensor-core version for the mixed precisions)
 int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev,
                   double* grad_e_dev, double2* grad_psi_dev);
+int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev,
+                        double* grad_e_dev, double2* grad_psi_dev);
+int gamma_s_build(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev);
+int scatter_gradients(lrs_ctx* ctx, int n, const double2* gpo, const double2* gpu, const double* ge,
+                      double* grad_e, double2* grad_psi);
 
 }  // namespace lrs

@@ -57,6 +57,7 @@ struct Unit {
   int site;
   long long slab0;   // output offset of the site (multi-site launches)
   int ld;            // output leading dimension (multi-site launches)
+  int m_valid, n_valid;   // extent of the output (multi-site launches)
 };
 
 // Units of a launch.  With a site table the units of all sites are numbered
@@ -83,7 +84,9 @@ __device__ __forceinline__ Unit decode_unit(const TcShape& sh, const SiteTile* _
     x.yb = st.b_row0 + x.tn * TN;
     x.site = lo;
     x.slab0 = st.slab0;
-    x.ld = st.np;
+    x.ld = st.ldc;
+    x.m_valid = st.m_valid;
+    x.n_valid = st.n_valid;
   } else {
     x.b = u % sh.batches;
     const int t = u / sh.batches;
@@ -94,6 +97,8 @@ __device__ __forceinline__ Unit decode_unit(const TcShape& sh, const SiteTile* _
     x.site = 0;
     x.slab0 = 0;
     x.ld = sh.m_tiles * TILE_M;
+    x.m_valid = x.ld;
+    x.n_valid = sh.n_tiles * TN;
   }
   return x;
 }
@@ -400,6 +405,56 @@ struct Chi0Store {
       v.w = fmaf(-m.w, s[1][i + 3], r.w * s[0][i + 3]);
       *reinterpret_cast<float4*>(dst + i) = v;
     }
+  }
+};
+
+// Adjoint: the Green's functions themselves, Go and Gu^T of one frequency,
+// as complex fp32 [np][np] (ld = unit.ld).
+struct GStore {
+  float2* go;
+  float2* gu;
+  float* scratch;   // [gridDim.x][2][128][tile_n]
+  int tile_n;
+  template <int COLS>
+  __device__ void save_phase0(const float (&s)[2][COLS], int lrow, int lcol0) const {
+    float* base = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
+#pragma unroll
+    for (int part = 0; part < 2; ++part)
+#pragma unroll
+      for (int i = 0; i < COLS; i += 4)
+        *reinterpret_cast<float4*>(base + (size_t)part * 128 * tile_n + i) =
+            make_float4(s[part][i], s[part][i + 1], s[part][i + 2], s[part][i + 3]);
+  }
+  template <int COLS>
+  __device__ void store(const float (&s)[2][COLS], const Unit& x, int row, int lrow, int col0, int lcol0) const {
+    const float* g0 = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
+    float2* po = go + x.slab0 + (size_t)row * x.ld + col0;
+    float2* pu = gu + x.slab0 + (size_t)row * x.ld + col0;
+#pragma unroll
+    for (int i = 0; i < COLS; i += 2) {
+      const float2 r = *reinterpret_cast<const float2*>(g0 + i);
+      const float2 m = *reinterpret_cast<const float2*>(g0 + (size_t)128 * tile_n + i);
+      *reinterpret_cast<float4*>(po + i) = make_float4(r.x, m.x, r.y, m.y);
+      *reinterpret_cast<float4*>(pu + i) = make_float4(s[0][i], s[1][i], s[0][i + 1], s[1][i + 1]);
+    }
+  }
+};
+
+// Adjoint: a plain complex product D (fp32 re, im) into out + unit.slab0,
+// rows < m_valid, columns < n_valid.
+struct ZStore {
+  float2* out;
+  template <int COLS>
+  __device__ void save_phase0(const float (&)[2][COLS], int, int) const {}
+  template <int COLS>
+  __device__ void store(const float (&s)[2][COLS], const Unit& x, int row, int lrow, int col0, int lcol0) const {
+    (void)lrow;
+    (void)lcol0;
+    if (row >= x.m_valid) return;
+    float2* dst = out + x.slab0 + (size_t)row * x.ld + col0;
+#pragma unroll
+    for (int i = 0; i < COLS; ++i)
+      if (col0 + i < x.n_valid) dst[i] = make_float2(s[0][i], s[1][i]);
   }
 };
 

@@ -3,7 +3,8 @@
 Loss L = q^T W q on the 260-point site, q ~ N(0,1) (seed 2).  Gradients of
 all 256 band energies and of the site-grid orbitals; mu and the quadrature
 are held fixed.  Tolerances: 1e-9 relative vs the oracle gradient, 1e-6
-relative (vector norm) vs central differences with h = 1e-6 Ha.
+relative (vector norm) vs central differences with h = 1e-6 Ha.  The
+tensor-core adjoint of a bf16x3 context is gated at the mixed-path 1e-5.
 """
 import numpy as np
 import pytest
@@ -156,4 +157,22 @@ def test_autograd_function(lrs, case):
     oe, op = oracle_grads(ref, gamma_w=np.outer(q, q))
     assert rel_fro(e.grad.numpy(), oe) < 1e-9
     assert rel_fro(psi.grad.numpy(), op) < 1e-9
+    scr.close()
+
+
+def test_mixed_adjoint_on_tensor_cores(lrs, case):
+    """bf16x3 context: Green's functions recomputed and H products on tcgen05, gradients in FP64."""
+    wl, ref, q = case
+    scr = lrs.Screening(0, "bf16x3")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(wl.nfreq, mu=ref.pr.mu, zeta=ref.pr.zeta)
+    scr.set_site_orbitals(0, public_psi(ref.pr))
+    scr.build_chi0()
+    scr.solve_w()
+    ge, gp = scr.backward(0, grad_w=np.outer(q, q))
+    oe, op = oracle_grads(ref, gamma_w=np.outer(q, q))
+    err_e, err_p = rel_fro(ge, oe), rel_fro(gp, op)
+    print(f"mixed adjoint vs oracle gradient: energies {err_e:.2e}, orbitals {err_p:.2e}")
+    assert err_e < 1e-5 and err_p < 1e-5   # mixed-path tolerance (measured 1.4e-6, 1.9e-6)
     scr.close()
