@@ -63,6 +63,10 @@ extern "C" {
 #define LRS_DYSON_AUTO    0   /* lm basis when the site grid is a radial x angular product that it shrinks */
 #define LRS_DYSON_FULL    1   /* LU on the full npts x npts grid matrix */
 #define LRS_DYSON_LM      2   /* LU in the (radial shell, l, m) basis (product grids only) */
+#define LRS_OPT_DYSON_SOLVER     6  /* value: LRS_SOLVER_AUTO, LRS_SOLVER_LU or LRS_SOLVER_SPD (lm basis) */
+#define LRS_SOLVER_AUTO   0   /* SPD inverse when every radial Coulomb block has a Cholesky factor, else LU */
+#define LRS_SOLVER_LU     1   /* LU with partial pivoting of I - C X, C as right-hand sides */
+#define LRS_SOLVER_SPD    2   /* Z = F (I - F^T X F)^-1 F^T with C = F F^T (LRS_ERR_STATE if C has no factor) */
 
 typedef struct lrs_ctx lrs_ctx;
 
@@ -110,7 +114,14 @@ int lrs_set_stream(lrs_ctx* ctx, void* stream);
  * p = shell * nang + angular point with the same angular set on every shell -
  * in the basis of radial shells x real spherical harmonics l <= L where the
  * multipole Coulomb operator is block diagonal (Sec. VI.E).  Both give the
- * same W up to rounding.  Errors: LRS_ERR_ARG (unknown option or value).
+ * same W up to rounding.  In the lm basis, with X = Y^T Q chi0 Q Y and the
+ * block-diagonal Coulomb matrix C, the Dyson equation reads (I - C X) Z = C.
+ * LRS_OPT_DYSON_SOLVER chooses LU with partial pivoting for it, or - since C
+ * is positive definite (C = F F^T, F its Cholesky factor per l) and chi0 is
+ * negative semidefinite - the symmetric form Z = F (I - F^T X F)^-1 F^T, whose
+ * matrix has every eigenvalue >= 1 and is inverted in place by blocked
+ * Gauss-Jordan steps without pivoting (n^3 instead of 8/3 n^3 flop).
+ * Errors: LRS_ERR_ARG (unknown option or value).
  */
 int lrs_set_option(lrs_ctx* ctx, int option, int value);
 

@@ -83,10 +83,35 @@ int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts) {
         const double lo = std::min(rad[j], rad[k]), hi = std::max(rad[j], rad[k]);
         rl[((size_t)l * nrad + j) * nrad + k] = 4.0 * pi / (2.0 * l + 1.0) * std::pow(lo / hi, l) / hi;
       }
+  // Cholesky factor of each radial block (positive definite: it is the
+  // Coulomb kernel of the l-th multipole on distinct radii)
+  std::vector<double> fl(rl.size(), 0.0);
+  bool spd = true;
+  for (int l = 0; l <= L && spd; ++l) {
+    const double* a = &rl[(size_t)l * nrad * nrad];
+    double* f = &fl[(size_t)l * nrad * nrad];
+    for (int j = 0; j < nrad && spd; ++j) {
+      for (int k = 0; k <= j; ++k) {
+        double t = a[(size_t)j * nrad + k];
+        for (int m = 0; m < k; ++m) t -= f[(size_t)j * nrad + m] * f[(size_t)k * nrad + m];
+        if (k == j) {
+          if (!(t > 0.0)) { spd = false; break; }
+          f[(size_t)j * nrad + j] = std::sqrt(t);
+        } else {
+          f[(size_t)j * nrad + k] = t / f[(size_t)k * nrad + k];
+        }
+      }
+    }
+  }
   LRS_TRY(ensure(ctx, s.yang, yang.size()));
   LRS_TRY(ensure(ctx, s.rl, rl.size()));
   LRS_CUDA_TRY(cudaMemcpy(s.yang.ptr, yang.data(), yang.size() * sizeof(double), cudaMemcpyHostToDevice));
   LRS_CUDA_TRY(cudaMemcpy(s.rl.ptr, rl.data(), rl.size() * sizeof(double), cudaMemcpyHostToDevice));
+  s.spd = spd;
+  if (spd) {
+    LRS_TRY(ensure(ctx, s.fl, fl.size()));
+    LRS_CUDA_TRY(cudaMemcpy(s.fl.ptr, fl.data(), fl.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   s.product = true;
   s.nrad = nrad;
   s.nang = nang;
@@ -125,6 +150,52 @@ __global__ void lm_coulomb_kernel(const double* __restrict__ rl, int nrad, int L
   Cm[(size_t)row * r + col] = v;
 }
 
+// Radial-block products on the (j, lm) index, F given per l as [nrad][nrad]:
+//   left:  out[(j,lm), c] = add_i delta + alpha sum_j' f_l(j, j') in[(j',lm), c]
+//   right: out[c, (j,lm)] = add_i delta + alpha sum_j' in[c, (j',lm)] f_l(j', j)
+// with f_l(a, b) = F_l[b][a] when TF, else F_l[a][b].  SYM_IN reads `in` from
+// its lower triangle only (a symmetric matrix stored that way).
+template <bool TF, bool SYM_IN>
+__global__ void lm_left_kernel(const double* __restrict__ in, const double* __restrict__ F, int nrad, int L2,
+                               double alpha, double add_i, double* __restrict__ out) {
+  const int r = nrad * L2;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (col >= r || row >= r) return;
+  const int j = row / L2, lm = row % L2;
+  int l = 0;
+  while ((l + 1) * (l + 1) <= lm) ++l;
+  const double* f = F + (size_t)l * nrad * nrad;
+  double s = 0.0;
+  for (int jp = 0; jp < nrad; ++jp) {
+    const double c = TF ? f[(size_t)jp * nrad + j] : f[(size_t)j * nrad + jp];
+    const int src = jp * L2 + lm;
+    const double x = (!SYM_IN || src >= col) ? in[(size_t)src * r + col] : in[(size_t)col * r + src];
+    s = fma(c, x, s);
+  }
+  out[(size_t)row * r + col] = (row == col ? add_i : 0.0) + alpha * s;
+}
+
+template <bool TF>
+__global__ void lm_right_kernel(const double* __restrict__ in, const double* __restrict__ F, int nrad, int L2,
+                                double alpha, double add_i, double* __restrict__ out) {
+  const int r = nrad * L2;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;   // (j, lm)
+  const int row = blockIdx.y;
+  if (col >= r || row >= r) return;
+  const int j = col / L2, lm = col % L2;
+  int l = 0;
+  while ((l + 1) * (l + 1) <= lm) ++l;
+  const double* f = F + (size_t)l * nrad * nrad;
+  const double* x = in + (size_t)row * r + lm;
+  double s = 0.0;
+  for (int jp = 0; jp < nrad; ++jp) {
+    const double c = TF ? f[(size_t)j * nrad + jp] : f[(size_t)jp * nrad + j];
+    s = fma(x[(size_t)jp * L2], c, s);
+  }
+  out[(size_t)row * r + col] = (row == col ? add_i : 0.0) + alpha * s;
+}
+
 int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   const int n = s.npts, nrad = s.nrad, nang = s.nang;
   const int L2 = (s.lmax + 1) * (s.lmax + 1), r = nrad * L2;
@@ -144,13 +215,29 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   LRS_TRY(dgemm_batched(ctx, true, false, L2, r, nang, 1.0, Yang, L2, 0, s.wts.ptr, nang, T, r,
                         (long long)nang * r, nullptr, 0.0, X, r, (long long)L2 * r, nrad));
   dim3 g((r + 127) / 128, r);
-  lm_dyson_matrix_kernel<<<g, 128, 0, ctx->stream>>>(X, s.rl.ptr, nrad, L2, B);
-  LRS_TRY(after_launch(ctx, "lm_dyson_matrix_kernel"));
-  lm_coulomb_kernel<<<g, 128, 0, ctx->stream>>>(s.rl.ptr, nrad, L2, Z);
-  LRS_TRY(after_launch(ctx, "lm_coulomb_kernel"));
-  LRS_TRY(lu_factor(ctx, B, r, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));
-  LRS_TRY(ensure(ctx, ctx->ws.tinv, 2 * (size_t)((r + 31) / 32) * 32 * 32));
-  LRS_TRY(lu_solve_inv(ctx, B, r, ctx->ws.ipiv.ptr, Z, r, r, ctx->ws.tinv.ptr));
+  const bool use_spd = ctx->dyson_solver == LRS_SOLVER_SPD || (ctx->dyson_solver == LRS_SOLVER_AUTO && s.spd);
+  if (use_spd) {
+    if (!s.spd) return set_error(LRS_ERR_STATE, "SPD Dyson solver: a radial Coulomb block has no Cholesky factor");
+    // M = I - F^T X F (in Z), inverted in place; Z = F M^-1 F^T
+    lm_left_kernel<true, false><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, B);
+    LRS_TRY(after_launch(ctx, "lm_left_kernel"));
+    lm_right_kernel<false><<<g, 128, 0, ctx->stream>>>(B, s.fl.ptr, nrad, L2, -1.0, 1.0, Z);
+    LRS_TRY(after_launch(ctx, "lm_right_kernel"));
+    LRS_TRY(spd_inverse(ctx, Z, r, r, ctx->ws.status.ptr));
+    lm_left_kernel<false, true><<<g, 128, 0, ctx->stream>>>(Z, s.fl.ptr, nrad, L2, 1.0, 0.0, X);
+    LRS_TRY(after_launch(ctx, "lm_left_kernel"));
+    lm_right_kernel<true><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, Z);
+    LRS_TRY(after_launch(ctx, "lm_right_kernel"));
+    ctx->fp64_flops += 8.0 * (double)r * r * nrad;
+  } else {
+    lm_dyson_matrix_kernel<<<g, 128, 0, ctx->stream>>>(X, s.rl.ptr, nrad, L2, B);
+    LRS_TRY(after_launch(ctx, "lm_dyson_matrix_kernel"));
+    lm_coulomb_kernel<<<g, 128, 0, ctx->stream>>>(s.rl.ptr, nrad, L2, Z);
+    LRS_TRY(after_launch(ctx, "lm_coulomb_kernel"));
+    LRS_TRY(lu_factor(ctx, B, r, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));
+    LRS_TRY(ensure(ctx, ctx->ws.tinv, 2 * (size_t)((r + 31) / 32) * 32 * 32));
+    LRS_TRY(lu_solve_inv(ctx, B, r, ctx->ws.ipiv.ptr, Z, r, r, ctx->ws.tinv.ptr));
+  }
   // U[shell j, :] = Yang Z[j block, :]   (reuses T)
   double* U = T;
   LRS_TRY(dgemm_batched(ctx, false, false, nang, r, L2, 1.0, Yang, L2, 0, nullptr, 0, Z, r, (long long)L2 * r,

@@ -10,6 +10,7 @@
 // the tiling only has to keep all SMs busy.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "lrs_internal.h"
@@ -23,6 +24,15 @@ constexpr int NB = 32;   // LU panel width
 // Element offsets between the matrices of consecutive batch entries (blockIdx.z).
 struct BatchStrides {
   long long a = 0, ks = 0, b = 0, c = 0;
+  // Tile selection (square tiles of GT, so tile index = block index of the SPD inverse):
+  //   0: every tile of the grid
+  //   1: lower-triangle tiles (row block >= column block) ...
+  //   2: ... whose row and column blocks both differ from xk and xk + 1
+  //   3: the cross of block xk + 1 without block xk: blockIdx.y == 0 walks row
+  //      block xk + 1 (column blocks <= xk + 1), blockIdx.y == 1 column block xk + 1
+  //      (row blocks > xk + 1); blockIdx.x is the free block index
+  int select = 0;
+  int xk = 0;
 };
 
 template <bool TA, bool TB>
@@ -39,7 +49,16 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
   C += bs.c * blockIdx.z;
   if (ks) ks += bs.ks * blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  int bi = blockIdx.y, bj = blockIdx.x;
+  if (bs.select == 3) {
+    const int nx = bs.xk + 1;
+    if (blockIdx.y == 0) { bi = nx; bj = blockIdx.x; if (bj > nx || bj == bs.xk) return; }
+    else { bi = blockIdx.x; bj = nx; if (bi <= nx) return; }
+  } else if (bs.select >= 1) {
+    if (bj > bi) return;   // tile strictly above the diagonal
+    if (bs.select == 2 && (bi == bs.xk || bi == bs.xk + 1 || bj == bs.xk || bj == bs.xk + 1)) return;
+  }
+  const int i0 = bi * GT, j0 = bj * GT;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -617,6 +636,242 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
   LRS_CUDA_TRY(cudaMemcpyAsync(s.w.ptr, s.v.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   LRS_TRY(ensure(ctx, ctx->ws.tinv, 2 * (size_t)((n + NB - 1) / NB) * NB * NB));
   return lu_solve_inv(ctx, A, n, ctx->ws.ipiv.ptr, s.w.ptr, n, n, ctx->ws.tinv.ptr);
+}
+
+// ---------------------------------------------------------------- SPD inverse
+// In-place inverse of a symmetric positive definite matrix by blocked
+// Gauss-Jordan exchange steps.  Exchanging block k (pivot P = A_kk) maps
+//   A_kk -> P^-1,  A_ik -> A_ik P^-1,  A_kj -> -P^-1 A_kj,  A_ij -> A_ij - A_ik P^-1 A_kj,
+// and after every block has been exchanged the matrix is A^-1.  Every pivot
+// block of an SPD matrix is SPD (a Schur complement), so no pivoting is needed.
+// Only the lower triangle is stored: blocks (i, j) and (j, i) stay transposes
+// of each other up to the sign s = -1 when exactly one of the two block
+// indices has been exchanged.  Cost n^3 flop (lower-triangle rank-nb updates),
+// against 8/3 n^3 for LU plus n right-hand sides.
+constexpr int GJ_NB = 64;
+
+// Column block k of the current matrix from the lower triangle, C (n x kb,
+// leading dimension GJ_NB): rows i >= k0 read A[i][j] (A[j][i] above the
+// diagonal of the pivot block), rows i < k0 read -A[j][i].  E = sigma C with
+// sigma = -1 on rows i < k0, so that A_kj = E_j^T for every j != k.
+__global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict__ A, int n, int lda, int k0, int kb,
+                                                        double* __restrict__ C, double* __restrict__ E) {
+  __shared__ double t[GJ_NB][GJ_NB + 1];
+  const int i0 = blockIdx.x * GJ_NB;
+  if (i0 < k0) {   // k0 is a multiple of GJ_NB, so the whole row block lies below k0
+    for (int idx = threadIdx.x; idx < kb * GJ_NB; idx += blockDim.x) {
+      const int c = idx / GJ_NB, ii = idx % GJ_NB;
+      t[c][ii] = A[(size_t)(k0 + c) * lda + i0 + ii];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < GJ_NB * kb; idx += blockDim.x) {
+      const int ii = idx / kb, c = idx % kb;
+      const double v = t[c][ii];
+      C[(size_t)(i0 + ii) * GJ_NB + c] = -v;
+      E[(size_t)(i0 + ii) * GJ_NB + c] = v;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < GJ_NB * kb; idx += blockDim.x) {
+      const int ii = idx / kb, c = idx % kb, i = i0 + ii, j = k0 + c;
+      if (i >= n) continue;
+      const double v = (i >= j) ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
+      C[(size_t)i * GJ_NB + c] = v;
+      E[(size_t)i * GJ_NB + c] = v;
+    }
+  }
+}
+
+// Pinv = P^-1 for the kb x kb pivot block P = C[k0, k0 + kb) by scalar
+// exchange steps; a ragged block is padded with the identity.  Thread t holds
+// column t % 64 of rows t / 64 + 4 m (m < 16) in registers; per step the
+// owners of column p publish it divided by the pivot and the owners of row p
+// publish that row, then every element takes one FMA.  One SM retires two
+// DFMA per clock, so a 64 x 64 inverse is about 64 x 2048 clocks.  A pivot
+// that is not positive and finite sets status[0] = 2, status[1] = its column
+// (the matrix is not SPD).
+__global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict__ C, int k0, int kb,
+                                                       double* __restrict__ Pinv, int* __restrict__ status) {
+  __shared__ double colv[GJ_NB];   // column p, then column p / pivot
+  __shared__ double roww[GJ_NB];   // row p
+  __shared__ double dinv;
+  const int j = threadIdx.x & (GJ_NB - 1), ib = threadIdx.x >> 6;
+  double a[GJ_NB / 4];
+#pragma unroll
+  for (int m = 0; m < GJ_NB / 4; ++m) {
+    const int i = ib + 4 * m;
+    a[m] = (i < kb && j < kb) ? C[(size_t)(k0 + i) * GJ_NB + j] : (i == j ? 1.0 : 0.0);
+  }
+  for (int p = 0; p < GJ_NB; ++p) {
+    if (j == p) {
+#pragma unroll
+      for (int m = 0; m < GJ_NB / 4; ++m) colv[ib + 4 * m] = a[m];
+    }
+#pragma unroll
+    for (int m = 0; m < GJ_NB / 4; ++m)
+      if (ib + 4 * m == p) roww[j] = a[m];
+    __syncthreads();
+    const double piv = colv[p];
+    if (!(piv > 0.0) || !isfinite(piv)) {   // same value in every thread: uniform exit
+      if (threadIdx.x == 0 && atomicCAS(&status[0], 0, 2) == 0) status[1] = k0 + p;
+      break;
+    }
+    __syncthreads();
+    if (threadIdx.x < GJ_NB) {
+      const double d = 1.0 / piv;
+      colv[threadIdx.x] *= d;
+      if (threadIdx.x == 0) dinv = d;
+    }
+    __syncthreads();
+    const double rj = roww[j], d = dinv;
+#pragma unroll
+    for (int m = 0; m < GJ_NB / 4; ++m) {
+      const int i = ib + 4 * m;
+      const double ci = colv[i];
+      if (i == p) a[m] = (j == p) ? d : -rj * d;
+      else if (j == p) a[m] = ci;
+      else a[m] = fma(-ci, rj, a[m]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < GJ_NB / 4; ++m) {
+    const int i = ib + 4 * m;
+    if (i < kb && j < kb) Pinv[(size_t)i * GJ_NB + j] = a[m];
+  }
+}
+
+// D = C Pinv (n x kb), 16 rows per CTA so that every SM takes part.
+constexpr int GJ_DR = 16;
+__global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict__ C, int n, int kb,
+                                                       const double* __restrict__ Pinv, double* __restrict__ D) {
+  __shared__ double pv[GJ_NB][GJ_NB + 1];
+  __shared__ double cr[GJ_DR][GJ_NB + 1];
+  const int r0 = blockIdx.x * GJ_DR;
+  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+    const int i = idx / kb, j = idx % kb;
+    pv[i][j] = Pinv[(size_t)i * GJ_NB + j];
+  }
+  for (int idx = threadIdx.x; idx < GJ_DR * kb; idx += blockDim.x) {
+    const int i = idx / kb, j = idx % kb;
+    cr[i][j] = (r0 + i < n) ? C[(size_t)(r0 + i) * GJ_NB + j] : 0.0;
+  }
+  __syncthreads();
+  const int j = threadIdx.x & (GJ_NB - 1), ib = threadIdx.x >> 6;   // rows ib + 4 m, m < 4
+  if (j >= kb) return;
+  double acc[GJ_DR / 4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < kb; ++k) {
+    const double b = pv[k][j];
+#pragma unroll
+    for (int m = 0; m < GJ_DR / 4; ++m) acc[m] = fma(cr[ib + 4 * m][k], b, acc[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < GJ_DR / 4; ++m) {
+    const int r = r0 + ib + 4 * m;
+    if (r < n) D[(size_t)r * GJ_NB + j] = acc[m];
+  }
+}
+
+// After the trailing update: pivot block <- Pinv, column block k below it <- D
+// (= C Pinv), row block k left of it <- D^T (the exchanged A_kj = -P^-1 A_kj).
+__global__ void __launch_bounds__(256) gj_fix_kernel(double* __restrict__ A, int n, int lda, int k0, int kb,
+                                                     const double* __restrict__ D, const double* __restrict__ Pinv) {
+  __shared__ double t[GJ_NB][GJ_NB + 1];
+  const int i0 = blockIdx.x * GJ_NB;
+  if (i0 < k0) {
+    for (int idx = threadIdx.x; idx < GJ_NB * kb; idx += blockDim.x) {
+      const int ii = idx / kb, c = idx % kb;
+      t[c][ii] = D[(size_t)(i0 + ii) * GJ_NB + c];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kb * GJ_NB; idx += blockDim.x) {
+      const int c = idx / GJ_NB, ii = idx % GJ_NB;
+      A[(size_t)(k0 + c) * lda + i0 + ii] = t[c][ii];
+    }
+  } else if (i0 == k0) {
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+      const int i = idx / kb, j = idx % kb;
+      A[(size_t)(k0 + i) * lda + k0 + j] = Pinv[(size_t)i * GJ_NB + j];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < GJ_NB * kb; idx += blockDim.x) {
+      const int ii = idx / kb, c = idx % kb, i = i0 + ii;
+      if (i < n) A[(size_t)i * lda + k0 + c] = D[(size_t)i * GJ_NB + c];
+    }
+  }
+}
+
+// Schedule: the bulk of the trailing update of block k (every tile away from
+// blocks k and k + 1) runs on the context stream while a second, higher
+// priority stream updates the cross of block k + 1, writes the exchanged
+// block k (fix), and prepares the next panel (gather, pivot inverse, D) in the
+// other of two buffer sets.  The serial pivot inverse (one SM) thereby overlaps
+// the bulk GEMM.  Events: panel k ready -> bulk k; bulk k done -> cross k + 1.
+int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
+  static_assert(GT == GJ_NB, "tiles of the update must coincide with the pivot blocks");
+  if (n <= 0) return LRS_OK;
+  const size_t set = 3 * (size_t)n * GJ_NB + GJ_NB * GJ_NB;
+  LRS_TRY(ensure(ctx, ctx->ws.gj, 2 * set));
+  LRS_TRY(aux_stream_ready(ctx));
+  cudaStream_t s1 = ctx->stream, s2 = ctx->aux_stream;
+  double *Cb[2], *Eb[2], *Db[2], *Pb[2];
+  for (int q = 0; q < 2; ++q) {
+    Cb[q] = ctx->ws.gj.ptr + q * set;
+    Eb[q] = Cb[q] + (size_t)n * GJ_NB;
+    Db[q] = Eb[q] + (size_t)n * GJ_NB;
+    Pb[q] = Db[q] + (size_t)n * GJ_NB;
+  }
+  const int nblk = (n + GJ_NB - 1) / GJ_NB;
+  auto panel = [&](int kb_idx, int q) -> int {
+    const int k0 = kb_idx * GJ_NB, kb = std::min(GJ_NB, n - k0);
+    gj_gather_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Cb[q], Eb[q]);
+    LRS_TRY(after_launch(ctx, "gj_gather_kernel"));
+    gj_pivot_kernel<<<1, 256, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
+    LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
+    gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q]);
+    LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
+    ctx->fp64_flops += 2.0 * n * kb * kb;
+    return LRS_OK;
+  };
+  // fork the second stream from the context stream (also inside a graph capture)
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fork, s1));
+  LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
+  LRS_TRY(panel(0, 0));
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_panel, s2));
+  for (int k = 0; k < nblk; ++k) {
+    const int q = k & 1, k0 = k * GJ_NB, kb = std::min(GJ_NB, n - k0);
+    // bulk of the trailing update on the context stream
+    LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_panel, 0));
+    BatchStrides bulk;
+    bulk.select = 2;
+    bulk.xk = k;
+    dgemm_kernel<false, true><<<dim3(nblk, nblk, 1), 256, 0, s1>>>(n, n, kb, -1.0, Db[q], GJ_NB, nullptr, Eb[q],
+                                                                   GJ_NB, nullptr, 1.0, A, lda, bulk);
+    LRS_TRY(after_launch(ctx, "dgemm_kernel"));
+    ctx->fp64_flops += (double)n * n * kb;
+    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
+    // cross of block k + 1, exchange of block k, next panel on the second stream
+    if (k + 1 < nblk) {
+      BatchStrides cross;
+      cross.select = 3;
+      cross.xk = k;
+      dgemm_kernel<false, true><<<dim3(nblk, 2, 1), 256, 0, s2>>>(n, n, kb, -1.0, Db[q], GJ_NB, nullptr, Eb[q],
+                                                                  GJ_NB, nullptr, 1.0, A, lda, cross);
+      LRS_TRY(after_launch(ctx, "dgemm_kernel"));
+    }
+    gj_fix_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Db[q], Pb[q]);
+    LRS_TRY(after_launch(ctx, "gj_fix_kernel"));
+    if (k + 1 < nblk) {
+      // buffer set q ^ 1 was last read by bulk k - 1, which s2 has waited for
+      LRS_TRY(panel(k + 1, q ^ 1));
+      LRS_CUDA_TRY(cudaEventRecord(ctx->ev_panel, s2));
+      // the cross of block k + 2 and set q are touched by bulk k: wait for it
+      LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_bulk, 0));
+    }
+  }
+  // join
+  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_join, s2));
+  LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_join, 0));
+  return LRS_OK;
 }
 
 }  // namespace lrs

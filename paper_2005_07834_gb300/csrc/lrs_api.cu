@@ -57,6 +57,16 @@ void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes) {
   ctx->stats.device_bytes -= (int64_t)bytes;
 }
 
+int aux_stream_ready(lrs_ctx* ctx) {
+  if (ctx->aux_stream) return LRS_OK;
+  int lo = 0, hi = 0;
+  LRS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  LRS_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, hi));
+  for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_bulk, &ctx->ev_join})
+    LRS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return LRS_OK;
+}
+
 // A top-level stage starts a new measurement; ST_CHI0_MAIN intervals add up
 // until the next ST_CHI0 begins.
 int stage_begin(lrs_ctx* ctx, Stage s) {
@@ -182,6 +192,8 @@ static void free_site(lrs_ctx* ctx, Site& s) {
   release(ctx, s.v);
   release(ctx, s.yang);
   release(ctx, s.rl);
+  release(ctx, s.fl);
+  s.spd = false;
   s.product = false;
   s.has_psi = s.has_chi0 = s.has_w = false;
 }
@@ -196,6 +208,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.site_tiles);
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
   release(ctx, w.adj_tiles);
+  release(ctx, w.gj);
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
 
@@ -233,7 +246,12 @@ int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->num_sms = prop.multiProcessorCount;
   int rc = ensure(ctx, ctx->ws.status, 64);
-  if (rc) { delete ctx; return rc; }
+  if (rc == LRS_OK) rc = aux_stream_ready(ctx);
+  if (rc) {
+    const std::string msg = lrs_last_error();
+    lrs_destroy(ctx);
+    return set_error(rc, "%s", msg.c_str());
+  }
   cudaMemsetAsync(ctx->ws.status.ptr, 0, 64 * sizeof(int), ctx->stream);
   *out = ctx;
   return LRS_OK;
@@ -254,6 +272,9 @@ int lrs_destroy(lrs_ctx* ctx) {
   release(ctx, ctx->d_col_o); release(ctx, ctx->d_col_u);
   free_workspace(ctx);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_panel, ctx->ev_bulk, ctx->ev_join})
+    if (e) cudaEventDestroy(e);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   for (int s = 0; s < 6; ++s) {
     for (cudaEvent_t e : ctx->ev_begin[s]) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_end[s]) cudaEventDestroy(e);
@@ -270,6 +291,11 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
       if (value != LRS_DYSON_AUTO && value != LRS_DYSON_FULL && value != LRS_DYSON_LM)
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
+      return LRS_OK;
+    case LRS_OPT_DYSON_SOLVER:
+      if (value != LRS_SOLVER_AUTO && value != LRS_SOLVER_LU && value != LRS_SOLVER_SPD)
+        return set_error(LRS_ERR_ARG, "Dyson solver %d unknown", value);
+      ctx->dyson_solver = value;
       return LRS_OK;
     case LRS_OPT_WORKSPACE_GB:
       if (value < 1 || value > 4096) return set_error(LRS_ERR_ARG, "workspace budget %d GB out of range", value);
@@ -664,7 +690,9 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   if (status[0] != 0) {
     cudaMemsetAsync(ctx->ws.status.ptr, 0, 4 * sizeof(int), ctx->stream);
     for (int i : list) ctx->sites[i].has_w = false;
-    return set_error(LRS_ERR_NUMERIC, "Dyson LU: zero or non-finite pivot (status %d, column %d)", status[0], status[1]);
+    return set_error(LRS_ERR_NUMERIC, "Dyson %s: %s pivot (status %d, column %d)",
+                     status[0] == 2 ? "SPD inverse" : "LU", status[0] == 2 ? "non-positive or non-finite"
+                     : "zero or non-finite", status[0], status[1]);
   }
   return LRS_OK;
 }

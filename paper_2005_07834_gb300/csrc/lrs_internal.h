@@ -82,6 +82,8 @@ struct Site {
   int nrad = 0, nang = 0;
   DevBuf<double> yang;              // [nang][(lmax+1)^2] real spherical harmonics
   DevBuf<double> rl;                // [lmax+1][nrad][nrad] 4pi/(2l+1) r<^l / r>^(l+1)
+  DevBuf<double> fl;                // [lmax+1][nrad][nrad] lower Cholesky factor of each rl block
+  bool spd = false;                 // fl exists (every rl block is positive definite)
 };
 
 // Split-precision operand planes of one matrix [rows_pad][k_pad] (4 planes:
@@ -140,6 +142,7 @@ struct Workspace {
   DevBuf<float2> g32;                   // Go, Gu^T of one frequency
   DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
+  DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
   DevBuf<uint16_t> proj_a, proj_b;      // projection: phase planes, coefficient planes
   DevBuf<float> scales;                 // chi0: fp16 operand scales per frequency
   DevBuf<float> proj_scale;             // projection: coefficient scale and unscale
@@ -156,6 +159,7 @@ struct lrs_ctx {
   int seg_chunks = 4;                  // chi0 tensor-core accumulation segment (K chunks of 32)
   int proj_seg_chunks = 2;             // projection accumulation segment (K chunks of 32)
   int dyson_basis = LRS_DYSON_AUTO;    // full grid or lm basis
+  int dyson_solver = LRS_SOLVER_AUTO;  // lm basis: LU of I - C X, or the SPD inverse
   int chi0_tn = 128;                   // chi0 tensor-core tile width (64 or 128)
   double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
@@ -187,6 +191,9 @@ struct lrs_ctx {
   std::vector<lrs::SiteTile> site_tiles_dev;   // copy of the table last uploaded
   const lrs::SiteTile* site_tiles_dev_ptr = nullptr;
   cudaGraphExec_t graph_exec = nullptr;        // recorded multi-site build
+  // second stream of the SPD inverse (higher priority) and its fork/join events
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_panel = nullptr, ev_bulk = nullptr, ev_join = nullptr;
 
   lrs_stats_t stats{};
   double fp64_flops = 0;               // running count of FP64 flop issued by the linear algebra
@@ -202,6 +209,8 @@ namespace lrs {
 
 enum Stage { ST_PROJECT = 0, ST_CHI0 = 1, ST_W = 2, ST_BACKWARD = 3, ST_CHI0_MAIN = 4 };
 int stage_begin(lrs_ctx* ctx, Stage s);
+// Creates the second stream and its events on first use.
+int aux_stream_ready(lrs_ctx* ctx);
 int stage_end(lrs_ctx* ctx, Stage s);
 
 // ---------------------------------------------------------------- launchers
@@ -238,6 +247,9 @@ int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status);
 int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb);
 int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb,
                  double* tinv);
+// In-place inverse of an SPD matrix; lower triangle in and out.  status[0] = 2
+// (status[1] = column) on a pivot that is not positive and finite.
+int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status);
 
 // lm-basis Dyson on product grids (k_dyson_lm.cu)
 int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);

@@ -25,6 +25,8 @@ LRS_FP64, LRS_MIXED_BF16X3, LRS_MIXED_FP16X3 = 0, 1, 2
 LRS_PROJ_EXACT = 0
 LRS_OPT_DYSON_BASIS, LRS_OPT_CHI0_SEGMENT, LRS_OPT_PROJ_SEGMENT, LRS_OPT_CHI0_TILE_N = 1, 2, 3, 4
 LRS_DYSON_AUTO, LRS_DYSON_FULL, LRS_DYSON_LM = 0, 1, 2
+LRS_OPT_WORKSPACE_GB, LRS_OPT_DYSON_SOLVER = 5, 6
+LRS_SOLVER_AUTO, LRS_SOLVER_LU, LRS_SOLVER_SPD = 0, 1, 2
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
 

@@ -123,12 +123,14 @@ def test_state_and_argument_errors(lrs):
     scr.close()
 
 
-@pytest.mark.parametrize("basis", ["full", "lm"])
+@pytest.mark.parametrize("basis", ["full", "lm-lu", "lm-spd"])
 def test_dyson_bases_match_oracle(lrs, cfg_260, basis):
     ref = cfg_260
     wl = synth.single_site_260()
     scr = lrs.Screening(0, "fp64")
     scr.set_option(lrs.LRS_OPT_DYSON_BASIS, lrs.LRS_DYSON_FULL if basis == "full" else lrs.LRS_DYSON_LM)
+    if basis != "full":
+        scr.set_option(lrs.LRS_OPT_DYSON_SOLVER, lrs.LRS_SOLVER_LU if basis == "lm-lu" else lrs.LRS_SOLVER_SPD)
     scr.load(wl.orbitals)
     scr.set_sites(wl.sites)
     scr.set_frequency_quadrature(12)
@@ -153,4 +155,28 @@ def test_non_product_grid_uses_full_basis(lrs):
     with pytest.raises(lrs.LrsError) as e:
         scr.solve_w()
     assert e.value.code == lrs.LRS_ERR_ARG
+    scr.close()
+
+
+def test_spd_and_lu_dyson_agree_on_a_large_site(lrs):
+    """Symmetric (Gauss-Jordan) and LU lm-basis solvers on a 48-shell x 110-point
+    site (r = 48 * 81 = 3888, several pivot blocks and a ragged last one) from the
+    same chi0: the two float64 solutions of one linear system agree to 1e-11."""
+    wl = synth.single_site_260()
+    wl.sites = [synth.site_grid(wl.sites[0].center, 48, 110, 4.0)]
+    scr = lrs.Screening(0, "bf16x3")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(8)
+    scr.project()
+    scr.build_chi0()
+    ws = []
+    for solver in (lrs.LRS_SOLVER_LU, lrs.LRS_SOLVER_SPD):
+        scr.set_option(lrs.LRS_OPT_DYSON_SOLVER, solver)
+        scr.solve_w()
+        ws.append(scr.get_w(0))
+    v = scr.get_v(0)
+    err = rel_fro(ws[1] - v, ws[0] - v)
+    print(f"SPD vs LU lm-basis W - v: {err:.2e}")
+    assert err < 1e-11
     scr.close()
