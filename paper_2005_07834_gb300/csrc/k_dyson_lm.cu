@@ -153,8 +153,10 @@ __global__ void lm_coulomb_kernel(const double* __restrict__ rl, int nrad, int L
 // Radial-block products on the (j, lm) index, F given per l as [nrad][nrad]:
 //   left:  out[(j,lm), c] = add_i delta + alpha sum_j' f_l(j, j') in[(j',lm), c]
 //   right: out[c, (j,lm)] = add_i delta + alpha sum_j' in[c, (j',lm)] f_l(j', j)
-// with f_l(a, b) = F_l[b][a] when TF, else F_l[a][b].  SYM_IN reads `in` from
-// its lower triangle only (a symmetric matrix stored that way).
+// with f_l(a, b) = F_l[b][a] when TF, else F_l[a][b].  F_l is lower triangular
+// (a Cholesky factor), so only j' >= j (TF) or j' <= j (not TF) contribute.
+// SYM_IN reads `in` from its lower triangle only (a symmetric matrix stored
+// that way).
 template <bool TF, bool SYM_IN>
 __global__ void lm_left_kernel(const double* __restrict__ in, const double* __restrict__ F, int nrad, int L2,
                                double alpha, double add_i, double* __restrict__ out) {
@@ -167,7 +169,8 @@ __global__ void lm_left_kernel(const double* __restrict__ in, const double* __re
   while ((l + 1) * (l + 1) <= lm) ++l;
   const double* f = F + (size_t)l * nrad * nrad;
   double s = 0.0;
-  for (int jp = 0; jp < nrad; ++jp) {
+  const int lo = TF ? j : 0, hi = TF ? nrad : j + 1;
+  for (int jp = lo; jp < hi; ++jp) {
     const double c = TF ? f[(size_t)jp * nrad + j] : f[(size_t)j * nrad + jp];
     const int src = jp * L2 + lm;
     const double x = (!SYM_IN || src >= col) ? in[(size_t)src * r + col] : in[(size_t)col * r + src];
@@ -189,7 +192,8 @@ __global__ void lm_right_kernel(const double* __restrict__ in, const double* __r
   const double* f = F + (size_t)l * nrad * nrad;
   const double* x = in + (size_t)row * r + lm;
   double s = 0.0;
-  for (int jp = 0; jp < nrad; ++jp) {
+  const int lo = TF ? 0 : j, hi = TF ? j + 1 : nrad;
+  for (int jp = lo; jp < hi; ++jp) {
     const double c = TF ? f[(size_t)j * nrad + jp] : f[(size_t)jp * nrad + j];
     s = fma(x[(size_t)jp * L2], c, s);
   }
@@ -211,15 +215,21 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   // T[:, j' block] = chi0[:, shell j'] diag(Q_j') Yang        (one launch, batch = shell)
   LRS_TRY(dgemm_batched(ctx, false, false, n, L2, nang, 1.0, s.chi0.ptr, n, nang, s.wts.ptr, nang, Yang, L2, 0,
                         nullptr, 0.0, T, r, L2, nrad));
-  // X[j block, :] = Yang^T diag(Q_j) T[shell j, :]
-  LRS_TRY(dgemm_batched(ctx, true, false, L2, r, nang, 1.0, Yang, L2, 0, s.wts.ptr, nang, T, r,
-                        (long long)nang * r, nullptr, 0.0, X, r, (long long)L2 * r, nrad));
-  dim3 g((r + 127) / 128, r);
+  // X = Y^T Q T is symmetric; its transpose is formed, X^T[:, j block] = T[shell j, :]^T diag(Q_j) Yang,
+  // so that the 81- (generally (L+1)^2-) wide side of the product is a tile column.  The SPD
+  // route reads only its lower triangle.
   const bool use_spd = ctx->dyson_solver == LRS_SOLVER_SPD || (ctx->dyson_solver == LRS_SOLVER_AUTO && s.spd);
+  if (use_spd && !s.spd) return set_error(LRS_ERR_STATE, "SPD Dyson solver: a radial Coulomb block has no Cholesky factor");
+  if (use_spd)
+    LRS_TRY(dgemm_batched_lower(ctx, true, false, r, L2, nang, T, r, (long long)nang * r, s.wts.ptr, nang, Yang,
+                                L2, X, r, nrad));
+  else
+    LRS_TRY(dgemm_batched(ctx, true, false, r, L2, nang, 1.0, T, r, (long long)nang * r, s.wts.ptr, nang, Yang,
+                          L2, 0, nullptr, 0.0, X, r, L2, nrad));
+  dim3 g((r + 127) / 128, r);
   if (use_spd) {
-    if (!s.spd) return set_error(LRS_ERR_STATE, "SPD Dyson solver: a radial Coulomb block has no Cholesky factor");
     // M = I - F^T X F (in Z), inverted in place; Z = F M^-1 F^T
-    lm_left_kernel<true, false><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, B);
+    lm_left_kernel<true, true><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, B);
     LRS_TRY(after_launch(ctx, "lm_left_kernel"));
     lm_right_kernel<false><<<g, 128, 0, ctx->stream>>>(B, s.fl.ptr, nrad, L2, -1.0, 1.0, Z);
     LRS_TRY(after_launch(ctx, "lm_right_kernel"));
@@ -228,7 +238,7 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
     LRS_TRY(after_launch(ctx, "lm_left_kernel"));
     lm_right_kernel<true><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, Z);
     LRS_TRY(after_launch(ctx, "lm_right_kernel"));
-    ctx->fp64_flops += 8.0 * (double)r * r * nrad;
+    ctx->fp64_flops += 4.0 * (double)r * r * nrad;   // four triangular radial-block products
   } else {
     lm_dyson_matrix_kernel<<<g, 128, 0, ctx->stream>>>(X, s.rl.ptr, nrad, L2, B);
     LRS_TRY(after_launch(ctx, "lm_dyson_matrix_kernel"));
@@ -242,9 +252,9 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   double* U = T;
   LRS_TRY(dgemm_batched(ctx, false, false, nang, r, L2, 1.0, Yang, L2, 0, nullptr, 0, Z, r, (long long)L2 * r,
                         nullptr, 0.0, U, r, (long long)nang * r, nrad));
-  // W[:, shell j'] = U[:, j' block] Yang^T
-  return dgemm_batched(ctx, false, true, n, nang, L2, 1.0, U, r, L2, nullptr, 0, Yang, L2, 0, nullptr, 0.0, s.w.ptr,
-                       n, nang, nrad);
+  // W[:, shell j'] = U[:, j' block] Yang^T on and below the diagonal, then mirrored (W is symmetric)
+  LRS_TRY(dgemm_batched_lower(ctx, false, true, n, nang, L2, U, r, L2, nullptr, 0, Yang, L2, s.w.ptr, n, nrad));
+  return mirror_lower(ctx, s.w.ptr, n, n);
 }
 
 }  // namespace lrs

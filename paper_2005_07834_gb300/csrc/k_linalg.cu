@@ -24,46 +24,36 @@ constexpr int NB = 32;   // LU panel width
 // Element offsets between the matrices of consecutive batch entries (blockIdx.z).
 struct BatchStrides {
   long long a = 0, ks = 0, b = 0, c = 0;
-  // Tile selection (square tiles of GT, so tile index = block index of the SPD inverse):
-  //   0: every tile of the grid
-  //   1: lower-triangle tiles (row block >= column block) ...
-  //   2: ... whose row and column blocks both differ from xk and xk + 1
-  //   3: the cross of block xk + 1 without block xk: blockIdx.y == 0 walks row
-  //      block xk + 1 (column blocks <= xk + 1), blockIdx.y == 1 column block xk + 1
-  //      (row blocks > xk + 1); blockIdx.x is the free block index
-  int select = 0;
-  int xk = 0;
+  // > 0: C is the column block blockIdx.z * lower_col of a symmetric matrix and
+  // only tiles holding an element on or below its diagonal are computed
+  int lower_col = 0;
 };
 
-template <bool TA, bool TB>
+// C tile of GT rows x TNW columns per CTA (TNW = 64, 96 or 112: the 81- and
+// 110-wide products of the lm-basis change fit one tile), 256 threads, each
+// 4 rows x TNW/16 columns.
+template <bool TA, bool TB, int TNW>
 __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double alpha,
                                                     const double* __restrict__ A, int lda,
                                                     const double* __restrict__ ks,
                                                     const double* __restrict__ B, int ldb,
                                                     const double* __restrict__ cs, double beta,
                                                     double* __restrict__ C, int ldc, BatchStrides bs) {
+  constexpr int CJ = TNW / 16;
   __shared__ double As[GKC][GT + 1];
-  __shared__ double Bs[GKC][GT + 1];
+  __shared__ double Bs[GKC][TNW + 1];
   A += bs.a * blockIdx.z;
   B += bs.b * blockIdx.z;
   C += bs.c * blockIdx.z;
   if (ks) ks += bs.ks * blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  int bi = blockIdx.y, bj = blockIdx.x;
-  if (bs.select == 3) {
-    const int nx = bs.xk + 1;
-    if (blockIdx.y == 0) { bi = nx; bj = blockIdx.x; if (bj > nx || bj == bs.xk) return; }
-    else { bi = blockIdx.x; bj = nx; if (bi <= nx) return; }
-  } else if (bs.select >= 1) {
-    if (bj > bi) return;   // tile strictly above the diagonal
-    if (bs.select == 2 && (bi == bs.xk || bi == bs.xk + 1 || bj == bs.xk || bj == bs.xk + 1)) return;
-  }
-  const int i0 = bi * GT, j0 = bj * GT;
-  double acc[4][4];
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * TNW;
+  if (bs.lower_col > 0 && i0 + GT <= (int)blockIdx.z * bs.lower_col + j0) return;
+  double acc[4][CJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < CJ; ++j) acc[i][j] = 0.0;
   for (int k0 = 0; k0 < k; k0 += GKC) {
     for (int idx = threadIdx.x; idx < GKC * GT; idx += 256) {
       int r, kk;
@@ -76,9 +66,9 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
       }
       As[kk][r] = a;
     }
-    for (int idx = threadIdx.x; idx < GKC * GT; idx += 256) {
+    for (int idx = threadIdx.x; idx < GKC * TNW; idx += 256) {
       int c, kk;
-      if (TB) { c = idx / GKC; kk = idx % GKC; } else { kk = idx / GT; c = idx % GT; }
+      if (TB) { c = idx / GKC; kk = idx % GKC; } else { kk = idx / TNW; c = idx % TNW; }
       int gj = j0 + c, gk = k0 + kk;
       double b = 0.0;
       if (gj < n && gk < k) b = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
@@ -87,15 +77,15 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GKC; ++kk) {
-      double a[4], b[4];
+      double a[4], b[CJ];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < CJ; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < CJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -104,7 +94,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
     int gi = i0 + ty + 16 * i;
     if (gi >= m) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < CJ; ++j) {
       int gj = j0 + tx + 16 * j;
       if (gj >= n) continue;
       double v = alpha * acc[i][j];
@@ -115,28 +105,81 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
   }
 }
 
+template <int TNW>
+static void launch_dgemm(lrs_ctx* ctx, bool ta, bool tb, dim3 grid, int m, int n, int k, double alpha,
+                         const double* a, int lda, const double* ks, const double* b, int ldb, const double* cs,
+                         double beta, double* c, int ldc, const BatchStrides& bs) {
+  if (!ta && !tb)
+    dgemm_kernel<false, false, TNW><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else if (ta && !tb)
+    dgemm_kernel<true, false, TNW><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else if (!ta && tb)
+    dgemm_kernel<false, true, TNW><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else
+    dgemm_kernel<true, true, TNW><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+}
+
 int dgemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
                   long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
                   long long stride_b, const double* cs, double beta, double* c, int ldc, long long stride_c,
                   int batch) {
   if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
   ctx->fp64_flops += 2.0 * m * (double)n * (k > 0 ? k : 0) * batch;
-  dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch);
+  // tile width: one tile for 64 < n <= 112 (less padding than two 64-wide tiles)
+  const int tnw = (n > 64 && n <= 96) ? 96 : (n > 96 && n <= 112) ? 112 : 64;
+  dim3 grid((n + tnw - 1) / tnw, (m + GT - 1) / GT, batch);
   if (k <= 0) k = 0;
   BatchStrides bs;
   bs.a = stride_a;
   bs.ks = stride_ks;
   bs.b = stride_b;
   bs.c = stride_c;
-  if (!ta && !tb)
-    dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
-  else if (ta && !tb)
-    dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
-  else if (!ta && tb)
-    dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
-  else
-    dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  if (tnw == 96) launch_dgemm<96>(ctx, ta, tb, grid, m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else if (tnw == 112) launch_dgemm<112>(ctx, ta, tb, grid, m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
+  else launch_dgemm<64>(ctx, ta, tb, grid, m, n, k, alpha, a, lda, ks, b, ldb, cs, beta, c, ldc, bs);
   return after_launch(ctx, "dgemm_kernel");
+}
+
+int dgemm_batched_lower(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, const double* a, int lda,
+                        long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                        double* c, int ldc, int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
+  ctx->fp64_flops += 1.0 * m * (double)n * (k > 0 ? k : 0) * batch;   // about half the tiles
+  const int tnw = (n > 64 && n <= 96) ? 96 : (n > 96 && n <= 112) ? 112 : 64;
+  dim3 grid((n + tnw - 1) / tnw, (m + GT - 1) / GT, batch);
+  BatchStrides bs;
+  bs.a = stride_a;
+  bs.ks = stride_ks;
+  bs.c = n;
+  bs.lower_col = n;
+  if (tnw == 96) launch_dgemm<96>(ctx, ta, tb, grid, m, n, k, 1.0, a, lda, ks, b, ldb, nullptr, 0.0, c, ldc, bs);
+  else if (tnw == 112) launch_dgemm<112>(ctx, ta, tb, grid, m, n, k, 1.0, a, lda, ks, b, ldb, nullptr, 0.0, c, ldc, bs);
+  else launch_dgemm<64>(ctx, ta, tb, grid, m, n, k, 1.0, a, lda, ks, b, ldb, nullptr, 0.0, c, ldc, bs);
+  return after_launch(ctx, "dgemm_kernel");
+}
+
+// Upper triangle of a symmetric matrix from its lower triangle (32 x 32 tiles).
+__global__ void __launch_bounds__(256) mirror_lower_kernel(double* __restrict__ a, int n, int lda) {
+  __shared__ double t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;   // destination tile (bi, bj), bi <= bj
+  if (bi > bj) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {   // source tile (bj, bi), row bj*32 + r
+    const int i = bj * 32 + r, j = bi * 32 + tx;
+    t[r][tx] = (i < n && j < n) ? a[(size_t)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    if (i < n && j < n && j > i) a[(size_t)i * lda + j] = t[tx][r];
+  }
+}
+
+int mirror_lower(lrs_ctx* ctx, double* a, int n, int lda) {
+  if (n <= 0) return LRS_OK;
+  const int nb = (n + 31) / 32;
+  mirror_lower_kernel<<<dim3(nb, nb), 256, 0, ctx->stream>>>(a, n, lda);
+  return after_launch(ctx, "mirror_lower_kernel");
 }
 
 int dgemm_t(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
@@ -648,7 +691,9 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
 // of each other up to the sign s = -1 when exactly one of the two block
 // indices has been exchanged.  Cost n^3 flop (lower-triangle rank-nb updates),
 // against 8/3 n^3 for LU plus n right-hand sides.
-constexpr int GJ_NB = 64;
+constexpr int GJ_NB = 32;               // pivot block width
+constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread pivot and apply kernels
+constexpr int GJ_PM = GJ_NB / GJ_PR;     // pivot rows per thread
 
 // Column block k of the current matrix from the lower triangle, C (n x kb,
 // leading dimension GJ_NB): rows i >= k0 read A[i][j] (A[j][i] above the
@@ -683,10 +728,10 @@ __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict
 
 // Pinv = P^-1 for the kb x kb pivot block P = C[k0, k0 + kb) by scalar
 // exchange steps; a ragged block is padded with the identity.  Thread t holds
-// column t % 64 of rows t / 64 + 4 m (m < 16) in registers; per step the
+// column t % GJ_NB of rows t / GJ_NB + GJ_PR m in registers; per step the
 // owners of column p publish it divided by the pivot and the owners of row p
 // publish that row, then every element takes one FMA.  One SM retires two
-// DFMA per clock, so a 64 x 64 inverse is about 64 x 2048 clocks.  A pivot
+// DFMA per clock, so an nb x nb inverse is about nb^3 / 2 clocks.  A pivot
 // that is not positive and finite sets status[0] = 2, status[1] = its column
 // (the matrix is not SPD).
 __global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict__ C, int k0, int kb,
@@ -694,21 +739,21 @@ __global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict_
   __shared__ double colv[GJ_NB];   // column p, then column p / pivot
   __shared__ double roww[GJ_NB];   // row p
   __shared__ double dinv;
-  const int j = threadIdx.x & (GJ_NB - 1), ib = threadIdx.x >> 6;
-  double a[GJ_NB / 4];
+  const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;
+  double a[GJ_PM];
 #pragma unroll
-  for (int m = 0; m < GJ_NB / 4; ++m) {
-    const int i = ib + 4 * m;
+  for (int m = 0; m < GJ_PM; ++m) {
+    const int i = ib + GJ_PR * m;
     a[m] = (i < kb && j < kb) ? C[(size_t)(k0 + i) * GJ_NB + j] : (i == j ? 1.0 : 0.0);
   }
   for (int p = 0; p < GJ_NB; ++p) {
     if (j == p) {
 #pragma unroll
-      for (int m = 0; m < GJ_NB / 4; ++m) colv[ib + 4 * m] = a[m];
+      for (int m = 0; m < GJ_PM; ++m) colv[ib + GJ_PR * m] = a[m];
     }
 #pragma unroll
-    for (int m = 0; m < GJ_NB / 4; ++m)
-      if (ib + 4 * m == p) roww[j] = a[m];
+    for (int m = 0; m < GJ_PM; ++m)
+      if (ib + GJ_PR * m == p) roww[j] = a[m];
     __syncthreads();
     const double piv = colv[p];
     if (!(piv > 0.0) || !isfinite(piv)) {   // same value in every thread: uniform exit
@@ -724,8 +769,8 @@ __global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict_
     __syncthreads();
     const double rj = roww[j], d = dinv;
 #pragma unroll
-    for (int m = 0; m < GJ_NB / 4; ++m) {
-      const int i = ib + 4 * m;
+    for (int m = 0; m < GJ_PM; ++m) {
+      const int i = ib + GJ_PR * m;
       const double ci = colv[i];
       if (i == p) a[m] = (j == p) ? d : -rj * d;
       else if (j == p) a[m] = ci;
@@ -734,8 +779,8 @@ __global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict_
     __syncthreads();
   }
 #pragma unroll
-  for (int m = 0; m < GJ_NB / 4; ++m) {
-    const int i = ib + 4 * m;
+  for (int m = 0; m < GJ_PM; ++m) {
+    const int i = ib + GJ_PR * m;
     if (i < kb && j < kb) Pinv[(size_t)i * GJ_NB + j] = a[m];
   }
 }
@@ -756,17 +801,19 @@ __global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict_
     cr[i][j] = (r0 + i < n) ? C[(size_t)(r0 + i) * GJ_NB + j] : 0.0;
   }
   __syncthreads();
-  const int j = threadIdx.x & (GJ_NB - 1), ib = threadIdx.x >> 6;   // rows ib + 4 m, m < 4
+  const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;   // rows ib + GJ_PR m
   if (j >= kb) return;
-  double acc[GJ_DR / 4] = {0.0, 0.0, 0.0, 0.0};
+  double acc[GJ_DR / GJ_PR];
+#pragma unroll
+  for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = 0.0;
   for (int k = 0; k < kb; ++k) {
     const double b = pv[k][j];
 #pragma unroll
-    for (int m = 0; m < GJ_DR / 4; ++m) acc[m] = fma(cr[ib + 4 * m][k], b, acc[m]);
+    for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = fma(cr[ib + GJ_PR * m][k], b, acc[m]);
   }
 #pragma unroll
-  for (int m = 0; m < GJ_DR / 4; ++m) {
-    const int r = r0 + ib + 4 * m;
+  for (int m = 0; m < GJ_DR / GJ_PR; ++m) {
+    const int r = r0 + ib + GJ_PR * m;
     if (r < n) D[(size_t)r * GJ_NB + j] = acc[m];
   }
 }
@@ -800,6 +847,74 @@ __global__ void __launch_bounds__(256) gj_fix_kernel(double* __restrict__ A, int
   }
 }
 
+// Trailing update A_ij -= D_i E_j^T of the exchange of block k on 32 x 32
+// tiles of the lower triangle (a pivot block spans GJ_TB x GJ_TB tiles).  The
+// FP64 pipe of one SM is saturated by a few warps, so small tiles cost no
+// throughput and balance the SMs: a step has thousands of equal tiles.
+//   MODE 0 (bulk):  1-D grid over the lower-triangle tiles; tiles in pivot
+//                   blocks k and k + 1 (rows or columns) are left out.
+//   MODE 1 (cross): the tiles of pivot block k + 1 (its row to the left of the
+//                   diagonal, its column below it) outside block k; grid (T, 2 GJ_TB).
+constexpr int UT = 32;
+constexpr int GJ_TB = GJ_NB / UT;   // update tiles per pivot block and dimension
+template <int MODE>
+__global__ void __launch_bounds__(128) gj_update_kernel(double* __restrict__ A, int n, int lda, int kb, int k,
+                                                        const double* __restrict__ D,
+                                                        const double* __restrict__ E) {
+  __shared__ double Ds[GJ_NB][UT + 1];
+  __shared__ double Es[GJ_NB][UT + 1];
+  const int T = (n + UT - 1) / UT;
+  int ti, tj;
+  if (MODE == 0) {
+    const long long t = blockIdx.x;
+    ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while ((long long)ti * (ti + 1) / 2 > t) --ti;
+    tj = (int)(t - (long long)ti * (ti + 1) / 2);
+    const int bi = ti / GJ_TB, bj = tj / GJ_TB;
+    if (bi == k || bi == k + 1 || bj == k || bj == k + 1) return;
+  } else {
+    const int nx = GJ_TB * (k + 1);
+    if ((int)blockIdx.y < GJ_TB) {
+      ti = nx + blockIdx.y;
+      tj = blockIdx.x;
+      if (ti >= T || tj > ti || tj / GJ_TB == k) return;
+    } else {
+      tj = nx + blockIdx.y - GJ_TB;
+      ti = blockIdx.x;
+      if (tj >= T || ti / GJ_TB <= k + 1) return;
+    }
+  }
+  const int i0 = ti * UT, j0 = tj * UT;
+  for (int idx = threadIdx.x; idx < UT * kb; idx += blockDim.x) {
+    const int r = idx / kb, c = idx % kb;
+    Ds[c][r] = (i0 + r < n) ? D[(size_t)(i0 + r) * GJ_NB + c] : 0.0;
+    Es[c][r] = (j0 + r < n) ? E[(size_t)(j0 + r) * GJ_NB + c] : 0.0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // rows ty, ty + 16; columns tx + 8 c
+  double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
+  for (int kk = 0; kk < kb; ++kk) {
+    const double a0 = Ds[kk][ty], a1 = Ds[kk][ty + 16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double b = Es[kk][tx + 8 * c];
+      acc[0][c] = fma(a0, b, acc[0][c]);
+      acc[1][c] = fma(a1, b, acc[1][c]);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = i0 + ty + 16 * h;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 8 * c;
+      if (j < n) A[(size_t)i * lda + j] -= acc[h][c];
+    }
+  }
+}
+
 // Schedule: the bulk of the trailing update of block k (every tile away from
 // blocks k and k + 1) runs on the context stream while a second, higher
 // priority stream updates the cross of block k + 1, writes the exchanged
@@ -807,7 +922,7 @@ __global__ void __launch_bounds__(256) gj_fix_kernel(double* __restrict__ A, int
 // other of two buffer sets.  The serial pivot inverse (one SM) thereby overlaps
 // the bulk GEMM.  Events: panel k ready -> bulk k; bulk k done -> cross k + 1.
 int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
-  static_assert(GT == GJ_NB, "tiles of the update must coincide with the pivot blocks");
+  static_assert(GJ_NB % UT == 0 && GJ_TB >= 1, "a pivot block spans whole update tiles");
   if (n <= 0) return LRS_OK;
   const size_t set = 3 * (size_t)n * GJ_NB + GJ_NB * GJ_NB;
   LRS_TRY(ensure(ctx, ctx->ws.gj, 2 * set));
@@ -821,6 +936,7 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     Pb[q] = Db[q] + (size_t)n * GJ_NB;
   }
   const int nblk = (n + GJ_NB - 1) / GJ_NB;
+  const long long nt = (n + UT - 1) / UT;   // 32-wide update tiles per dimension
   auto panel = [&](int kb_idx, int q) -> int {
     const int k0 = kb_idx * GJ_NB, kb = std::min(GJ_NB, n - k0);
     gj_gather_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Cb[q], Eb[q]);
@@ -841,22 +957,14 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     const int q = k & 1, k0 = k * GJ_NB, kb = std::min(GJ_NB, n - k0);
     // bulk of the trailing update on the context stream
     LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_panel, 0));
-    BatchStrides bulk;
-    bulk.select = 2;
-    bulk.xk = k;
-    dgemm_kernel<false, true><<<dim3(nblk, nblk, 1), 256, 0, s1>>>(n, n, kb, -1.0, Db[q], GJ_NB, nullptr, Eb[q],
-                                                                   GJ_NB, nullptr, 1.0, A, lda, bulk);
-    LRS_TRY(after_launch(ctx, "dgemm_kernel"));
+    gj_update_kernel<0><<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
+    LRS_TRY(after_launch(ctx, "gj_update_kernel"));
     ctx->fp64_flops += (double)n * n * kb;
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
     // cross of block k + 1, exchange of block k, next panel on the second stream
     if (k + 1 < nblk) {
-      BatchStrides cross;
-      cross.select = 3;
-      cross.xk = k;
-      dgemm_kernel<false, true><<<dim3(nblk, 2, 1), 256, 0, s2>>>(n, n, kb, -1.0, Db[q], GJ_NB, nullptr, Eb[q],
-                                                                  GJ_NB, nullptr, 1.0, A, lda, cross);
-      LRS_TRY(after_launch(ctx, "dgemm_kernel"));
+      gj_update_kernel<1><<<dim3(nt, 2 * GJ_TB, 1), 128, 0, s2>>>(A, n, lda, kb, k, Db[q], Eb[q]);
+      LRS_TRY(after_launch(ctx, "gj_update_kernel"));
     }
     gj_fix_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Db[q], Pb[q]);
     LRS_TRY(after_launch(ctx, "gj_fix_kernel"));

@@ -243,6 +243,13 @@ int dgemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double al
                   long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
                   long long stride_b, const double* cs, double beta, double* c, int ldc, long long stride_c,
                   int batch);
+// Column blocks j of a symmetric C (C + j n, width n): only tiles on or below
+// the diagonal; alpha = 1, beta = 0.
+int dgemm_batched_lower(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, const double* a, int lda,
+                        long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                        double* c, int ldc, int batch);
+// Upper triangle of a symmetric matrix from its lower triangle.
+int mirror_lower(lrs_ctx* ctx, double* a, int n, int lda);
 int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status);
 int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb);
 int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb,
