@@ -33,6 +33,13 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # (profiles/ncu_chi0_single-site-3520_bf16x3.md), valid only for the kernel revision named.
 CHI0_TRAFFIC = {("single-site-3520", "bf16x3", "r1"): 23.26e9}
 
+
+def kernel_revision(version, name):
+    """Revision tag that follows `name` in the library version string (ncu counters are only
+    reused while the kernel they were taken on is unchanged)."""
+    tok = version.split()
+    return tok[tok.index(name) + 1] if name in tok[:-1] else None
+
 WORKLOADS = {
     "single-site-3520": "single_site_3520",
     "single-site-260": "single_site_260",
@@ -40,6 +47,23 @@ WORKLOADS = {
     "large-cell-16-sites": "large_cell_16_sites",
 }
 MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
+
+
+# (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per gj_update_kernel<0> launch
+DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6}
+
+
+def dyson_roofline(st, workload=None, version=None):
+    if not st.get("w_main_launches"):
+        return None
+    ms = st["ms_w_main"]
+    r = {"bound": "alu", "kernel": "gj_update_kernel<0> (SPD-inverse trailing update)",
+         "achieved": st["flop_w_main"] / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+         "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz", "launches": st["w_main_launches"],
+         "avg_launch_us": 1e3 * ms / st["w_main_launches"],
+         "traffic": DYSON_TRAFFIC.get((workload, version))}
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
 
 
 def load_peaks():
@@ -270,17 +294,15 @@ def run_ours(args):
                 "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk}
     roof["frac"] = roof["achieved"] / roof["peak"]
     version = lrs.lrs_version().decode()
-    roof["traffic"] = CHI0_TRAFFIC.get((args.workload, args.precision, version.split()[-1]))
+    roof["traffic"] = CHI0_TRAFFIC.get((args.workload, args.precision, kernel_revision(version, "chi0-tc")))
     roof["kernel"] = "chi0_fp64_kernel" if args.precision == "fp64" else "zgemm_tc_kernel<chi0>"
     roof["library"] = version
-    # FP64 Dyson: the flop the lm-basis LU actually executes, against the FP64 FMA peak
-    roof_w = {"bound": "alu", "kernel": "dgemm_kernel + lu_panel_cluster_kernel + trsm (Dyson stage)",
-              "achieved": st["flop_w_executed"] / (st["ms_w"] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-              "unit": "TFLOP/s", "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz",
-              "flop_executed": st["flop_w_executed"], "flop_full_grid_formula": st["flop_w"]}
-    roof_w["frac"] = roof_w["achieved"] / roof_w["peak"]
+    # FP64 Dyson: its dominant kernel is the trailing update of the SPD inverse (one launch per
+    # pivot block), timed per launch with CUDA events on its stream inside the library; algorithmic
+    # flop per launch = 2 kb x the lower-triangle elements it updates
+    roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"))
     # the roofline object describes the kernel that dominates the step; the other is kept beside it
-    dominant_w = st["ms_w"] > st["ms_chi0"]
+    dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
 
     # the plain FP64 path on the same workload, one untimed-warm step (for "mixed vs FP64 plain")
     plain = None
@@ -331,6 +353,10 @@ def run_ours(args):
                          "w": st["ms_w"]},
             "roofline": roof_w if dominant_w else roof,
             "roofline_chi0" if dominant_w else "roofline_dyson": roof if dominant_w else roof_w,
+            "dyson_stage": {"ms": st["ms_w"], "flop_executed": st["flop_w_executed"],
+                            "tflops_executed": st["flop_w_executed"] / (st["ms_w"] * 1e-3) / 1e12,
+                            "frac_fp64_peak": st["flop_w_executed"] / (st["ms_w"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                            "flop_full_grid_formula": st["flop_w"]},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "device_bytes_peak": st["device_bytes_peak"], "plain_fp64": plain,
         }
@@ -418,6 +444,8 @@ def run_ours_multisite(args):
             "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk, "traffic": None,
             "kernel": "zgemm_tc_kernel<chi0> (all sites, one launch per workspace group)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"))
+    dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -445,7 +473,9 @@ def run_ours_multisite(args):
             "tflops": flop_all / (ms * 1e-3) / 1e12,
             "stage_ms_eager": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
                                "w": st["ms_w"]},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
+            "roofline": roof_w if dominant_w else roof,
+            "roofline_chi0" if dominant_w else "roofline_dyson": roof if dominant_w else roof_w,
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
             "device_bytes_peak": st["device_bytes_peak"], "generation_s": t_gen,
         }
         print(json.dumps(line), flush=True)

@@ -83,6 +83,9 @@ typedef struct lrs_stats_t {
   int64_t device_bytes_peak;
   int status_word;        /* last device-side status (0 = ok) */
   double flop_w_executed; /* float64 flop actually executed by the last lrs_solve_w (GEMM, TRSM, LU) */
+  double ms_w_main;       /* device time of the SPD-inverse trailing-update launches of the last lrs_solve_w */
+  double flop_w_main;     /* their algorithmic flop: 2 kb x (lower-triangle elements updated), summed */
+  int64_t w_main_launches;/* how many such launches */
 } lrs_stats_t;
 
 /* Last error message of the calling thread ("" if none). */

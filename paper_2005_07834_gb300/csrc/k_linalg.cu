@@ -957,8 +957,18 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     const int q = k & 1, k0 = k * GJ_NB, kb = std::min(GJ_NB, n - k0);
     // bulk of the trailing update on the context stream
     LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_panel, 0));
+    LRS_TRY(stage_begin(ctx, ST_W_MAIN));
     gj_update_kernel<0><<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
     LRS_TRY(after_launch(ctx, "gj_update_kernel"));
+    LRS_TRY(stage_end(ctx, ST_W_MAIN));
+    {
+      // lower-triangle elements outside the rows and columns of blocks k and k + 1
+      const double b0 = k0, b1 = std::min(n, k0 + 2 * GJ_NB), nn = n;
+      const double rows_in = (b1 * (b1 + 1) - b0 * (b0 + 1)) / 2.0;   // sum of (i + 1), i in [b0, b1)
+      const double elems = nn * (nn + 1) / 2.0 - rows_in - (b1 - b0) * (nn - b1);
+      ctx->w_main_flop += 2.0 * kb * elems;
+      ++ctx->w_main_launches;
+    }
     ctx->fp64_flops += (double)n * n * kb;
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
     // cross of block k + 1, exchange of block k, next panel on the second stream

@@ -67,12 +67,13 @@ int aux_stream_ready(lrs_ctx* ctx) {
   return LRS_OK;
 }
 
-// A top-level stage starts a new measurement; ST_CHI0_MAIN intervals add up
-// until the next ST_CHI0 begins.
+// A top-level stage starts a new measurement; ST_CHI0_MAIN (ST_W_MAIN)
+// intervals add up until the next ST_CHI0 (ST_W) begins.
 int stage_begin(lrs_ctx* ctx, Stage s) {
   if (ctx->capturing) return LRS_OK;   // stage timings are not part of a recorded graph
-  if (s != ST_CHI0_MAIN) ctx->ev_used[s] = 0;
+  if (s != ST_CHI0_MAIN && s != ST_W_MAIN) ctx->ev_used[s] = 0;
   if (s == ST_CHI0) ctx->ev_used[ST_CHI0_MAIN] = 0;
+  if (s == ST_W) ctx->ev_used[ST_W_MAIN] = 0;
   const size_t i = ctx->ev_used[s];
   if (i >= ctx->ev_begin[s].size()) {
     cudaEvent_t b = nullptr, e = nullptr;
@@ -222,7 +223,7 @@ const char* lrs_last_error(void) { return g_last_error.c_str(); }
 
 // The chi0 tensor-core kernel revision lets measurements quote profiler
 // counters only for the kernel version they were taken on.
-const char* lrs_version(void) { return "lrs 0.2 (sm_103a) chi0-tc r1"; }
+const char* lrs_version(void) { return "lrs 0.3 (sm_103a) chi0-tc r1 dyson-gj r1"; }
 
 int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   clear_error();
@@ -668,6 +669,8 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   LRS_TRY(stage_begin(ctx, ST_W));
   double flop = 0;
   const double fp64_before = ctx->fp64_flops;
+  ctx->w_main_flop = 0;
+  ctx->w_main_launches = 0;
   for (int i : list) {
     Site& s = ctx->sites[i];
     LRS_TRY(dyson_solve(ctx, s));
@@ -677,6 +680,8 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   LRS_TRY(stage_end(ctx, ST_W));
   ctx->stats.flop_w = flop;
   ctx->stats.flop_w_executed = ctx->fp64_flops - fp64_before;
+  ctx->stats.flop_w_main = ctx->w_main_flop;
+  ctx->stats.w_main_launches = ctx->w_main_launches;
   if (ctx->capturing) return LRS_OK;   // checked after each replay by lrs_graph_launch's caller
   // zero pivots / non-finite values are reported through the status word
   int status[16] = {0};
@@ -906,6 +911,7 @@ int lrs_synchronize(lrs_ctx* ctx) {
   ctx->stats.ms_w = ctx->ms_acc[ST_W];
   ctx->stats.ms_backward = ctx->ms_acc[ST_BACKWARD];
   ctx->stats.ms_chi0_main = ctx->ms_acc[ST_CHI0_MAIN];
+  ctx->stats.ms_w_main = ctx->ms_acc[ST_W_MAIN];
   return LRS_OK;
 }
 

@@ -197,6 +197,8 @@ struct lrs_ctx {
 
   lrs_stats_t stats{};
   double fp64_flops = 0;               // running count of FP64 flop issued by the linear algebra
+  double w_main_flop = 0;              // algorithmic flop of the SPD-inverse bulk updates of the last solve
+  int64_t w_main_launches = 0;
   // stage timing: event pairs of the stage's intervals since its last reset
   // (the main chi0 kernel runs once per workspace group of one build)
   std::vector<cudaEvent_t> ev_begin[6], ev_end[6];
@@ -207,7 +209,7 @@ struct lrs_ctx {
 
 namespace lrs {
 
-enum Stage { ST_PROJECT = 0, ST_CHI0 = 1, ST_W = 2, ST_BACKWARD = 3, ST_CHI0_MAIN = 4 };
+enum Stage { ST_PROJECT = 0, ST_CHI0 = 1, ST_W = 2, ST_BACKWARD = 3, ST_CHI0_MAIN = 4, ST_W_MAIN = 5 };
 int stage_begin(lrs_ctx* ctx, Stage s);
 // Creates the second stream and its events on first use.
 int aux_stream_ready(lrs_ctx* ctx);

@@ -34,7 +34,8 @@ class lrs_stats_t(C.Structure):
     _fields_ = [("ms_project", C.c_double), ("ms_chi0", C.c_double), ("ms_w", C.c_double),
                 ("ms_backward", C.c_double), ("ms_chi0_main", C.c_double), ("flop_chi0", C.c_double),
                 ("flop_w", C.c_double), ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
-                ("device_bytes_peak", C.c_int64), ("status_word", C.c_int), ("flop_w_executed", C.c_double)]
+                ("device_bytes_peak", C.c_int64), ("status_word", C.c_int), ("flop_w_executed", C.c_double),
+                ("ms_w_main", C.c_double), ("flop_w_main", C.c_double), ("w_main_launches", C.c_int64)]
 
 
 if not os.path.exists(LIB_PATH):
