@@ -11,6 +11,9 @@ Every function is a plain, slow, obviously correct restatement of the paper,
 in float64/complex128 NumPy:
 
   projection.project_direct   Eq. (bloch), Sec. VI.B method 1 (direct Fourier sum)
+  projection.project_fft_lagrange
+                              Sec. VI.B method 2 (FFT to the cell grid, 3rd-degree
+                              Lagrange interpolation, Bloch phase)
   quadrature.*                Eq. (chi1) with the single-grid map of App. D.1
                               ("Energy integration"); mu mid-gap, zeta rule
   chi0.chi0_pairs             sum over occupied/unoccupied pairs implied by
