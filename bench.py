@@ -66,6 +66,10 @@ def dyson_roofline(st, workload=None, version=None):
     return r
 
 
+def proj_mode(lrs, args):
+    return lrs.LRS_PROJ_FFT_LAGRANGE3 if args.projection == "fft" else lrs.LRS_PROJ_EXACT
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -217,8 +221,10 @@ def run_ours(args):
     scr.set_sites([s])
     scr.set_frequency_quadrature(wl.nfreq)
 
+    pmode = proj_mode(lrs, args)
+
     def step():
-        scr.project()
+        scr.project(mode=pmode)
         scr.build_chi0()
         scr.solve_w()
 
@@ -270,7 +276,7 @@ def run_ours(args):
             scr2.load(o)
             scr2.set_sites([s])
             scr2.set_frequency_quadrature(wl.nfreq)
-            scr2.project()
+            scr2.project(mode=pmode)
             scr2.build_chi0()
             scr2.solve_w()
             scr2.get_w(0)
@@ -315,7 +321,7 @@ def run_ours(args):
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        scr3.project()
+        scr3.project(mode=pmode)
         scr3.build_chi0()
         scr3.solve_w()
         p1.record(stream)
@@ -345,7 +351,7 @@ def run_ours(args):
             "dtype": {"fp64": "f64", "bf16x3": "bf16x3/f32acc/f64", "fp16x3": "fp16x3/f32acc/f64"}[args.precision],
             "data": "synthetic (seeded generator; no DFT orbitals)",
             "config": {"workload": args.workload, "npts": n, "K": K, "nfreq": nf, "ng": o.ng,
-                       "precision": args.precision, "replicas_per_gpu": 1,
+                       "precision": args.precision, "replicas_per_gpu": 1, "projection": args.projection,
                        "l2": "inputs larger than L2 (coefficients %d MB, orbitals %d MB)" % (
                            o.coeff.nbytes >> 20, (n * K * 16) >> 20)},
             "tflops": (flop_chi0 + 14.0 / 3.0 * n ** 3) / (ms * 1e-3) / 1e12,
@@ -400,8 +406,10 @@ def run_ours_multisite(args):
     scr.set_sites(wl.sites)
     scr.set_frequency_quadrature(wl.nfreq)
     tuned = None
+    pmode = proj_mode(lrs, args)
+    scr.set_option(lrs.LRS_OPT_GRAPH_PROJECTION, pmode)
     if args.precision != "fp64":
-        scr.project()
+        scr.project(mode=pmode)
         tuned = scr.autotune()
     scr.graph_capture()
     scr.synchronize()
@@ -430,7 +438,7 @@ def run_ours_multisite(args):
     nsites = len(wl.sites)
     value = nsites_total * 1e3 / ms
     # stage split of one eager build (event-timed inside the library)
-    scr.project()
+    scr.project(mode=pmode)
     scr.build_chi0()
     scr.solve_w()
     st = scr.stats()
@@ -468,6 +476,7 @@ def run_ours_multisite(args):
             "data": "synthetic (seeded generator; no DFT orbitals)",
             "config": {"workload": args.workload, "sites": nsites, "npts_min": min(sizes), "npts_max": max(sizes),
                        "npts_sum": sum(sizes), "K": K, "nfreq": wl.nfreq, "ng": o.ng, "precision": args.precision,
+                       "projection": args.projection,
                        "graph": "one CUDA graph replay per step", "autotuned": tuned,
                        "l2": "inputs larger than L2"},
             "tflops": flop_all / (ms * 1e-3) / 1e12,
@@ -494,6 +503,8 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the one-step timing of the plain FP64 path on the same workload")
     ap.add_argument("--workload", default="single-site-3520", choices=sorted(WORKLOADS))
+    ap.add_argument("--projection", default="exact", choices=["exact", "fft"],
+                    help="Sec. VI.B method 1 (direct sum) or method 2 (FFT + cubic Lagrange, auto grid)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

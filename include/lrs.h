@@ -53,6 +53,8 @@ extern "C" {
 
 /* projection modes */
 #define LRS_PROJ_EXACT    0   /* direct Fourier sum, Sec. VI.B method 1 */
+#define LRS_PROJ_FFT_LAGRANGE3 1 /* FFT to the cell grid, 3rd-degree Lagrange interpolation, Sec. VI.B method 2 */
+#define LRS_FFT_MAX_N   256   /* largest FFT length per lattice direction */
 
 /* options (lrs_set_option) */
 #define LRS_OPT_DYSON_BASIS      1  /* value: LRS_DYSON_AUTO, LRS_DYSON_FULL or LRS_DYSON_LM */
@@ -67,6 +69,7 @@ extern "C" {
 #define LRS_SOLVER_AUTO   0   /* SPD inverse when every radial Coulomb block has a Cholesky factor, else LU */
 #define LRS_SOLVER_LU     1   /* LU with partial pivoting of I - C X, C as right-hand sides */
 #define LRS_SOLVER_SPD    2   /* Z = F (I - F^T X F)^-1 F^T with C = F F^T (LRS_ERR_STATE if C has no factor) */
+#define LRS_OPT_GRAPH_PROJECTION 7  /* value: LRS_PROJ_EXACT (default) or LRS_PROJ_FFT_LAGRANGE3, recorded by lrs_graph_capture */
 
 typedef struct lrs_ctx lrs_ctx;
 
@@ -184,11 +187,36 @@ int lrs_get_frequency_quadrature(lrs_ctx* ctx, double* t, double* w);
 
 /*
  * Project the orbitals onto the grids of `nsite` sites (`sites` = NULL means
- * all): psi_kb(tau + r_p) by the direct Fourier sum (Eq. (bloch), Sec. VI.B
- * method 1), as a complex contraction over G in the context's precision.
- * Errors: LRS_ERR_STATE (no orbitals/sites), LRS_ERR_ARG, LRS_ERR_OOM.
+ * all), psi_kb(tau + r_p), by
+ *   LRS_PROJ_EXACT          the direct Fourier sum (Eq. (bloch), Sec. VI.B
+ *                           method 1), a complex contraction over G in the
+ *                           context's precision;
+ *   LRS_PROJ_FFT_LAGRANGE3  Sec. VI.B method 2: u_kb on the grid x_m =
+ *                           sum_i (m_i / N_i) a_i by inverse FFT of C_kb(G)
+ *                           (fp32 in mixed contexts, float64 in LRS_FP64),
+ *                           3rd-degree Lagrange interpolation through the
+ *                           nodes floor(s_i) - 1 .. floor(s_i) + 2 of each
+ *                           lattice direction (s_i = N_i times the
+ *                           fractional coordinate, indices periodic), then
+ *                           exp(i k.r) / sqrt(Omega).  An approximation whose
+ *                           error falls as N^-4 (lrs_set_fft_grid).  Device
+ *                           memory: one grid N1 N2 N3 nbands complex.
+ * Errors: LRS_ERR_STATE (no orbitals/sites), LRS_ERR_ARG (grid cannot hold
+ * the G set), LRS_ERR_UNSUPPORTED (unknown mode, no FFT length), LRS_ERR_OOM.
  */
 int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode);
+
+/*
+ * FFT grid of LRS_PROJ_FFT_LAGRANGE3: N_i points along lattice vector a_i,
+ * each 2^a 3^b <= LRS_FFT_MAX_N and >= 2 max|n_i| + 1 over the loaded G set
+ * (checked at projection).  n1 = n2 = n3 = 0 selects per direction the
+ * smallest such length >= 2 (2 max|n_i| + 1) (oversampling 2).
+ * lrs_get_fft_grid returns the grid a projection would use now.
+ * Errors: LRS_ERR_ARG (not 2^a 3^b, out of range), LRS_ERR_STATE (get
+ * without orbitals).
+ */
+int lrs_set_fft_grid(lrs_ctx* ctx, int n1, int n2, int n3);
+int lrs_get_fft_grid(lrs_ctx* ctx, int* n /* [3] */);
 
 /*
  * Set / get the site-grid orbitals directly (bypassing lrs_project).
@@ -277,7 +305,8 @@ int lrs_solve_w_static(int npts, int lmax, const double* pts_dev, const double* 
                        const double* chi0_dev, double* w_dev, void* stream);
 
 /*
- * Record the whole build of `nsite` sites (NULL = all) - projection, chi0 in
+ * Record the whole build of `nsite` sites (NULL = all) - projection (mode
+ * LRS_OPT_GRAPH_PROJECTION), chi0 in
  * one persistent tensor-core launch over every (site, tile, tile, frequency)
  * unit, and the Dyson solves - as a CUDA graph on the context stream, which
  * must not be the legacy default stream.  The call first runs the build once

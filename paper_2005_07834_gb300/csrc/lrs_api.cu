@@ -210,6 +210,8 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
+  release(ctx, w.fft_grid); release(ctx, w.fft_index); release(ctx, w.fft_tw);
+  w.fft_plan_ok = false;
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
 
@@ -293,6 +295,11 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
       return LRS_OK;
+    case LRS_OPT_GRAPH_PROJECTION:
+      if (value != LRS_PROJ_EXACT && value != LRS_PROJ_FFT_LAGRANGE3)
+        return set_error(LRS_ERR_ARG, "projection mode %d unknown", value);
+      ctx->graph_projection = value;
+      return LRS_OK;
     case LRS_OPT_DYSON_SOLVER:
       if (value != LRS_SOLVER_AUTO && value != LRS_SOLVER_LU && value != LRS_SOLVER_SPD)
         return set_error(LRS_ERR_ARG, "Dyson solver %d unknown", value);
@@ -369,6 +376,7 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   ctx->kw.assign(kweights, kweights + nk);
   ctx->energies.assign(energies, energies + (size_t)nk * nbands);
   ctx->gvec.assign(gvec, gvec + 3 * (size_t)ng);
+  ctx->ws.fft_plan_ok = false;   // the FFT index tables follow the G set
   for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = 0;
   for (int gi = 0; gi < ng; ++gi)
     for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = std::max(ctx->gmax_idx[i], std::abs(gvec[3 * gi + i]));
@@ -525,22 +533,48 @@ int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode) {
   clear_error();
   if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
   if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
-  if (mode != LRS_PROJ_EXACT) return set_error(LRS_ERR_UNSUPPORTED, "projection mode %d not available", mode);
+  if (mode != LRS_PROJ_EXACT && mode != LRS_PROJ_FFT_LAGRANGE3)
+    return set_error(LRS_ERR_UNSUPPORTED, "projection mode %d not available", mode);
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
   std::vector<int> list;
   LRS_TRY(site_list(ctx, nsite, sites, list));
   for (int i : list) LRS_TRY(alloc_psi(ctx, ctx->sites[i]));
   LRS_TRY(stage_begin(ctx, ST_PROJECT));
+  if (mode == LRS_PROJ_FFT_LAGRANGE3) {
+    LRS_TRY(project_fft(ctx, list));
+  } else {
+    for (int i : list) {
+      Site& s = ctx->sites[i];
+      if (ctx->precision == LRS_FP64) LRS_TRY(project_fp64(ctx, s));
+      else LRS_TRY(project_mixed(ctx, s));
+    }
+  }
   for (int i : list) {
     Site& s = ctx->sites[i];
-    if (ctx->precision == LRS_FP64) LRS_TRY(project_fp64(ctx, s));
-    else LRS_TRY(project_mixed(ctx, s));
     s.has_psi = true;
     s.has_chi0 = s.has_w = false;
   }
   LRS_TRY(stage_end(ctx, ST_PROJECT));
   return LRS_OK;
+}
+
+int lrs_set_fft_grid(lrs_ctx* ctx, int n1, int n2, int n3) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  const int n[3] = {n1, n2, n3};
+  const bool automatic = n1 == 0 && n2 == 0 && n3 == 0;
+  for (int d = 0; d < 3 && !automatic; ++d)
+    if (!fft_length_ok(n[d])) return set_error(LRS_ERR_ARG, "FFT length %d is not 2^a 3^b in [1, %d]", n[d], LRS_FFT_MAX_N);
+  for (int d = 0; d < 3; ++d) ctx->fft_n[d] = n[d];
+  return LRS_OK;
+}
+
+int lrs_get_fft_grid(lrs_ctx* ctx, int* n) {
+  clear_error();
+  if (!ctx || !n) return set_error(LRS_ERR_ARG, "NULL argument");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  return fft_grid_dims(ctx, n);
 }
 
 int lrs_set_energies(lrs_ctx* ctx, const double* energies) {
@@ -795,7 +829,7 @@ int lrs_graph_capture(lrs_ctx* ctx, int nsite, const int* sites) {
   if (ctx->stream == nullptr)
     return set_error(LRS_ERR_STATE, "graph capture needs a non-default stream (lrs_create/lrs_set_stream)");
   // one eager build allocates every buffer, builds cached operands and checks the status words
-  LRS_TRY(lrs_project(ctx, nsite, sites, LRS_PROJ_EXACT));
+  LRS_TRY(lrs_project(ctx, nsite, sites, ctx->graph_projection));
   LRS_TRY(lrs_build_chi0(ctx, nsite, sites));
   LRS_TRY(lrs_solve_w(ctx, nsite, sites));
   DeviceGuard g(ctx->device);
@@ -807,7 +841,7 @@ int lrs_graph_capture(lrs_ctx* ctx, int nsite, const int* sites) {
   }
   LRS_CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   ctx->capturing = true;
-  int rc = lrs_project(ctx, nsite, sites, LRS_PROJ_EXACT);
+  int rc = lrs_project(ctx, nsite, sites, ctx->graph_projection);
   if (rc == LRS_OK) rc = lrs_build_chi0(ctx, nsite, sites);
   if (rc == LRS_OK) rc = lrs_solve_w(ctx, nsite, sites);
   ctx->capturing = false;

@@ -143,6 +143,14 @@ struct Workspace {
   DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
+  // FFT projection: grid [N1][N2][N3][nb] of one k-point (fp32 or fp64 complex), index tables, twiddles
+  DevBuf<double2> fft_grid;
+  DevBuf<int> fft_index;                // col_xy | col_ptr | ent_g | ent_z | populated x (offsets fft_off)
+  DevBuf<double2> fft_tw;               // exp(2 pi i j / N_d), d = 1, 2, 3
+  int fft_off[5] = {0, 0, 0, 0, 0};
+  int fft_ncol = 0, fft_nx = 0;
+  int fft_plan_n[3] = {0, 0, 0};
+  bool fft_plan_ok = false;
   DevBuf<uint16_t> proj_a, proj_b;      // projection: phase planes, coefficient planes
   DevBuf<float> scales;                 // chi0: fp16 operand scales per frequency
   DevBuf<float> proj_scale;             // projection: coefficient scale and unscale
@@ -161,6 +169,8 @@ struct lrs_ctx {
   int dyson_basis = LRS_DYSON_AUTO;    // full grid or lm basis
   int dyson_solver = LRS_SOLVER_AUTO;  // lm basis: LU of I - C X, or the SPD inverse
   int chi0_tn = 128;                   // chi0 tensor-core tile width (64 or 128)
+  int fft_n[3] = {0, 0, 0};            // FFT grid of the method-2 projection (0: automatic)
+  int graph_projection = LRS_PROJ_EXACT;  // projection mode recorded by lrs_graph_capture
   double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
 
@@ -219,6 +229,10 @@ int stage_end(lrs_ctx* ctx, Stage s);
 // Projection (k_project.cu)
 int project_fp64(lrs_ctx* ctx, Site& s);
 int project_mixed(lrs_ctx* ctx, Site& s);
+// Method 2 (k_fft.cu): FFT to the cell grid + 3rd-degree Lagrange interpolation, all listed sites.
+int project_fft(lrs_ctx* ctx, const std::vector<int>& sites);
+int fft_grid_dims(lrs_ctx* ctx, int n[3]);
+bool fft_length_ok(int n);
 
 // Denominators d[f][col] = w/(mu + i t_f - eps) (k_chi0_fp64.cu)
 int build_denominators(lrs_ctx* ctx);

@@ -22,10 +22,11 @@ LIB_PATH = os.environ.get("LRS_LIBRARY", os.path.join(_HERE, "liblrs.so"))
 LRS_OK, LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA, LRS_ERR_STATE = 0, 1, 2, 3, 4
 LRS_ERR_TIMEOUT, LRS_ERR_NUMERIC, LRS_ERR_UNSUPPORTED = 5, 6, 7
 LRS_FP64, LRS_MIXED_BF16X3, LRS_MIXED_FP16X3 = 0, 1, 2
-LRS_PROJ_EXACT = 0
+LRS_PROJ_EXACT, LRS_PROJ_FFT_LAGRANGE3 = 0, 1
+LRS_FFT_MAX_N = 256
 LRS_OPT_DYSON_BASIS, LRS_OPT_CHI0_SEGMENT, LRS_OPT_PROJ_SEGMENT, LRS_OPT_CHI0_TILE_N = 1, 2, 3, 4
 LRS_DYSON_AUTO, LRS_DYSON_FULL, LRS_DYSON_LM = 0, 1, 2
-LRS_OPT_WORKSPACE_GB, LRS_OPT_DYSON_SOLVER = 5, 6
+LRS_OPT_WORKSPACE_GB, LRS_OPT_DYSON_SOLVER, LRS_OPT_GRAPH_PROJECTION = 5, 6, 7
 LRS_SOLVER_AUTO, LRS_SOLVER_LU, LRS_SOLVER_SPD = 0, 1, 2
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
@@ -59,6 +60,8 @@ _SIGS = {
     "lrs_set_frequency_quadrature": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _DP, _DP]),
     "lrs_get_frequency_quadrature": (C.c_int, [_P, _DP, _DP]),
     "lrs_project": (C.c_int, [_P, C.c_int, _IP, C.c_int]),
+    "lrs_set_fft_grid": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "lrs_get_fft_grid": (C.c_int, [_P, _IP]),
     "lrs_set_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_build_chi0": (C.c_int, [_P, C.c_int, _IP]),
@@ -201,6 +204,14 @@ class Screening:
     def project(self, sites=None, mode=LRS_PROJ_EXACT):
         n, p, _keep = self._sites(sites)
         _check(lrs_project(self.ctx, n, p, mode), "lrs_project")
+
+    def set_fft_grid(self, n1=0, n2=0, n3=0):
+        _check(lrs_set_fft_grid(self.ctx, int(n1), int(n2), int(n3)), "lrs_set_fft_grid")
+
+    def get_fft_grid(self):
+        n = (C.c_int * 3)()
+        _check(lrs_get_fft_grid(self.ctx, n), "lrs_get_fft_grid")
+        return tuple(n)
 
     def set_site_orbitals(self, site, psi):
         psi, view = _c128_view(psi)
