@@ -222,6 +222,7 @@ def run_ours(args):
     scr.set_frequency_quadrature(wl.nfreq)
 
     pmode = proj_mode(lrs, args)
+    scr.set_fft_grid(*wl.fft_grid)
 
     def step():
         scr.project(mode=pmode)
@@ -276,6 +277,7 @@ def run_ours(args):
             scr2.load(o)
             scr2.set_sites([s])
             scr2.set_frequency_quadrature(wl.nfreq)
+            scr2.set_fft_grid(*wl.fft_grid)
             scr2.project(mode=pmode)
             scr2.build_chi0()
             scr2.solve_w()
@@ -321,6 +323,7 @@ def run_ours(args):
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         p0.record(stream)
+        scr3.set_fft_grid(*wl.fft_grid)
         scr3.project(mode=pmode)
         scr3.build_chi0()
         scr3.solve_w()
@@ -399,7 +402,7 @@ def run_ours_multisite(args):
         # sites are independent: each rank builds its own share (no data-path collective)
         from paper_2005_07834_gb300 import sharding
         mine = sharding.shard_sites(wl.sites, K, wl.nfreq, rank, world)
-        wl = type(wl)(wl.name, o, [wl.sites[i] for i in mine], wl.nfreq)
+        wl = type(wl)(wl.name, o, [wl.sites[i] for i in mine], wl.nfreq, wl.fft_grid)
     stream = torch.cuda.Stream()
     scr = lrs.Screening(local, args.precision, stream.cuda_stream)
     scr.load(o)
@@ -407,6 +410,7 @@ def run_ours_multisite(args):
     scr.set_frequency_quadrature(wl.nfreq)
     tuned = None
     pmode = proj_mode(lrs, args)
+    scr.set_fft_grid(*wl.fft_grid)
     scr.set_option(lrs.LRS_OPT_GRAPH_PROJECTION, pmode)
     if args.precision != "fp64":
         scr.project(mode=pmode)
@@ -504,7 +508,7 @@ def main():
                     help="skip the one-step timing of the plain FP64 path on the same workload")
     ap.add_argument("--workload", default="single-site-3520", choices=sorted(WORKLOADS))
     ap.add_argument("--projection", default="exact", choices=["exact", "fft"],
-                    help="Sec. VI.B method 1 (direct sum) or method 2 (FFT + cubic Lagrange, auto grid)")
+                    help="Sec. VI.B method 1 (direct sum) or method 2 (FFT + cubic Lagrange on the workload's grid)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_z_kernel(const double2* __res
                                                             const int* __restrict__ col_xy,
                                                             const int* __restrict__ col_ptr,
                                                             const int* __restrict__ ent_g,
-                                                            const int* __restrict__ ent_z, int N3,
+                                                            const int* __restrict__ ent_z, int ncol, int N3,
                                                             const double2* __restrict__ tw_d,
                                                             typename Cplx<T>::type* __restrict__ grid) {
   using C = typename Cplx<T>::type;
@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_z_kernel(const double2* __res
   C* X = reinterpret_cast<C*>(fft_smem);
   C* Y = X + N3 * BC;
   C* tw = Y + N3 * BC;
-  const int c = blockIdx.x, b0 = blockIdx.y * BC;
+  // band chunk fastest: neighbouring CTAs read adjacent bands of the same rows
+  const int c = blockIdx.y + blockIdx.z * gridDim.y, b0 = blockIdx.x * BC;
+  if (c >= ncol) return;
   for (int i = threadIdx.x; i < N3 * BC; i += blockDim.x) X[i] = C{(T)0, (T)0};
   for (int i = threadIdx.x; i < N3; i += blockDim.x) tw[i] = C{(T)tw_d[i].x, (T)tw_d[i].y};
   __syncthreads();
@@ -127,13 +129,14 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_z_kernel(const double2* __res
   }
 }
 
-// In-place transform of length N along one axis.  Line l = (ai, ci), ai <
-// na, ci < nc: a = a_list[ai] (or ai), elements at a sa + ci sc + i stride.
+// In-place transform of length N along one axis.  Line (ai, ci) =
+// (blockIdx.y, blockIdx.z): a = a_list[ai] (or ai), elements at
+// a sa + ci sc + i stride; blockIdx.x is the band chunk.
 template <typename T>
 __global__ void __launch_bounds__(FFT_THREADS) fft_line_kernel(typename Cplx<T>::type* __restrict__ grid, int nb,
                                                                int N, long long stride,
                                                                const int* __restrict__ a_list, long long sa,
-                                                               int nc, long long sc,
+                                                               long long sc,
                                                                const double2* __restrict__ tw_d) {
   using C = typename Cplx<T>::type;
   constexpr int BC = FftBands<T>::BC;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_line_kernel(typename Cplx<T>:
   C* X = reinterpret_cast<C*>(fft_smem);
   C* Y = X + N * BC;
   C* tw = Y + N * BC;
-  const int ai = blockIdx.x / nc, ci = blockIdx.x % nc, b0 = blockIdx.y * BC;
+  const int ai = blockIdx.y, ci = blockIdx.z, b0 = blockIdx.x * BC;
   const long long a = a_list ? a_list[ai] : ai;
   const size_t base = (size_t)(a * sa + ci * sc);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = C{(T)tw_d[i].x, (T)tw_d[i].y};
@@ -349,17 +352,19 @@ static int project_fft_t(lrs_ctx* ctx, const std::vector<int>& list, const int n
     const int nocc = ctx->nocc[k];
     LRS_CUDA_TRY(cudaMemsetAsync(grid, 0, grid_bytes, ctx->stream));
     const double2* ck = ctx->coeff.ptr + (size_t)k * ctx->ng * nb;
-    fft_z_kernel<T><<<dim3(ws.fft_ncol, nchunk), FFT_THREADS, fft_smem_bytes<T>(n[2]), ctx->stream>>>(
-        ck, nb, col_xy, col_ptr, ent_g, ent_z, n[2], tw3, grid);
+    const unsigned cy = (unsigned)std::min(ws.fft_ncol, 32768), cz = (unsigned)((ws.fft_ncol + cy - 1) / cy);
+    fft_z_kernel<T><<<dim3(nchunk, cy, cz), FFT_THREADS, fft_smem_bytes<T>(n[2]), ctx->stream>>>(
+        ck, nb, col_xy, col_ptr, ent_g, ent_z, ws.fft_ncol, n[2], tw3, grid);
     LRS_TRY(after_launch(ctx, "fft_z_kernel"));
     // y: lines (populated x, z), stride N3 nb
-    fft_line_kernel<T><<<dim3((unsigned)ws.fft_nx * n[2], nchunk), FFT_THREADS, fft_smem_bytes<T>(n[1]),
-                         ctx->stream>>>(grid, nb, n[1], (long long)n[2] * nb, xs, (long long)n[1] * n[2] * nb, n[2],
+    fft_line_kernel<T><<<dim3(nchunk, (unsigned)ws.fft_nx, (unsigned)n[2]), FFT_THREADS, fft_smem_bytes<T>(n[1]),
+                         ctx->stream>>>(grid, nb, n[1], (long long)n[2] * nb, xs, (long long)n[1] * n[2] * nb,
                                         (long long)nb, tw2);
     LRS_TRY(after_launch(ctx, "fft_line_kernel"));
     // x: lines (y, z), stride N2 N3 nb
-    fft_line_kernel<T><<<dim3((unsigned)n[1] * n[2], nchunk), FFT_THREADS, fft_smem_bytes<T>(n[0]), ctx->stream>>>(
-        grid, nb, n[0], (long long)n[1] * n[2] * nb, nullptr, (long long)n[2] * nb, n[2], (long long)nb, tw1);
+    fft_line_kernel<T><<<dim3(nchunk, (unsigned)n[1], (unsigned)n[2]), FFT_THREADS, fft_smem_bytes<T>(n[0]),
+                         ctx->stream>>>(grid, nb, n[0], (long long)n[1] * n[2] * nb, nullptr, (long long)n[2] * nb,
+                                        (long long)nb, tw1);
     LRS_TRY(after_launch(ctx, "fft_line_kernel"));
     for (int d = 0; d < 3; ++d) geo.k[d] = ctx->kpts[3 * (size_t)k + d];
     for (int i : list) {

@@ -73,6 +73,7 @@ class Workload:
     orbitals: Orbitals
     sites: list = field(default_factory=list)
     nfreq: int = 16
+    fft_grid: tuple = (0, 0, 0)   # cell grid of the method-2 projection (0: automatic)
 
 
 def cubic_cell(a: float) -> np.ndarray:
@@ -148,7 +149,7 @@ def single_site_260(seed=0) -> Workload:
     k, w = gamma_centred_kmesh(cell, 2)
     orb = draw_orbitals(cell, k, w, 3.0, 8, 24, seed)
     site = site_grid(np.full(3, 5.0), 10, 26, 4.0)
-    return Workload("single-site-260pt-k8-b32", orb, [site], nfreq=12)
+    return Workload("single-site-260pt-k8-b32", orb, [site], nfreq=12, fft_grid=(16, 16, 16))
 
 
 def single_site_3520(seed=0) -> Workload:
@@ -157,7 +158,7 @@ def single_site_3520(seed=0) -> Workload:
     k, w = gamma_centred_kmesh(cell, 2)
     orb = draw_orbitals(cell, k, w, 4.0, 128, 512, seed)
     site = site_grid(np.full(3, 10.0), 32, 110, 6.0)
-    return Workload("single-site-3520pt-k8-b640", orb, [site], nfreq=16)
+    return Workload("single-site-3520pt-k8-b640", orb, [site], nfreq=16, fft_grid=(48, 48, 48))
 
 
 def batched_sites(orbitals: Orbitals, nsites=64, seed=1, radius=4.0) -> list:
@@ -171,7 +172,8 @@ def batched_sites(orbitals: Orbitals, nsites=64, seed=1, radius=4.0) -> list:
 
 def batched_64_sites(seed=0) -> Workload:
     base = single_site_260(seed)
-    return Workload("batched-64-sites-k8-b32", base.orbitals, batched_sites(base.orbitals), nfreq=16)
+    return Workload("batched-64-sites-k8-b32", base.orbitals, batched_sites(base.orbitals), nfreq=16,
+                    fft_grid=(16, 16, 16))
 
 
 def large_cell_16_sites(seed=0) -> Workload:
@@ -183,7 +185,7 @@ def large_cell_16_sites(seed=0) -> Workload:
     rng = np.random.default_rng(1)
     centres = rng.uniform(0.0, 1.0, (16, 3)) @ cell
     sites = [site_grid(c, 48, 194, 6.0) for c in centres]
-    return Workload("large-cell-16-sites-k2-b4096", orb, sites, nfreq=20)
+    return Workload("large-cell-16-sites-k2-b4096", orb, sites, nfreq=20, fft_grid=(96, 96, 96))
 
 
 def tiny(nk=1, nocc=3, nunocc=5, gmax=2.0, a=6.0, nrad=3, nang=14, seed=0) -> Workload:
