@@ -22,6 +22,8 @@ in float64/complex128 NumPy:
                               functions (Sec. VI.D) multiplied and summed
   coulomb.coulomb_multipole   multipole form of v, Sec. VI.E
   dyson.screened_interaction  W = v + v chi0 W, Eq. (eq-reducible), (eq-W)
+  induced.induced_potential   core-hole response in the (r, l, m) basis, Sec. VI.E,
+                              with the short-range v1 of Eq. (eq-partition)
   grad.*                      analytic gradients of a scalar loss of W in pair
                               form (the paper has no gradients)
 
