@@ -207,6 +207,37 @@ int lrs_get_frequency_quadrature(lrs_ctx* ctx, double* t, double* w);
 int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode);
 
 /*
+ * Whether site `site` was recognised as a radial x angular product grid
+ * (p = shell * nang + a, the same directions on every shell) and its shape;
+ * nrad = nang = 0 otherwise.  Any output may be NULL.  Errors: LRS_ERR_ARG.
+ */
+int lrs_site_grid_shape(lrs_ctx* ctx, int site, int* product, int* nrad, int* nang);
+
+/*
+ * Induced density and potential of a screened spherical short-range potential
+ * at the site centre (the core-hole response of Sec. VI.E).  The potential is
+ * the short-range part of Eq. (eq-partition) for v_ext = q / r:
+ *   v1(r) = q (1/r - 1/R_S) for r < R_S (shell_radius), 0 beyond.
+ * With chi0 of the site expanded in real spherical harmonics Y_lm, l <= lresp
+ * (Y_l^0, sqrt(2) Re Y_l^m for m > 0, sqrt(2) Im Y_l^|m| for m < 0, Y_l^m the
+ * complex harmonics with the Condon-Shortley phase; index l^2 + l + m), the
+ * paper's S = I - chi0_lm v and chi = S^-1 chi0_lm are formed with every
+ * radial integral taken by the grid's radial quadrature, and
+ *   rho_lm(r_j)   = int d^3r' chi_(lm;00)(r_j, r') v1(r')      (sqrt(4 pi) Y_00 v1)
+ *   v_ind_lm(r_j) = int dr r^2 rho_lm(r) 4 pi/(2l+1) r_<^l / r_>^(l+1)
+ * lresp = 0 is the paper's default; lresp = L (the site's lmax) keeps every l
+ * and then equals v Q chi Q v1 of the full-grid Dyson equation.
+ * Requires chi0 (lrs_build_chi0) and a product grid; FP64 in every precision.
+ * Outputs (host, each may be NULL): rho_lm and vind_lm [nrad][(lresp+1)^2],
+ * vind_grid [npts] = sum_lm v_ind_lm(r_j) Y_lm(Omega_a).  Synchronous.
+ * Errors: LRS_ERR_ARG (site, lresp outside [0, lmax], shell radius),
+ * LRS_ERR_STATE (no chi0, during graph capture), LRS_ERR_UNSUPPORTED (not a
+ * product grid), LRS_ERR_NUMERIC (singular S).
+ */
+int lrs_induced_potential(lrs_ctx* ctx, int site, double q, double shell_radius, int lresp, double* rho_lm,
+                          double* vind_lm, double* vind_grid);
+
+/*
  * FFT grid of LRS_PROJ_FFT_LAGRANGE3: N_i points along lattice vector a_i,
  * each 2^a 3^b <= LRS_FFT_MAX_N and >= 2 max|n_i| + 1 over the loaded G set
  * (checked at projection).  n1 = n2 = n3 = 0 selects per direction the

@@ -211,6 +211,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
   release(ctx, w.fft_grid); release(ctx, w.fft_index); release(ctx, w.fft_tw);
+  release(ctx, w.induced);
   w.fft_plan_ok = false;
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
@@ -557,6 +558,34 @@ int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode) {
   }
   LRS_TRY(stage_end(ctx, ST_PROJECT));
   return LRS_OK;
+}
+
+int lrs_site_grid_shape(lrs_ctx* ctx, int site, int* product, int* nrad, int* nang) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (site < 0 || site >= (int)ctx->sites.size()) return set_error(LRS_ERR_ARG, "site %d out of range", site);
+  const Site& s = ctx->sites[site];
+  if (product) *product = s.product ? 1 : 0;
+  if (nrad) *nrad = s.product ? s.nrad : 0;
+  if (nang) *nang = s.product ? s.nang : 0;
+  return LRS_OK;
+}
+
+int lrs_induced_potential(lrs_ctx* ctx, int site, double q, double shell_radius, int lresp, double* rho_lm,
+                          double* vind_lm, double* vind_grid) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (site < 0 || site >= (int)ctx->sites.size()) return set_error(LRS_ERR_ARG, "site %d out of range", site);
+  Site& s = ctx->sites[site];
+  if (!s.has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", site);
+  if (!s.product) return set_error(LRS_ERR_UNSUPPORTED, "site %d is not a radial x angular product grid", site);
+  if (lresp < 0 || lresp > s.lmax) return set_error(LRS_ERR_ARG, "l_resp %d outside [0, %d]", lresp, s.lmax);
+  if (!(shell_radius > 0.0) || !std::isfinite(shell_radius) || !std::isfinite(q))
+    return set_error(LRS_ERR_ARG, "shell radius must be positive and finite, q finite");
+  if (ctx->capturing) return set_error(LRS_ERR_STATE, "the induced response cannot be recorded in a graph");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  return induced_potential(ctx, s, q, shell_radius, lresp, rho_lm, vind_lm, vind_grid);
 }
 
 int lrs_set_fft_grid(lrs_ctx* ctx, int n1, int n2, int n3) {

@@ -143,6 +143,7 @@ struct Workspace {
   DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
+  DevBuf<double> induced;               // induced response: T, X, B, right-hand side, outputs
   // FFT projection: grid [N1][N2][N3][nb] of one k-point (fp32 or fp64 complex), index tables, twiddles
   DevBuf<double2> fft_grid;
   DevBuf<int> fft_index;                // col_xy | col_ptr | ent_g | ent_z | populated x (offsets fft_off)
@@ -277,6 +278,11 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status);
 // lm-basis Dyson on product grids (k_dyson_lm.cu)
 int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);
 int dyson_solve_lm(lrs_ctx* ctx, Site& s);
+
+// Induced density / potential of a screened short-range spherical potential (k_induced.cu);
+// host outputs (rho_lm, vind_lm: [nrad][(lresp+1)^2]; grid: [npts]), each may be NULL.
+int induced_potential(lrs_ctx* ctx, Site& s, double q, double rs, int lresp, double* rho_lm, double* vind_lm,
+                      double* vind_grid);
 
 // Adjoint (k_adjoint.cu: float64; k_tc.cu: tensor-core version for the mixed precisions)
 int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev,

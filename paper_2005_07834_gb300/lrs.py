@@ -61,6 +61,8 @@ _SIGS = {
     "lrs_get_frequency_quadrature": (C.c_int, [_P, _DP, _DP]),
     "lrs_project": (C.c_int, [_P, C.c_int, _IP, C.c_int]),
     "lrs_set_fft_grid": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "lrs_induced_potential": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _DP, _DP, _DP]),
+    "lrs_site_grid_shape": (C.c_int, [_P, C.c_int, _IP, _IP, _IP]),
     "lrs_get_fft_grid": (C.c_int, [_P, _IP]),
     "lrs_set_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
@@ -204,6 +206,23 @@ class Screening:
     def project(self, sites=None, mode=LRS_PROJ_EXACT):
         n, p, _keep = self._sites(sites)
         _check(lrs_project(self.ctx, n, p, mode), "lrs_project")
+
+    def site_grid_shape(self, site):
+        """(is a product grid, shells, directions per shell)."""
+        p, nr, na = C.c_int(), C.c_int(), C.c_int()
+        _check(lrs_site_grid_shape(self.ctx, int(site), C.byref(p), C.byref(nr), C.byref(na)), "lrs_site_grid_shape")
+        return bool(p.value), nr.value, na.value
+
+    def induced_potential(self, site, q, shell_radius, lresp=0):
+        """Returns (rho_lm [nrad, (lresp+1)^2], vind_lm [nrad, (lresp+1)^2], vind_grid [npts])."""
+        _, nrad, _ = self.site_grid_shape(site)
+        l2 = (lresp + 1) ** 2
+        rho = np.zeros((nrad, l2))
+        vind = np.zeros((nrad, l2))
+        grid = np.zeros(self.npts[site])
+        _check(lrs_induced_potential(self.ctx, int(site), float(q), float(shell_radius), int(lresp), _dp(rho),
+                                     _dp(vind), _dp(grid)), "lrs_induced_potential")
+        return rho, vind, grid
 
     def set_fft_grid(self, n1=0, n2=0, n3=0):
         _check(lrs_set_fft_grid(self.ctx, int(n1), int(n2), int(n3)), "lrs_set_fft_grid")
