@@ -24,6 +24,8 @@ in float64/complex128 NumPy:
   dyson.screened_interaction  W = v + v chi0 W, Eq. (eq-reducible), (eq-W)
   induced.induced_potential   core-hole response in the (r, l, m) basis, Sec. VI.E,
                               with the short-range v1 of Eq. (eq-partition)
+  alda.*                      ALDA vertex, Eq. (chi-alda) and (kxc_alda); density and
+                              the exchange-only kernel of the uniform gas
   grad.*                      analytic gradients of a scalar loss of W in pair
                               form (the paper has no gradients)
 
