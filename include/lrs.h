@@ -69,6 +69,10 @@ extern "C" {
 #define LRS_SOLVER_AUTO   0   /* SPD inverse when every radial Coulomb block has a Cholesky factor, else LU */
 #define LRS_SOLVER_LU     1   /* LU with partial pivoting of I - C X, C as right-hand sides */
 #define LRS_SOLVER_SPD    2   /* Z = F (I - F^T X F)^-1 F^T with C = F F^T (LRS_ERR_STATE if C has no factor) */
+/* exchange-correlation kernel of the ALDA vertex (lrs_set_fxc) */
+#define LRS_FXC_NONE      0   /* RPA */
+#define LRS_FXC_USER      1   /* f(r_p) = dv_xc/dn at n(r_p), supplied per grid point */
+#define LRS_FXC_ALDA_X    2   /* exchange-only ALDA of the site density: f = -(1/3)(3/pi)^(1/3) n^(-2/3) */
 #define LRS_OPT_GRAPH_PROJECTION 7  /* value: LRS_PROJ_EXACT (default) or LRS_PROJ_FFT_LAGRANGE3, recorded by lrs_graph_capture */
 
 typedef struct lrs_ctx lrs_ctx;
@@ -205,6 +209,31 @@ int lrs_get_frequency_quadrature(lrs_ctx* ctx, double* t, double* w);
  * the G set), LRS_ERR_UNSUPPORTED (unknown mode, no FFT length), LRS_ERR_OOM.
  */
 int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode);
+
+/*
+ * ALDA vertex correction (Sec. VII "Beyond RPA screening", Eq. (chi-alda)
+ * and (kxc_alda)): chi~ = (1 - chi0 (v + f_xc))^-1 chi0 with the contact
+ * kernel f_xc(r, r') = delta(r - r') f(r).  Once set for a site, lrs_solve_w
+ * returns W~ = v + v chi~ v and lrs_induced_potential screens with chi~; both
+ * use the dressed polarizability chi_eff = (I - chi0 diag(f w))^-1 chi0
+ * (an FP64 LU with npts right-hand sides) in the RPA Dyson solve of either
+ * basis.  lrs_get_chi0 still returns chi0.  kind LRS_FXC_USER takes f
+ * (Ha bohr^3, host [npts]) from `fxc`; LRS_FXC_ALDA_X computes the
+ * exchange-only kernel from the density of the site orbitals at each solve;
+ * LRS_FXC_NONE returns to the RPA.  The correlation parametrisations the
+ * paper uses are not built in (pass them through LRS_FXC_USER).  The adjoint
+ * (lrs_backward) refuses sites with a kernel (LRS_ERR_UNSUPPORTED).
+ * Invalidates the site's W.  Errors: LRS_ERR_ARG.
+ */
+int lrs_set_fxc(lrs_ctx* ctx, int site, int kind, const double* fxc);
+
+/* Electron density n(r_p) = 2 sum_k w_k sum_occ |psi_kv(r_p)|^2 of the site
+ * orbitals (host [npts]).  Errors: LRS_ERR_ARG, LRS_ERR_STATE (no orbitals). */
+int lrs_get_density(lrs_ctx* ctx, int site, double* n);
+
+/* The kernel f(r_p) a solve would use now (host [npts]).
+ * Errors: LRS_ERR_ARG, LRS_ERR_STATE (no kernel set, no orbitals). */
+int lrs_get_fxc(lrs_ctx* ctx, int site, double* fxc);
 
 /*
  * Whether site `site` was recognised as a radial x angular product grid

@@ -213,7 +213,7 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   double* Z = B + rr;                     // [r][r]
   const double* Yang = s.yang.ptr;        // [nang][L2]
   // T[:, j' block] = chi0[:, shell j'] diag(Q_j') Yang        (one launch, batch = shell)
-  LRS_TRY(dgemm_batched(ctx, false, false, n, L2, nang, 1.0, s.chi0.ptr, n, nang, s.wts.ptr, nang, Yang, L2, 0,
+  LRS_TRY(dgemm_batched(ctx, false, false, n, L2, nang, 1.0, s.response_chi(), n, nang, s.wts.ptr, nang, Yang, L2, 0,
                         nullptr, 0.0, T, r, L2, nrad));
   // X = Y^T Q T is symmetric; its transpose is formed, X^T[:, j block] = T[shell j, :]^T diag(Q_j) Yang,
   // so that the 81- (generally (L+1)^2-) wide side of the product is a tile column.  The SPD

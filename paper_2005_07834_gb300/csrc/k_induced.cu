@@ -107,7 +107,7 @@ int induced_potential(lrs_ctx* ctx, Site& s, double q, double rs, int lresp, dou
   double* vind = rho + d;
   double* grid = vind + d;
   // T[:, (j, lm)] = chi0[:, shell j] diag(w_j) Y_sub;  X[(j, lm), :] = Y_sub^T diag(w_j) T[shell j, :]
-  LRS_TRY(dgemm_batched(ctx, false, false, n, L2s, nang, 1.0, s.chi0.ptr, n, nang, s.wts.ptr, nang, s.yang.ptr, L2,
+  LRS_TRY(dgemm_batched(ctx, false, false, n, L2s, nang, 1.0, s.response_chi(), n, nang, s.wts.ptr, nang, s.yang.ptr, L2,
                         0, nullptr, 0.0, T, d, L2s, nrad));
   LRS_TRY(dgemm_batched(ctx, true, false, L2s, d, nang, 1.0, s.yang.ptr, L2, 0, s.wts.ptr, nang, T, d,
                         (long long)nang * d, nullptr, 0.0, X, d, (long long)L2s * d, nrad));

@@ -672,7 +672,7 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
   s.has_v = true;
   double* A = ctx->ws.dyson_a.ptr;
   // A = I - (v Q)(chi0 Q)
-  LRS_TRY(dgemm_t(ctx, false, false, n, n, n, -1.0, s.v.ptr, n, s.wts.ptr, s.chi0.ptr, n, s.wts.ptr, 0.0, A, n));
+  LRS_TRY(dgemm_t(ctx, false, false, n, n, n, -1.0, s.v.ptr, n, s.wts.ptr, s.response_chi(), n, s.wts.ptr, 0.0, A, n));
   add_identity_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(A, n, n, 1.0);
   LRS_TRY(after_launch(ctx, "add_identity_kernel"));
   LRS_TRY(lu_factor(ctx, A, n, ctx->ws.ipiv.ptr, ctx->ws.status.ptr));

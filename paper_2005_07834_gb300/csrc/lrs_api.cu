@@ -50,11 +50,16 @@ void drop_graph(lrs_ctx* ctx) {
   ctx->graph_exec = nullptr;
 }
 
+void dev_free_temp(lrs_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->stats.device_bytes -= (int64_t)bytes;
+}
+
 void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes) {
   if (!p) return;
   drop_graph(ctx);
-  cudaFree(p);
-  ctx->stats.device_bytes -= (int64_t)bytes;
+  dev_free_temp(ctx, p, bytes);
 }
 
 int aux_stream_ready(lrs_ctx* ctx) {
@@ -195,6 +200,9 @@ static void free_site(lrs_ctx* ctx, Site& s) {
   release(ctx, s.rl);
   release(ctx, s.fl);
   s.spd = false;
+  release(ctx, s.fxc);
+  release(ctx, s.chi_eff);
+  s.fxc_kind = LRS_FXC_NONE;
   s.product = false;
   s.has_psi = s.has_chi0 = s.has_w = false;
 }
@@ -560,6 +568,55 @@ int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode) {
   return LRS_OK;
 }
 
+int lrs_set_fxc(lrs_ctx* ctx, int site, int kind, const double* fxc) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  LRS_TRY(check_site(ctx, site));
+  if (kind != LRS_FXC_NONE && kind != LRS_FXC_USER && kind != LRS_FXC_ALDA_X)
+    return set_error(LRS_ERR_ARG, "f_xc kind %d unknown", kind);
+  Site& s = ctx->sites[site];
+  if (kind == LRS_FXC_USER) {
+    if (!fxc) return set_error(LRS_ERR_ARG, "fxc is NULL");
+    if (!finite_all(fxc, (size_t)s.npts)) return set_error(LRS_ERR_ARG, "non-finite f_xc value");
+    DeviceGuard g(ctx->device);
+    if (g.rc) return g.rc;
+    LRS_TRY(ensure(ctx, s.fxc, (size_t)s.npts));
+    LRS_CUDA_TRY(cudaMemcpyAsync(s.fxc.ptr, fxc, s.npts * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  s.fxc_kind = kind;
+  s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_get_density(lrs_ctx* ctx, int site, double* n) {
+  clear_error();
+  if (!ctx || !n) return set_error(LRS_ERR_ARG, "NULL argument");
+  LRS_TRY(check_site(ctx, site));
+  Site& s = ctx->sites[site];
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_TRY(ensure(ctx, ctx->ws.alda_n, (size_t)s.npts));
+  LRS_TRY(site_density(ctx, s, ctx->ws.alda_n.ptr));
+  LRS_CUDA_TRY(cudaMemcpyAsync(n, ctx->ws.alda_n.ptr, s.npts * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
+int lrs_get_fxc(lrs_ctx* ctx, int site, double* fxc) {
+  clear_error();
+  if (!ctx || !fxc) return set_error(LRS_ERR_ARG, "NULL argument");
+  LRS_TRY(check_site(ctx, site));
+  Site& s = ctx->sites[site];
+  if (s.fxc_kind == LRS_FXC_NONE) return set_error(LRS_ERR_STATE, "site %d has no f_xc kernel", site);
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_TRY(site_fxc(ctx, s));
+  LRS_CUDA_TRY(cudaMemcpyAsync(fxc, s.fxc.ptr, s.npts * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
 int lrs_site_grid_shape(lrs_ctx* ctx, int site, int* product, int* nrad, int* nang) {
   clear_error();
   if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
@@ -585,6 +642,7 @@ int lrs_induced_potential(lrs_ctx* ctx, int site, double q, double shell_radius,
   if (ctx->capturing) return set_error(LRS_ERR_STATE, "the induced response cannot be recorded in a graph");
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
+  if (s.fxc_kind != LRS_FXC_NONE) LRS_TRY(alda_dress(ctx, s));
   return induced_potential(ctx, s, q, shell_radius, lresp, rho_lm, vind_lm, vind_grid);
 }
 
@@ -736,6 +794,7 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   ctx->w_main_launches = 0;
   for (int i : list) {
     Site& s = ctx->sites[i];
+    if (s.fxc_kind != LRS_FXC_NONE) LRS_TRY(alda_dress(ctx, s));
     LRS_TRY(dyson_solve(ctx, s));
     s.has_w = true;
     flop += 14.0 / 3.0 * (double)s.npts * s.npts * s.npts;
@@ -806,6 +865,8 @@ int lrs_backward_dev(lrs_ctx* ctx, int site, const double* grad_w_dev, const dou
   if (!grad_energies_dev || !grad_psi_dev) return set_error(LRS_ERR_ARG, "null output pointer");
   if (!grad_w_dev && !grad_chi0_dev) return set_error(LRS_ERR_ARG, "grad_w and grad_chi0 are both NULL");
   Site& s = ctx->sites[site];
+  if (s.fxc_kind != LRS_FXC_NONE)
+    return set_error(LRS_ERR_UNSUPPORTED, "the adjoint covers the RPA screening only (site %d has an ALDA kernel)", site);
   if (!s.has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", site);
   if (grad_w_dev && !s.has_w) return set_error(LRS_ERR_STATE, "site %d has no W", site);
   if (ctx->nf == 0) return set_error(LRS_ERR_STATE, "no quadrature");
@@ -845,10 +906,10 @@ int lrs_backward(lrs_ctx* ctx, int site, const double* grad_w, const double* gra
   if (!rc && cudaMemcpyAsync(grad_psi, gp, ne * s.npts * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
     rc = set_error(LRS_ERR_CUDA, "copy of grad_psi failed");
   cudaStreamSynchronize(ctx->stream);
-  if (gw) dev_free_bytes(ctx, gw, nn * sizeof(double));
-  if (gc) dev_free_bytes(ctx, gc, nn * sizeof(double));
-  if (ge) dev_free_bytes(ctx, ge, ne * sizeof(double));
-  if (gp) dev_free_bytes(ctx, gp, ne * s.npts * sizeof(double2));
+  if (gw) dev_free_temp(ctx, gw, nn * sizeof(double));
+  if (gc) dev_free_temp(ctx, gc, nn * sizeof(double));
+  if (ge) dev_free_temp(ctx, ge, ne * sizeof(double));
+  if (gp) dev_free_temp(ctx, gp, ne * s.npts * sizeof(double2));
   return rc;
 }
 

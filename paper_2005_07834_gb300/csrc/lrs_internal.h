@@ -44,6 +44,8 @@ struct DevBuf {
 int dev_alloc_bytes(lrs_ctx* ctx, void** p, size_t bytes);
 // Frees workspace memory; a recorded graph (which may read it) is dropped.
 void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes);
+// Frees a temporary of one API call (never seen by a recorded graph).
+void dev_free_temp(lrs_ctx* ctx, void* p, size_t bytes);
 // Drops the recorded multi-site graph, if any.
 void drop_graph(lrs_ctx* ctx);
 
@@ -84,6 +86,11 @@ struct Site {
   DevBuf<double> rl;                // [lmax+1][nrad][nrad] 4pi/(2l+1) r<^l / r>^(l+1)
   DevBuf<double> fl;                // [lmax+1][nrad][nrad] lower Cholesky factor of each rl block
   bool spd = false;                 // fl exists (every rl block is positive definite)
+  // ALDA vertex: kernel kind, f(r_p) [npts], dressed polarizability (I - chi0 D)^-1 chi0 [npts][npts]
+  int fxc_kind = LRS_FXC_NONE;
+  DevBuf<double> fxc, chi_eff;
+  // polarizability the Dyson solve and the induced response use
+  const double* response_chi() const { return fxc_kind != LRS_FXC_NONE ? chi_eff.ptr : chi0.ptr; }
 };
 
 // Split-precision operand planes of one matrix [rows_pad][k_pad] (4 planes:
@@ -144,6 +151,7 @@ struct Workspace {
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
   DevBuf<double> induced;               // induced response: T, X, B, right-hand side, outputs
+  DevBuf<double> alda_n;                // site density for the exchange-only ALDA kernel
   // FFT projection: grid [N1][N2][N3][nb] of one k-point (fp32 or fp64 complex), index tables, twiddles
   DevBuf<double2> fft_grid;
   DevBuf<int> fft_index;                // col_xy | col_ptr | ent_g | ent_z | populated x (offsets fft_off)
@@ -278,6 +286,12 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status);
 // lm-basis Dyson on product grids (k_dyson_lm.cu)
 int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);
 int dyson_solve_lm(lrs_ctx* ctx, Site& s);
+
+// ALDA (k_alda.cu): density n = 2 sum w |psi_o|^2 into n_dev [npts]; kernel f of the site
+// (s.fxc); chi_eff = (I - chi0 diag(f w))^-1 chi0 into s.chi_eff.
+int site_density(lrs_ctx* ctx, Site& s, double* n_dev);
+int site_fxc(lrs_ctx* ctx, Site& s);
+int alda_dress(lrs_ctx* ctx, Site& s);
 
 // Induced density / potential of a screened short-range spherical potential (k_induced.cu);
 // host outputs (rho_lm, vind_lm: [nrad][(lresp+1)^2]; grid: [npts]), each may be NULL.

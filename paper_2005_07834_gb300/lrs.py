@@ -28,6 +28,7 @@ LRS_OPT_DYSON_BASIS, LRS_OPT_CHI0_SEGMENT, LRS_OPT_PROJ_SEGMENT, LRS_OPT_CHI0_TI
 LRS_DYSON_AUTO, LRS_DYSON_FULL, LRS_DYSON_LM = 0, 1, 2
 LRS_OPT_WORKSPACE_GB, LRS_OPT_DYSON_SOLVER, LRS_OPT_GRAPH_PROJECTION = 5, 6, 7
 LRS_SOLVER_AUTO, LRS_SOLVER_LU, LRS_SOLVER_SPD = 0, 1, 2
+LRS_FXC_NONE, LRS_FXC_USER, LRS_FXC_ALDA_X = 0, 1, 2
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
 
@@ -63,6 +64,9 @@ _SIGS = {
     "lrs_set_fft_grid": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "lrs_induced_potential": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _DP, _DP, _DP]),
     "lrs_site_grid_shape": (C.c_int, [_P, C.c_int, _IP, _IP, _IP]),
+    "lrs_set_fxc": (C.c_int, [_P, C.c_int, C.c_int, _DP]),
+    "lrs_get_density": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_get_fxc": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_fft_grid": (C.c_int, [_P, _IP]),
     "lrs_set_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
@@ -206,6 +210,21 @@ class Screening:
     def project(self, sites=None, mode=LRS_PROJ_EXACT):
         n, p, _keep = self._sites(sites)
         _check(lrs_project(self.ctx, n, p, mode), "lrs_project")
+
+    def set_fxc(self, site, kind, fxc=None):
+        if fxc is not None:
+            fxc = _f64(np.asarray(fxc, np.float64).reshape(-1))
+        _check(lrs_set_fxc(self.ctx, int(site), int(kind), _dp(fxc) if fxc is not None else None), "lrs_set_fxc")
+
+    def get_density(self, site):
+        out = np.empty(self.npts[site])
+        _check(lrs_get_density(self.ctx, int(site), _dp(out)), "lrs_get_density")
+        return out
+
+    def get_fxc(self, site):
+        out = np.empty(self.npts[site])
+        _check(lrs_get_fxc(self.ctx, int(site), _dp(out)), "lrs_get_fxc")
+        return out
 
     def site_grid_shape(self, site):
         """(is a product grid, shells, directions per shell)."""
