@@ -26,6 +26,7 @@ in float64/complex128 NumPy:
                               with the short-range v1 of Eq. (eq-partition)
   alda.*                      ALDA vertex, Eq. (chi-alda) and (kxc_alda); density and
                               the exchange-only kernel of the uniform gas
+  augment.augment             all-electron augmentation, Eq. (eq-aug1), (eq-aug2)
   grad.*                      analytic gradients of a scalar loss of W in pair
                               form (the paper has no gradients)
 
