@@ -211,6 +211,25 @@ int lrs_get_frequency_quadrature(lrs_ctx* ctx, double* t, double* w);
 int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode);
 
 /*
+ * All-electron augmentation of the projected site orbitals (Sec. VI.C,
+ * Eq. (eq-aug1) and (eq-aug2)), in place, for every orbital column:
+ *   psi <- psi + sum_{l <= lmax_aug, m} sum_{nu,nu'} Y_lm [phi_ae_{nu l} - phi_ps_{nu l}]
+ *               (A_l^-1)_{nu nu'} <phi_ps_{nu' l} Y_lm | psi>,
+ *   A_{nu nu'; l} = int_0^{r_aug} dr r^2 phi_ps_{nu l} phi_ps_{nu' l},
+ * the radial integral taken by the grid's radial quadrature over the shells
+ * with r_j <= r_aug and the projection by the point weights on those shells
+ * (Y_lm the real harmonics of lrs_induced_potential).  phi_ae, phi_ps: host
+ * [lmax_aug + 1][nnu][nrad] radial functions on the site's shells (for
+ * example optimal projector functions; an atom at the site centre).
+ * Requires projected orbitals and a product grid; invalidates chi0 and W.
+ * Errors: LRS_ERR_ARG (lmax_aug > lmax, nnu outside [1, 64], radius, non-finite
+ * values), LRS_ERR_STATE (no orbitals, during capture), LRS_ERR_UNSUPPORTED
+ * (not a product grid), LRS_ERR_NUMERIC (singular overlap A_l).
+ */
+int lrs_augment(lrs_ctx* ctx, int site, int lmax_aug, int nnu, double r_aug, const double* phi_ae,
+                const double* phi_ps);
+
+/*
  * ALDA vertex correction (Sec. VII "Beyond RPA screening", Eq. (chi-alda)
  * and (kxc_alda)): chi~ = (1 - chi0 (v + f_xc))^-1 chi0 with the contact
  * kernel f_xc(r, r') = delta(r - r') f(r).  Once set for a site, lrs_solve_w

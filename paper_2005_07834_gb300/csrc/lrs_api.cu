@@ -220,6 +220,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.gj);
   release(ctx, w.fft_grid); release(ctx, w.fft_index); release(ctx, w.fft_tw);
   release(ctx, w.induced);
+  release(ctx, w.alda_n); release(ctx, w.aug_tab); release(ctx, w.aug_coef);
   w.fft_plan_ok = false;
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
 }
@@ -565,6 +566,28 @@ int lrs_project(lrs_ctx* ctx, int nsite, const int* sites, int mode) {
     s.has_chi0 = s.has_w = false;
   }
   LRS_TRY(stage_end(ctx, ST_PROJECT));
+  return LRS_OK;
+}
+
+int lrs_augment(lrs_ctx* ctx, int site, int lmax_aug, int nnu, double r_aug, const double* phi_ae,
+                const double* phi_ps) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  LRS_TRY(check_site(ctx, site));
+  Site& s = ctx->sites[site];
+  if (!s.has_psi) return set_error(LRS_ERR_STATE, "site %d has no orbitals (project first)", site);
+  if (!s.product) return set_error(LRS_ERR_UNSUPPORTED, "site %d is not a radial x angular product grid", site);
+  if (lmax_aug < 0 || lmax_aug > s.lmax) return set_error(LRS_ERR_ARG, "l_aug %d outside [0, %d]", lmax_aug, s.lmax);
+  if (nnu < 1 || nnu > 64) return set_error(LRS_ERR_ARG, "%d partial waves per l outside [1, 64]", nnu);
+  if (!(r_aug > 0.0) || !std::isfinite(r_aug)) return set_error(LRS_ERR_ARG, "augmentation radius must be positive");
+  const size_t nv = (size_t)(lmax_aug + 1) * nnu * s.nrad;
+  if (!phi_ae || !phi_ps) return set_error(LRS_ERR_ARG, "NULL partial waves");
+  if (!finite_all(phi_ae, nv) || !finite_all(phi_ps, nv)) return set_error(LRS_ERR_ARG, "non-finite partial wave");
+  if (ctx->capturing) return set_error(LRS_ERR_STATE, "augmentation cannot be recorded in a graph");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  LRS_TRY(augment_site(ctx, s, lmax_aug, nnu, r_aug, phi_ae, phi_ps));
+  s.has_chi0 = s.has_w = false;
   return LRS_OK;
 }
 

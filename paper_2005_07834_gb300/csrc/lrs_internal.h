@@ -152,6 +152,8 @@ struct Workspace {
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
   DevBuf<double> induced;               // induced response: T, X, B, right-hand side, outputs
   DevBuf<double> alda_n;                // site density for the exchange-only ALDA kernel
+  DevBuf<double> aug_tab;               // augmentation: pseudo waves, corrections, shell mask
+  DevBuf<double2> aug_coef;             // augmentation: <phi_ps Y_lm | psi> per orbital column
   // FFT projection: grid [N1][N2][N3][nb] of one k-point (fp32 or fp64 complex), index tables, twiddles
   DevBuf<double2> fft_grid;
   DevBuf<int> fft_index;                // col_xy | col_ptr | ent_g | ent_z | populated x (offsets fft_off)
@@ -292,6 +294,10 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s);
 int site_density(lrs_ctx* ctx, Site& s, double* n_dev);
 int site_fxc(lrs_ctx* ctx, Site& s);
 int alda_dress(lrs_ctx* ctx, Site& s);
+
+// Augmentation of the site orbitals in place (k_augment.cu); phi_* host [lmax_aug+1][nnu][nrad].
+int augment_site(lrs_ctx* ctx, Site& s, int lmax_aug, int nnu, double r_aug, const double* phi_ae,
+                 const double* phi_ps);
 
 // Induced density / potential of a screened short-range spherical potential (k_induced.cu);
 // host outputs (rho_lm, vind_lm: [nrad][(lresp+1)^2]; grid: [npts]), each may be NULL.

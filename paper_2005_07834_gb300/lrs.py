@@ -65,6 +65,7 @@ _SIGS = {
     "lrs_induced_potential": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _DP, _DP, _DP]),
     "lrs_site_grid_shape": (C.c_int, [_P, C.c_int, _IP, _IP, _IP]),
     "lrs_set_fxc": (C.c_int, [_P, C.c_int, C.c_int, _DP]),
+    "lrs_augment": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, _DP, _DP]),
     "lrs_get_density": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_fxc": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_fft_grid": (C.c_int, [_P, _IP]),
@@ -210,6 +211,14 @@ class Screening:
     def project(self, sites=None, mode=LRS_PROJ_EXACT):
         n, p, _keep = self._sites(sites)
         _check(lrs_project(self.ctx, n, p, mode), "lrs_project")
+
+    def augment(self, site, phi_ae, phi_ps, r_aug):
+        """phi_ae, phi_ps: [lmax_aug + 1][nnu][nrad] radial functions on the site's shells."""
+        ae = _f64(np.asarray(phi_ae, np.float64))
+        ps = _f64(np.asarray(phi_ps, np.float64))
+        assert ae.shape == ps.shape and ae.ndim == 3
+        _check(lrs_augment(self.ctx, int(site), ae.shape[0] - 1, ae.shape[1], float(r_aug), _dp(ae), _dp(ps)),
+               "lrs_augment")
 
     def set_fxc(self, site, kind, fxc=None):
         if fxc is not None:
