@@ -45,6 +45,7 @@ WORKLOADS = {
     "single-site-260": "single_site_260",
     "batched-64-sites": "batched_64_sites",
     "large-cell-16-sites": "large_cell_16_sites",
+    "gamma-site-3520": "gamma_site_3520",
 }
 MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 
@@ -290,7 +291,8 @@ def run_ours(args):
 
     peaks = load_peaks()
     n, K, nf = s.npts, o.nk * o.nbands, wl.nfreq
-    flop_chi0 = 8.0 * n * n * K * nf
+    # complex x complex products: 8 flop per multiply-add; Gamma-point real orbitals make B real (4)
+    flop_chi0 = (4.0 if scr.orbitals_are_real() else 8.0) * n * n * K * nf
     main_ms = st["ms_chi0_main"]
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
@@ -355,6 +357,7 @@ def run_ours(args):
             "data": "synthetic (seeded generator; no DFT orbitals)",
             "config": {"workload": args.workload, "npts": n, "K": K, "nfreq": nf, "ng": o.ng,
                        "precision": args.precision, "replicas_per_gpu": 1, "projection": args.projection,
+                       "real_orbitals": bool(scr.orbitals_are_real()),
                        "l2": "inputs larger than L2 (coefficients %d MB, orbitals %d MB)" % (
                            o.coeff.nbytes >> 20, (n * K * 16) >> 20)},
             "tflops": (flop_chi0 + 14.0 / 3.0 * n ** 3) / (ms * 1e-3) / 1e12,

@@ -74,6 +74,9 @@ extern "C" {
 #define LRS_FXC_USER      1   /* f(r_p) = dv_xc/dn at n(r_p), supplied per grid point */
 #define LRS_FXC_ALDA_X    2   /* exchange-only ALDA of the site density: f = -(1/3)(3/pi)^(1/3) n^(-2/3) */
 #define LRS_OPT_GRAPH_PROJECTION 7  /* value: LRS_PROJ_EXACT (default) or LRS_PROJ_FFT_LAGRANGE3, recorded by lrs_graph_capture */
+#define LRS_OPT_REAL_ORBITALS    8  /* value: LRS_REAL_AUTO (default) or LRS_REAL_OFF */
+#define LRS_REAL_AUTO     0   /* Gamma-point real orbitals (Sec. VI.F) use real-operand tensor-core contractions */
+#define LRS_REAL_OFF      1   /* always the complex contractions */
 
 typedef struct lrs_ctx lrs_ctx;
 
@@ -245,6 +248,16 @@ int lrs_augment(lrs_ctx* ctx, int site, int lmax_aug, int nnu, double r_aug, con
  * Invalidates the site's W.  Errors: LRS_ERR_ARG.
  */
 int lrs_set_fxc(lrs_ctx* ctx, int site, int kind, const double* fxc);
+
+/*
+ * Whether the loaded orbitals are real (Sec. VI.F, Gamma point with
+ * time-reversal symmetry): one k-point at k = 0, the G set closed under
+ * G -> -G and C_b(-G) = conj C_b(G) for every band (to 1e-12 of max |C|).
+ * Then psi is real, the B operand of the Green's-function products is real and
+ * the mixed-precision chi0 issues half the tensor-core products (unless
+ * LRS_OPT_REAL_ORBITALS is LRS_REAL_OFF).  Errors: LRS_ERR_ARG, LRS_ERR_STATE.
+ */
+int lrs_orbitals_are_real(lrs_ctx* ctx, int* is_real);
 
 /* Electron density n(r_p) = 2 sum_k w_k sum_occ |psi_kv(r_p)|^2 of the site
  * orbitals (host [npts]).  Errors: LRS_ERR_ARG, LRS_ERR_STATE (no orbitals). */

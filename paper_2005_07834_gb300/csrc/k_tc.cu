@@ -327,6 +327,8 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
   sh.units = (int)units;
   sh.sites = ctx->ws.site_tiles.ptr + toff;
   sh.nsites = ns;
+  // Gamma-point real orbitals: B = [psi_o | conj psi_u] is real
+  sh.real_b = ctx->real_orbitals && ctx->real_mode == LRS_REAL_AUTO ? 1 : 0;
   Chi0Store epi{ctx->ws.slab.ptr, ctx->ws.tc_scratch.ptr, 0, TN};
   LRS_TRY(stage_begin(ctx, ST_CHI0_MAIN));
   LRS_TRY((launch_tc<TN, 2, FMT, Chi0Store>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0>")));
@@ -390,7 +392,7 @@ int project_mixed(lrs_ctx* ctx, Site& s) {
   CUtensorMap ma, mb;
   LRS_TRY(make_operand_map(&ma, ctx->ws.proj_a.ptr, ld, 2 * (uint64_t)Np, TILE_M));
   LRS_TRY(make_operand_map(&mb, ctx->ws.proj_b.ptr, ld, 2 * (uint64_t)ctx->nk * nbp, PROJ_TN));
-  TcShape sh;
+  TcShape sh{};
   sh.m_tiles = Np / TILE_M;
   sh.n_tiles = nbp / PROJ_TN;
   sh.batches = ctx->nk;

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <unordered_map>
 
 #include "lrs_internal.h"
 
@@ -166,6 +167,30 @@ static bool finite_all(const double* p, size_t n) {
   return true;
 }
 
+// Gamma-point real orbitals (Sec. VI.F): one k-point at k = 0 and, for every
+// G, -G in the set with C_b(-G) = conj C_b(G) (to 1e-12 of the largest |C|).
+static bool orbitals_are_real(int nk, const double* kpts, int ng, const int* gvec, int nb, const double* coeff) {
+  if (nk != 1 || kpts[0] != 0.0 || kpts[1] != 0.0 || kpts[2] != 0.0) return false;
+  auto key = [](int a, int b, int c) {
+    return ((long long)(a + (1 << 20)) << 42) | ((long long)(b + (1 << 20)) << 21) | (long long)(c + (1 << 20));
+  };
+  std::unordered_map<long long, int> index;
+  index.reserve((size_t)ng * 2);
+  for (int g = 0; g < ng; ++g) index[key(gvec[3 * g], gvec[3 * g + 1], gvec[3 * g + 2])] = g;
+  double cmax = 0.0;
+  for (size_t i = 0; i < 2 * (size_t)ng * nb; ++i) cmax = std::max(cmax, std::fabs(coeff[i]));
+  const double tol = 1e-12 * cmax;
+  for (int g = 0; g < ng; ++g) {
+    const auto it = index.find(key(-gvec[3 * g], -gvec[3 * g + 1], -gvec[3 * g + 2]));
+    if (it == index.end()) return false;
+    const double* a = coeff + 2 * (size_t)g * nb;
+    const double* b = coeff + 2 * (size_t)it->second * nb;
+    for (int k = 0; k < nb; ++k)
+      if (std::fabs(a[2 * k] - b[2 * k]) > tol || std::fabs(a[2 * k + 1] + b[2 * k + 1]) > tol) return false;
+  }
+  return true;
+}
+
 static int check_site(lrs_ctx* ctx, int site) {
   if (site < 0 || site >= (int)ctx->sites.size())
     return set_error(LRS_ERR_ARG, "site %d out of range (have %zu)", site, ctx->sites.size());
@@ -305,6 +330,10 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
       return LRS_OK;
+    case LRS_OPT_REAL_ORBITALS:
+      if (value != LRS_REAL_AUTO && value != LRS_REAL_OFF) return set_error(LRS_ERR_ARG, "real-orbital mode %d", value);
+      ctx->real_mode = value;
+      return LRS_OK;
     case LRS_OPT_GRAPH_PROJECTION:
       if (value != LRS_PROJ_EXACT && value != LRS_PROJ_FFT_LAGRANGE3)
         return set_error(LRS_ERR_ARG, "projection mode %d unknown", value);
@@ -387,6 +416,7 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   ctx->energies.assign(energies, energies + (size_t)nk * nbands);
   ctx->gvec.assign(gvec, gvec + 3 * (size_t)ng);
   ctx->ws.fft_plan_ok = false;   // the FFT index tables follow the G set
+  ctx->real_orbitals = orbitals_are_real(nk, kpts, ng, gvec, nbands, coeff);
   for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = 0;
   for (int gi = 0; gi < ng; ++gi)
     for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = std::max(ctx->gmax_idx[i], std::abs(gvec[3 * gi + i]));
@@ -609,6 +639,14 @@ int lrs_set_fxc(lrs_ctx* ctx, int site, int kind, const double* fxc) {
   }
   s.fxc_kind = kind;
   s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_orbitals_are_real(lrs_ctx* ctx, int* is_real) {
+  clear_error();
+  if (!ctx || !is_real) return set_error(LRS_ERR_ARG, "NULL argument");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  *is_real = ctx->real_orbitals ? 1 : 0;
   return LRS_OK;
 }
 

@@ -182,6 +182,8 @@ struct lrs_ctx {
   int chi0_tn = 128;                   // chi0 tensor-core tile width (64 or 128)
   int fft_n[3] = {0, 0, 0};            // FFT grid of the method-2 projection (0: automatic)
   int graph_projection = LRS_PROJ_EXACT;  // projection mode recorded by lrs_graph_capture
+  bool real_orbitals = false;          // one k-point at Gamma with C(-G) = conj C(G): orbitals are real
+  int real_mode = LRS_REAL_AUTO;       // use the real-orbital contractions when the orbitals are real
   double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
 

@@ -49,6 +49,7 @@ struct TcShape {
   int units;         // total work units
   const struct SiteTile* sites;   // multi-site table (NULL: one problem)
   int nsites;
+  int real_b;        // 1: B is real (its imaginary planes are neither loaded nor multiplied)
 };
 
 struct Unit {
@@ -206,12 +207,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             atomicCAS(status, 0, TC_TIMEOUT_PRODUCER);
             goto producer_done;
           }
-          mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
+          mbar_arrive_expect_tx(&full_bar[stage], sh.real_b ? STAGE_BYTES - B_TILE : STAGE_BYTES);
           const uint32_t s = smem_base + stage * STAGE_BYTES;
           tma_load_2d(s, &tmA, &full_bar[stage], c * 64, ya);
           tma_load_2d(s + TILE_BYTES, &tmA, &full_bar[stage], c * 64, ya + sh.a_im_rows);
           tma_load_2d(s + 2 * TILE_BYTES, &tmB, &full_bar[stage], c * 64, yb);
-          tma_load_2d(s + 2 * TILE_BYTES + B_TILE, &tmB, &full_bar[stage], c * 64, yb + sh.b_im_rows);
+          if (!sh.real_b)
+            tma_load_2d(s + 2 * TILE_BYTES + B_TILE, &tmB, &full_bar[stage], c * 64, yb + sh.b_im_rows);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
       }
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int stage = 0, set = 0;
       uint32_t phase = 0, set_phase = 0;
       const int nseg = plan.count();
+      const bool real_b = sh.real_b != 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         for (int sg = 0; sg < nseg && ok; ++sg) {
@@ -250,6 +253,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t s = smem_base + stage * STAGE_BYTES;
             const uint32_t aR = s, aI = s + TILE_BYTES, bR = s + 2 * TILE_BYTES, bI = bR + B_TILE;
+            if (real_b) {
+              // real B (Gamma-point real orbitals): Re = Ar Br, Im = Ai Br
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;
+                const uint32_t a0 = (c == 0 && ks == 0) ? 0u : 1u;
+                mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
+                mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
+                mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
+                mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, a0);
+                mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
+                mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
+              }
+              mma_commit(&empty_bar[stage]);
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+              continue;
+            }
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
               const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;

@@ -29,6 +29,7 @@ LRS_DYSON_AUTO, LRS_DYSON_FULL, LRS_DYSON_LM = 0, 1, 2
 LRS_OPT_WORKSPACE_GB, LRS_OPT_DYSON_SOLVER, LRS_OPT_GRAPH_PROJECTION = 5, 6, 7
 LRS_SOLVER_AUTO, LRS_SOLVER_LU, LRS_SOLVER_SPD = 0, 1, 2
 LRS_FXC_NONE, LRS_FXC_USER, LRS_FXC_ALDA_X = 0, 1, 2
+LRS_OPT_REAL_ORBITALS, LRS_REAL_AUTO, LRS_REAL_OFF = 8, 0, 1
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
 
@@ -66,6 +67,7 @@ _SIGS = {
     "lrs_site_grid_shape": (C.c_int, [_P, C.c_int, _IP, _IP, _IP]),
     "lrs_set_fxc": (C.c_int, [_P, C.c_int, C.c_int, _DP]),
     "lrs_augment": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, _DP, _DP]),
+    "lrs_orbitals_are_real": (C.c_int, [_P, _IP]),
     "lrs_get_density": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_fxc": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_fft_grid": (C.c_int, [_P, _IP]),
@@ -211,6 +213,11 @@ class Screening:
     def project(self, sites=None, mode=LRS_PROJ_EXACT):
         n, p, _keep = self._sites(sites)
         _check(lrs_project(self.ctx, n, p, mode), "lrs_project")
+
+    def orbitals_are_real(self):
+        v = C.c_int()
+        _check(lrs_orbitals_are_real(self.ctx, C.byref(v)), "lrs_orbitals_are_real")
+        return bool(v.value)
 
     def augment(self, site, phi_ae, phi_ps, r_aug):
         """phi_ae, phi_ps: [lmax_aug + 1][nnu][nrad] radial functions on the site's shells."""

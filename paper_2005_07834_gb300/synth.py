@@ -143,6 +143,59 @@ def loss_weights(npts: int, seed: int = 2) -> np.ndarray:
 # site grids of a few thousand points, tens of bands per cell).
 # ----------------------------------------------------------------------------
 
+def draw_real_orbitals(cell, gmax, nocc, nunocc, seed=0) -> Orbitals:
+    """Gamma-point orbitals with time-reversal symmetry (real in real space).
+
+    Draw order: a real matrix R [ng x nb] standard normal, occupied energies
+    U[-1,-0.1] sorted, unoccupied U[0.1,3.0] sorted.  The rows of R are the
+    coefficients in the real orthonormal basis {1, sqrt(2) cos(G.r), sqrt(2)
+    sin(G.r)} (one cos and one sin row per pair +-G, G the lexicographically
+    larger of the pair), each times exp(-|G|^2/2); reduced QR keeps Q; then
+    C(G) = (a - i b)/sqrt(2), C(-G) = (a + i b)/sqrt(2), C(0) = a, a unitary map,
+    so the columns stay orthonormal and C(-G) = conj C(G).
+    """
+    rng = np.random.default_rng(seed)
+    gvec = g_sphere(cell, gmax)
+    recip = 2.0 * np.pi * np.linalg.inv(cell).T
+    gnorm = np.linalg.norm(gvec @ recip, axis=1)
+    env = np.exp(-gnorm ** 2 / 2.0)
+    ng, nb = len(gvec), nocc + nunocc
+    index = {tuple(g): i for i, g in enumerate(gvec)}
+    zero = index[(0, 0, 0)]
+    pos = [i for i, g in enumerate(gvec) if tuple(g) > (0, 0, 0)]
+    neg = [index[tuple(-gvec[i])] for i in pos]
+    r = rng.standard_normal((ng, nb))
+    eo = np.sort(rng.uniform(-1.0, -0.1, nocc))
+    eu = np.sort(rng.uniform(0.1, 3.0, nunocc))
+    rows = np.concatenate([[zero], pos, pos])            # basis order: 1, cos rows, sin rows
+    q, _ = np.linalg.qr(r * env[rows][:, None])
+    coeff = np.empty((ng, nb), np.complex128)
+    npair = len(pos)
+    a, b = q[1:1 + npair], q[1 + npair:]
+    coeff[zero] = q[0]
+    coeff[pos] = (a - 1j * b) / np.sqrt(2.0)
+    coeff[neg] = (a + 1j * b) / np.sqrt(2.0)
+    energies = np.concatenate([eo, eu])[None, :]
+    return Orbitals(np.asarray(cell, float), np.zeros((1, 3)), np.ones(1), gvec, coeff[None], energies,
+                    np.full(1, nocc, np.int32))
+
+
+def gamma_site_260(seed=0) -> Workload:
+    """Gamma-point real orbitals: a = 10 bohr, |G| <= 3, 64 occ + 192 unocc, 10 GL x 26 Lebedev, 12 freq."""
+    cell = cubic_cell(10.0)
+    orb = draw_real_orbitals(cell, 3.0, 64, 192, seed)
+    site = site_grid(np.full(3, 5.0), 10, 26, 4.0)
+    return Workload("gamma-site-260pt-b256", orb, [site], nfreq=12, fft_grid=(16, 16, 16))
+
+
+def gamma_site_3520(seed=0) -> Workload:
+    """Gamma-point real orbitals: a = 20 bohr, |G| <= 4, 1024 occ + 4096 unocc, 32 GL x 110 Lebedev, 16 freq."""
+    cell = cubic_cell(20.0)
+    orb = draw_real_orbitals(cell, 4.0, 1024, 4096, seed)
+    site = site_grid(np.full(3, 10.0), 32, 110, 6.0)
+    return Workload("gamma-site-3520pt-b5120", orb, [site], nfreq=16, fft_grid=(48, 48, 48))
+
+
 def single_site_260(seed=0) -> Workload:
     """a = 10 bohr, |G| <= 3, 2x2x2 k, 8 occ + 24 unocc per k, 10 GL x 26 Lebedev, 12 freq."""
     cell = cubic_cell(10.0)
