@@ -58,7 +58,11 @@ def dyson_roofline(st, workload=None, version=None):
     if not st.get("w_main_launches"):
         return None
     ms = st["ms_w_main"]
-    r = {"bound": "alu", "kernel": "gj_update_kernel<0> (SPD-inverse trailing update)",
+    tc = st.get("dyson_update_tc", False)
+    r = {"bound": "alu",
+         "kernel": ("oz_update_kernel (SPD-inverse trailing update, float64-accurate bf16 slices on tcgen05; "
+                    "FP64-equivalent rate against the FP64 FMA peak)") if tc
+         else "gj_update_kernel<0> (SPD-inverse trailing update)",
          "achieved": st["flop_w_main"] / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
          "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz", "launches": st["w_main_launches"],
          "avg_launch_us": 1e3 * ms / st["w_main_launches"],
@@ -310,6 +314,7 @@ def run_ours(args):
     # FP64 Dyson: its dominant kernel is the trailing update of the SPD inverse (one launch per
     # pivot block), timed per launch with CUDA events on its stream inside the library; algorithmic
     # flop per launch = 2 kb x the lower-triangle elements it updates
+    st["dyson_update_tc"] = args.precision != "fp64"   # LRS_UPDATE_AUTO: tensor cores in the mixed precisions
     roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"))
     # the roofline object describes the kernel that dominates the step; the other is kept beside it
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
@@ -459,6 +464,7 @@ def run_ours_multisite(args):
             "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk, "traffic": None,
             "kernel": "zgemm_tc_kernel<chi0> (all sites, one launch per workspace group)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    st["dyson_update_tc"] = args.precision != "fp64"
     roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"))
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
     if rank == 0:

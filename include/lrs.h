@@ -75,6 +75,10 @@ extern "C" {
 #define LRS_FXC_ALDA_X    2   /* exchange-only ALDA of the site density: f = -(1/3)(3/pi)^(1/3) n^(-2/3) */
 #define LRS_OPT_GRAPH_PROJECTION 7  /* value: LRS_PROJ_EXACT (default) or LRS_PROJ_FFT_LAGRANGE3, recorded by lrs_graph_capture */
 #define LRS_OPT_REAL_ORBITALS    8  /* value: LRS_REAL_AUTO (default) or LRS_REAL_OFF */
+#define LRS_OPT_DYSON_UPDATE     9  /* value: LRS_UPDATE_AUTO (default), LRS_UPDATE_FP64 or LRS_UPDATE_TC */
+#define LRS_UPDATE_AUTO   0   /* tensor cores in the mixed precisions, the FP64 pipe in LRS_FP64 */
+#define LRS_UPDATE_FP64   1   /* trailing update of the SPD inverse with float64 FMAs */
+#define LRS_UPDATE_TC     2   /* float64-accurate update from exact bf16 slices on the tensor cores */
 #define LRS_REAL_AUTO     0   /* Gamma-point real orbitals (Sec. VI.F) use real-operand tensor-core contractions */
 #define LRS_REAL_OFF      1   /* always the complex contractions */
 
@@ -134,6 +138,12 @@ int lrs_set_stream(lrs_ctx* ctx, void* stream);
  * negative semidefinite - the symmetric form Z = F (I - F^T X F)^-1 F^T, whose
  * matrix has every eigenvalue >= 1 and is inverted in place by blocked
  * Gauss-Jordan steps without pivoting (n^3 instead of 8/3 n^3 flop).
+ * LRS_OPT_DYSON_UPDATE selects the arithmetic of that inverse's rank-32
+ * trailing updates: float64 FMAs, or the tensor cores on operands cut into
+ * seven exact bf16 slices per row (power-of-two row scales), 28 slice products
+ * accumulated per level exactly in fp32 and combined in float64 - an error
+ * bound of about 6e-16 of |D|max |E|max per element, as for a float64 dot
+ * product of 32 terms.
  * Errors: LRS_ERR_ARG (unknown option or value).
  */
 int lrs_set_option(lrs_ctx* ctx, int option, int value);

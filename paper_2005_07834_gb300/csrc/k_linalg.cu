@@ -937,6 +937,27 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
   }
   const int nblk = (n + GJ_NB - 1) / GJ_NB;
   const long long nt = (n + UT - 1) / UT;   // 32-wide update tiles per dimension
+  // bulk updates on the tensor cores (float64-accurate slices) or the FP64 pipe
+  const bool tc = ctx->dyson_update == LRS_UPDATE_TC ||
+                  (ctx->dyson_update == LRS_UPDATE_AUTO && ctx->precision != LRS_FP64);
+  const int rows_pad = oz_rows_pad(n);
+  const size_t pe = oz_plane_elems(n);
+  uint16_t* dpl[2] = {nullptr, nullptr};
+  uint16_t* epl[2] = {nullptr, nullptr};
+  int* dsc[2] = {nullptr, nullptr};
+  int* esc[2] = {nullptr, nullptr};
+  CUtensorMap md[2], me[2];
+  if (tc) {
+    LRS_TRY(ensure(ctx, ctx->ws.oz_planes, 4 * pe));
+    LRS_TRY(ensure(ctx, ctx->ws.oz_expo, 4 * (size_t)rows_pad));
+    for (int q = 0; q < 2; ++q) {
+      dpl[q] = ctx->ws.oz_planes.ptr + (2 * q) * pe;
+      epl[q] = ctx->ws.oz_planes.ptr + (2 * q + 1) * pe;
+      dsc[q] = ctx->ws.oz_expo.ptr + (2 * q) * (size_t)rows_pad;
+      esc[q] = ctx->ws.oz_expo.ptr + (2 * q + 1) * (size_t)rows_pad;
+      LRS_TRY(oz_make_maps(ctx, dpl[q], epl[q], rows_pad, &md[q], &me[q]));
+    }
+  }
   auto panel = [&](int kb_idx, int q) -> int {
     const int k0 = kb_idx * GJ_NB, kb = std::min(GJ_NB, n - k0);
     gj_gather_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Cb[q], Eb[q]);
@@ -946,6 +967,10 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q]);
     LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
     ctx->fp64_flops += 2.0 * n * kb * kb;
+    if (tc) {
+      LRS_TRY(oz_prepare(ctx, Db[q], GJ_NB, n, kb, dpl[q], rows_pad, dsc[q], s2));
+      LRS_TRY(oz_prepare(ctx, Eb[q], GJ_NB, n, kb, epl[q], rows_pad, esc[q], s2));
+    }
     return LRS_OK;
   };
   // fork the second stream from the context stream (also inside a graph capture)
@@ -958,8 +983,13 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     // bulk of the trailing update on the context stream
     LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_panel, 0));
     LRS_TRY(stage_begin(ctx, ST_W_MAIN));
-    gj_update_kernel<0><<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
-    LRS_TRY(after_launch(ctx, "gj_update_kernel"));
+    if (tc) {
+      LRS_TRY(oz_update(ctx, md[q], me[q], A, n, lda, dsc[q], esc[q], k0, std::min(n, k0 + 2 * GJ_NB), rows_pad,
+                        s1));
+    } else {
+      gj_update_kernel<0><<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
+      LRS_TRY(after_launch(ctx, "gj_update_kernel"));
+    }
     LRS_TRY(stage_end(ctx, ST_W_MAIN));
     {
       // lower-triangle elements outside the rows and columns of blocks k and k + 1
@@ -969,7 +999,7 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
       ctx->w_main_flop += 2.0 * kb * elems;
       ++ctx->w_main_launches;
     }
-    ctx->fp64_flops += (double)n * n * kb;
+    if (!tc) ctx->fp64_flops += (double)n * n * kb;
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
     // cross of block k + 1, exchange of block k, next panel on the second stream
     if (k + 1 < nblk) {

@@ -1,0 +1,323 @@
+// Float64-accurate rank-32 update C -= D E^T on the tensor cores, for the
+// trailing update of the SPD inverse of the Dyson solve.
+//
+// Every row of D and of E (32 float64 values) is scaled by a power of two,
+// x = 2^e a with |a| < 1, and cut into integer slices
+//   a = sum_{t=1..7} 2^(-8 t) s_t,   s_1 = rint(256 a), s_{t+1} = rint(256 r_t),
+//   r_t = 256 r_{t-1} - s_t (r_0 = a),
+// so |s_1| <= 256, |s_t| <= 128 (t > 1): each slice is exact in bf16 and the
+// residual after seven slices is below 2^-57 |a|max.  The products of the 28
+// slice pairs with t + u <= 8 are issued as bf16 tcgen05 MMAs (K = 32, two K16
+// steps each) into seven fp32 accumulators in TMEM, one per level t + u.  A
+// level sum is an integer below 7 * 32 * 2^16 < 2^24, hence exact in fp32.
+// The epilogue combines the levels in float64 with their factors 2^-8(t+u)
+// and the row scales, and subtracts from C.  The dropped pairs (t + u >= 9)
+// bound the error by about 6e-16 |D|max |E|max per element, on a par with a
+// float64 dot product of 32 terms; the update runs at tensor-core speed
+// instead of the 2 DFMA per SM per clock of the float64 pipe.
+//
+// Tiles of 128 x 64 elements of the lower triangle; elements in the rows or
+// columns of the excluded pivot blocks (the side stream of the SPD inverse
+// updates those) are left untouched.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "lrs_internal.h"
+#include "tc_common.cuh"
+
+namespace lrs {
+using namespace tc;
+
+constexpr int OZ_SLICES = 7;
+constexpr int OZ_PLANES = 4;                   // two slices per 128-byte row (the last half of plane 3 is zero)
+constexpr int OZ_LEVELS = 7;                   // t + u = 2 .. 8
+constexpr int OZ_TM = 128, OZ_TN = 64;
+constexpr int OZ_A_PLANE = OZ_TM * 128;        // bytes of one A plane tile
+constexpr int OZ_B_PLANE = OZ_TN * 128;
+constexpr int OZ_STAGE = OZ_PLANES * (OZ_A_PLANE + OZ_B_PLANE);
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * 9 * 8;   // per-warp [32][9] float64 staging of C updates
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + OZ_STAGE_EPI + 1024;
+constexpr int OZ_THREADS = 320;                // producer, MMA issuer, 8 epilogue warps
+constexpr int OZ_TMEM_COLS = 512;              // 7 levels x 64 columns used
+
+// Slices of the first kb <= 32 columns of X [n][ldx] into planes
+// [OZ_PLANES][rows_pad][64] bf16 and the row exponents e (scale 2^e).  Rows >= n are zero.
+__global__ void oz_slice_kernel(const double* __restrict__ X, int ldx, int n, int kb, int rows_pad,
+                                uint16_t* __restrict__ planes, int* __restrict__ expo) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int k = threadIdx.x & 31;
+  if (row >= rows_pad) return;
+  const double x = (row < n && k < kb) ? X[(size_t)row * ldx + k] : 0.0;
+  double m = fabs(x);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);                  // m = f 2^e, f in [0.5, 1)
+  if (k == 0) expo[row] = e;
+  double r = ldexp(x, -e);                     // |r| < 1
+  const size_t plane = (size_t)rows_pad * 64;
+#pragma unroll
+  for (int t = 0; t < 2 * OZ_PLANES; ++t) {
+    double sl = 0.0;
+    if (t < OZ_SLICES) {
+      r *= 256.0;
+      sl = rint(r);
+      r -= sl;
+    }
+    const __nv_bfloat16 b = __double2bfloat16(sl);   // an integer of at most 9 bits: exact
+    planes[(t >> 1) * plane + (size_t)row * 64 + (t & 1) * 32 + k] = __bfloat16_as_ushort(b);
+  }
+}
+
+struct OzUpdate {
+  double* C;
+  int n, ldc;
+  const int* ed;        // row exponents of D (output rows)
+  const int* ee;        // row exponents of E (output columns)
+  int x0, x1;           // rows / columns in [x0, x1) are left to the side stream
+  int row_tiles, col_tiles;
+  int a_plane_rows, b_plane_rows;   // padded rows of one plane (row offset between planes)
+};
+
+__device__ __forceinline__ bool oz_decode(const OzUpdate& p, int u, int& bi, int& bj) {
+  bi = u / p.col_tiles;
+  bj = u % p.col_tiles;
+  return bj * OZ_TN <= bi * OZ_TM + OZ_TM - 1;   // tile reaches the lower triangle
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_update_kernel(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmE,
+                     const OzUpdate p, int* status) {
+  __shared__ __align__(8) uint64_t full_bar[OZ_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[OZ_STAGES];
+  __shared__ __align__(8) uint64_t accf_bar;
+  __shared__ __align__(8) uint64_t acce_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  extern __shared__ uint8_t oz_smem_raw[];
+  const uint32_t smem_base = (smem_u32(oz_smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = p.row_tiles * p.col_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accf_bar, 1);
+    mbar_init(&acce_bar, OZ_EPI_WARPS);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_map(&tmD);
+    tma_prefetch_map(&tmE);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, OZ_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer: all slice planes of a tile
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        int bi, bj;
+        if (!oz_decode(p, u, bi, bj)) continue;
+        if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) {
+          abort_flag = 1;
+          atomicCAS(status, 0, TC_TIMEOUT_PRODUCER);
+          break;
+        }
+        mbar_arrive_expect_tx(&full_bar[stage], OZ_STAGE);
+        const uint32_t s = smem_base + stage * OZ_STAGE;
+        for (int q = 0; q < OZ_PLANES; ++q) {
+          tma_load_2d(s + q * OZ_A_PLANE, &tmD, &full_bar[stage], 0, q * p.a_plane_rows + bi * OZ_TM);
+          tma_load_2d(s + OZ_PLANES * OZ_A_PLANE + q * OZ_B_PLANE, &tmE, &full_bar[stage], 0,
+                      q * p.b_plane_rows + bj * OZ_TN);
+        }
+        if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issue: 28 slice pairs x 2 K16 steps
+    if (lane == 0) {
+      constexpr uint32_t ID = idesc_f16(OZ_TM, OZ_TN, 1, false);
+      int stage = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        int bi, bj;
+        if (!oz_decode(p, u, bi, bj)) continue;
+        if (!mbar_wait(&acce_bar, acc_phase ^ 1u, &abort_flag) || !mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+          abort_flag = 1;
+          atomicCAS(status, 0, TC_TIMEOUT_MMA);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t s = smem_base + stage * OZ_STAGE;
+        const uint32_t sa = s, sb = s + OZ_PLANES * OZ_A_PLANE;
+#pragma unroll
+        for (int t = 0; t < OZ_SLICES; ++t) {
+#pragma unroll
+          for (int v = 0; v < OZ_SLICES; ++v) {
+            if (t + v > OZ_SLICES - 1) continue;                 // keep t + u <= 8 (1-based)
+            const uint32_t d = tbase + (t + v) * OZ_TN;
+            const uint32_t ao = sa + (t >> 1) * OZ_A_PLANE + (t & 1) * 64;
+            const uint32_t bo = sb + (v >> 1) * OZ_B_PLANE + (v & 1) * 64;
+            // pairs are issued t-major, so (0, level) is the first product into each level
+            const uint32_t first = (t == 0) ? 0u : 1u;
+            mma_f16(d, sw128_desc(ao), sw128_desc(bo), ID, first);
+            mma_f16(d, sw128_desc(ao + 32), sw128_desc(bo + 32), ID, 1u);
+          }
+        }
+        mma_commit(&empty_bar[stage]);
+        mma_commit(&accf_bar);
+        if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
+        acc_phase ^= 1u;
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue: combine the levels, C -= D E^T
+    // Level sums are integers below 2^23 in fp32.  They are combined exactly in
+    // two 64-bit integers, hi = a0 2^16 + a1 2^8 + a2 (< 2^40) and lo = a3 2^24
+    // + a4 2^16 + a5 2^8 + a6 (< 2^48), so that the product is
+    // 2^(e_i + f_j) (2^-32 hi + 2^-64 lo), formed with two exact conversions and
+    // one FMA.  Each warp stages its 32 x 8 values per chunk in shared memory
+    // and applies them to C row by row (coalesced).
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+    double* stg = reinterpret_cast<double*>(oz_smem_raw + (smem_base - smem_u32(oz_smem_raw)) +
+                                            OZ_STAGES * OZ_STAGE) + (warp - 2) * 32 * 9;
+    uint32_t acc_phase = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      int bi, bj;
+      if (!oz_decode(p, u, bi, bj)) continue;
+      int got = 1;
+      if (lane == 0) got = mbar_wait(&accf_bar, acc_phase, &abort_flag) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) {
+        if (lane == 0) {
+          abort_flag = 1;
+          atomicCAS(status, 0, TC_TIMEOUT_EPILOGUE);
+        }
+        break;
+      }
+      tc_fence_after();
+      const int row0 = bi * OZ_TM + quarter * 32;
+      const int my_row = row0 + lane;
+      const int ei = my_row < p.n ? p.ed[my_row] : 0;
+      const int col0 = bj * OZ_TN + half * 32;
+#pragma unroll 1
+      for (int ch = 0; ch < 4; ++ch) {
+        // this lane's share of C for the chunk, loaded first so that the L2 latency
+        // overlaps the TMEM reads and the level combination
+        double cv[8];
+        bool ok[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int r = it * 4 + (lane >> 3), c = lane & 7;
+          const int i = row0 + r, j = col0 + ch * 8 + c;
+          ok[it] = i < p.n && j <= i && !(i >= p.x0 && i < p.x1) && !(j >= p.x0 && j < p.x1);
+          cv[it] = ok[it] ? p.C[(size_t)i * p.ldc + j] : 0.0;
+        }
+        float a[OZ_LEVELS][8];
+#pragma unroll
+        for (int lv = 0; lv < OZ_LEVELS; ++lv) tmem_ld8(tbase + lane_off + lv * OZ_TN + half * 32 + ch * 8, a[lv]);
+        tmem_ld_wait();
+        long long hi[8], lo[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          hi[c] = (long long)__float2int_rn(a[0][c]) * 65536 + (long long)__float2int_rn(a[1][c]) * 256 +
+                  (long long)__float2int_rn(a[2][c]);
+          lo[c] = (long long)__float2int_rn(a[3][c]) * 16777216 + (long long)__float2int_rn(a[4][c]) * 65536 +
+                  (long long)__float2int_rn(a[5][c]) * 256 + (long long)__float2int_rn(a[6][c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = col0 + ch * 8 + c;
+          const int k = ei + (j < p.n ? p.ee[j] : 0) - 32;       // product scale 2^k for hi, 2^(k-32) for lo
+          double s1, s2;
+          if (k > -990 && k < 990) {
+            s1 = __longlong_as_double((long long)(k + 1023) << 52);
+            s2 = __longlong_as_double((long long)(k - 32 + 1023) << 52);
+          } else {
+            s1 = ldexp(1.0, k);
+            s2 = ldexp(1.0, k - 32);
+          }
+          stg[lane * 9 + c] = fma((double)hi[c], s1, (double)lo[c] * s2);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int r = it * 4 + (lane >> 3), c = lane & 7;
+          if (ok[it]) p.C[(size_t)(row0 + r) * p.ldc + col0 + ch * 8 + c] = cv[it] - stg[r * 9 + c];
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar);
+      acc_phase ^= 1u;
+    }
+  }
+  // teardown: every role has finished or given up; wait for the others before freeing TMEM
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag) {
+    // let copies and MMAs already issued land before the shared memory and TMEM go away
+    const uint64_t t0 = global_timer_ns();
+    while (global_timer_ns() - t0 < 200000ull) {
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, OZ_TMEM_COLS);
+  }
+}
+
+int oz_prepare(lrs_ctx* ctx, const double* X, int ldx, int n, int kb, uint16_t* planes, int rows_pad,
+               int* expo, cudaStream_t stream) {
+  oz_slice_kernel<<<(rows_pad + 7) / 8, 256, 0, stream>>>(X, ldx, n, kb, rows_pad, planes, expo);
+  return after_launch(ctx, "oz_slice_kernel");
+}
+
+int oz_make_maps(lrs_ctx* ctx, const uint16_t* dplanes, const uint16_t* eplanes, int rows_pad, CUtensorMap* md,
+                 CUtensorMap* me) {
+  LRS_TRY(make_operand_map(md, dplanes, 64, (uint64_t)OZ_PLANES * rows_pad, OZ_TM));
+  return make_operand_map(me, eplanes, 64, (uint64_t)OZ_PLANES * rows_pad, OZ_TN);
+}
+
+int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double* C, int n, int ldc,
+              const int* ed, const int* ee, int x0, int x1, int rows_pad, cudaStream_t stream) {
+  OzUpdate p;
+  p.C = C;
+  p.n = n;
+  p.ldc = ldc;
+  p.ed = ed;
+  p.ee = ee;
+  p.x0 = x0;
+  p.x1 = x1;
+  p.row_tiles = (n + OZ_TM - 1) / OZ_TM;
+  p.col_tiles = (n + OZ_TN - 1) / OZ_TN;
+  p.a_plane_rows = rows_pad;
+  p.b_plane_rows = rows_pad;
+  if (!ctx->capturing)
+    LRS_CUDA_TRY(cudaFuncSetAttribute(oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  const int grid = std::min(p.row_tiles * p.col_tiles, ctx->num_sms);
+  oz_update_kernel<<<grid, OZ_THREADS, OZ_SMEM, stream>>>(md, me, p, ctx->ws.status.ptr + 8);
+  return after_launch(ctx, "oz_update_kernel");
+}
+
+int oz_rows_pad(int n) { return (n + OZ_TM - 1) / OZ_TM * OZ_TM; }
+size_t oz_plane_elems(int n) { return (size_t)OZ_PLANES * oz_rows_pad(n) * 64; }
+
+}  // namespace lrs

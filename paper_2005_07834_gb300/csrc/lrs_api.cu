@@ -67,6 +67,7 @@ int aux_stream_ready(lrs_ctx* ctx) {
   if (ctx->aux_stream) return LRS_OK;
   int lo = 0, hi = 0;
   LRS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  ctx->prio_greatest = hi;
   LRS_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, hi));
   for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_bulk, &ctx->ev_join})
     LRS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -243,6 +244,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
+  release(ctx, w.oz_planes); release(ctx, w.oz_expo);
   release(ctx, w.fft_grid); release(ctx, w.fft_index); release(ctx, w.fft_tw);
   release(ctx, w.induced);
   release(ctx, w.alda_n); release(ctx, w.aug_tab); release(ctx, w.aug_coef);
@@ -260,7 +262,7 @@ const char* lrs_last_error(void) { return g_last_error.c_str(); }
 
 // The chi0 tensor-core kernel revision lets measurements quote profiler
 // counters only for the kernel version they were taken on.
-const char* lrs_version(void) { return "lrs 0.3 (sm_103a) chi0-tc r1 dyson-gj r1"; }
+const char* lrs_version(void) { return "lrs 0.4 (sm_103a) chi0-tc r1 dyson-gj r2"; }
 
 int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   clear_error();
@@ -329,6 +331,11 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
       if (value != LRS_DYSON_AUTO && value != LRS_DYSON_FULL && value != LRS_DYSON_LM)
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
+      return LRS_OK;
+    case LRS_OPT_DYSON_UPDATE:
+      if (value != LRS_UPDATE_AUTO && value != LRS_UPDATE_FP64 && value != LRS_UPDATE_TC)
+        return set_error(LRS_ERR_ARG, "Dyson update mode %d unknown", value);
+      ctx->dyson_update = value;
       return LRS_OK;
     case LRS_OPT_REAL_ORBITALS:
       if (value != LRS_REAL_AUTO && value != LRS_REAL_OFF) return set_error(LRS_ERR_ARG, "real-orbital mode %d", value);
@@ -1005,7 +1012,8 @@ int lrs_graph_capture(lrs_ctx* ctx, int nsite, const int* sites) {
     return set_error(rc, "while recording the graph: %s", err.c_str());
   }
   if (e != cudaSuccess) return set_error(LRS_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+  // per-node priorities (the tensor-core launches carry the highest one)
+  e = cudaGraphInstantiate(&ctx->graph_exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     ctx->graph_exec = nullptr;

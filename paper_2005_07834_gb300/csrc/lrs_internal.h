@@ -2,6 +2,7 @@
 // kernel launchers implemented in the k_*.cu translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -150,6 +151,8 @@ struct Workspace {
   DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
+  DevBuf<uint16_t> oz_planes;           // SPD inverse on tensor cores: slice planes of D, E (two sets)
+  DevBuf<int> oz_expo;                  // and their row exponents
   DevBuf<double> induced;               // induced response: T, X, B, right-hand side, outputs
   DevBuf<double> alda_n;                // site density for the exchange-only ALDA kernel
   DevBuf<double> aug_tab;               // augmentation: pseudo waves, corrections, shell mask
@@ -179,6 +182,7 @@ struct lrs_ctx {
   int proj_seg_chunks = 2;             // projection accumulation segment (K chunks of 32)
   int dyson_basis = LRS_DYSON_AUTO;    // full grid or lm basis
   int dyson_solver = LRS_SOLVER_AUTO;  // lm basis: LU of I - C X, or the SPD inverse
+  int dyson_update = LRS_UPDATE_AUTO;  // trailing update of the SPD inverse: FP64 pipe or tensor cores
   int chi0_tn = 128;                   // chi0 tensor-core tile width (64 or 128)
   int fft_n[3] = {0, 0, 0};            // FFT grid of the method-2 projection (0: automatic)
   int graph_projection = LRS_PROJ_EXACT;  // projection mode recorded by lrs_graph_capture
@@ -216,6 +220,7 @@ struct lrs_ctx {
   cudaGraphExec_t graph_exec = nullptr;        // recorded multi-site build
   // second stream of the SPD inverse (higher priority) and its fork/join events
   cudaStream_t aux_stream = nullptr;
+  int prio_greatest = 0;               // numerically smallest (highest) stream priority of the device
   cudaEvent_t ev_fork = nullptr, ev_panel = nullptr, ev_bulk = nullptr, ev_join = nullptr;
 
   lrs_stats_t stats{};
@@ -283,6 +288,18 @@ int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status);
 int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb);
 int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb,
                  double* tinv);
+// Tensor-core float64-accurate rank-32 update (k_ozaki.cu): slices of X [n][ldx] (kb columns)
+// into planes / row scales; maps over the planes; C -= D E^T on the lower triangle outside
+// rows and columns [x0, x1).
+int oz_prepare(lrs_ctx* ctx, const double* X, int ldx, int n, int kb, uint16_t* planes, int rows_pad,
+               int* expo, cudaStream_t stream);
+int oz_make_maps(lrs_ctx* ctx, const uint16_t* dplanes, const uint16_t* eplanes, int rows_pad, CUtensorMap* md,
+                 CUtensorMap* me);
+int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double* C, int n, int ldc,
+              const int* ed, const int* ee, int x0, int x1, int rows_pad, cudaStream_t stream);
+int oz_rows_pad(int n);
+size_t oz_plane_elems(int n);
+
 // In-place inverse of an SPD matrix; lower triangle in and out.  status[0] = 2
 // (status[1] = column) on a pivot that is not positive and finite.
 int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status);

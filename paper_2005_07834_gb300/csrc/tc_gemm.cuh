@@ -386,8 +386,22 @@ int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const 
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int grid = std::min(sh.units, ctx->num_sms);
   if (grid <= 0) return LRS_OK;
-  zgemm_tc_kernel<TN, NPHASE, FMT, Epi><<<grid, TC_THREADS, smem, ctx->stream>>>(ma, mb, sh, epi,
-                                                                                 ctx->ws.status.ptr + 8);
+  // The persistent tensor-core CTAs take the highest launch priority, so that on
+  // SMs shared with FP64 kernels of another build (or stream) they are placed
+  // first and the smaller FP64 CTAs fill the remaining shared memory.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = ctx->prio_greatest;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, zgemm_tc_kernel<TN, NPHASE, FMT, Epi>, ma, mb, sh, epi,
+                                     ctx->ws.status.ptr + 8);
+  if (e != cudaSuccess) return set_error(LRS_ERR_CUDA, "%s launch: %s", name, cudaGetErrorString(e));
   return after_launch(ctx, name);
 }
 

@@ -123,7 +123,7 @@ def test_state_and_argument_errors(lrs):
     scr.close()
 
 
-@pytest.mark.parametrize("basis", ["full", "lm-lu", "lm-spd"])
+@pytest.mark.parametrize("basis", ["full", "lm-lu", "lm-spd", "lm-spd-tc"])
 def test_dyson_bases_match_oracle(lrs, cfg_260, basis):
     ref = cfg_260
     wl = synth.single_site_260()
@@ -131,6 +131,8 @@ def test_dyson_bases_match_oracle(lrs, cfg_260, basis):
     scr.set_option(lrs.LRS_OPT_DYSON_BASIS, lrs.LRS_DYSON_FULL if basis == "full" else lrs.LRS_DYSON_LM)
     if basis != "full":
         scr.set_option(lrs.LRS_OPT_DYSON_SOLVER, lrs.LRS_SOLVER_LU if basis == "lm-lu" else lrs.LRS_SOLVER_SPD)
+    if basis == "lm-spd-tc":      # float64-accurate trailing updates from bf16 slices on the tensor cores
+        scr.set_option(lrs.LRS_OPT_DYSON_UPDATE, lrs.LRS_UPDATE_TC)
     scr.load(wl.orbitals)
     scr.set_sites(wl.sites)
     scr.set_frequency_quadrature(12)
@@ -179,4 +181,28 @@ def test_spd_and_lu_dyson_agree_on_a_large_site(lrs):
     err = rel_fro(ws[1] - v, ws[0] - v)
     print(f"SPD vs LU lm-basis W - v: {err:.2e}")
     assert err < 1e-11
+    scr.close()
+
+
+def test_tensor_core_update_is_float64_accurate(lrs):
+    """SPD inverse of the 48 x 110 site (r = 3888) with the trailing updates on the
+    tensor cores vs float64 FMAs, from the same chi0 (FP64 context): W - v agrees
+    to 1e-12, i.e. the sliced products carry float64 accuracy."""
+    wl = synth.single_site_260()
+    wl.sites = [synth.site_grid(wl.sites[0].center, 48, 110, 4.0)]
+    scr = lrs.Screening(0, "fp64")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(8)
+    scr.project()
+    scr.build_chi0()
+    ws = []
+    for mode in (lrs.LRS_UPDATE_FP64, lrs.LRS_UPDATE_TC):
+        scr.set_option(lrs.LRS_OPT_DYSON_UPDATE, mode)
+        scr.solve_w()
+        ws.append(scr.get_w(0))
+    v = scr.get_v(0)
+    err = rel_fro(ws[1] - v, ws[0] - v)
+    print(f"tensor-core vs float64 trailing updates, W - v: {err:.2e}")
+    assert err < 1e-12
     scr.close()
