@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "lrs_internal.h"
+#include "oz_slice.cuh"
 
 namespace lrs {
 
@@ -700,7 +701,9 @@ constexpr int GJ_PM = GJ_NB / GJ_PR;     // pivot rows per thread
 // diagonal of the pivot block), rows i < k0 read -A[j][i].  E = sigma C with
 // sigma = -1 on rows i < k0, so that A_kj = E_j^T for every j != k.
 __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict__ A, int n, int lda, int k0, int kb,
-                                                        double* __restrict__ C, double* __restrict__ E) {
+                                                        double* __restrict__ C, double* __restrict__ E,
+                                                        uint16_t* __restrict__ eplanes, size_t plane_stride,
+                                                        int* __restrict__ eexp) {
   __shared__ double t[GJ_NB][GJ_NB + 1];
   const int i0 = blockIdx.x * GJ_NB;
   if (i0 < k0) {   // k0 is a multiple of GJ_NB, so the whole row block lies below k0
@@ -722,6 +725,17 @@ __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict
       const double v = (i >= j) ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
       C[(size_t)i * GJ_NB + c] = v;
       E[(size_t)i * GJ_NB + c] = v;
+    }
+  }
+  if (eplanes) {
+    // slices of the rows of E for the tensor-core update, one warp per row
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int rr = threadIdx.x >> 5; rr < GJ_NB; rr += blockDim.x >> 5) {
+      const int row = i0 + rr;
+      if (row >= n) break;
+      const double x = lane < kb ? E[(size_t)row * GJ_NB + lane] : 0.0;
+      oz_slice_row(x, lane, row, plane_stride, eplanes, eexp);
     }
   }
 }
@@ -788,7 +802,9 @@ __global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict_
 // D = C Pinv (n x kb), 16 rows per CTA so that every SM takes part.
 constexpr int GJ_DR = 16;
 __global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict__ C, int n, int kb,
-                                                       const double* __restrict__ Pinv, double* __restrict__ D) {
+                                                       const double* __restrict__ Pinv, double* __restrict__ D,
+                                                       uint16_t* __restrict__ dplanes, size_t plane_stride,
+                                                       int* __restrict__ dexp) {
   __shared__ double pv[GJ_NB][GJ_NB + 1];
   __shared__ double cr[GJ_DR][GJ_NB + 1];
   const int r0 = blockIdx.x * GJ_DR;
@@ -801,20 +817,23 @@ __global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict_
     cr[i][j] = (r0 + i < n) ? C[(size_t)(r0 + i) * GJ_NB + j] : 0.0;
   }
   __syncthreads();
-  const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;   // rows ib + GJ_PR m
-  if (j >= kb) return;
+  const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;   // rows ib + GJ_PR m (a warp per row group)
   double acc[GJ_DR / GJ_PR];
 #pragma unroll
   for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = 0.0;
-  for (int k = 0; k < kb; ++k) {
-    const double b = pv[k][j];
+  if (j < kb) {
+    for (int k = 0; k < kb; ++k) {
+      const double b = pv[k][j];
 #pragma unroll
-    for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = fma(cr[ib + GJ_PR * m][k], b, acc[m]);
+      for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = fma(cr[ib + GJ_PR * m][k], b, acc[m]);
+    }
   }
 #pragma unroll
   for (int m = 0; m < GJ_DR / GJ_PR; ++m) {
     const int r = r0 + ib + GJ_PR * m;
-    if (r < n) D[(size_t)r * GJ_NB + j] = acc[m];
+    if (r < n && j < kb) D[(size_t)r * GJ_NB + j] = acc[m];
+    // slices of the row of D for the tensor-core update (the warp holds the whole row)
+    if (dplanes && r < n) oz_slice_row(acc[m], j, r, plane_stride, dplanes, dexp);
   }
 }
 
@@ -957,20 +976,19 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
       esc[q] = ctx->ws.oz_expo.ptr + (2 * q + 1) * (size_t)rows_pad;
       LRS_TRY(oz_make_maps(ctx, dpl[q], epl[q], rows_pad, &md[q], &me[q]));
     }
+    // rows beyond n stay zero; rows below n are rewritten by every panel
+    LRS_CUDA_TRY(cudaMemsetAsync(ctx->ws.oz_planes.ptr, 0, 4 * pe * sizeof(uint16_t), s1));
   }
   auto panel = [&](int kb_idx, int q) -> int {
     const int k0 = kb_idx * GJ_NB, kb = std::min(GJ_NB, n - k0);
-    gj_gather_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Cb[q], Eb[q]);
+    const size_t stride = (size_t)rows_pad * 64;
+    gj_gather_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Cb[q], Eb[q], epl[q], stride, esc[q]);
     LRS_TRY(after_launch(ctx, "gj_gather_kernel"));
     gj_pivot_kernel<<<1, 256, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
     LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
-    gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q]);
+    gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q], dpl[q], stride, dsc[q]);
     LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
     ctx->fp64_flops += 2.0 * n * kb * kb;
-    if (tc) {
-      LRS_TRY(oz_prepare(ctx, Db[q], GJ_NB, n, kb, dpl[q], rows_pad, dsc[q], s2));
-      LRS_TRY(oz_prepare(ctx, Eb[q], GJ_NB, n, kb, epl[q], rows_pad, esc[q], s2));
-    }
     return LRS_OK;
   };
   // fork the second stream from the context stream (also inside a graph capture)

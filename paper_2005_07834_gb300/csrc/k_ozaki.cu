@@ -3,10 +3,9 @@
 //
 // Every row of D and of E (32 float64 values) is scaled by a power of two,
 // x = 2^e a with |a| < 1, and cut into integer slices
-//   a = sum_{t=1..7} 2^(-8 t) s_t,   s_1 = rint(256 a), s_{t+1} = rint(256 r_t),
-//   r_t = 256 r_{t-1} - s_t (r_0 = a),
-// so |s_1| <= 256, |s_t| <= 128 (t > 1): each slice is exact in bf16 and the
-// residual after seven slices is below 2^-57 |a|max.  The products of the 28
+//   a = sum_{t=1..7} 2^(-8 t) s_t   (base-256 digits of round(a 2^56)),
+// |s_1| <= 256, |s_t| <= 128 (t > 1): each slice is exact in bf16 and the
+// representation error is below 2^-57 |a|max.  The products of the 28
 // slice pairs with t + u <= 8 are issued as bf16 tcgen05 MMAs (K = 32, two K16
 // steps each) into seven fp32 accumulators in TMEM, one per level t + u.  A
 // level sum is an integer below 7 * 32 * 2^16 < 2^24, hence exact in fp32.
@@ -24,52 +23,25 @@
 #include <cmath>
 
 #include "lrs_internal.h"
+#include "oz_slice.cuh"
 #include "tc_common.cuh"
 
 namespace lrs {
 using namespace tc;
 
-constexpr int OZ_SLICES = 7;
-constexpr int OZ_PLANES = 4;                   // two slices per 128-byte row (the last half of plane 3 is zero)
+constexpr int OZ_SLICES = OZ_SLICE_COUNT;
+constexpr int OZ_PLANES = OZ_PLANE_COUNT;      // two slices per 128-byte row (the last half of plane 3 is zero)
 constexpr int OZ_LEVELS = 7;                   // t + u = 2 .. 8
 constexpr int OZ_TM = 128, OZ_TN = 64;
 constexpr int OZ_A_PLANE = OZ_TM * 128;        // bytes of one A plane tile
 constexpr int OZ_B_PLANE = OZ_TN * 128;
 constexpr int OZ_STAGE = OZ_PLANES * (OZ_A_PLANE + OZ_B_PLANE);
-constexpr int OZ_STAGES = 2;
+constexpr int OZ_STAGES = 1;
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * 9 * 8;   // per-warp [32][9] float64 staging of C updates
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + OZ_STAGE_EPI + 1024;
 constexpr int OZ_THREADS = 320;                // producer, MMA issuer, 8 epilogue warps
 constexpr int OZ_TMEM_COLS = 512;              // 7 levels x 64 columns used
-
-// Slices of the first kb <= 32 columns of X [n][ldx] into planes
-// [OZ_PLANES][rows_pad][64] bf16 and the row exponents e (scale 2^e).  Rows >= n are zero.
-__global__ void oz_slice_kernel(const double* __restrict__ X, int ldx, int n, int kb, int rows_pad,
-                                uint16_t* __restrict__ planes, int* __restrict__ expo) {
-  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int k = threadIdx.x & 31;
-  if (row >= rows_pad) return;
-  const double x = (row < n && k < kb) ? X[(size_t)row * ldx + k] : 0.0;
-  double m = fabs(x);
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);                  // m = f 2^e, f in [0.5, 1)
-  if (k == 0) expo[row] = e;
-  double r = ldexp(x, -e);                     // |r| < 1
-  const size_t plane = (size_t)rows_pad * 64;
-#pragma unroll
-  for (int t = 0; t < 2 * OZ_PLANES; ++t) {
-    double sl = 0.0;
-    if (t < OZ_SLICES) {
-      r *= 256.0;
-      sl = rint(r);
-      r -= sl;
-    }
-    const __nv_bfloat16 b = __double2bfloat16(sl);   // an integer of at most 9 bits: exact
-    planes[(t >> 1) * plane + (size_t)row * 64 + (t & 1) * 32 + k] = __bfloat16_as_ushort(b);
-  }
-}
 
 struct OzUpdate {
   double* C;
@@ -282,12 +254,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     tc_fence_after();
     tmem_dealloc(tbase, OZ_TMEM_COLS);
   }
-}
-
-int oz_prepare(lrs_ctx* ctx, const double* X, int ldx, int n, int kb, uint16_t* planes, int rows_pad,
-               int* expo, cudaStream_t stream) {
-  oz_slice_kernel<<<(rows_pad + 7) / 8, 256, 0, stream>>>(X, ldx, n, kb, rows_pad, planes, expo);
-  return after_launch(ctx, "oz_slice_kernel");
 }
 
 int oz_make_maps(lrs_ctx* ctx, const uint16_t* dplanes, const uint16_t* eplanes, int rows_pad, CUtensorMap* md,

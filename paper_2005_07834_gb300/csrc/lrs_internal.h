@@ -288,11 +288,9 @@ int lu_factor(lrs_ctx* ctx, double* A, int n, int* ipiv, int* status);
 int lu_solve(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb);
 int lu_solve_inv(lrs_ctx* ctx, const double* LU, int n, const int* ipiv, double* B, int nrhs, int ldb,
                  double* tinv);
-// Tensor-core float64-accurate rank-32 update (k_ozaki.cu): slices of X [n][ldx] (kb columns)
-// into planes / row scales; maps over the planes; C -= D E^T on the lower triangle outside
-// rows and columns [x0, x1).
-int oz_prepare(lrs_ctx* ctx, const double* X, int ldx, int n, int kb, uint16_t* planes, int rows_pad,
-               int* expo, cudaStream_t stream);
+// Tensor-core float64-accurate rank-32 update (k_ozaki.cu; the slices come from
+// oz_slice_row, oz_slice.cuh): maps over the slice planes; C -= D E^T on the lower
+// triangle outside rows and columns [x0, x1).
 int oz_make_maps(lrs_ctx* ctx, const uint16_t* dplanes, const uint16_t* eplanes, int rows_pad, CUtensorMap* md,
                  CUtensorMap* me);
 int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double* C, int n, int ldc,
