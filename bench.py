@@ -51,7 +51,7 @@ MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 
 
 # (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per gj_update_kernel<0> launch
-DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6}
+DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"): 28.5e6}
 
 
 def dyson_roofline(st, workload=None, version=None):
@@ -506,6 +506,106 @@ def run_ours_multisite(args):
         torch.distributed.destroy_process_group()
 
 
+def run_rows(args):
+    """One JSON line per next-row operation on the 3520-point site (bf16x3 context unless
+    --precision says otherwise): device time by CUDA events around the call on the
+    library's stream (median of --steps after --warmup), algorithmic work, roofline."""
+    import torch
+    from paper_2005_07834_gb300 import lrs, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    peaks = load_peaks()
+    wl = synth.single_site_3520()
+    o, s = wl.orbitals, wl.sites[0]
+    n, K, nf = s.npts, o.nk * o.nbands, wl.nfreq
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(max(1, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    def line(row, what, ms, work, unit, bound, peak, peak_source, extra=None):
+        d = {"row": row, "operation": what, "workload": "single-site-3520", "precision": args.precision,
+             "ms": ms, "unit": unit, "achieved": work / (ms * 1e-3) / (1e9 if unit == "GB/s" else 1e12),
+             "bound": bound, "peak": peak, "peak_source": peak_source}
+        d["frac"] = d["achieved"] / peak
+        d.update(extra or {})
+        print(json.dumps(d), flush=True)
+
+    scr = lrs.Screening(0, args.precision, stream.cuda_stream)
+    scr.load(o)
+    scr.set_sites([s])
+    scr.set_frequency_quadrature(nf)
+    scr.set_fft_grid(*wl.fft_grid)
+    hbm = peaks["hbm_gbs"]
+    # f1: FFT + cubic Lagrange projection; HBM-bound: per k the grid is written once by the z pass,
+    # read and written by the y and x passes, read by the gather (4 passes over N^3 nb complex64)
+    ms = timed(lambda: scr.project(mode=lrs.LRS_PROJ_FFT_LAGRANGE3))
+    n3 = int(np.prod(wl.fft_grid))
+    elem = 8 if args.precision != "fp64" else 16
+    byt = o.nk * (n3 * o.nbands * elem * 5 + o.ng * o.nbands * 16) + n * K * 16
+    line("f1", "project FFT 48^3 + Lagrange", ms, byt, "GB/s", "hbm", hbm, "copy, measured",
+         {"bytes_model": "per k: 5 grid passes N^3 nb complex + coefficients; psi written"})
+    ms_exact = timed(lambda: scr.project(mode=lrs.LRS_PROJ_EXACT))
+    line("a2", "project exact (tensor cores)", ms_exact, 8.0 * n * o.ng * K, "TFLOP/s", "tensor",
+         peaks["bf16_tflops"], "bf16 burst, measured", {"note": "3 products issued per algorithmic product"})
+    scr.build_chi0()
+    s_lmax, nrad, nang = s.lmax, s.nrad, s.nang
+    # f2: induced response; FP64 work = projection of chi0 onto Y_lm (2 n^2 (l+1)^2) + the solve
+    for lresp in (0, s_lmax):
+        l2 = (lresp + 1) ** 2
+        d = nrad * l2
+        ms = timed(lambda: scr.induced_potential(0, -1.0, 1.5, lresp))
+        flop = 2.0 * n * n * l2 + 2.0 * l2 * d * n + 2.0 / 3.0 * d ** 3 + 2.0 * d * d * nrad
+        line("f2", f"induced potential l_resp={lresp}", ms, flop, "TFLOP/s", "alu", FP64_PEAK_TFLOPS,
+             "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz", {"note": "synchronous call incl. host copies"})
+    # f3: ALDA dressing chi_eff = (I - chi0 D)^-1 chi0 (LU + n right-hand sides): 8/3 n^3
+    scr.set_fxc(0, lrs.LRS_FXC_ALDA_X)
+    ms_w_alda = timed(lambda: scr.solve_w())
+    st = scr.stats()
+    scr.set_fxc(0, lrs.LRS_FXC_NONE)
+    ms_w = timed(lambda: scr.solve_w())
+    line("f3", "ALDA dressing (solve_w with kernel minus RPA solve_w)", ms_w_alda - ms_w, 8.0 / 3.0 * n ** 3,
+         "TFLOP/s", "alu", FP64_PEAK_TFLOPS, "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+         {"ms_solve_w_alda": ms_w_alda, "ms_solve_w_rpa": ms_w})
+    # f4: augmentation, l <= 2, two partial waves per l: 2 x (projection + update) = 16 n nproj K flop
+    radii = np.linalg.norm(s.pts[::nang], axis=1)
+    ps = np.array([[radii ** l * np.exp(-a * radii ** 2) for a in (0.5, 1.1)] for l in range(3)])
+    bump = np.where(radii < 2.0, np.sin(np.pi * radii / 2.0) ** 2, 0.0)
+    ae = ps + 0.1 * bump[None, None, :]
+    ms = timed(lambda: scr.augment(0, ae, ps, 2.0))
+    nproj = 9 * 2
+    n_in = int(np.sum(radii <= 2.0)) * nang     # points on the shells inside the augmentation radius
+    # projection and update: a real weight times a complex orbital, 4 flop each, over the inside points
+    line("f4", "augmentation (9 lm x 2 partial waves, r_a = 2)", ms, 8.0 * n_in * nproj * K, "TFLOP/s", "alu",
+         FP64_PEAK_TFLOPS, "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+         {"points_inside": n_in, "note": "synchronous call incl. host setup of the overlaps"})
+    scr.close()
+    # f1': Gamma-point real orbitals: chi0 with the real-operand contraction (4 n^2 K nf flop)
+    wg = synth.gamma_site_3520()
+    sg = lrs.Screening(0, args.precision, stream.cuda_stream)
+    sg.load(wg.orbitals)
+    sg.set_sites(wg.sites)
+    sg.set_frequency_quadrature(wg.nfreq)
+    sg.project()
+    ms = timed(lambda: sg.build_chi0())
+    st = sg.stats()
+    line("f1-gamma", "chi0, Gamma-point real orbitals", st["ms_chi0_main"], 4.0 * n * n * K * wg.nfreq, "TFLOP/s",
+         "tensor", peaks["bf16_tflops_sustained"], "bf16 sustained, measured",
+         {"ms_build_chi0": ms, "issued_frac": 3 * 4.0 * n * n * K * wg.nfreq / (st["ms_chi0_main"] * 1e-3) / 1e12
+          / peaks["bf16_tflops_sustained"]})
+    sg.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -520,8 +620,13 @@ def main():
                     help="Sec. VI.B method 1 (direct sum) or method 2 (FFT + cubic Lagrange on the workload's grid)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows", action="store_true",
+                    help="time each next-row operation (FFT projection, induced response, ALDA, augmentation, "
+                         "Gamma point) on the 3520-point site instead of the build")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.rows:
+        run_rows(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload in MULTI_SITE:
         run_ours_multisite(args)
