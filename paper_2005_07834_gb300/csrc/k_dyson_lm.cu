@@ -212,15 +212,27 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   double* B = X + rr;                     // [r][r]
   double* Z = B + rr;                     // [r][r]
   const double* Yang = s.yang.ptr;        // [nang][L2]
+  // The four basis changes (T, X, U, W) run on the tensor cores from exact bf16
+  // slices (float64-accurate, k_ozgemm.cu) wherever the trailing updates of the
+  // SPD inverse do, else with float64 FMAs.
+  const bool tc = ctx->dyson_update == LRS_UPDATE_TC ||
+                  (ctx->dyson_update == LRS_UPDATE_AUTO && ctx->precision != LRS_FP64);
   // T[:, j' block] = chi0[:, shell j'] diag(Q_j') Yang        (one launch, batch = shell)
-  LRS_TRY(dgemm_batched(ctx, false, false, n, L2, nang, 1.0, s.response_chi(), n, nang, s.wts.ptr, nang, Yang, L2, 0,
-                        nullptr, 0.0, T, r, L2, nrad));
+  if (tc)
+    LRS_TRY(oz_gemm_batched(ctx, false, false, n, L2, nang, 1.0, s.response_chi(), n, nang, s.wts.ptr, nang, Yang,
+                            L2, 0, 0.0, T, r, L2, nrad, 0));
+  else
+    LRS_TRY(dgemm_batched(ctx, false, false, n, L2, nang, 1.0, s.response_chi(), n, nang, s.wts.ptr, nang, Yang, L2,
+                          0, nullptr, 0.0, T, r, L2, nrad));
   // X = Y^T Q T is symmetric; its transpose is formed, X^T[:, j block] = T[shell j, :]^T diag(Q_j) Yang,
   // so that the 81- (generally (L+1)^2-) wide side of the product is a tile column.  The SPD
   // route reads only its lower triangle.
   const bool use_spd = ctx->dyson_solver == LRS_SOLVER_SPD || (ctx->dyson_solver == LRS_SOLVER_AUTO && s.spd);
   if (use_spd && !s.spd) return set_error(LRS_ERR_STATE, "SPD Dyson solver: a radial Coulomb block has no Cholesky factor");
-  if (use_spd)
+  if (tc)
+    LRS_TRY(oz_gemm_batched(ctx, true, false, r, L2, nang, 1.0, T, r, (long long)nang * r, s.wts.ptr, nang, Yang,
+                            L2, 0, 0.0, X, r, L2, nrad, use_spd ? L2 : 0));
+  else if (use_spd)
     LRS_TRY(dgemm_batched_lower(ctx, true, false, r, L2, nang, T, r, (long long)nang * r, s.wts.ptr, nang, Yang,
                                 L2, X, r, nrad));
   else
@@ -250,10 +262,18 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
   }
   // U[shell j, :] = Yang Z[j block, :]   (reuses T)
   double* U = T;
-  LRS_TRY(dgemm_batched(ctx, false, false, nang, r, L2, 1.0, Yang, L2, 0, nullptr, 0, Z, r, (long long)L2 * r,
-                        nullptr, 0.0, U, r, (long long)nang * r, nrad));
+  if (tc)
+    LRS_TRY(oz_gemm_batched(ctx, false, false, nang, r, L2, 1.0, Yang, L2, 0, nullptr, 0, Z, r, (long long)L2 * r,
+                            0.0, U, r, (long long)nang * r, nrad, 0));
+  else
+    LRS_TRY(dgemm_batched(ctx, false, false, nang, r, L2, 1.0, Yang, L2, 0, nullptr, 0, Z, r, (long long)L2 * r,
+                          nullptr, 0.0, U, r, (long long)nang * r, nrad));
   // W[:, shell j'] = U[:, j' block] Yang^T on and below the diagonal, then mirrored (W is symmetric)
-  LRS_TRY(dgemm_batched_lower(ctx, false, true, n, nang, L2, U, r, L2, nullptr, 0, Yang, L2, s.w.ptr, n, nrad));
+  if (tc)
+    LRS_TRY(oz_gemm_batched(ctx, false, true, n, nang, L2, 1.0, U, r, L2, nullptr, 0, Yang, L2, 0, 0.0, s.w.ptr, n,
+                            nang, nrad, nang));
+  else
+    LRS_TRY(dgemm_batched_lower(ctx, false, true, n, nang, L2, U, r, L2, nullptr, 0, Yang, L2, s.w.ptr, n, nrad));
   return mirror_lower(ctx, s.w.ptr, n, n);
 }
 

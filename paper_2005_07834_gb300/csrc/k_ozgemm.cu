@@ -1,0 +1,483 @@
+// Float64-accurate batched GEMM on the tensor cores,
+//   C_b = alpha op(A_b) diag(ks_b) op(B_b) + beta C_b,
+// for the basis changes of the lm-basis Dyson solve (Sec. VI.E: T = chi0 Q Y,
+// X = Y^T Q T, U = Y Z, W = U Y^T, one batch entry per radial shell).
+//
+// Packing (oz_pack_kernel): every row of op(A) diag(ks) and of op(B)^T is
+// scaled by a power of two, x = 2^e a with |a| < 1 (e the exponent of the row's
+// largest magnitude), and written as the integer N = round(a 2^56) in base 128
+// with balanced digits,
+//   a = sum_{t=0..7} s_t 128^-(t+1),  |s_0| <= 128, |s_t| <= 64 (t > 0),
+// each digit exact in bf16; the representation error is below 2^-57 of the
+// row maximum.  Slices 2q and 2q + 1 share one 128-byte row of plane q (the
+// [hi | lo] layout the swizzled operand tiles use), per K chunk of 32.
+//
+// Products (oz_gemm_kernel): the 36 slice pairs with t + u <= 7 are issued as
+// bf16 tcgen05 MMAs into eight fp32 accumulators in TMEM, one per level
+// t + u.  Over a K segment of 128 a level sum is an integer of magnitude at
+// most 128 (2 128 64 + 6 64 64) < 2^23, so the tensor cores accumulate it
+// exactly.  The epilogue combines the levels of a segment as two 64-bit
+// integers, converts them exactly and scales them by 2^(e_i + f_j) with one
+// rounding; segments add in float64.  The dropped pairs (t + u >= 8) and the
+// representation errors bound the error by about 2^-54 K |A|row max |B|row max
+// per element, the bound of a float64 dot product of K terms.
+//
+// Tiles of 128 x 64 outputs, one persistent CTA per SM: a TMA producer warp,
+// an MMA-issuing warp and eight epilogue warps; two pipeline stages of one K
+// chunk (four A and four B planes, 96 KB) each.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "lrs_internal.h"
+#include "tc_common.cuh"
+
+namespace lrs {
+using namespace tc;
+
+constexpr int OG_SLICES = 8;                   // base-128 digits per value
+constexpr int OG_PLANES = 4;                   // two slices per 128-byte row
+constexpr int OG_LEVELS = 8;                   // t + u = 0 .. 7
+constexpr int OG_TM = 128, OG_TN = 64;
+constexpr int OG_A_PLANE = OG_TM * 128;        // bytes of one A plane tile (one K chunk of 32)
+constexpr int OG_B_PLANE = OG_TN * 128;
+constexpr int OG_STAGE = OG_PLANES * (OG_A_PLANE + OG_B_PLANE);
+constexpr int OG_STAGES = 2;
+constexpr int OG_SEG = 4;                      // K chunks of 32 per exact accumulation segment
+constexpr int OG_EPI_WARPS = 8;
+constexpr int OG_STAGE_EPI = OG_EPI_WARPS * 32 * 9 * 8;   // per-warp [32][9] float64 staging
+constexpr int OG_SMEM = OG_STAGES * OG_STAGE + OG_STAGE_EPI + 1024;
+constexpr int OG_THREADS = 320;
+constexpr int OG_TMEM_COLS = 512;              // 8 levels x 64 columns
+constexpr int OG_BAD_EXP = 1 << 20;            // row exponent of a row holding a NaN or an infinity
+
+static_assert(OG_SMEM <= 227 * 1024, "shared memory of one CTA");
+
+// ---------------------------------------------------------------- slicing
+// Operand X (rows x k, logical) with X[i][kk] = (trans ? x[kk ld + i] : x[i ld + kk]) ks[kk]
+// into planes[b][q][kc][rows_pad][64] and expo[b][rows_pad].  One CTA: 32 rows, all of K,
+// read through 32 x 32 shared-memory tiles so that both layouts are read coalesced.
+struct OgPack {
+  const double* x;
+  int ld;
+  long long stride;
+  const double* ks;
+  long long stride_ks;
+  int trans;
+  int rows, k, rows_pad, nchunks;
+  uint16_t* planes;
+  int* expo;
+};
+
+__device__ __forceinline__ void og_load_tile(const OgPack& p, const double* x, const double* ks, int i0, int k0,
+                                             double (*t)[33]) {
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    int ii, kk;
+    if (p.trans) { kk = idx >> 5; ii = idx & 31; } else { ii = idx >> 5; kk = idx & 31; }
+    const int i = i0 + ii, k = k0 + kk;
+    double v = 0.0;
+    if (i < p.rows && k < p.k) {
+      v = p.trans ? x[(size_t)k * p.ld + i] : x[(size_t)i * p.ld + k];
+      if (ks) v *= ks[k];
+    }
+    t[kk][ii] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_pack_kernel(const OgPack p) {
+  __shared__ double t[32][33];
+  const int b = blockIdx.y;
+  const double* x = p.x + p.stride * b;
+  const double* ks = p.ks ? p.ks + p.stride_ks * b : nullptr;
+  const int i0 = blockIdx.x * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // pass 1: row maxima (rows warp, warp + 8, warp + 16, warp + 24)
+  double mx[4] = {0.0, 0.0, 0.0, 0.0};
+  bool bad[4] = {false, false, false, false};
+  for (int kc = 0; kc < p.nchunks; ++kc) {
+    og_load_tile(p, x, ks, i0, kc * 32, t);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const double v = t[lane][warp + 8 * r];
+      if (!isfinite(v)) bad[r] = true;
+      else mx[r] = fmax(mx[r], fabs(v));
+    }
+    __syncthreads();
+  }
+  int e[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    double m = mx[r];
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const bool any_bad = __any_sync(0xffffffffu, bad[r]);
+    e[r] = 0;
+    if (m > 0.0) frexp(m, &e[r]);            // m = f 2^e, f in [0.5, 1)
+    if (any_bad) e[r] = OG_BAD_EXP;
+    if (lane == 0) p.expo[(size_t)b * p.rows_pad + i0 + warp + 8 * r] = e[r];
+  }
+  // pass 2: digits (the tiles are read again, from L2)
+  const size_t chunk_elems = (size_t)p.rows_pad * 64;
+  uint16_t* base = p.planes + (size_t)b * OG_PLANES * p.nchunks * chunk_elems;
+  for (int kc = 0; kc < p.nchunks; ++kc) {
+    og_load_tile(p, x, ks, i0, kc * 32, t);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = i0 + warp + 8 * r;
+      double v = t[lane][warp + 8 * r];
+      if (e[r] == OG_BAD_EXP) v = 0.0;
+      // N = round(v 2^(56 - e)), |N| <= 2^56; balanced base-128 digits s_7 .. s_1, leading s_0
+      long long N = __double2ll_rn(ldexp(v, 56 - e[r]));
+      int dig[OG_SLICES];
+#pragma unroll
+      for (int s = OG_SLICES - 1; s > 0; --s) {
+        const long long d = ((N + 64) & 127) - 64;
+        dig[s] = (int)d;
+        N = (N - d) / 128;                     // exact
+      }
+      dig[0] = (int)N;
+#pragma unroll
+      for (int s = 0; s < OG_SLICES; ++s) {
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)dig[s]);   // at most 8 significant bits: exact
+        base[((size_t)(s >> 1) * p.nchunks + kc) * chunk_elems + (size_t)row * 64 + (s & 1) * 32 + lane] =
+            __bfloat16_as_ushort(h);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- products
+struct OgGemm {
+  double* C;
+  int ldc;
+  long long stride_c;
+  int m, n;
+  double alpha, beta;
+  const int* ea;           // [a batches][a_rows_pad]
+  const int* eb;           // [b batches][b_rows_pad]
+  int a_shared, b_shared;  // one packed operand serves every batch entry
+  int a_rows_pad, b_rows_pad, nchunks;
+  int row_tiles, col_tiles, batch;
+  int lower_col;           // > 0: C_b is column block b * lower_col of a symmetric matrix (lower tiles only)
+};
+
+__device__ __forceinline__ bool og_decode(const OgGemm& p, int u, int& b, int& bi, int& bj) {
+  const int per = p.row_tiles * p.col_tiles;
+  b = u / per;
+  const int rem = u - b * per;
+  bi = rem / p.col_tiles;
+  bj = rem - bi * p.col_tiles;
+  return p.lower_col <= 0 || bi * OG_TM + OG_TM - 1 >= b * p.lower_col + bj * OG_TN;
+}
+
+__global__ void __launch_bounds__(OG_THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const OgGemm p, int* status) {
+  __shared__ __align__(8) uint64_t full_bar[OG_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[OG_STAGES];
+  __shared__ __align__(8) uint64_t accf_bar;
+  __shared__ __align__(8) uint64_t acce_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  extern __shared__ uint8_t og_smem_raw[];
+  const uint32_t smem_base = (smem_u32(og_smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = p.batch * p.row_tiles * p.col_tiles;
+  const int nseg = (p.nchunks + OG_SEG - 1) / OG_SEG;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OG_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accf_bar, 1);
+    mbar_init(&acce_bar, OG_EPI_WARPS);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_map(&tmA);
+    tma_prefetch_map(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, OG_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer: all slice planes of one K chunk per stage
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+        int b, bi, bj;
+        if (!og_decode(p, u, b, bi, bj)) continue;
+        const int ab = p.a_shared ? 0 : b, bb = p.b_shared ? 0 : b;
+        for (int kc = 0; kc < p.nchunks; ++kc) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_PRODUCER);
+            stop = true;
+            break;
+          }
+          mbar_arrive_expect_tx(&full_bar[stage], OG_STAGE);
+          const uint32_t s = smem_base + stage * OG_STAGE;
+          for (int q = 0; q < OG_PLANES; ++q) {
+            tma_load_2d(s + q * OG_A_PLANE, &tmA, &full_bar[stage], 0,
+                        ((ab * OG_PLANES + q) * p.nchunks + kc) * p.a_rows_pad + bi * OG_TM);
+            tma_load_2d(s + OG_PLANES * OG_A_PLANE + q * OG_B_PLANE, &tmB, &full_bar[stage], 0,
+                        ((bb * OG_PLANES + q) * p.nchunks + kc) * p.b_rows_pad + bj * OG_TN);
+          }
+          if (++stage == OG_STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issue: 36 slice pairs x 2 K16 steps per chunk
+    if (lane == 0) {
+      constexpr uint32_t ID = idesc_f16(OG_TM, OG_TN, 1, false);
+      int stage = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+        int b, bi, bj;
+        if (!og_decode(p, u, b, bi, bj)) continue;
+        for (int sg = 0; sg < nseg && !stop; ++sg) {
+          if (!mbar_wait(&acce_bar, acc_phase ^ 1u, &abort_flag)) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_MMA);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const int kc1 = min(p.nchunks, (sg + 1) * OG_SEG);
+          for (int kc = sg * OG_SEG; kc < kc1; ++kc) {
+            if (!mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+              abort_flag = 1;
+              atomicCAS(status, 0, TC_TIMEOUT_MMA);
+              stop = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t s = smem_base + stage * OG_STAGE;
+            const uint32_t sa = s, sb = s + OG_PLANES * OG_A_PLANE;
+            const uint32_t seg_first = (kc == sg * OG_SEG) ? 1u : 0u;
+#pragma unroll
+            for (int t = 0; t < OG_SLICES; ++t) {
+#pragma unroll
+              for (int v = 0; v < OG_SLICES; ++v) {
+                if (t + v > OG_LEVELS - 1) continue;
+                const uint32_t d = tbase + (t + v) * OG_TN;
+                const uint32_t ao = sa + (t >> 1) * OG_A_PLANE + (t & 1) * 64;
+                const uint32_t bo = sb + (v >> 1) * OG_B_PLANE + (v & 1) * 64;
+                // pairs are issued t-major, so (0, level) is the first product into each level
+                const uint32_t acc = (seg_first && t == 0) ? 0u : 1u;
+                mma_f16(d, sw128_desc(ao), sw128_desc(bo), ID, acc);
+                mma_f16(d, sw128_desc(ao + 32), sw128_desc(bo + 32), ID, 1u);
+              }
+            }
+            mma_commit(&empty_bar[stage]);
+            if (++stage == OG_STAGES) { stage = 0; phase ^= 1u; }
+          }
+          if (stop) break;
+          mma_commit(&accf_bar);
+          acc_phase ^= 1u;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue: combine the levels, C = alpha sum + beta C
+    // Level sums S_0 .. S_7 (integers below 2^23 in fp32) are combined exactly as
+    // hi = S_0 2^21 + S_1 2^14 + S_2 2^7 + S_3 and lo = S_4 2^21 + S_5 2^14 + S_6 2^7 + S_7
+    // (below 2^45 each), so that the segment's product is 2^(e_i + f_j - 35) (hi + 2^-28 lo):
+    // two exact conversions and one FMA.  Each warp stages 32 rows x 8 columns in shared
+    // memory and writes them row-wise (coalesced).
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+    double* stg = reinterpret_cast<double*>(og_smem_raw + (smem_base - smem_u32(og_smem_raw)) +
+                                            OG_STAGES * OG_STAGE) + (warp - 2) * 32 * 9;
+    uint32_t acc_phase = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+      int b, bi, bj;
+      if (!og_decode(p, u, b, bi, bj)) continue;
+      const int ab = p.a_shared ? 0 : b, bb = p.b_shared ? 0 : b;
+      double* C = p.C + p.stride_c * b;
+      const int row0 = bi * OG_TM + quarter * 32;
+      const int col0 = bj * OG_TN + half * 32;
+      const int ei = p.ea[(size_t)ab * p.a_rows_pad + row0 + lane];   // padded rows hold 0
+      for (int sg = 0; sg < nseg; ++sg) {
+        int got = 1;
+        if (lane == 0) got = mbar_wait(&accf_bar, acc_phase, &abort_flag) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          if (lane == 0) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_EPILOGUE);
+          }
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const bool read_c = sg > 0 || p.beta != 0.0;
+        const double cscale = sg > 0 ? 1.0 : p.beta;
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+          double cv[8];
+          bool ok[8];
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int i = row0 + it * 4 + (lane >> 3), j = col0 + ch * 8 + (lane & 7);
+            ok[it] = i < p.m && j < p.n;
+            cv[it] = (ok[it] && read_c) ? C[(size_t)i * p.ldc + j] : 0.0;
+          }
+          float a[OG_LEVELS][8];
+#pragma unroll
+          for (int lv = 0; lv < OG_LEVELS; ++lv) tmem_ld8(tbase + lane_off + lv * OG_TN + half * 32 + ch * 8, a[lv]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const long long hi = (long long)__float2int_rn(a[0][c]) * 2097152 +
+                                 (long long)__float2int_rn(a[1][c]) * 16384 +
+                                 (long long)__float2int_rn(a[2][c]) * 128 + (long long)__float2int_rn(a[3][c]);
+            const long long lo = (long long)__float2int_rn(a[4][c]) * 2097152 +
+                                 (long long)__float2int_rn(a[5][c]) * 16384 +
+                                 (long long)__float2int_rn(a[6][c]) * 128 + (long long)__float2int_rn(a[7][c]);
+            const int j = col0 + ch * 8 + c;
+            const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
+            double val;
+            if (ei == OG_BAD_EXP || fj == OG_BAD_EXP) {
+              val = __longlong_as_double(0x7ff8000000000000ll);   // NaN, as a float64 product would give
+            } else {
+              const int k = ei + fj - 35;
+              double s1, s2;
+              if (k > -990 && k < 990) {
+                s1 = __longlong_as_double((long long)(k + 1023) << 52);
+                s2 = __longlong_as_double((long long)(k - 28 + 1023) << 52);
+              } else {
+                s1 = ldexp(1.0, k);
+                s2 = ldexp(1.0, k - 28);
+              }
+              val = fma((double)hi, s1, (double)lo * s2);
+            }
+            stg[lane * 9 + c] = val;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int r = it * 4 + (lane >> 3), c = lane & 7;
+            if (ok[it]) {
+              const double v = p.alpha * stg[r * 9 + c];
+              C[(size_t)(row0 + r) * p.ldc + col0 + ch * 8 + c] = read_c ? fma(cscale, cv[it], v) : v;
+            }
+          }
+          __syncwarp();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar);
+        acc_phase ^= 1u;
+      }
+    }
+  }
+  // teardown: every role has finished or given up; wait for the others before freeing TMEM
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag) {
+    // let copies and MMAs already issued land before the shared memory and TMEM go away
+    const uint64_t t0 = global_timer_ns();
+    while (global_timer_ns() - t0 < 200000ull) {
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, OG_TMEM_COLS);
+  }
+}
+
+static int og_pack(lrs_ctx* ctx, const double* x, int ld, long long stride, const double* ks, long long stride_ks,
+                   bool trans, int rows, int k, int rows_pad, int nchunks, int batches, uint16_t* planes, int* expo) {
+  OgPack p;
+  p.x = x;
+  p.ld = ld;
+  p.stride = stride;
+  p.ks = ks;
+  p.stride_ks = stride_ks;
+  p.trans = trans ? 1 : 0;
+  p.rows = rows;
+  p.k = k;
+  p.rows_pad = rows_pad;
+  p.nchunks = nchunks;
+  p.planes = planes;
+  p.expo = expo;
+  oz_pack_kernel<<<dim3(rows_pad / 32, batches), 256, 0, ctx->stream>>>(p);
+  return after_launch(ctx, "oz_pack_kernel");
+}
+
+int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+                    long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                    long long stride_b, double beta, double* c, int ldc, long long stride_c, int batch,
+                    int lower_col) {
+  if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
+  if (k <= 0)   // C = beta C: nothing for the tensor cores to do
+    return dgemm_batched(ctx, ta, tb, m, n, 0, alpha, a, lda, stride_a, ks, stride_ks, b, ldb, stride_b, nullptr,
+                         beta, c, ldc, stride_c, batch);
+  const int nchunks = (k + 31) / 32;
+  const int a_rows_pad = (m + OG_TM - 1) / OG_TM * OG_TM;
+  const int b_rows_pad = (n + OG_TN - 1) / OG_TN * OG_TN;
+  const bool a_shared = stride_a == 0 && (ks == nullptr || stride_ks == 0);
+  const bool b_shared = stride_b == 0;
+  const int a_batches = a_shared ? 1 : batch, b_batches = b_shared ? 1 : batch;
+  const size_t a_elems = (size_t)a_batches * OG_PLANES * nchunks * a_rows_pad * 64;
+  const size_t b_elems = (size_t)b_batches * OG_PLANES * nchunks * b_rows_pad * 64;
+  LRS_TRY(ensure(ctx, ctx->ws.og_planes, a_elems + b_elems));
+  LRS_TRY(ensure(ctx, ctx->ws.og_expo, (size_t)a_batches * a_rows_pad + (size_t)b_batches * b_rows_pad));
+  uint16_t* pa = ctx->ws.og_planes.ptr;
+  uint16_t* pb = pa + a_elems;
+  int* xa = ctx->ws.og_expo.ptr;
+  int* xb = xa + (size_t)a_batches * a_rows_pad;
+  // op(A) diag(ks): rows i, K index kk; op(B)^T: rows j (output columns), K index kk
+  LRS_TRY(og_pack(ctx, a, lda, a_shared ? 0 : stride_a, ks, a_shared ? 0 : stride_ks, ta, m, k, a_rows_pad, nchunks,
+                  a_batches, pa, xa));
+  LRS_TRY(og_pack(ctx, b, ldb, b_shared ? 0 : stride_b, nullptr, 0, !tb, n, k, b_rows_pad, nchunks, b_batches, pb,
+                  xb));
+  CUtensorMap ma, mb;
+  LRS_TRY(make_operand_map(&ma, pa, 64, (uint64_t)a_batches * OG_PLANES * nchunks * a_rows_pad, OG_TM));
+  LRS_TRY(make_operand_map(&mb, pb, 64, (uint64_t)b_batches * OG_PLANES * nchunks * b_rows_pad, OG_TN));
+  OgGemm p;
+  p.C = c;
+  p.ldc = ldc;
+  p.stride_c = stride_c;
+  p.m = m;
+  p.n = n;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.ea = xa;
+  p.eb = xb;
+  p.a_shared = a_shared ? 1 : 0;
+  p.b_shared = b_shared ? 1 : 0;
+  p.a_rows_pad = a_rows_pad;
+  p.b_rows_pad = b_rows_pad;
+  p.nchunks = nchunks;
+  p.row_tiles = a_rows_pad / OG_TM;
+  p.col_tiles = b_rows_pad / OG_TN;
+  p.batch = batch;
+  p.lower_col = lower_col;
+  if (!ctx->capturing)
+    LRS_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OG_SMEM));
+  const long long units = (long long)batch * p.row_tiles * p.col_tiles;
+  const int grid = (int)std::min<long long>(units, ctx->num_sms);
+  oz_gemm_kernel<<<grid, OG_THREADS, OG_SMEM, ctx->stream>>>(ma, mb, p, ctx->ws.status.ptr + 8);
+  return after_launch(ctx, "oz_gemm_kernel");
+}
+
+}  // namespace lrs

@@ -244,7 +244,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
-  release(ctx, w.oz_planes); release(ctx, w.oz_expo);
+  release(ctx, w.oz_planes); release(ctx, w.oz_expo); release(ctx, w.og_planes); release(ctx, w.og_expo);
   release(ctx, w.fft_grid); release(ctx, w.fft_index); release(ctx, w.fft_tw);
   release(ctx, w.induced);
   release(ctx, w.alda_n); release(ctx, w.aug_tab); release(ctx, w.aug_coef);

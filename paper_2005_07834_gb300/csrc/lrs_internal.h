@@ -153,6 +153,8 @@ struct Workspace {
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
   DevBuf<uint16_t> oz_planes;           // SPD inverse on tensor cores: slice planes of D, E (two sets)
   DevBuf<int> oz_expo;                  // and their row exponents
+  DevBuf<uint16_t> og_planes;           // float64-accurate tensor-core GEMM: slice planes of both operands
+  DevBuf<int> og_expo;                  // and their row exponents
   DevBuf<double> induced;               // induced response: T, X, B, right-hand side, outputs
   DevBuf<double> alda_n;                // site density for the exchange-only ALDA kernel
   DevBuf<double> aug_tab;               // augmentation: pseudo waves, corrections, shell mask
@@ -297,6 +299,14 @@ int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double
               const int* ed, const int* ee, int x0, int x1, int rows_pad, cudaStream_t stream);
 int oz_rows_pad(int n);
 size_t oz_plane_elems(int n);
+// Float64-accurate batched GEMM on the tensor cores (k_ozgemm.cu), the
+// arguments of dgemm_batched (no column scale); lower_col > 0 computes only
+// the tiles of C_b = C + b lower_col that reach the lower triangle of a
+// symmetric matrix, as dgemm_batched_lower.
+int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+                    long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                    long long stride_b, double beta, double* c, int ldc, long long stride_c, int batch,
+                    int lower_col);
 
 // In-place inverse of an SPD matrix; lower triangle in and out.  status[0] = 2
 // (status[1] = column) on a pivot that is not positive and finite.

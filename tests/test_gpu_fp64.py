@@ -123,15 +123,16 @@ def test_state_and_argument_errors(lrs):
     scr.close()
 
 
-@pytest.mark.parametrize("basis", ["full", "lm-lu", "lm-spd", "lm-spd-tc"])
+@pytest.mark.parametrize("basis", ["full", "lm-lu", "lm-lu-tc", "lm-spd", "lm-spd-tc"])
 def test_dyson_bases_match_oracle(lrs, cfg_260, basis):
     ref = cfg_260
     wl = synth.single_site_260()
     scr = lrs.Screening(0, "fp64")
     scr.set_option(lrs.LRS_OPT_DYSON_BASIS, lrs.LRS_DYSON_FULL if basis == "full" else lrs.LRS_DYSON_LM)
     if basis != "full":
-        scr.set_option(lrs.LRS_OPT_DYSON_SOLVER, lrs.LRS_SOLVER_LU if basis == "lm-lu" else lrs.LRS_SOLVER_SPD)
-    if basis == "lm-spd-tc":      # float64-accurate trailing updates from bf16 slices on the tensor cores
+        scr.set_option(lrs.LRS_OPT_DYSON_SOLVER,
+                       lrs.LRS_SOLVER_LU if basis.startswith("lm-lu") else lrs.LRS_SOLVER_SPD)
+    if basis.endswith("-tc"):     # float64-accurate basis changes and updates from bf16 slices on the tensor cores
         scr.set_option(lrs.LRS_OPT_DYSON_UPDATE, lrs.LRS_UPDATE_TC)
     scr.load(wl.orbitals)
     scr.set_sites(wl.sites)
@@ -185,9 +186,10 @@ def test_spd_and_lu_dyson_agree_on_a_large_site(lrs):
 
 
 def test_tensor_core_update_is_float64_accurate(lrs):
-    """SPD inverse of the 48 x 110 site (r = 3888) with the trailing updates on the
-    tensor cores vs float64 FMAs, from the same chi0 (FP64 context): W - v agrees
-    to 1e-12, i.e. the sliced products carry float64 accuracy."""
+    """SPD inverse of the 48 x 110 site (r = 3888) with the basis changes and the
+    trailing updates on the tensor cores vs float64 FMAs, from the same chi0
+    (FP64 context): W - v agrees to 1e-12, i.e. the sliced products carry
+    float64 accuracy."""
     wl = synth.single_site_260()
     wl.sites = [synth.site_grid(wl.sites[0].center, 48, 110, 4.0)]
     scr = lrs.Screening(0, "fp64")
@@ -205,4 +207,32 @@ def test_tensor_core_update_is_float64_accurate(lrs):
     err = rel_fro(ws[1] - v, ws[0] - v)
     print(f"tensor-core vs float64 trailing updates, W - v: {err:.2e}")
     assert err < 1e-12
+    scr.close()
+
+
+def test_tensor_core_basis_change_over_several_k_segments(lrs):
+    """12 shells x 194 directions (L = 11: 144 harmonics, r = 1728): the basis
+    changes contract over K = 194 and 144, more than one exactly accumulated
+    segment of 128, and 144 output columns span three tiles with a ragged one.
+    Tensor-core vs float64-FMA arithmetic from the same chi0: W - v agrees to 1e-12."""
+    wl = synth.single_site_260()
+    wl.sites = [synth.site_grid(wl.sites[0].center, 12, 194, 3.0)]
+    scr = lrs.Screening(0, "bf16x3")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(8)
+    scr.project()
+    scr.build_chi0()
+    ws = []
+    for solver in (lrs.LRS_SOLVER_SPD, lrs.LRS_SOLVER_LU):
+        scr.set_option(lrs.LRS_OPT_DYSON_SOLVER, solver)
+        for mode in (lrs.LRS_UPDATE_FP64, lrs.LRS_UPDATE_TC):
+            scr.set_option(lrs.LRS_OPT_DYSON_UPDATE, mode)
+            scr.solve_w()
+            ws.append(scr.get_w(0))
+    v = scr.get_v(0)
+    for name, (a, b) in (("SPD", (ws[0], ws[1])), ("LU", (ws[2], ws[3]))):
+        err = rel_fro(b - v, a - v)
+        print(f"{name}: tensor-core vs float64 arithmetic, W - v: {err:.2e}")
+        assert err < 1e-12
     scr.close()
