@@ -693,114 +693,150 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
 // indices has been exchanged.  Cost n^3 flop (lower-triangle rank-nb updates),
 // against 8/3 n^3 for LU plus n right-hand sides.
 constexpr int GJ_NB = 32;               // pivot block width
-constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread pivot and apply kernels
-constexpr int GJ_PM = GJ_NB / GJ_PR;     // pivot rows per thread
+constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread apply kernel
 
 // Column block k of the current matrix from the lower triangle, C (n x kb,
-// leading dimension GJ_NB): rows i >= k0 read A[i][j] (A[j][i] above the
-// diagonal of the pivot block), rows i < k0 read -A[j][i].  E = sigma C with
-// sigma = -1 on rows i < k0, so that A_kj = E_j^T for every j != k.
+// leading dimension GJ_NB): element (i, j), j in block k, is stored at
+// (max(i, j), min(i, j)); rows i < k0 take it with the sign -1 (one of the two
+// blocks exchanged).  E = sigma C with sigma = -1 on rows i < k0, so that
+// A_kj = E_j^T for every j != k.
+//
+// The exchange of the previous block kp (= k - 1, D_p = C_p P^-1, E_p) has not
+// been applied to block k (the bulk update leaves blocks kp and k out): the
+// gather applies it on the fly, stored(r, s) - D_p[r] . E_p[s], except on the
+// rows of block kp, which the exchange itself rewrote (gj_fix_kernel).  Block k
+// of A is rewritten by its own exchange, so the updated values are not stored.
+// GJ_GR rows per CTA, one warp per row (lane = column in the block).
+constexpr int GJ_GR = 8;
 __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict__ A, int n, int lda, int k0, int kb,
-                                                        double* __restrict__ C, double* __restrict__ E,
-                                                        uint16_t* __restrict__ eplanes, size_t plane_stride,
-                                                        int* __restrict__ eexp) {
-  __shared__ double t[GJ_NB][GJ_NB + 1];
-  const int i0 = blockIdx.x * GJ_NB;
-  if (i0 < k0) {   // k0 is a multiple of GJ_NB, so the whole row block lies below k0
-    for (int idx = threadIdx.x; idx < kb * GJ_NB; idx += blockDim.x) {
-      const int c = idx / GJ_NB, ii = idx % GJ_NB;
-      t[c][ii] = A[(size_t)(k0 + c) * lda + i0 + ii];
+                                                        const double* __restrict__ Dp, const double* __restrict__ Ep,
+                                                        int kp0, int kpb, double* __restrict__ C,
+                                                        double* __restrict__ E, uint16_t* __restrict__ eplanes,
+                                                        size_t plane_stride, int* __restrict__ eexp) {
+  __shared__ double dr[GJ_GR][GJ_NB + 1], er[GJ_GR][GJ_NB + 1];   // D_p, E_p rows of this CTA's rows
+  __shared__ double dk[GJ_NB][GJ_NB + 1], ek[GJ_NB][GJ_NB + 1];   // D_p, E_p rows of block k
+  const int i0 = blockIdx.x * GJ_GR;
+  const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+  if (Dp) {
+    for (int idx = threadIdx.x; idx < GJ_GR * GJ_NB; idx += blockDim.x) {
+      const int rr = idx / GJ_NB, cc = idx % GJ_NB, i = i0 + rr;
+      dr[rr][cc] = (i < n && cc < kpb) ? Dp[(size_t)i * GJ_NB + cc] : 0.0;
+      er[rr][cc] = (i < n && cc < kpb) ? Ep[(size_t)i * GJ_NB + cc] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < GJ_NB * GJ_NB; idx += blockDim.x) {
+      const int rr = idx / GJ_NB, cc = idx % GJ_NB, j = k0 + rr;
+      dk[rr][cc] = (rr < kb && cc < kpb) ? Dp[(size_t)j * GJ_NB + cc] : 0.0;
+      ek[rr][cc] = (rr < kb && cc < kpb) ? Ep[(size_t)j * GJ_NB + cc] : 0.0;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < GJ_NB * kb; idx += blockDim.x) {
-      const int ii = idx / kb, c = idx % kb;
-      const double v = t[c][ii];
-      C[(size_t)(i0 + ii) * GJ_NB + c] = -v;
-      E[(size_t)(i0 + ii) * GJ_NB + c] = v;
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < GJ_NB * kb; idx += blockDim.x) {
-      const int ii = idx / kb, c = idx % kb, i = i0 + ii, j = k0 + c;
-      if (i >= n) continue;
-      const double v = (i >= j) ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
-      C[(size_t)i * GJ_NB + c] = v;
-      E[(size_t)i * GJ_NB + c] = v;
-    }
   }
-  if (eplanes) {
-    // slices of the rows of E for the tensor-core update, one warp per row
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int rr = threadIdx.x >> 5; rr < GJ_NB; rr += blockDim.x >> 5) {
-      const int row = i0 + rr;
-      if (row >= n) break;
-      const double x = lane < kb ? E[(size_t)row * GJ_NB + lane] : 0.0;
-      oz_slice_row(x, lane, row, plane_stride, eplanes, eexp);
+  const int i = i0 + r;
+  if (i >= n) return;                          // whole warp: one row per warp
+  const int j = k0 + c;
+  double v = 0.0;
+  if (c < kb) {
+    v = (i >= j) ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
+    if (Dp && !(i >= kp0 && i < kp0 + kpb)) {
+      // stored (max, min): D_p of the larger index, E_p of the smaller
+      const double* d = (i >= j) ? dr[r] : dk[c];
+      const double* e = (i >= j) ? ek[c] : er[r];
+      double acc = 0.0;
+#pragma unroll 8
+      for (int kk = 0; kk < GJ_NB; ++kk) acc = fma(d[kk], e[kk], acc);
+      v -= acc;
     }
+    const bool flip = i < k0;
+    C[(size_t)i * GJ_NB + c] = flip ? -v : v;
+    E[(size_t)i * GJ_NB + c] = v;
   }
+  // slices of the row of E for the tensor-core update
+  if (eplanes) oz_slice_row(c < kb ? v : 0.0, c, i, plane_stride, eplanes, eexp);
 }
 
 // Pinv = P^-1 for the kb x kb pivot block P = C[k0, k0 + kb) by scalar
-// exchange steps; a ragged block is padded with the identity.  Thread t holds
-// column t % GJ_NB of rows t / GJ_NB + GJ_PR m in registers; per step the
-// owners of column p publish it divided by the pivot and the owners of row p
-// publish that row, then every element takes one FMA.  One SM retires two
-// DFMA per clock, so an nb x nb inverse is about nb^3 / 2 clocks.  A pivot
-// that is not positive and finite sets status[0] = 2, status[1] = its column
-// (the matrix is not SPD).
-__global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict__ C, int k0, int kb,
-                                                       double* __restrict__ Pinv, int* __restrict__ status) {
-  __shared__ double colv[GJ_NB];   // column p, then column p / pivot
-  __shared__ double roww[GJ_NB];   // row p
-  __shared__ double dinv;
-  const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;
+// exchange steps; a ragged block is padded with the identity.  Eight warps
+// update the matrix: thread t holds column t % 32 of rows t / 32 + 8 m in
+// registers, and the owners of the next pivot's column and row publish them
+// into shared buffers that alternate between steps (one barrier per step, one
+// FP64 operation per element).  A ninth warp keeps the diagonal, lane i
+// repeating the update of element (i, i), and forms the next pivot's
+// reciprocal while the others update, so the division stays off the step's
+// critical path.  An SM retires two DFMA per clock, so the 32 x 32 inverse
+// costs about 32^3 / 2 clocks.  A pivot that is not positive and finite sets
+// status[0] = 2, status[1] = its column (the matrix is not SPD).
+constexpr int GJ_PW = 8;                  // update warps of the pivot kernel
+constexpr int GJ_PM = GJ_NB / GJ_PW;      // rows per thread
+__global__ void __launch_bounds__((GJ_PW + 1) * 32) gj_pivot_kernel(const double* __restrict__ C, int k0, int kb,
+                                                                    double* __restrict__ Pinv,
+                                                                    int* __restrict__ status) {
+  __shared__ double colv[2][GJ_NB], roww[2][GJ_NB], dinv[2];
+  const int j = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool diag_warp = w == GJ_PW;
   double a[GJ_PM];
-#pragma unroll
-  for (int m = 0; m < GJ_PM; ++m) {
-    const int i = ib + GJ_PR * m;
-    a[m] = (i < kb && j < kb) ? C[(size_t)(k0 + i) * GJ_NB + j] : (i == j ? 1.0 : 0.0);
-  }
-  for (int p = 0; p < GJ_NB; ++p) {
-    if (j == p) {
-#pragma unroll
-      for (int m = 0; m < GJ_PM; ++m) colv[ib + GJ_PR * m] = a[m];
-    }
-#pragma unroll
-    for (int m = 0; m < GJ_PM; ++m)
-      if (ib + GJ_PR * m == p) roww[j] = a[m];
-    __syncthreads();
-    const double piv = colv[p];
-    if (!(piv > 0.0) || !isfinite(piv)) {   // same value in every thread: uniform exit
-      if (threadIdx.x == 0 && atomicCAS(&status[0], 0, 2) == 0) status[1] = k0 + p;
-      break;
-    }
-    __syncthreads();
-    if (threadIdx.x < GJ_NB) {
-      const double d = 1.0 / piv;
-      colv[threadIdx.x] *= d;
-      if (threadIdx.x == 0) dinv = d;
-    }
-    __syncthreads();
-    const double rj = roww[j], d = dinv;
+  if (!diag_warp) {
 #pragma unroll
     for (int m = 0; m < GJ_PM; ++m) {
-      const int i = ib + GJ_PR * m;
-      const double ci = colv[i];
-      if (i == p) a[m] = (j == p) ? d : -rj * d;
-      else if (j == p) a[m] = ci;
-      else a[m] = fma(-ci, rj, a[m]);
+      const int i = w + GJ_PW * m;
+      a[m] = (i < kb && j < kb) ? C[(size_t)(k0 + i) * GJ_NB + j] : (i == j ? 1.0 : 0.0);
+    }
+    // publish column 0 and row 0
+    if (j == 0) {
+#pragma unroll
+      for (int m = 0; m < GJ_PM; ++m) colv[0][w + GJ_PW * m] = a[m];
+    }
+    if (w == 0) roww[0][j] = a[0];
+  } else {
+    a[0] = (j < kb) ? C[(size_t)(k0 + j) * GJ_NB + j] : 1.0;   // lane j: element (j, j)
+    if (j == 0) dinv[0] = 1.0 / a[0];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int p = 0; p < GJ_NB; ++p) {
+    const int b = p & 1, nb = b ^ 1, q = p + 1;
+    const double piv = colv[b][p];
+    if (!(piv > 0.0) || !isfinite(piv)) {     // same value in every thread: uniform exit
+      if (threadIdx.x == 0 && atomicCAS(&status[0], 0, 2) == 0) status[1] = k0 + p;
+      return;
+    }
+    const double d = dinv[b];
+    if (diag_warp) {
+      // the same operations as the update of element (j, j) below
+      const double t = roww[b][j] * d;
+      if (j != p) a[0] = fma(-colv[b][j], t, a[0]);
+      if (j == q) dinv[nb] = 1.0 / a[0];
+    } else {
+      const double t = roww[b][j] * d;        // row p, column j, over the pivot
+#pragma unroll
+      for (int m = 0; m < GJ_PM; ++m) {
+        const int i = w + GJ_PW * m;
+        const double ci = colv[b][i];
+        if (i == p) a[m] = (j == p) ? d : -t;
+        else if (j == p) a[m] = ci * d;
+        else a[m] = fma(-ci, t, a[m]);
+      }
+      // publish the next step's column and row
+      if (q < GJ_NB) {
+        if (j == q) {
+#pragma unroll
+          for (int m = 0; m < GJ_PM; ++m) colv[nb][w + GJ_PW * m] = a[m];
+        }
+#pragma unroll
+        for (int m = 0; m < GJ_PM; ++m)
+          if (w + GJ_PW * m == q) roww[nb][j] = a[m];
+      }
     }
     __syncthreads();
   }
+  if (diag_warp) return;
 #pragma unroll
   for (int m = 0; m < GJ_PM; ++m) {
-    const int i = ib + GJ_PR * m;
+    const int i = w + GJ_PW * m;
     if (i < kb && j < kb) Pinv[(size_t)i * GJ_NB + j] = a[m];
   }
 }
 
-// D = C Pinv (n x kb), 16 rows per CTA so that every SM takes part.
-constexpr int GJ_DR = 16;
+// D = C Pinv (n x kb), 8 rows per CTA so that every SM takes part.
+constexpr int GJ_DR = 8;
 __global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict__ C, int n, int kb,
                                                        const double* __restrict__ Pinv, double* __restrict__ D,
                                                        uint16_t* __restrict__ dplanes, size_t plane_stride,
@@ -867,24 +903,21 @@ __global__ void __launch_bounds__(256) gj_fix_kernel(double* __restrict__ A, int
 }
 
 // Trailing update A_ij -= D_i E_j^T of the exchange of block k on 32 x 32
-// tiles of the lower triangle (a pivot block spans GJ_TB x GJ_TB tiles).  The
-// FP64 pipe of one SM is saturated by a few warps, so small tiles cost no
-// throughput and balance the SMs: a step has thousands of equal tiles.
-//   MODE 0 (bulk):  1-D grid over the lower-triangle tiles; tiles in pivot
-//                   blocks k and k + 1 (rows or columns) are left out.
-//   MODE 1 (cross): the tiles of pivot block k + 1 (its row to the left of the
-//                   diagonal, its column below it) outside block k; grid (T, 2 GJ_TB).
+// tiles of the lower triangle (a pivot block spans GJ_TB x GJ_TB tiles), on the
+// float64 pipe.  The FP64 pipe of one SM is saturated by a few warps, so small
+// tiles cost no throughput and balance the SMs: a step has thousands of equal
+// tiles.  1-D grid over the lower-triangle tiles; tiles in pivot blocks k and
+// k + 1 (rows or columns) are left out (the exchange of block k rewrites its
+// own, and the gather of block k + 1 applies this update to that block).
 constexpr int UT = 32;
 constexpr int GJ_TB = GJ_NB / UT;   // update tiles per pivot block and dimension
-template <int MODE>
 __global__ void __launch_bounds__(128) gj_update_kernel(double* __restrict__ A, int n, int lda, int kb, int k,
                                                         const double* __restrict__ D,
                                                         const double* __restrict__ E) {
   __shared__ double Ds[GJ_NB][UT + 1];
   __shared__ double Es[GJ_NB][UT + 1];
-  const int T = (n + UT - 1) / UT;
   int ti, tj;
-  if (MODE == 0) {
+  {
     const long long t = blockIdx.x;
     ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while ((long long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
@@ -892,17 +925,6 @@ __global__ void __launch_bounds__(128) gj_update_kernel(double* __restrict__ A, 
     tj = (int)(t - (long long)ti * (ti + 1) / 2);
     const int bi = ti / GJ_TB, bj = tj / GJ_TB;
     if (bi == k || bi == k + 1 || bj == k || bj == k + 1) return;
-  } else {
-    const int nx = GJ_TB * (k + 1);
-    if ((int)blockIdx.y < GJ_TB) {
-      ti = nx + blockIdx.y;
-      tj = blockIdx.x;
-      if (ti >= T || tj > ti || tj / GJ_TB == k) return;
-    } else {
-      tj = nx + blockIdx.y - GJ_TB;
-      ti = blockIdx.x;
-      if (tj >= T || ti / GJ_TB <= k + 1) return;
-    }
   }
   const int i0 = ti * UT, j0 = tj * UT;
   for (int idx = threadIdx.x; idx < UT * kb; idx += blockDim.x) {
@@ -936,10 +958,11 @@ __global__ void __launch_bounds__(128) gj_update_kernel(double* __restrict__ A, 
 
 // Schedule: the bulk of the trailing update of block k (every tile away from
 // blocks k and k + 1) runs on the context stream while a second, higher
-// priority stream updates the cross of block k + 1, writes the exchanged
-// block k (fix), and prepares the next panel (gather, pivot inverse, D) in the
-// other of two buffer sets.  The serial pivot inverse (one SM) thereby overlaps
-// the bulk GEMM.  Events: panel k ready -> bulk k; bulk k done -> cross k + 1.
+// priority stream writes the exchanged block k (fix) and prepares the next
+// panel (gather with the update of block k applied on the fly, pivot inverse,
+// D) in the other of two buffer sets.  The serial pivot inverse (one SM)
+// thereby overlaps the bulk update.  Events: panel k ready -> bulk k; bulk k
+// done -> panel k + 2 (its block and its buffer set are touched by bulk k).
 int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
   static_assert(GJ_NB % UT == 0 && GJ_TB >= 1, "a pivot block spans whole update tiles");
   if (n <= 0) return LRS_OK;
@@ -982,9 +1005,15 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
   auto panel = [&](int kb_idx, int q) -> int {
     const int k0 = kb_idx * GJ_NB, kb = std::min(GJ_NB, n - k0);
     const size_t stride = (size_t)rows_pad * 64;
-    gj_gather_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Cb[q], Eb[q], epl[q], stride, esc[q]);
+    // the exchange of the previous block (buffer set q ^ 1) is applied to block kb_idx here
+    const int qp = q ^ 1, kp0 = k0 - GJ_NB;
+    const bool prev = kb_idx > 0;
+    gj_gather_kernel<<<(n + GJ_GR - 1) / GJ_GR, 256, 0, s2>>>(A, n, lda, k0, kb, prev ? Db[qp] : nullptr,
+                                                              prev ? Eb[qp] : nullptr, kp0, GJ_NB, Cb[q], Eb[q],
+                                                              epl[q], stride, esc[q]);
     LRS_TRY(after_launch(ctx, "gj_gather_kernel"));
-    gj_pivot_kernel<<<1, 256, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
+    if (prev) ctx->fp64_flops += 2.0 * n * kb * GJ_NB;
+    gj_pivot_kernel<<<1, (GJ_PW + 1) * 32, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
     LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
     gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q], dpl[q], stride, dsc[q]);
     LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
@@ -1005,7 +1034,7 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
       LRS_TRY(oz_update(ctx, md[q], me[q], A, n, lda, dsc[q], esc[q], k0, std::min(n, k0 + 2 * GJ_NB), rows_pad,
                         s1));
     } else {
-      gj_update_kernel<0><<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
+      gj_update_kernel<<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
       LRS_TRY(after_launch(ctx, "gj_update_kernel"));
     }
     LRS_TRY(stage_end(ctx, ST_W_MAIN));
@@ -1019,18 +1048,14 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     }
     if (!tc) ctx->fp64_flops += (double)n * n * kb;
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
-    // cross of block k + 1, exchange of block k, next panel on the second stream
-    if (k + 1 < nblk) {
-      gj_update_kernel<1><<<dim3(nt, 2 * GJ_TB, 1), 128, 0, s2>>>(A, n, lda, kb, k, Db[q], Eb[q]);
-      LRS_TRY(after_launch(ctx, "gj_update_kernel"));
-    }
+    // exchange of block k, next panel on the second stream
     gj_fix_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Db[q], Pb[q]);
     LRS_TRY(after_launch(ctx, "gj_fix_kernel"));
     if (k + 1 < nblk) {
       // buffer set q ^ 1 was last read by bulk k - 1, which s2 has waited for
       LRS_TRY(panel(k + 1, q ^ 1));
       LRS_CUDA_TRY(cudaEventRecord(ctx->ev_panel, s2));
-      // the cross of block k + 2 and set q are touched by bulk k: wait for it
+      // block k + 2 and set q are touched by bulk k: wait for it
       LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_bulk, 0));
     }
   }

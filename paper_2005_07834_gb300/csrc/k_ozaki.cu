@@ -2,18 +2,19 @@
 // trailing update of the SPD inverse of the Dyson solve.
 //
 // Every row of D and of E (32 float64 values) is scaled by a power of two,
-// x = 2^e a with |a| < 1, and cut into integer slices
+// x = 2^e a with |a| < 1/2, and cut into integer slices
 //   a = sum_{t=1..7} 2^(-8 t) s_t   (base-256 digits of round(a 2^56)),
-// |s_1| <= 256, |s_t| <= 128 (t > 1): each slice is exact in bf16 and the
-// representation error is below 2^-57 |a|max.  The products of the 28
-// slice pairs with t + u <= 8 are issued as bf16 tcgen05 MMAs (K = 32, two K16
-// steps each) into seven fp32 accumulators in TMEM, one per level t + u.  A
-// level sum is an integer below 7 * 32 * 2^16 < 2^24, hence exact in fp32.
-// The epilogue combines the levels in float64 with their factors 2^-8(t+u)
-// and the row scales, and subtracts from C.  The dropped pairs (t + u >= 9)
-// bound the error by about 6e-16 |D|max |E|max per element, on a par with a
-// float64 dot product of 32 terms; the update runs at tensor-core speed
-// instead of the 2 DFMA per SM per clock of the float64 pipe.
+// |s_t| <= 128: each slice is exact in bf16 and the representation error is
+// at most 2^-56 2^e (oz_slice.cuh).  The products of the 28 slice pairs with
+// t + u <= 8 are issued as bf16 tcgen05 MMAs (K = 32, two K16 steps each) into
+// seven fp32 accumulators in TMEM, one per level t + u.  A level sum is an
+// integer of magnitude at most 7 * 32 * 2^14 < 2^22, hence exact in fp32.
+// The epilogue combines the levels as 64-bit integers, rounds the product to
+// float64 with integer instructions (oz_combine.cuh) and subtracts it from C.
+// The dropped pairs (t + u >= 9) bound the error by about 6e-16 |D|max |E|max
+// per element, on a par with a float64 dot product of 32 terms; the update
+// runs at tensor-core speed instead of the 2 DFMA per SM per clock of the
+// float64 pipe.
 //
 // Tiles of 128 x 64 elements of the lower triangle; elements in the rows or
 // columns of the excluded pivot blocks (the side stream of the SPD inverse
@@ -23,6 +24,7 @@
 #include <cmath>
 
 #include "lrs_internal.h"
+#include "oz_combine.cuh"
 #include "oz_slice.cuh"
 #include "tc_common.cuh"
 
@@ -38,7 +40,7 @@ constexpr int OZ_B_PLANE = OZ_TN * 128;
 constexpr int OZ_STAGE = OZ_PLANES * (OZ_A_PLANE + OZ_B_PLANE);
 constexpr int OZ_STAGES = 1;
 constexpr int OZ_EPI_WARPS = 8;
-constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * 9 * 8;   // per-warp [32][9] float64 staging of C updates
+constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * 33 * 8;  // per-warp [32][33] float64 staging of C updates
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + OZ_STAGE_EPI + 1024;
 constexpr int OZ_THREADS = 320;                // producer, MMA issuer, 8 epilogue warps
 constexpr int OZ_TMEM_COLS = 512;              // 7 levels x 64 columns used
@@ -158,25 +160,42 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else {
     // ------------------------------------------------ epilogue: combine the levels, C -= D E^T
-    // Level sums are integers below 2^23 in fp32.  They are combined exactly in
-    // two 64-bit integers, hi = a0 2^16 + a1 2^8 + a2 (< 2^40) and lo = a3 2^24
-    // + a4 2^16 + a5 2^8 + a6 (< 2^48), so that the product is
-    // 2^(e_i + f_j) (2^-32 hi + 2^-64 lo), formed with two exact conversions and
-    // one FMA.  Each warp stages its 32 x 8 values per chunk in shared memory
-    // and applies them to C row by row (coalesced).
+    // Each warp owns 32 rows (its TMEM lane quarter) x 32 columns of the tile.  Its
+    // share of C is copied into a [32][33] shared-memory stage (cp.async, 256
+    // contiguous bytes per row) before the accumulators are ready, so the memory
+    // latency overlaps the MMAs.  Level sums are integers of magnitude below 2^22 in
+    // fp32 (read as int32 by one fp32 add each), combined exactly in two 64-bit
+    // integers, hi = a0 2^16 + a1 2^8 + a2 (< 2^38) and lo = a3 2^24 + a4 2^16 + a5 2^8
+    // + a6 (< 2^48), so that the product is 2^(e_i + f_j) (2^-32 hi + 2^-64 lo); that
+    // value is rounded to float64 with integer instructions and subtracted from the
+    // staged C (the only float64 operation per element).  TMEM is then released to
+    // the next tile's MMAs, and the stage is written back row by row.
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
     double* stg = reinterpret_cast<double*>(oz_smem_raw + (smem_base - smem_u32(oz_smem_raw)) +
-                                            OZ_STAGES * OZ_STAGE) + (warp - 2) * 32 * 9;
+                                            OZ_STAGES * OZ_STAGE) + (warp - 2) * 32 * 33;
+    const uint32_t stg_s = smem_u32(stg);
     uint32_t acc_phase = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
       int bi, bj;
       if (!oz_decode(p, u, bi, bj)) continue;
+      const int row0 = bi * OZ_TM + quarter * 32;
+      const int col0 = bj * OZ_TN + half * 32;
+      const int j = col0 + lane;                 // this lane's column when C is read and written
+      const bool col_ok = j < p.n && !(j >= p.x0 && j < p.x1);
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const int i = row0 + r;
+        if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1))
+          cp_async8(stg_s + (uint32_t)(r * 33 + lane) * 8u, p.C + (size_t)i * p.ldc + j);
+      }
+      cp_async_commit();
       int got = 1;
       if (lane == 0) got = mbar_wait(&accf_bar, acc_phase, &abort_flag) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) {
+        cp_async_wait_all();
         if (lane == 0) {
           abort_flag = 1;
           atomicCAS(status, 0, TC_TIMEOUT_EPILOGUE);
@@ -184,61 +203,43 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int row0 = bi * OZ_TM + quarter * 32;
-      const int my_row = row0 + lane;
+      cp_async_wait_all();
+      __syncwarp();
+      const int my_row = row0 + lane;            // this lane's row when TMEM is read
       const int ei = my_row < p.n ? p.ed[my_row] : 0;
-      const int col0 = bj * OZ_TN + half * 32;
 #pragma unroll 1
       for (int ch = 0; ch < 4; ++ch) {
-        // this lane's share of C for the chunk, loaded first so that the L2 latency
-        // overlaps the TMEM reads and the level combination
-        double cv[8];
-        bool ok[8];
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int r = it * 4 + (lane >> 3), c = lane & 7;
-          const int i = row0 + r, j = col0 + ch * 8 + c;
-          ok[it] = i < p.n && j <= i && !(i >= p.x0 && i < p.x1) && !(j >= p.x0 && j < p.x1);
-          cv[it] = ok[it] ? p.C[(size_t)i * p.ldc + j] : 0.0;
-        }
         float a[OZ_LEVELS][8];
 #pragma unroll
         for (int lv = 0; lv < OZ_LEVELS; ++lv) tmem_ld8(tbase + lane_off + lv * OZ_TN + half * 32 + ch * 8, a[lv]);
         tmem_ld_wait();
-        long long hi[8], lo[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          hi[c] = (long long)__float2int_rn(a[0][c]) * 65536 + (long long)__float2int_rn(a[1][c]) * 256 +
-                  (long long)__float2int_rn(a[2][c]);
-          lo[c] = (long long)__float2int_rn(a[3][c]) * 16777216 + (long long)__float2int_rn(a[4][c]) * 65536 +
-                  (long long)__float2int_rn(a[5][c]) * 256 + (long long)__float2int_rn(a[6][c]);
+          const long long hi = (long long)oz_level_int(a[0][c]) * 65536 + (long long)oz_level_int(a[1][c]) * 256 +
+                               (long long)oz_level_int(a[2][c]);
+          const long long lo = (long long)oz_level_int(a[3][c]) * 16777216 +
+                               (long long)oz_level_int(a[4][c]) * 65536 + (long long)oz_level_int(a[5][c]) * 256 +
+                               (long long)oz_level_int(a[6][c]);
+          const int jc = col0 + ch * 8 + c;
+          const int k = ei + (jc < p.n ? p.ee[jc] : 0) - 32;     // product = 2^k (hi + 2^-32 lo)
+          // one 64-bit integer, hi 2^24 + floor(lo / 2^8) < 2^62 (the dropped bits are below
+          // 2^-56 of |D|row |E|row), converted with integer instructions; entries of the stage
+          // outside the update hold stale values and are not written back
+          double* q = stg + lane * 33 + ch * 8 + c;
+          *q = *q - oz_i64_times_pow2(hi * 16777216ll + (lo >> 8), k - 24);
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int j = col0 + ch * 8 + c;
-          const int k = ei + (j < p.n ? p.ee[j] : 0) - 32;       // product scale 2^k for hi, 2^(k-32) for lo
-          double s1, s2;
-          if (k > -990 && k < 990) {
-            s1 = __longlong_as_double((long long)(k + 1023) << 52);
-            s2 = __longlong_as_double((long long)(k - 32 + 1023) << 52);
-          } else {
-            s1 = ldexp(1.0, k);
-            s2 = ldexp(1.0, k - 32);
-          }
-          stg[lane * 9 + c] = fma((double)hi[c], s1, (double)lo[c] * s2);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int r = it * 4 + (lane >> 3), c = lane & 7;
-          if (ok[it]) p.C[(size_t)(row0 + r) * p.ldc + col0 + ch * 8 + c] = cv[it] - stg[r * 9 + c];
-        }
-        __syncwarp();
       }
+      // the accumulators have been read: the next tile's MMAs may start
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar);
       acc_phase ^= 1u;
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const int i = row0 + r;
+        if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1)) p.C[(size_t)i * p.ldc + j] = stg[r * 33 + lane];
+      }
+      __syncwarp();
     }
   }
   // teardown: every role has finished or given up; wait for the others before freeing TMEM

@@ -4,21 +4,21 @@
 // X = Y^T Q T, U = Y Z, W = U Y^T, one batch entry per radial shell).
 //
 // Packing (oz_pack_kernel): every row of op(A) diag(ks) and of op(B)^T is
-// scaled by a power of two, x = 2^e a with |a| < 1 (e the exponent of the row's
-// largest magnitude), and written as the integer N = round(a 2^56) in base 128
-// with balanced digits,
-//   a = sum_{t=0..7} s_t 128^-(t+1),  |s_0| <= 128, |s_t| <= 64 (t > 0),
-// each digit exact in bf16; the representation error is below 2^-57 of the
-// row maximum.  Slices 2q and 2q + 1 share one 128-byte row of plane q (the
-// [hi | lo] layout the swizzled operand tiles use), per K chunk of 32.
+// scaled by a power of two, x = 2^e a with |a| < 1/2 (e from the largest
+// exponent of the row), and written as the integer N = round(a 2^56) in base
+// 128 with balanced digits,
+//   a = sum_{t=0..7} s_t 128^-(t+1),  |s_t| <= 64,
+// each digit exact in bf16; the representation error is at most 2^-56 2^e.
+// Slices 2q and 2q + 1 share one 128-byte row of plane q (the [hi | lo]
+// layout the swizzled operand tiles use), per K chunk of 32.  Integer and
+// fp32 instructions only (oz_combine.cuh), apart from the product with ks.
 //
 // Products (oz_gemm_kernel): the 36 slice pairs with t + u <= 7 are issued as
 // bf16 tcgen05 MMAs into eight fp32 accumulators in TMEM, one per level
 // t + u.  Over a K segment of 128 a level sum is an integer of magnitude at
-// most 128 (2 128 64 + 6 64 64) < 2^23, so the tensor cores accumulate it
-// exactly.  The epilogue combines the levels of a segment as two 64-bit
-// integers, converts them exactly and scales them by 2^(e_i + f_j) with one
-// rounding; segments add in float64.  The dropped pairs (t + u >= 8) and the
+// most 128 * 8 * 64 * 64 = 2^22, so the tensor cores accumulate it exactly.  The epilogue combines the levels of a segment as 64-bit integers
+// and rounds the product to float64 with integer instructions (oz_combine.cuh);
+// segments add in float64.  The dropped pairs (t + u >= 8) and the
 // representation errors bound the error by about 2^-54 K |A|row max |B|row max
 // per element, the bound of a float64 dot product of K terms.
 //
@@ -31,6 +31,7 @@
 #include <cmath>
 
 #include "lrs_internal.h"
+#include "oz_combine.cuh"
 #include "tc_common.cuh"
 
 namespace lrs {
@@ -85,6 +86,29 @@ __device__ __forceinline__ void og_load_tile(const OgPack& p, const double* x, c
   }
 }
 
+// Digits of one value (lane k of a row with scale e): planes[(s / 2) nchunks + kc][row][(s % 2) 32 + k].
+__device__ __forceinline__ void og_put_digits(double v, int e, uint16_t* base, size_t chunk_elems, int nchunks,
+                                              int kc, int row, int lane) {
+  // N = round(v 2^(56 - e)), |N| <= 2^55; balanced base-128 digits s_7 .. s_1 in [-64, 63], leading s_0
+  long long N = oz_fixed56(v, e);
+  int dig[OG_SLICES];
+#pragma unroll
+  for (int s = OG_SLICES - 1; s > 0; --s) {
+    const long long d = ((N + 64) & 127) - 64;
+    dig[s] = (int)d;
+    N = (N - d) >> 7;                          // exact
+  }
+  dig[0] = (int)N;
+#pragma unroll
+  for (int s = 0; s < OG_SLICES; ++s)
+    base[((size_t)(s >> 1) * nchunks + kc) * chunk_elems + (size_t)row * 64 + (s & 1) * 32 + lane] =
+        oz_int_to_bf16_bits(dig[s]);
+}
+
+// One CTA: 32 rows (warp w holds rows w, w + 8, w + 16, w + 24, lane = K index within a chunk).
+// Up to OG_HOLD chunks stay in registers between the row scale and the digits; longer rows are
+// read twice (the second time from L2).
+constexpr int OG_HOLD = 8;
 __global__ void __launch_bounds__(256) oz_pack_kernel(const OgPack p) {
   __shared__ double t[32][33];
   const int b = blockIdx.y;
@@ -92,60 +116,54 @@ __global__ void __launch_bounds__(256) oz_pack_kernel(const OgPack p) {
   const double* ks = p.ks ? p.ks + p.stride_ks * b : nullptr;
   const int i0 = blockIdx.x * 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // pass 1: row maxima (rows warp, warp + 8, warp + 16, warp + 24)
-  double mx[4] = {0.0, 0.0, 0.0, 0.0};
-  bool bad[4] = {false, false, false, false};
+  const bool hold = p.nchunks <= OG_HOLD;
+  double v[OG_HOLD][4];
+  int emax[4] = {0, 0, 0, 0};
+  // pass 1: largest exponent field per row
   for (int kc = 0; kc < p.nchunks; ++kc) {
     og_load_tile(p, x, ks, i0, kc * 32, t);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const double v = t[lane][warp + 8 * r];
-      if (!isfinite(v)) bad[r] = true;
-      else mx[r] = fmax(mx[r], fabs(v));
+      const double y = t[lane][warp + 8 * r];
+      emax[r] = max(emax[r], oz_exp_field(y));
+#pragma unroll
+      for (int c = 0; c < OG_HOLD; ++c)
+        if (c == kc) v[c][r] = y;
     }
     __syncthreads();
   }
   int e[4];
+  bool bad[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    double m = mx[r];
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const bool any_bad = __any_sync(0xffffffffu, bad[r]);
-    e[r] = 0;
-    if (m > 0.0) frexp(m, &e[r]);            // m = f 2^e, f in [0.5, 1)
-    if (any_bad) e[r] = OG_BAD_EXP;
+    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax[r]);
+    bad[r] = E == 0x7FF;                       // an infinity or a NaN in the row
+    e[r] = bad[r] ? OG_BAD_EXP : oz_row_scale(E);
     if (lane == 0) p.expo[(size_t)b * p.rows_pad + i0 + warp + 8 * r] = e[r];
   }
-  // pass 2: digits (the tiles are read again, from L2)
+  // pass 2: digits
   const size_t chunk_elems = (size_t)p.rows_pad * 64;
   uint16_t* base = p.planes + (size_t)b * OG_PLANES * p.nchunks * chunk_elems;
-  for (int kc = 0; kc < p.nchunks; ++kc) {
-    og_load_tile(p, x, ks, i0, kc * 32, t);
-    __syncthreads();
+  if (hold) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int row = i0 + warp + 8 * r;
-      double v = t[lane][warp + 8 * r];
-      if (e[r] == OG_BAD_EXP) v = 0.0;
-      // N = round(v 2^(56 - e)), |N| <= 2^56; balanced base-128 digits s_7 .. s_1, leading s_0
-      long long N = __double2ll_rn(ldexp(v, 56 - e[r]));
-      int dig[OG_SLICES];
+    for (int c = 0; c < OG_HOLD; ++c) {
+      if (c >= p.nchunks) break;
 #pragma unroll
-      for (int s = OG_SLICES - 1; s > 0; --s) {
-        const long long d = ((N + 64) & 127) - 64;
-        dig[s] = (int)d;
-        N = (N - d) / 128;                     // exact
-      }
-      dig[0] = (int)N;
-#pragma unroll
-      for (int s = 0; s < OG_SLICES; ++s) {
-        const __nv_bfloat16 h = __float2bfloat16_rn((float)dig[s]);   // at most 8 significant bits: exact
-        base[((size_t)(s >> 1) * p.nchunks + kc) * chunk_elems + (size_t)row * 64 + (s & 1) * 32 + lane] =
-            __bfloat16_as_ushort(h);
-      }
+      for (int r = 0; r < 4; ++r)
+        og_put_digits(bad[r] ? 0.0 : v[c][r], bad[r] ? 0 : e[r], base, chunk_elems, p.nchunks, c,
+                      i0 + warp + 8 * r, lane);
     }
-    __syncthreads();
+  } else {
+    for (int kc = 0; kc < p.nchunks; ++kc) {
+      og_load_tile(p, x, ks, i0, kc * 32, t);
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        og_put_digits(bad[r] ? 0.0 : t[lane][warp + 8 * r], bad[r] ? 0 : e[r], base, chunk_elems, p.nchunks, kc,
+                      i0 + warp + 8 * r, lane);
+      __syncthreads();
+    }
   }
 }
 
@@ -295,11 +313,13 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
     }
   } else {
     // ------------------------------------------------ epilogue: combine the levels, C = alpha sum + beta C
-    // Level sums S_0 .. S_7 (integers below 2^23 in fp32) are combined exactly as
+    // Level sums S_0 .. S_7 (integers of magnitude at most 2^22 in fp32, read as int32 by one
+    // fp32 add each) are combined exactly as
     // hi = S_0 2^21 + S_1 2^14 + S_2 2^7 + S_3 and lo = S_4 2^21 + S_5 2^14 + S_6 2^7 + S_7
-    // (below 2^45 each), so that the segment's product is 2^(e_i + f_j - 35) (hi + 2^-28 lo):
-    // two exact conversions and one FMA.  Each warp stages 32 rows x 8 columns in shared
-    // memory and writes them row-wise (coalesced).
+    // (below 2^41 and 2^44), so that the segment's product is 2^(e_i + f_j - 35) (hi + 2^-28 lo),
+    // rounded to float64 with integer instructions: with alpha = 1 and beta = 0 the epilogue
+    // issues no float64 operation.  Each warp stages 32 rows x 8 columns in shared memory and
+    // writes them row-wise (coalesced).
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
@@ -346,37 +366,27 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
           tmem_ld_wait();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            const long long hi = (long long)__float2int_rn(a[0][c]) * 2097152 +
-                                 (long long)__float2int_rn(a[1][c]) * 16384 +
-                                 (long long)__float2int_rn(a[2][c]) * 128 + (long long)__float2int_rn(a[3][c]);
-            const long long lo = (long long)__float2int_rn(a[4][c]) * 2097152 +
-                                 (long long)__float2int_rn(a[5][c]) * 16384 +
-                                 (long long)__float2int_rn(a[6][c]) * 128 + (long long)__float2int_rn(a[7][c]);
+            const long long hi = (long long)oz_level_int(a[0][c]) * 2097152 +
+                                 (long long)oz_level_int(a[1][c]) * 16384 +
+                                 (long long)oz_level_int(a[2][c]) * 128 + (long long)oz_level_int(a[3][c]);
+            const long long lo = (long long)oz_level_int(a[4][c]) * 2097152 +
+                                 (long long)oz_level_int(a[5][c]) * 16384 +
+                                 (long long)oz_level_int(a[6][c]) * 128 + (long long)oz_level_int(a[7][c]);
             const int j = col0 + ch * 8 + c;
             const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
-            double val;
-            if (ei == OG_BAD_EXP || fj == OG_BAD_EXP) {
-              val = __longlong_as_double(0x7ff8000000000000ll);   // NaN, as a float64 product would give
-            } else {
-              const int k = ei + fj - 35;
-              double s1, s2;
-              if (k > -990 && k < 990) {
-                s1 = __longlong_as_double((long long)(k + 1023) << 52);
-                s2 = __longlong_as_double((long long)(k - 28 + 1023) << 52);
-              } else {
-                s1 = ldexp(1.0, k);
-                s2 = ldexp(1.0, k - 28);
-              }
-              val = fma((double)hi, s1, (double)lo * s2);
-            }
-            stg[lane * 9 + c] = val;
+            // one 64-bit integer, hi 2^20 + floor(lo / 2^8) < 2^63 (the dropped bits are below
+            // 2^-55 of |A|row |B|row), rounded to float64 with integer instructions
+            stg[lane * 9 + c] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
+                                    ? __longlong_as_double(0x7ff8000000000000ll)   // NaN, as in float64
+                                    : oz_i64_times_pow2(hi * 1048576ll + (lo >> 8), ei + fj - 55);
           }
           __syncwarp();
 #pragma unroll
           for (int it = 0; it < 8; ++it) {
             const int r = it * 4 + (lane >> 3), c = lane & 7;
             if (ok[it]) {
-              const double v = p.alpha * stg[r * 9 + c];
+              double v = stg[r * 9 + c];
+              if (p.alpha != 1.0) v *= p.alpha;
               C[(size_t)(row0 + r) * p.ldc + col0 + ch * 8 + c] = read_c ? fma(cscale, cv[it], v) : v;
             }
           }

@@ -1,0 +1,82 @@
+// Integer-instruction helpers of the float64-accurate tensor-core kernels
+// (k_ozaki.cu, k_ozgemm.cu): slicing a float64 into integer digits, and
+// rounding an exact integer combination of slice-product levels back to
+// float64.
+//
+// GB300 retires two float64 operations (and about sixteen conversions) per
+// SM per clock against 128 fp32 or int32 ones, so slicing and epilogues that
+// scale, round and convert in float64 are bound by those pipes.  Everything
+// here works on the bits with fp32 and int32 instructions.
+#pragma once
+
+#include <cstdint>
+
+namespace lrs {
+
+// Biased exponent field of a float64 (0 for zero and subnormals, 0x7FF for
+// infinities and NaN).
+__device__ __forceinline__ int oz_exp_field(double x) {
+  return (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
+}
+
+// Row scale from the largest exponent field of the row: every element has
+// |x| < 2^(e - 1) with e = max(E, 1) - 1021, so x 2^-e lies in (-1/2, 1/2).
+__device__ __forceinline__ int oz_row_scale(int max_exp_field) {
+  return (max_exp_field > 1 ? max_exp_field : 1) - 1021;
+}
+
+// round(x 2^(56 - e)) for |x| < 2^(e - 1) (so |result| <= 2^55), rounding
+// halves away from zero, from the bits of x.
+__device__ __forceinline__ long long oz_fixed56(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)(b >> 52) & 0x7FF;
+  const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
+  const unsigned long long mx = E ? (frac | 0x10000000000000ull) : frac;   // x = mx 2^(ex)
+  const int ex = E ? E - 1075 : -1074;
+  const int sh = ex + 56 - e;   // <= 2 by the bound on x
+  unsigned long long n;
+  if (sh >= 0) n = mx << sh;
+  else if (sh > -64) n = (mx + (1ull << (-sh - 1))) >> (-sh);
+  else n = 0;
+  return (b >> 63) ? -(long long)n : (long long)n;
+}
+
+// bf16 bit pattern of an integer |d| <= 256 (exact: at most 8 significant
+// bits): the integer is placed in the mantissa of 1.5 2^23 by an integer add,
+// recovered as an fp32 by one fp32 subtraction, and its top 16 bits are the
+// bf16 value.
+__device__ __forceinline__ uint16_t oz_int_to_bf16_bits(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+// An integer |S| <= 2^22 held exactly in fp32 (a level sum read from TMEM) as
+// an int32: S + 1.5 2^23 lies in [2^23, 2^24], where consecutive integers are
+// consecutive bit patterns.
+__device__ __forceinline__ int oz_level_int(float s) {
+  return __float_as_int(s + 12582912.0f) - 0x4B400000;
+}
+
+// v 2^k rounded to the nearest float64 (ties to even) from the bits of v:
+// find the leading one, keep 53 bits, round on the 11 dropped bits and add
+// the exponent.  Results outside the normal range take a float64 path
+// (ldexp), which the slice scaling makes rare.
+__device__ __forceinline__ double oz_i64_times_pow2(long long v, int k) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const unsigned long long m = a << lz;                 // leading one at bit 63
+  unsigned long long mant = m >> 11;                    // 53 bits, leading one at bit 52
+  const unsigned int rem = (unsigned int)(m & 0x7FFull);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  const int e = 63 - lz + k;                            // exponent of the leading one
+  if (e > -1020 && e < 1022) {
+    // the leading one of mant adds one to the biased exponent field; a rounding carry
+    // to 2^53 adds another and leaves a zero fraction, as it should
+    return __longlong_as_double((long long)(sign | ((((unsigned long long)(e + 1022)) << 52) + mant)));
+  }
+  return ldexp((double)v, k);
+}
+
+}  // namespace lrs

@@ -193,6 +193,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------------------------- asynchronous global -> shared copies
+__device__ __forceinline__ void cp_async8(uint32_t smem_dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Round-to-nearest split x = hi + lo into two 16-bit floats: bf16 (FMT 1,
 // residual O(2^-16 |x|)) or fp16 (FMT 0, residual O(2^-22 |x|) for inputs
 // pre-scaled into the normal fp16 range).  Returns the raw bit patterns.
