@@ -693,7 +693,7 @@ int dyson_solve(lrs_ctx* ctx, Site& s) {
 // indices has been exchanged.  Cost n^3 flop (lower-triangle rank-nb updates),
 // against 8/3 n^3 for LU plus n right-hand sides.
 constexpr int GJ_NB = 32;               // pivot block width
-constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread apply kernel
+constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread pivot and apply kernels
 
 // Column block k of the current matrix from the lower triangle, C (n x kb,
 // leading dimension GJ_NB): element (i, j), j in block k, is stored at
@@ -704,8 +704,9 @@ constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread apply k
 // The exchange of the previous block kp (= k - 1, D_p = C_p P^-1, E_p) has not
 // been applied to block k (the bulk update leaves blocks kp and k out): the
 // gather applies it on the fly, stored(r, s) - D_p[r] . E_p[s], except on the
-// rows of block kp, which the exchange itself rewrote (gj_fix_kernel).  Block k
-// of A is rewritten by its own exchange, so the updated values are not stored.
+// rows of block kp, where the exchange itself writes D_p (read here from D_p,
+// so the gather does not wait for gj_fix_kernel).  Block k of A is rewritten
+// by its own exchange, so the updated values are not stored.
 // GJ_GR rows per CTA, one warp per row (lane = column in the block).
 constexpr int GJ_GR = 8;
 __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict__ A, int n, int lda, int k0, int kb,
@@ -735,15 +736,23 @@ __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict
   const int j = k0 + c;
   double v = 0.0;
   if (c < kb) {
-    v = (i >= j) ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
+    if (Dp && i >= kp0 && i < kp0 + kpb) {
+      // stored (j, i) in the column block of kp below its diagonal: the exchange of kp
+      // writes D_p there (gj_fix_kernel, which may still be running)
+      v = dk[c][i - kp0];
+    } else {
+      v = (i >= j) ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
+    }
     if (Dp && !(i >= kp0 && i < kp0 + kpb)) {
       // stored (max, min): D_p of the larger index, E_p of the smaller
       const double* d = (i >= j) ? dr[r] : dk[c];
       const double* e = (i >= j) ? ek[c] : er[r];
-      double acc = 0.0;
-#pragma unroll 8
-      for (int kk = 0; kk < GJ_NB; ++kk) acc = fma(d[kk], e[kk], acc);
-      v -= acc;
+      // four partial sums: a 32-long chain of dependent float64 FMAs would pay their
+      // latency 32 times
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int kk = 0; kk < GJ_NB; ++kk) acc[kk & 3] = fma(d[kk], e[kk], acc[kk & 3]);
+      v -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     const bool flip = i < k0;
     C[(size_t)i * GJ_NB + c] = flip ? -v : v;
@@ -753,84 +762,66 @@ __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict
   if (eplanes) oz_slice_row(c < kb ? v : 0.0, c, i, plane_stride, eplanes, eexp);
 }
 
+constexpr int GJ_PM = GJ_NB / GJ_PR;     // pivot rows per thread
 // Pinv = P^-1 for the kb x kb pivot block P = C[k0, k0 + kb) by scalar
-// exchange steps; a ragged block is padded with the identity.  Eight warps
-// update the matrix: thread t holds column t % 32 of rows t / 32 + 8 m in
-// registers, and the owners of the next pivot's column and row publish them
-// into shared buffers that alternate between steps (one barrier per step, one
-// FP64 operation per element).  A ninth warp keeps the diagonal, lane i
-// repeating the update of element (i, i), and forms the next pivot's
-// reciprocal while the others update, so the division stays off the step's
-// critical path.  An SM retires two DFMA per clock, so the 32 x 32 inverse
-// costs about 32^3 / 2 clocks.  A pivot that is not positive and finite sets
-// status[0] = 2, status[1] = its column (the matrix is not SPD).
-constexpr int GJ_PW = 8;                  // update warps of the pivot kernel
-constexpr int GJ_PM = GJ_NB / GJ_PW;      // rows per thread
-__global__ void __launch_bounds__((GJ_PW + 1) * 32) gj_pivot_kernel(const double* __restrict__ C, int k0, int kb,
-                                                                    double* __restrict__ Pinv,
-                                                                    int* __restrict__ status) {
-  __shared__ double colv[2][GJ_NB], roww[2][GJ_NB], dinv[2];
-  const int j = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const bool diag_warp = w == GJ_PW;
+// exchange steps; a ragged block is padded with the identity.  (Variants with
+// one barrier per step, the reciprocal on a separate warp, the lower triangle
+// only, or a division-free scaled form all measured slower on GB300: the
+// float64 latency of each step's dependent operations, not the FMA count,
+// sets the pace, and here the division runs while the FP64 units are idle.)  Thread t holds
+// column t % GJ_NB of rows t / GJ_NB + GJ_PR m in registers; per step the
+// owners of column p publish it divided by the pivot and the owners of row p
+// publish that row, then every element takes one FMA.  One SM retires two
+// DFMA per clock, so an nb x nb inverse is about nb^3 / 2 clocks.  A pivot
+// that is not positive and finite sets status[0] = 2, status[1] = its column
+// (the matrix is not SPD).
+__global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict__ C, int k0, int kb,
+                                                       double* __restrict__ Pinv, int* __restrict__ status) {
+  __shared__ double colv[GJ_NB];   // column p, then column p / pivot
+  __shared__ double roww[GJ_NB];   // row p
+  __shared__ double dinv;
+  const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;
   double a[GJ_PM];
-  if (!diag_warp) {
+#pragma unroll
+  for (int m = 0; m < GJ_PM; ++m) {
+    const int i = ib + GJ_PR * m;
+    a[m] = (i < kb && j < kb) ? C[(size_t)(k0 + i) * GJ_NB + j] : (i == j ? 1.0 : 0.0);
+  }
+  for (int p = 0; p < GJ_NB; ++p) {
+    if (j == p) {
+#pragma unroll
+      for (int m = 0; m < GJ_PM; ++m) colv[ib + GJ_PR * m] = a[m];
+    }
+#pragma unroll
+    for (int m = 0; m < GJ_PM; ++m)
+      if (ib + GJ_PR * m == p) roww[j] = a[m];
+    __syncthreads();
+    const double piv = colv[p];
+    if (!(piv > 0.0) || !isfinite(piv)) {   // same value in every thread: uniform exit
+      if (threadIdx.x == 0 && atomicCAS(&status[0], 0, 2) == 0) status[1] = k0 + p;
+      break;
+    }
+    __syncthreads();
+    if (threadIdx.x < GJ_NB) {
+      const double d = 1.0 / piv;
+      colv[threadIdx.x] *= d;
+      if (threadIdx.x == 0) dinv = d;
+    }
+    __syncthreads();
+    const double rj = roww[j], d = dinv;
 #pragma unroll
     for (int m = 0; m < GJ_PM; ++m) {
-      const int i = w + GJ_PW * m;
-      a[m] = (i < kb && j < kb) ? C[(size_t)(k0 + i) * GJ_NB + j] : (i == j ? 1.0 : 0.0);
-    }
-    // publish column 0 and row 0
-    if (j == 0) {
-#pragma unroll
-      for (int m = 0; m < GJ_PM; ++m) colv[0][w + GJ_PW * m] = a[m];
-    }
-    if (w == 0) roww[0][j] = a[0];
-  } else {
-    a[0] = (j < kb) ? C[(size_t)(k0 + j) * GJ_NB + j] : 1.0;   // lane j: element (j, j)
-    if (j == 0) dinv[0] = 1.0 / a[0];
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int p = 0; p < GJ_NB; ++p) {
-    const int b = p & 1, nb = b ^ 1, q = p + 1;
-    const double piv = colv[b][p];
-    if (!(piv > 0.0) || !isfinite(piv)) {     // same value in every thread: uniform exit
-      if (threadIdx.x == 0 && atomicCAS(&status[0], 0, 2) == 0) status[1] = k0 + p;
-      return;
-    }
-    const double d = dinv[b];
-    if (diag_warp) {
-      // the same operations as the update of element (j, j) below
-      const double t = roww[b][j] * d;
-      if (j != p) a[0] = fma(-colv[b][j], t, a[0]);
-      if (j == q) dinv[nb] = 1.0 / a[0];
-    } else {
-      const double t = roww[b][j] * d;        // row p, column j, over the pivot
-#pragma unroll
-      for (int m = 0; m < GJ_PM; ++m) {
-        const int i = w + GJ_PW * m;
-        const double ci = colv[b][i];
-        if (i == p) a[m] = (j == p) ? d : -t;
-        else if (j == p) a[m] = ci * d;
-        else a[m] = fma(-ci, t, a[m]);
-      }
-      // publish the next step's column and row
-      if (q < GJ_NB) {
-        if (j == q) {
-#pragma unroll
-          for (int m = 0; m < GJ_PM; ++m) colv[nb][w + GJ_PW * m] = a[m];
-        }
-#pragma unroll
-        for (int m = 0; m < GJ_PM; ++m)
-          if (w + GJ_PW * m == q) roww[nb][j] = a[m];
-      }
+      const int i = ib + GJ_PR * m;
+      const double ci = colv[i];
+      if (i == p) a[m] = (j == p) ? d : -rj * d;
+      else if (j == p) a[m] = ci;
+      else a[m] = fma(-ci, rj, a[m]);
     }
     __syncthreads();
   }
-  if (diag_warp) return;
 #pragma unroll
   for (int m = 0; m < GJ_PM; ++m) {
-    const int i = w + GJ_PW * m;
+    const int i = ib + GJ_PR * m;
     if (i < kb && j < kb) Pinv[(size_t)i * GJ_NB + j] = a[m];
   }
 }
@@ -844,32 +835,37 @@ __global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict_
   __shared__ double pv[GJ_NB][GJ_NB + 1];
   __shared__ double cr[GJ_DR][GJ_NB + 1];
   const int r0 = blockIdx.x * GJ_DR;
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    const int i = idx / kb, j = idx % kb;
-    pv[i][j] = Pinv[(size_t)i * GJ_NB + j];
+  // zero beyond kb, so that the product can run over all GJ_NB terms
+  for (int idx = threadIdx.x; idx < GJ_NB * GJ_NB; idx += blockDim.x) {
+    const int i = idx / GJ_NB, j = idx % GJ_NB;
+    pv[i][j] = (i < kb && j < kb) ? Pinv[(size_t)i * GJ_NB + j] : 0.0;
   }
-  for (int idx = threadIdx.x; idx < GJ_DR * kb; idx += blockDim.x) {
-    const int i = idx / kb, j = idx % kb;
-    cr[i][j] = (r0 + i < n) ? C[(size_t)(r0 + i) * GJ_NB + j] : 0.0;
+  for (int idx = threadIdx.x; idx < GJ_DR * GJ_NB; idx += blockDim.x) {
+    const int i = idx / GJ_NB, j = idx % GJ_NB;
+    cr[i][j] = (r0 + i < n && j < kb) ? C[(size_t)(r0 + i) * GJ_NB + j] : 0.0;
   }
   __syncthreads();
   const int j = threadIdx.x % GJ_NB, ib = threadIdx.x / GJ_NB;   // rows ib + GJ_PR m (a warp per row group)
-  double acc[GJ_DR / GJ_PR];
+  // four partial sums per element: a kb-long chain of dependent float64 FMAs would pay
+  // their latency kb times (entries beyond kb are zero)
+  double acc[GJ_DR / GJ_PR][4];
 #pragma unroll
-  for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = 0.0;
+  for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m][0] = acc[m][1] = acc[m][2] = acc[m][3] = 0.0;
   if (j < kb) {
-    for (int k = 0; k < kb; ++k) {
+#pragma unroll
+    for (int k = 0; k < GJ_NB; ++k) {
       const double b = pv[k][j];
 #pragma unroll
-      for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m] = fma(cr[ib + GJ_PR * m][k], b, acc[m]);
+      for (int m = 0; m < GJ_DR / GJ_PR; ++m) acc[m][k & 3] = fma(cr[ib + GJ_PR * m][k], b, acc[m][k & 3]);
     }
   }
 #pragma unroll
   for (int m = 0; m < GJ_DR / GJ_PR; ++m) {
     const int r = r0 + ib + GJ_PR * m;
-    if (r < n && j < kb) D[(size_t)r * GJ_NB + j] = acc[m];
+    const double dv = (acc[m][0] + acc[m][1]) + (acc[m][2] + acc[m][3]);
+    if (r < n && j < kb) D[(size_t)r * GJ_NB + j] = dv;
     // slices of the row of D for the tensor-core update (the warp holds the whole row)
-    if (dplanes && r < n) oz_slice_row(acc[m], j, r, plane_stride, dplanes, dexp);
+    if (dplanes && r < n) oz_slice_row(dv, j, r, plane_stride, dplanes, dexp);
   }
 }
 
@@ -958,18 +954,19 @@ __global__ void __launch_bounds__(128) gj_update_kernel(double* __restrict__ A, 
 
 // Schedule: the bulk of the trailing update of block k (every tile away from
 // blocks k and k + 1) runs on the context stream while a second, higher
-// priority stream writes the exchanged block k (fix) and prepares the next
-// panel (gather with the update of block k applied on the fly, pivot inverse,
-// D) in the other of two buffer sets.  The serial pivot inverse (one SM)
-// thereby overlaps the bulk update.  Events: panel k ready -> bulk k; bulk k
-// done -> panel k + 2 (its block and its buffer set are touched by bulk k).
+// priority stream prepares the next panel (gather with the update of block k
+// applied on the fly, pivot inverse, D) in the other of two buffer sets, and
+// a third writes the exchanged block k into A (fix).  The serial pivot inverse
+// (one SM) thereby overlaps the bulk update.  Events: panel k ready -> fix k;
+// panel k + 1 and fix k done -> bulk k + 1; bulk k done -> panel k + 2 (its
+// block and its buffer set are touched by bulk k).
 int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
   static_assert(GJ_NB % UT == 0 && GJ_TB >= 1, "a pivot block spans whole update tiles");
   if (n <= 0) return LRS_OK;
   const size_t set = 3 * (size_t)n * GJ_NB + GJ_NB * GJ_NB;
   LRS_TRY(ensure(ctx, ctx->ws.gj, 2 * set));
   LRS_TRY(aux_stream_ready(ctx));
-  cudaStream_t s1 = ctx->stream, s2 = ctx->aux_stream;
+  cudaStream_t s1 = ctx->stream, s2 = ctx->aux_stream, s3 = ctx->aux_stream2;
   double *Cb[2], *Eb[2], *Db[2], *Pb[2];
   for (int q = 0; q < 2; ++q) {
     Cb[q] = ctx->ws.gj.ptr + q * set;
@@ -1013,7 +1010,7 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
                                                               epl[q], stride, esc[q]);
     LRS_TRY(after_launch(ctx, "gj_gather_kernel"));
     if (prev) ctx->fp64_flops += 2.0 * n * kb * GJ_NB;
-    gj_pivot_kernel<<<1, (GJ_PW + 1) * 32, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
+    gj_pivot_kernel<<<1, 256, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
     LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
     gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q], dpl[q], stride, dsc[q]);
     LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
@@ -1048,15 +1045,23 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     }
     if (!tc) ctx->fp64_flops += (double)n * n * kb;
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
-    // exchange of block k, next panel on the second stream
-    gj_fix_kernel<<<nblk, 256, 0, s2>>>(A, n, lda, k0, kb, Db[q], Pb[q]);
+    // exchange of block k on the third stream (after panel k, which s2 has finished
+    // enqueueing), next panel on the second
+    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fork, s2));
+    LRS_CUDA_TRY(cudaStreamWaitEvent(s3, ctx->ev_fork, 0));
+    gj_fix_kernel<<<nblk, 256, 0, s3>>>(A, n, lda, k0, kb, Db[q], Pb[q]);
     LRS_TRY(after_launch(ctx, "gj_fix_kernel"));
+    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fix, s3));
     if (k + 1 < nblk) {
       // buffer set q ^ 1 was last read by bulk k - 1, which s2 has waited for
       LRS_TRY(panel(k + 1, q ^ 1));
+      // bulk k + 1 updates block k, which the exchange has just written
+      LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_fix, 0));
       LRS_CUDA_TRY(cudaEventRecord(ctx->ev_panel, s2));
       // block k + 2 and set q are touched by bulk k: wait for it
       LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_bulk, 0));
+    } else {
+      LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_fix, 0));
     }
   }
   // join

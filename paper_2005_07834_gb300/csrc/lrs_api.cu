@@ -69,7 +69,8 @@ int aux_stream_ready(lrs_ctx* ctx) {
   LRS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
   ctx->prio_greatest = hi;
   LRS_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, hi));
-  for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_bulk, &ctx->ev_join})
+  LRS_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream2, cudaStreamNonBlocking, hi));
+  for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_bulk, &ctx->ev_join, &ctx->ev_fix})
     LRS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   return LRS_OK;
 }
@@ -312,9 +313,10 @@ int lrs_destroy(lrs_ctx* ctx) {
   release(ctx, ctx->d_col_o); release(ctx, ctx->d_col_u);
   free_workspace(ctx);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
-  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_panel, ctx->ev_bulk, ctx->ev_join})
+  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_panel, ctx->ev_bulk, ctx->ev_join, ctx->ev_fix})
     if (e) cudaEventDestroy(e);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+  if (ctx->aux_stream2) cudaStreamDestroy(ctx->aux_stream2);
   for (int s = 0; s < 6; ++s) {
     for (cudaEvent_t e : ctx->ev_begin[s]) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_end[s]) cudaEventDestroy(e);

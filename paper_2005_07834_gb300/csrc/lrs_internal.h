@@ -220,8 +220,10 @@ struct lrs_ctx {
   std::vector<lrs::SiteTile> site_tiles_dev;   // copy of the table last uploaded
   const lrs::SiteTile* site_tiles_dev_ptr = nullptr;
   cudaGraphExec_t graph_exec = nullptr;        // recorded multi-site build
-  // second stream of the SPD inverse (higher priority) and its fork/join events
+  // second and third streams of the SPD inverse (higher priority) and their events
   cudaStream_t aux_stream = nullptr;
+  cudaStream_t aux_stream2 = nullptr;
+  cudaEvent_t ev_fix = nullptr;
   int prio_greatest = 0;               // numerically smallest (highest) stream priority of the device
   cudaEvent_t ev_fork = nullptr, ev_panel = nullptr, ev_bulk = nullptr, ev_join = nullptr;
 
