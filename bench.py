@@ -420,6 +420,8 @@ def run_ours_multisite(args):
     pmode = proj_mode(lrs, args)
     scr.set_fft_grid(*wl.fft_grid)
     scr.set_option(lrs.LRS_OPT_GRAPH_PROJECTION, pmode)
+    if args.dyson_lanes:
+        scr.set_option(lrs.LRS_OPT_DYSON_LANES, args.dyson_lanes)
     if args.precision != "fp64":
         scr.project(mode=pmode)
         tuned = scr.autotune()
@@ -491,6 +493,7 @@ def run_ours_multisite(args):
                        "npts_sum": sum(sizes), "K": K, "nfreq": wl.nfreq, "ng": o.ng, "precision": args.precision,
                        "projection": args.projection,
                        "graph": "one CUDA graph replay per step", "autotuned": tuned,
+                       "dyson_lanes": args.dyson_lanes or 2,
                        "l2": "inputs larger than L2"},
             "tflops": flop_all / (ms * 1e-3) / 1e12,
             "stage_ms_eager": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
@@ -618,6 +621,8 @@ def main():
     ap.add_argument("--workload", default="single-site-3520", choices=sorted(WORKLOADS))
     ap.add_argument("--projection", default="exact", choices=["exact", "fft"],
                     help="Sec. VI.B method 1 (direct sum) or method 2 (FFT + cubic Lagrange on the workload's grid)")
+    ap.add_argument("--dyson-lanes", type=int, default=0,
+                    help="concurrent Dyson solves of the multi-site workloads (0: the library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rows", action="store_true",

@@ -76,6 +76,7 @@ extern "C" {
 #define LRS_OPT_GRAPH_PROJECTION 7  /* value: LRS_PROJ_EXACT (default) or LRS_PROJ_FFT_LAGRANGE3, recorded by lrs_graph_capture */
 #define LRS_OPT_REAL_ORBITALS    8  /* value: LRS_REAL_AUTO (default) or LRS_REAL_OFF */
 #define LRS_OPT_DYSON_UPDATE     9  /* value: LRS_UPDATE_AUTO (default), LRS_UPDATE_FP64 or LRS_UPDATE_TC */
+#define LRS_OPT_DYSON_LANES     10  /* value: 1..8 concurrent Dyson solves in one lrs_solve_w call (default 2) */
 #define LRS_UPDATE_AUTO   0   /* tensor cores in the mixed precisions, the FP64 pipe in LRS_FP64 */
 #define LRS_UPDATE_FP64   1   /* trailing update of the SPD inverse with float64 FMAs */
 #define LRS_UPDATE_TC     2   /* float64-accurate update from exact bf16 slices on the tensor cores */
@@ -144,6 +145,10 @@ int lrs_set_stream(lrs_ctx* ctx, void* stream);
  * accumulated per level exactly in fp32 and combined in float64 - an error
  * bound of about 6e-16 of |D|max |E|max per element, as for a float64 dot
  * product of 32 terms.
+ * LRS_OPT_DYSON_LANES sets how many sites of one lrs_solve_w call are solved
+ * concurrently, each on its own streams and workspace (sites are dealt to the
+ * lanes by decreasing cost); a single site's serial pivot chain then overlaps
+ * the others' bulk updates.  Each lane holds the workspace of its largest site.
  * Errors: LRS_ERR_ARG (unknown option or value).
  */
 int lrs_set_option(lrs_ctx* ctx, int option, int value);

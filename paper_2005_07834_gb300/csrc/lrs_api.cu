@@ -75,6 +75,55 @@ int aux_stream_ready(lrs_ctx* ctx) {
   return LRS_OK;
 }
 
+// Lanes 1 .. n - 1 of lrs_solve_w (lane 0 is the context): streams (the first
+// at the lowest priority, the panel streams at the highest), events.
+static int lanes_ready(lrs_ctx* ctx, int n) {
+  LRS_TRY(aux_stream_ready(ctx));
+  if (!ctx->ev_lanes) LRS_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_lanes, cudaEventDisableTiming));
+  int lo = 0, hi = 0;
+  LRS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  while ((int)ctx->lanes.size() < n - 1) {
+    ctx->lanes.emplace_back();
+    DysonLane& l = ctx->lanes.back();
+    LRS_CUDA_TRY(cudaStreamCreateWithPriority(&l.s1, cudaStreamNonBlocking, lo));
+    LRS_CUDA_TRY(cudaStreamCreateWithPriority(&l.s2, cudaStreamNonBlocking, hi));
+    LRS_CUDA_TRY(cudaStreamCreateWithPriority(&l.s3, cudaStreamNonBlocking, hi));
+    for (cudaEvent_t* e : {&l.ev_fork, &l.ev_panel, &l.ev_bulk, &l.ev_join, &l.ev_fix, &l.ev_done})
+      LRS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  return LRS_OK;
+}
+
+// Exchanges the context's streams, events and Dyson workspace with a lane's
+// (host-side enqueueing of one lane's solves; called again to swap back).
+static void lane_swap(lrs_ctx* ctx, DysonLane& l) {
+  std::swap(ctx->stream, l.s1);
+  std::swap(ctx->aux_stream, l.s2);
+  std::swap(ctx->aux_stream2, l.s3);
+  std::swap(ctx->ev_fork, l.ev_fork);
+  std::swap(ctx->ev_panel, l.ev_panel);
+  std::swap(ctx->ev_bulk, l.ev_bulk);
+  std::swap(ctx->ev_join, l.ev_join);
+  std::swap(ctx->ev_fix, l.ev_fix);
+  Workspace& w = ctx->ws;
+  std::swap(w.dyson_a, l.dyson_a);
+  std::swap(w.tinv, l.tinv);
+  std::swap(w.gj, l.gj);
+  std::swap(w.alda_n, l.alda_n);
+  std::swap(w.ipiv, l.ipiv);
+  std::swap(w.oz_expo, l.oz_expo);
+  std::swap(w.og_expo, l.og_expo);
+  std::swap(w.oz_planes, l.oz_planes);
+  std::swap(w.og_planes, l.og_planes);
+  std::swap(w.ru, l.ru);
+}
+
+static void release_lane_buffers(lrs_ctx* ctx, DysonLane& l) {
+  release(ctx, l.dyson_a); release(ctx, l.tinv); release(ctx, l.gj); release(ctx, l.alda_n);
+  release(ctx, l.ipiv); release(ctx, l.oz_expo); release(ctx, l.og_expo);
+  release(ctx, l.oz_planes); release(ctx, l.og_planes); release(ctx, l.ru);
+}
+
 // A top-level stage starts a new measurement; ST_CHI0_MAIN (ST_W_MAIN)
 // intervals add up until the next ST_CHI0 (ST_W) begins.
 int stage_begin(lrs_ctx* ctx, Stage s) {
@@ -251,6 +300,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.alda_n); release(ctx, w.aug_tab); release(ctx, w.aug_coef);
   w.fft_plan_ok = false;
   release(ctx, w.proj_a); release(ctx, w.proj_b); release(ctx, w.scales); release(ctx, w.proj_scale);
+  for (DysonLane& l : ctx->lanes) release_lane_buffers(ctx, l);
 }
 
 }  // namespace lrs
@@ -317,6 +367,13 @@ int lrs_destroy(lrs_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->aux_stream2) cudaStreamDestroy(ctx->aux_stream2);
+  for (DysonLane& l : ctx->lanes) {
+    for (cudaEvent_t e : {l.ev_fork, l.ev_panel, l.ev_bulk, l.ev_join, l.ev_fix, l.ev_done})
+      if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {l.s1, l.s2, l.s3})
+      if (st) cudaStreamDestroy(st);
+  }
+  if (ctx->ev_lanes) cudaEventDestroy(ctx->ev_lanes);
   for (int s = 0; s < 6; ++s) {
     for (cudaEvent_t e : ctx->ev_begin[s]) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_end[s]) cudaEventDestroy(e);
@@ -333,6 +390,10 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
       if (value != LRS_DYSON_AUTO && value != LRS_DYSON_FULL && value != LRS_DYSON_LM)
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
+      return LRS_OK;
+    case LRS_OPT_DYSON_LANES:
+      if (value < 1 || value > 8) return set_error(LRS_ERR_ARG, "Dyson lanes %d out of [1, 8]", value);
+      ctx->dyson_lanes = value;
       return LRS_OK;
     case LRS_OPT_DYSON_UPDATE:
       if (value != LRS_UPDATE_AUTO && value != LRS_UPDATE_FP64 && value != LRS_UPDATE_TC)
@@ -862,12 +923,56 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   const double fp64_before = ctx->fp64_flops;
   ctx->w_main_flop = 0;
   ctx->w_main_launches = 0;
-  for (int i : list) {
-    Site& s = ctx->sites[i];
-    if (s.fxc_kind != LRS_FXC_NONE) LRS_TRY(alda_dress(ctx, s));
-    LRS_TRY(dyson_solve(ctx, s));
-    s.has_w = true;
-    flop += 14.0 / 3.0 * (double)s.npts * s.npts * s.npts;
+  const int nl = std::min<int>(ctx->dyson_lanes, (int)list.size());
+  if (nl <= 1) {
+    for (int i : list) {
+      Site& s = ctx->sites[i];
+      if (s.fxc_kind != LRS_FXC_NONE) LRS_TRY(alda_dress(ctx, s));
+      LRS_TRY(dyson_solve(ctx, s));
+      s.has_w = true;
+      flop += 14.0 / 3.0 * (double)s.npts * s.npts * s.npts;
+    }
+  } else {
+    // deal the sites to the lanes by decreasing cost (the lane with the least work so far
+    // takes the next), so that each lane sizes its workspace on its first site
+    LRS_TRY(lanes_ready(ctx, nl));
+    std::vector<int> order(list);
+    auto cost = [&](int i) { return std::pow((double)ctx->sites[i].npts, 3.0); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<std::vector<int>> dealt(nl);
+    std::vector<double> load(nl, 0.0);
+    for (int i : order) {
+      const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      dealt[l].push_back(i);
+      load[l] += cost(i);
+    }
+    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_lanes, ctx->stream));
+    for (int l = 0; l < nl; ++l) {
+      if (l > 0) {
+        lane_swap(ctx, ctx->lanes[l - 1]);
+        cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_lanes, 0);
+        if (e != cudaSuccess) {
+          lane_swap(ctx, ctx->lanes[l - 1]);
+          return set_error(LRS_ERR_CUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
+        }
+      }
+      int rc = LRS_OK;
+      for (int i : dealt[l]) {
+        Site& s = ctx->sites[i];
+        if (s.fxc_kind != LRS_FXC_NONE) rc = alda_dress(ctx, s);
+        if (rc == LRS_OK) rc = dyson_solve(ctx, s);
+        if (rc != LRS_OK) break;
+        s.has_w = true;
+        flop += 14.0 / 3.0 * (double)s.npts * s.npts * s.npts;
+      }
+      if (l > 0) {
+        cudaError_t e = cudaEventRecord(ctx->lanes[l - 1].ev_done, ctx->stream);
+        lane_swap(ctx, ctx->lanes[l - 1]);
+        if (rc == LRS_OK && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->lanes[l - 1].ev_done, 0);
+        if (rc == LRS_OK && e != cudaSuccess) rc = set_error(LRS_ERR_CUDA, "lane join: %s", cudaGetErrorString(e));
+      }
+      if (rc != LRS_OK) return rc;
+    }
   }
   LRS_TRY(stage_end(ctx, ST_W));
   ctx->stats.flop_w = flop;

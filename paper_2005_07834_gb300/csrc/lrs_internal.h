@@ -173,6 +173,19 @@ struct Workspace {
   bool coeff_planes_valid = false;
 };
 
+// Streams, events and Dyson-solve workspace of one lane of lrs_solve_w: the
+// sites of one call are spread over lanes whose solves run concurrently
+// (lane 0 is the context's own stream and workspace).
+struct DysonLane {
+  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_panel = nullptr, ev_bulk = nullptr, ev_join = nullptr, ev_fix = nullptr;
+  cudaEvent_t ev_done = nullptr;
+  DevBuf<double> dyson_a, tinv, gj, alda_n;
+  DevBuf<int> ipiv, oz_expo, og_expo;
+  DevBuf<uint16_t> oz_planes, og_planes;
+  DevBuf<RadialUnit> ru;
+};
+
 }  // namespace lrs
 
 struct lrs_ctx {
@@ -192,6 +205,9 @@ struct lrs_ctx {
   int real_mode = LRS_REAL_AUTO;       // use the real-orbital contractions when the orbitals are real
   double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
+  int dyson_lanes = 2;                 // concurrent Dyson solves of one lrs_solve_w call
+  std::vector<lrs::DysonLane> lanes;   // lanes 1.. (lane 0 is the context itself)
+  cudaEvent_t ev_lanes = nullptr;      // fork of the lanes from the context stream
 
   // orbitals
   bool has_orb = false;

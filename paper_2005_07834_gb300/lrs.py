@@ -31,6 +31,7 @@ LRS_SOLVER_AUTO, LRS_SOLVER_LU, LRS_SOLVER_SPD = 0, 1, 2
 LRS_FXC_NONE, LRS_FXC_USER, LRS_FXC_ALDA_X = 0, 1, 2
 LRS_OPT_REAL_ORBITALS, LRS_REAL_AUTO, LRS_REAL_OFF = 8, 0, 1
 LRS_OPT_DYSON_UPDATE, LRS_UPDATE_AUTO, LRS_UPDATE_FP64, LRS_UPDATE_TC = 9, 0, 1, 2
+LRS_OPT_DYSON_LANES = 10
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
 

@@ -92,3 +92,36 @@ def test_autotune_keeps_accuracy(lrs, workload):
         scr.build_chi0()
         assert rel_fro(scr.get_chi0(1), refs[1][0]) < TOL
     scr.close()
+
+
+@pytest.mark.parametrize("lanes", [2, 3, 8])
+def test_concurrent_dyson_lanes_match_one_lane(lrs, workload, lanes):
+    """The sites of one solve spread over concurrent lanes (own streams and
+    workspace) give W bit for bit equal to one lane, also when replayed from a
+    recorded graph; more lanes than sites is allowed."""
+    import torch
+    wl, refs = workload
+    scr = make(lrs, wl)
+    scr.project()
+    scr.build_chi0()
+    scr.set_option(lrs.LRS_OPT_DYSON_LANES, 1)
+    scr.solve_w()
+    one = [scr.get_w(i) for i in range(len(wl.sites))]
+    scr.set_option(lrs.LRS_OPT_DYSON_LANES, lanes)
+    scr.solve_w()
+    for i in range(len(wl.sites)):
+        assert np.array_equal(scr.get_w(i), one[i]), i
+    scr.close()
+    stream = torch.cuda.Stream()
+    scr = make(lrs, wl, stream.cuda_stream)
+    scr.set_option(lrs.LRS_OPT_DYSON_LANES, lanes)
+    scr.graph_capture()
+    scr.graph_launch()
+    scr.synchronize()
+    for i in range(len(wl.sites)):
+        assert np.array_equal(scr.get_w(i), one[i]), i
+        assert rel_fro(scr.get_w(i), refs[i][1]) < TOL
+    with pytest.raises(lrs.LrsError) as e:
+        scr.set_option(lrs.LRS_OPT_DYSON_LANES, 9)
+    assert e.value.code == lrs.LRS_ERR_ARG
+    scr.close()
