@@ -50,23 +50,36 @@ WORKLOADS = {
 MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 
 
-# (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per gj_update_kernel<0> launch
+# (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per launch of the update kernel
 DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"): 28.5e6}
 
 
-def dyson_roofline(st, workload=None, version=None):
+def dyson_roofline(st, workload=None, version=None, hbm_gbs=None):
+    """The SPD inverse's trailing update.  On the FP64 pipe (FP64 context) it is bound by the
+    FP64 FMA rate.  On the tensor cores its float64 work is one subtraction per element and its
+    algorithmic traffic one read and one write of each updated element of C (16 bytes; the
+    library counts 2 kb flop per updated element, kb = 32), so it is reported against the HBM
+    copy bandwidth, with the FP64-equivalent rate beside it."""
     if not st.get("w_main_launches"):
         return None
     ms = st["ms_w_main"]
     tc = st.get("dyson_update_tc", False)
-    r = {"bound": "alu",
-         "kernel": ("oz_update_kernel (SPD-inverse trailing update, float64-accurate bf16 slices on tcgen05; "
-                    "FP64-equivalent rate against the FP64 FMA peak)") if tc
-         else "gj_update_kernel<0> (SPD-inverse trailing update)",
-         "achieved": st["flop_w_main"] / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-         "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz", "launches": st["w_main_launches"],
-         "avg_launch_us": 1e3 * ms / st["w_main_launches"],
-         "traffic": DYSON_TRAFFIC.get((workload, version))}
+    fp64_eq = st["flop_w_main"] / (ms * 1e-3) / 1e12
+    common = {"launches": st["w_main_launches"], "avg_launch_us": 1e3 * ms / st["w_main_launches"],
+              "traffic": DYSON_TRAFFIC.get((workload, version))}
+    if tc and hbm_gbs:
+        algo_bytes = st["flop_w_main"] / (2.0 * 32) * 16.0
+        r = {"bound": "hbm",
+             "kernel": "oz_update_kernel (SPD-inverse trailing update, float64-accurate bf16 slices on tcgen05)",
+             "achieved": algo_bytes / (ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+             "peak_source": "HBM copy bandwidth, measured",
+             "algorithmic_bytes_per_launch": algo_bytes / st["w_main_launches"],
+             "fp64_equivalent_tflops": fp64_eq, "fp64_equivalent_vs_fp64_fma_peak": fp64_eq / FP64_PEAK_TFLOPS,
+             **common}
+    else:
+        r = {"bound": "alu", "kernel": "gj_update_kernel (SPD-inverse trailing update, FP64 FMA)",
+             "achieved": fp64_eq, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz", **common}
     r["frac"] = r["achieved"] / r["peak"]
     return r
 
@@ -315,7 +328,7 @@ def run_ours(args):
     # pivot block), timed per launch with CUDA events on its stream inside the library; algorithmic
     # flop per launch = 2 kb x the lower-triangle elements it updates
     st["dyson_update_tc"] = args.precision != "fp64"   # LRS_UPDATE_AUTO: tensor cores in the mixed precisions
-    roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"))
+    roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"), peaks["hbm_gbs"])
     # the roofline object describes the kernel that dominates the step; the other is kept beside it
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
 
@@ -467,7 +480,7 @@ def run_ours_multisite(args):
             "kernel": "zgemm_tc_kernel<chi0> (all sites, one launch per workspace group)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     st["dyson_update_tc"] = args.precision != "fp64"
-    roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"))
+    roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"), peaks["hbm_gbs"])
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
     if rank == 0:
         cpu = None
