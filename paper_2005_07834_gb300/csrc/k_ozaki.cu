@@ -39,10 +39,12 @@ constexpr int OZ_A_PLANE = OZ_TM * 128;        // bytes of one A plane tile
 constexpr int OZ_B_PLANE = OZ_TN * 128;
 constexpr int OZ_STAGE = OZ_PLANES * (OZ_A_PLANE + OZ_B_PLANE);
 constexpr int OZ_STAGES = 1;
-constexpr int OZ_EPI_WARPS = 8;
-constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * 33 * 8;  // per-warp [32][33] float64 staging of C updates
+constexpr int OZ_EPI_WARPS = 16;               // four per TMEM lane quarter, 16 columns each
+constexpr int OZ_EPI_COLS = OZ_TN / (OZ_EPI_WARPS / 4);
+constexpr int OZ_STG_LD = OZ_EPI_COLS + 1;      // padded row of a warp's staging tile
+constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * OZ_STG_LD * 8;   // per-warp [32][17] float64 staging of C
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + OZ_STAGE_EPI + 1024;
-constexpr int OZ_THREADS = 320;                // producer, MMA issuer, 8 epilogue warps
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;   // producer, MMA issuer, epilogue warps
 constexpr int OZ_TMEM_COLS = 512;              // 7 levels x 64 columns used
 
 struct OzUpdate {
@@ -160,37 +162,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else {
     // ------------------------------------------------ epilogue: combine the levels, C -= D E^T
-    // Each warp owns 32 rows (its TMEM lane quarter) x 32 columns of the tile.  Its
-    // share of C is copied into a [32][33] shared-memory stage (cp.async, 256
-    // contiguous bytes per row) before the accumulators are ready, so the memory
-    // latency overlaps the MMAs.  Level sums are integers of magnitude below 2^22 in
-    // fp32 (read as int32 by one fp32 add each), combined exactly in two 64-bit
-    // integers, hi = a0 2^16 + a1 2^8 + a2 (< 2^38) and lo = a3 2^24 + a4 2^16 + a5 2^8
-    // + a6 (< 2^48), so that the product is 2^(e_i + f_j) (2^-32 hi + 2^-64 lo); that
-    // value is rounded to float64 with integer instructions and subtracted from the
-    // staged C (the only float64 operation per element).  TMEM is then released to
-    // the next tile's MMAs, and the stage is written back row by row.
+    // Each warp owns 32 rows (its TMEM lane quarter) x 16 columns of the tile.  Its
+    // share of C is copied into a [32][17] shared-memory stage (cp.async) before the
+    // accumulators are ready, so the memory latency overlaps the MMAs.  Level sums S_L
+    // (integers of magnitude below 2^22 in fp32, read as int32 by one fp32 add each)
+    // are combined into one 64-bit integer in units of 2^-56 of the scaled product,
+    //   V = S_0 2^40 + S_1 2^32 + S_2 2^24 + S_3 2^16 + S_4 2^8 + S_5 + floor(S_6 / 2^8)
+    // (|V| < 2^60; the floor drops less than 2^-56 of the row scales' product), so
+    // the product is 2^(e_i + f_j - 56) V, rounded to float64 with integer
+    // instructions and subtracted from the staged C (the only float64 operation per
+    // element).  TMEM is then released to the next tile's MMAs, and the stage is
+    // written back, two rows of 16 columns per instruction.
+    const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int cg = ew >> 2;                      // column group of 16
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
     double* stg = reinterpret_cast<double*>(oz_smem_raw + (smem_base - smem_u32(oz_smem_raw)) +
-                                            OZ_STAGES * OZ_STAGE) + (warp - 2) * 32 * 33;
+                                            OZ_STAGES * OZ_STAGE) + ew * 32 * OZ_STG_LD;
     const uint32_t stg_s = smem_u32(stg);
+    const int wc = lane & 15, wr = lane >> 4;    // this lane's column and row parity when C moves
     uint32_t acc_phase = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
       int bi, bj;
       if (!oz_decode(p, u, bi, bj)) continue;
       const int row0 = bi * OZ_TM + quarter * 32;
-      const int col0 = bj * OZ_TN + half * 32;
-      const int j = col0 + lane;                 // this lane's column when C is read and written
+      const int col0 = bj * OZ_TN + cg * OZ_EPI_COLS;
+      const int j = col0 + wc;
       const bool col_ok = j < p.n && !(j >= p.x0 && j < p.x1);
-#pragma unroll 8
-      for (int r = 0; r < 32; ++r) {
+#pragma unroll 4
+      for (int r = wr; r < 32; r += 2) {
         const int i = row0 + r;
         if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1))
-          cp_async8(stg_s + (uint32_t)(r * 33 + lane) * 8u, p.C + (size_t)i * p.ldc + j);
+          cp_async8(stg_s + (uint32_t)(r * OZ_STG_LD + wc) * 8u, p.C + (size_t)i * p.ldc + j);
       }
       cp_async_commit();
+      // the row scale of this lane's TMEM row and the column scales of the 16 columns
+      const int my_row = row0 + lane;
+      const int ei = my_row < p.n ? p.ed[my_row] : 0;
+      const int fj_lane = (col0 + wc) < p.n ? p.ee[col0 + wc] : 0;
       int got = 1;
       if (lane == 0) got = mbar_wait(&accf_bar, acc_phase, &abort_flag) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
@@ -205,28 +214,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       tc_fence_after();
       cp_async_wait_all();
       __syncwarp();
-      const int my_row = row0 + lane;            // this lane's row when TMEM is read
-      const int ei = my_row < p.n ? p.ed[my_row] : 0;
-#pragma unroll 1
-      for (int ch = 0; ch < 4; ++ch) {
+#pragma unroll
+      for (int ch = 0; ch < OZ_EPI_COLS / 8; ++ch) {
         float a[OZ_LEVELS][8];
 #pragma unroll
-        for (int lv = 0; lv < OZ_LEVELS; ++lv) tmem_ld8(tbase + lane_off + lv * OZ_TN + half * 32 + ch * 8, a[lv]);
+        for (int lv = 0; lv < OZ_LEVELS; ++lv)
+          tmem_ld8(tbase + lane_off + lv * OZ_TN + cg * OZ_EPI_COLS + ch * 8, a[lv]);
         tmem_ld_wait();
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const long long hi = (long long)oz_level_int(a[0][c]) * 65536 + (long long)oz_level_int(a[1][c]) * 256 +
-                               (long long)oz_level_int(a[2][c]);
-          const long long lo = (long long)oz_level_int(a[3][c]) * 16777216 +
-                               (long long)oz_level_int(a[4][c]) * 65536 + (long long)oz_level_int(a[5][c]) * 256 +
-                               (long long)oz_level_int(a[6][c]);
-          const int jc = col0 + ch * 8 + c;
-          const int k = ei + (jc < p.n ? p.ee[jc] : 0) - 32;     // product = 2^k (hi + 2^-32 lo)
-          // one 64-bit integer, hi 2^24 + floor(lo / 2^8) < 2^62 (the dropped bits are below
-          // 2^-56 of |D|row |E|row), converted with integer instructions; entries of the stage
-          // outside the update hold stale values and are not written back
-          double* q = stg + lane * 33 + ch * 8 + c;
-          *q = *q - oz_i64_times_pow2(hi * 16777216ll + (lo >> 8), k - 24);
+          const long long V = ((long long)oz_level_int(a[0][c]) << 40) + ((long long)oz_level_int(a[1][c]) << 32) +
+                              ((long long)oz_level_int(a[2][c]) << 24) + ((long long)oz_level_int(a[3][c]) << 16) +
+                              ((long long)oz_level_int(a[4][c]) << 8) + (long long)oz_level_int(a[5][c]) +
+                              (long long)(oz_level_int(a[6][c]) >> 8);
+          const int fj = __shfl_sync(0xffffffffu, fj_lane, ch * 8 + c);
+          double* q = stg + lane * OZ_STG_LD + ch * 8 + c;
+          // entries of the stage outside the update hold stale values and are not written back
+          *q = *q - oz_i64_times_pow2(V, ei + fj - 56);
         }
       }
       // the accumulators have been read: the next tile's MMAs may start
@@ -234,10 +238,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar);
       acc_phase ^= 1u;
-#pragma unroll 8
-      for (int r = 0; r < 32; ++r) {
+#pragma unroll 4
+      for (int r = wr; r < 32; r += 2) {
         const int i = row0 + r;
-        if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1)) p.C[(size_t)i * p.ldc + j] = stg[r * 33 + lane];
+        if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1))
+          p.C[(size_t)i * p.ldc + j] = stg[r * OZ_STG_LD + wc];
       }
       __syncwarp();
     }
