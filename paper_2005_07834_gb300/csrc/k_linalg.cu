@@ -1005,14 +1005,21 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     // the exchange of the previous block (buffer set q ^ 1) is applied to block kb_idx here
     const int qp = q ^ 1, kp0 = k0 - GJ_NB;
     const bool prev = kb_idx > 0;
-    gj_gather_kernel<<<(n + GJ_GR - 1) / GJ_GR, 256, 0, s2>>>(A, n, lda, k0, kb, prev ? Db[qp] : nullptr,
-                                                              prev ? Eb[qp] : nullptr, kp0, GJ_NB, Cb[q], Eb[q],
-                                                              epl[q], stride, esc[q]);
+    // the side-chain kernels carry the highest launch priority, also as nodes of a recorded graph
+    const int pr = ctx->prio_greatest;
+    const double* dprev = prev ? Db[qp] : nullptr;
+    const double* eprev = prev ? Eb[qp] : nullptr;
+    LRS_CUDA_TRY(launch_with_priority(gj_gather_kernel, dim3((n + GJ_GR - 1) / GJ_GR), dim3(256), 0, s2, pr,
+                                      (const double*)A, n, lda, k0, kb, dprev, eprev, kp0, (int)GJ_NB, Cb[q], Eb[q],
+                                      epl[q], stride, esc[q]));
     LRS_TRY(after_launch(ctx, "gj_gather_kernel"));
     if (prev) ctx->fp64_flops += 2.0 * n * kb * GJ_NB;
-    gj_pivot_kernel<<<1, 256, 0, s2>>>(Cb[q], k0, kb, Pb[q], status);
+    LRS_CUDA_TRY(launch_with_priority(gj_pivot_kernel, dim3(1), dim3(256), 0, s2, pr, (const double*)Cb[q], k0, kb,
+                                      Pb[q], status));
     LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
-    gj_apply_kernel<<<(n + GJ_DR - 1) / GJ_DR, 256, 0, s2>>>(Cb[q], n, kb, Pb[q], Db[q], dpl[q], stride, dsc[q]);
+    LRS_CUDA_TRY(launch_with_priority(gj_apply_kernel, dim3((n + GJ_DR - 1) / GJ_DR), dim3(256), 0, s2, pr,
+                                      (const double*)Cb[q], n, kb, (const double*)Pb[q], Db[q], dpl[q], stride,
+                                      dsc[q]));
     LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
     ctx->fp64_flops += 2.0 * n * kb * kb;
     return LRS_OK;
@@ -1049,7 +1056,8 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     // enqueueing), next panel on the second
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fork, s2));
     LRS_CUDA_TRY(cudaStreamWaitEvent(s3, ctx->ev_fork, 0));
-    gj_fix_kernel<<<nblk, 256, 0, s3>>>(A, n, lda, k0, kb, Db[q], Pb[q]);
+    LRS_CUDA_TRY(launch_with_priority(gj_fix_kernel, dim3(nblk), dim3(256), 0, s3, ctx->prio_greatest, A, n, lda,
+                                      k0, kb, (const double*)Db[q], (const double*)Pb[q]));
     LRS_TRY(after_launch(ctx, "gj_fix_kernel"));
     LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fix, s3));
     if (k + 1 < nblk) {

@@ -314,11 +314,9 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
   } else {
     // ------------------------------------------------ epilogue: combine the levels, C = alpha sum + beta C
     // Level sums S_0 .. S_7 (integers of magnitude at most 2^22 in fp32, read as int32 by one
-    // fp32 add each) are combined exactly as
-    // hi = S_0 2^21 + S_1 2^14 + S_2 2^7 + S_3 and lo = S_4 2^21 + S_5 2^14 + S_6 2^7 + S_7
-    // (below 2^41 and 2^44), so that the segment's product is 2^(e_i + f_j - 35) (hi + 2^-28 lo),
-    // rounded to float64 with integer instructions: with alpha = 1 and beta = 0 the epilogue
-    // issues no float64 operation.  Each warp stages 32 rows x 8 columns in shared memory and
+    // fp32 add each) are combined into one 64-bit integer V, the segment's product being
+    // 2^(e_i + f_j - 56) V, rounded to float64 with integer instructions: with alpha = 1 and
+    // beta = 0 the epilogue issues no float64 operation.  Each warp stages 32 rows x 8 columns in shared memory and
     // writes them row-wise (coalesced).
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
@@ -366,19 +364,19 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
           tmem_ld_wait();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            const long long hi = (long long)oz_level_int(a[0][c]) * 2097152 +
-                                 (long long)oz_level_int(a[1][c]) * 16384 +
-                                 (long long)oz_level_int(a[2][c]) * 128 + (long long)oz_level_int(a[3][c]);
-            const long long lo = (long long)oz_level_int(a[4][c]) * 2097152 +
-                                 (long long)oz_level_int(a[5][c]) * 16384 +
-                                 (long long)oz_level_int(a[6][c]) * 128 + (long long)oz_level_int(a[7][c]);
+            // one 64-bit integer in units of 2^-56 of the scaled product,
+            // V = sum_L S_L 2^(42 - 7 L) with floor(S_7 / 2^7) (|V| < 2^62; the floor drops
+            // less than 2^-56 of the row scales' product), rounded to float64 with integer
+            // instructions
+            const long long V = ((long long)oz_level_int(a[0][c]) << 42) + ((long long)oz_level_int(a[1][c]) << 35) +
+                                ((long long)oz_level_int(a[2][c]) << 28) + ((long long)oz_level_int(a[3][c]) << 21) +
+                                ((long long)oz_level_int(a[4][c]) << 14) + ((long long)oz_level_int(a[5][c]) << 7) +
+                                (long long)oz_level_int(a[6][c]) + (long long)(oz_level_int(a[7][c]) >> 7);
             const int j = col0 + ch * 8 + c;
             const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
-            // one 64-bit integer, hi 2^20 + floor(lo / 2^8) < 2^63 (the dropped bits are below
-            // 2^-55 of |A|row |B|row), rounded to float64 with integer instructions
             stg[lane * 9 + c] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
                                     ? __longlong_as_double(0x7ff8000000000000ll)   // NaN, as in float64
-                                    : oz_i64_times_pow2(hi * 1048576ll + (lo >> 8), ei + fj - 55);
+                                    : oz_i64_times_pow2(V, ei + fj - 56);
           }
           __syncwarp();
 #pragma unroll

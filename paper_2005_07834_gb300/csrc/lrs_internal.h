@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lrs.h"
@@ -49,6 +50,24 @@ void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes);
 void dev_free_temp(lrs_ctx* ctx, void* p, size_t bytes);
 // Drops the recorded multi-site graph, if any.
 void drop_graph(lrs_ctx* ctx);
+
+// Launches `kernel` with a launch priority attribute, which (unlike the priority
+// of the stream) is kept by the node when the launch is recorded in a CUDA graph.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_with_priority(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 int priority, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = priority;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <typename T>
 int ensure(lrs_ctx* ctx, DevBuf<T>& b, size_t count) {

@@ -287,17 +287,21 @@ class Screening:
         n, p, _keep = self._sites(sites)
         _check(lrs_solve_w(self.ctx, n, p), "lrs_solve_w")
 
-    def _get(self, fn, site, name):
+    def _get(self, fn, site, name, out=None):
         n = self.npts[site]
-        out = np.empty((n, n))
+        if out is None:
+            out = np.empty((n, n))
+        elif out.shape != (n, n) or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"{name}: out must be a C-contiguous float64 array of shape ({n}, {n})")
         _check(fn(self.ctx, int(site), _dp(out)), name)
         return out
 
-    def get_chi0(self, site=0):
-        return self._get(lrs_get_chi0, site, "lrs_get_chi0")
+    def get_chi0(self, site=0, out=None):
+        return self._get(lrs_get_chi0, site, "lrs_get_chi0", out)
 
-    def get_w(self, site=0):
-        return self._get(lrs_get_w, site, "lrs_get_w")
+    def get_w(self, site=0, out=None):
+        """W of a site into a new array, or into `out` (e.g. pinned host memory)."""
+        return self._get(lrs_get_w, site, "lrs_get_w", out)
 
     def get_v(self, site=0):
         return self._get(lrs_get_v, site, "lrs_get_v")
