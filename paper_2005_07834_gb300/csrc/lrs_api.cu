@@ -220,7 +220,10 @@ static bool finite_all(const double* p, size_t n) {
 
 // Gamma-point real orbitals (Sec. VI.F): one k-point at k = 0 and, for every
 // G, -G in the set with C_b(-G) = conj C_b(G) (to 1e-12 of the largest |C|).
-static bool orbitals_are_real(int nk, const double* kpts, int ng, const int* gvec, int nb, const double* coeff) {
+// Gamma-point real orbitals (Sec. VI.F): one k-point at Gamma and C(-G) = conj C(G) for every
+// band and G (to 1e-12 of the largest coefficient component).  The host pairs each G with -G
+// (false if a partner is missing); the device compares the coefficients.
+static bool gamma_partners(int nk, const double* kpts, int ng, const int* gvec, std::vector<int>& partner) {
   if (nk != 1 || kpts[0] != 0.0 || kpts[1] != 0.0 || kpts[2] != 0.0) return false;
   auto key = [](int a, int b, int c) {
     return ((long long)(a + (1 << 20)) << 42) | ((long long)(b + (1 << 20)) << 21) | (long long)(c + (1 << 20));
@@ -228,18 +231,36 @@ static bool orbitals_are_real(int nk, const double* kpts, int ng, const int* gve
   std::unordered_map<long long, int> index;
   index.reserve((size_t)ng * 2);
   for (int g = 0; g < ng; ++g) index[key(gvec[3 * g], gvec[3 * g + 1], gvec[3 * g + 2])] = g;
-  double cmax = 0.0;
-  for (size_t i = 0; i < 2 * (size_t)ng * nb; ++i) cmax = std::max(cmax, std::fabs(coeff[i]));
-  const double tol = 1e-12 * cmax;
+  partner.resize(ng);
   for (int g = 0; g < ng; ++g) {
     const auto it = index.find(key(-gvec[3 * g], -gvec[3 * g + 1], -gvec[3 * g + 2]));
     if (it == index.end()) return false;
-    const double* a = coeff + 2 * (size_t)g * nb;
-    const double* b = coeff + 2 * (size_t)it->second * nb;
-    for (int k = 0; k < nb; ++k)
-      if (std::fabs(a[2 * k] - b[2 * k]) > tol || std::fabs(a[2 * k + 1] + b[2 * k + 1]) > tol) return false;
+    partner[g] = it->second;
   }
   return true;
+}
+
+// Largest |Re| or |Im| of n complex values as float64 bits (non-negative doubles order as
+// their bit patterns).
+__global__ void coeff_absmax_kernel(const double2* __restrict__ c, size_t n, unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fmax(fabs(c[i].x), fabs(c[i].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// bad = 1 if some C(G, b) differs from conj C(-G, b) by more than 1e-12 of the largest component.
+__global__ void gamma_real_check_kernel(const double2* __restrict__ c, const int* __restrict__ partner, int ng,
+                                        int nb, const unsigned long long* __restrict__ maxbits,
+                                        int* __restrict__ bad) {
+  const double tol = 1e-12 * __longlong_as_double((long long)*maxbits);
+  const size_t n = (size_t)ng * nb;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i / nb), b = (int)(i % nb);
+    const double2 x = c[i], y = c[(size_t)partner[g] * nb + b];
+    if (fabs(x.x - y.x) > tol || fabs(x.y + y.y) > tol) *bad = 1;
+  }
 }
 
 static int check_site(lrs_ctx* ctx, int site) {
@@ -486,7 +507,9 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   ctx->energies.assign(energies, energies + (size_t)nk * nbands);
   ctx->gvec.assign(gvec, gvec + 3 * (size_t)ng);
   ctx->ws.fft_plan_ok = false;   // the FFT index tables follow the G set
-  ctx->real_orbitals = orbitals_are_real(nk, kpts, ng, gvec, nbands, coeff);
+  std::vector<int> partner;
+  const bool gamma_candidate = gamma_partners(nk, kpts, ng, gvec, partner);
+  ctx->real_orbitals = false;
   for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = 0;
   for (int gi = 0; gi < ng; ++gi)
     for (int i = 0; i < 3; ++i) ctx->gmax_idx[i] = std::max(ctx->gmax_idx[i], std::abs(gvec[3 * gi + i]));
@@ -507,6 +530,31 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   LRS_TRY(ensure(ctx, ctx->w_o, Ko)); LRS_TRY(ensure(ctx, ctx->w_u, Ku));
   LRS_TRY(ensure(ctx, ctx->d_col_o, Ko)); LRS_TRY(ensure(ctx, ctx->d_col_u, Ku));
   LRS_CUDA_TRY(cudaMemcpyAsync(ctx->coeff.ptr, coeff, ncoef * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+  if (gamma_candidate) {
+    // scratch: partner [ng] ints, then the max bits and the flag
+    DevBuf<int> tmp;
+    const size_t words = (size_t)ng + 6;
+    LRS_TRY(ensure(ctx, tmp, words));
+    int* d_partner = tmp.ptr;
+    unsigned long long* d_max = reinterpret_cast<unsigned long long*>(tmp.ptr + ((ng + 1) & ~1));
+    int* d_bad = tmp.ptr + ((ng + 1) & ~1) + 2;
+    int rc = LRS_OK;
+    int bad = 1;
+    cudaError_t e = cudaMemcpyAsync(d_partner, partner.data(), ng * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_max, 0, 4 * sizeof(int), ctx->stream);
+    if (e == cudaSuccess) {
+      coeff_absmax_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->coeff.ptr, ncoef, d_max);
+      gamma_real_check_kernel<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->coeff.ptr, d_partner, ng, nbands,
+                                                                           d_max, d_bad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = set_error(LRS_ERR_CUDA, "Gamma-point check: %s", cudaGetErrorString(e));
+    dev_free_temp(ctx, tmp.ptr, words * sizeof(int));
+    if (rc != LRS_OK) return rc;
+    ctx->real_orbitals = bad == 0;
+  }
   LRS_CUDA_TRY(cudaMemcpyAsync(ctx->d_gvec.ptr, gvec, 3 * (size_t)ng * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   LRS_CUDA_TRY(cudaMemcpyAsync(ctx->d_kpts.ptr, kpts, 3 * (size_t)nk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   LRS_CUDA_TRY(cudaMemcpyAsync(ctx->e_o.ptr, eo.data(), Ko * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
