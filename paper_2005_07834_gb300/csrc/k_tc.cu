@@ -137,16 +137,27 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
 }
 
 // chi0 = (2/pi) sum_f W_f (X_f + X_f^T) / (scales[f] scales[nf])^2, float64 accumulation.
+// The result is symmetric: one CTA per pair of 32 x 32 tiles (bi <= bj) reads tiles (bi, bj) and
+// (bj, bi) of every frequency once, accumulates their symmetric sum once and writes both output
+// tiles (the transposed one through shared memory), so that each slab element is read once and
+// each float64 accumulation is done once.
 __global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf, const double* __restrict__ Wf,
                                    const float* __restrict__ scales, int n, double* __restrict__ chi0) {
   __shared__ float t[32][33];
+  __shared__ double o[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int r0 = bi * 32, c0 = bj * 32;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int f = 0; f < nf; ++f) {
     const float* s = slab + (size_t)f * Np * Np;
+    float direct[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) t[ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
+    for (int i = 0; i < 4; ++i) {
+      t[ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
+      direct[i] = s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
+    }
     __syncthreads();
     double w = Wf[f];
     if (scales) {
@@ -154,17 +165,23 @@ __global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int n
       w /= sc * sc;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float direct = s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
-      acc[i] = fma(w, (double)(direct + t[tx][ty + 8 * i]), acc[i]);
-    }
+    for (int i = 0; i < 4; ++i) acc[i] = fma(w, (double)(direct[i] + t[tx][ty + 8 * i]), acc[i]);
     __syncthreads();
   }
   const double c = 0.63661977236758134308;   // 2/pi
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = r0 + ty + 8 * i, q = c0 + tx;
-    if (r < n && q < n) chi0[(size_t)r * n + q] = c * acc[i];
+    const double v = c * acc[i];
+    if (r < n && q < n) chi0[(size_t)r * n + q] = v;
+    o[ty + 8 * i][tx] = v;
+  }
+  if (bi == bj) return;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = c0 + ty + 8 * i, q = r0 + tx;   // output tile (bj, bi): element (q', r') of o transposed
+    if (r < n && q < n) chi0[(size_t)r * n + q] = o[tx][ty + 8 * i];
   }
 }
 
