@@ -98,12 +98,30 @@ __global__ void chi0_scales_kernel(const double2* __restrict__ d_o, int Ko, cons
 // Planes: [2 (re, im)][rows][2*Kp] with rows = Np (B) or nf*Np (A).  `scales`
 // (NULL = 1) multiplies the A planes of frequency f by scales[f] and the B
 // planes by scales[nf].
+// The denominators of the A planes in fp32, dtab[f][k] = d_f(k) scales[f] (0 on padded
+// columns), formed once per launch: GB300 converts float64 at the FP64 rate, so converting them
+// per grid point (N times) dominated the operand preparation.
+__global__ void denom32_kernel(const double2* __restrict__ d_o, int Ko, const double2* __restrict__ d_u, int Ku,
+                               int Kop, int Kp, int nf, const float* __restrict__ scales, float2* __restrict__ dtab) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (k >= Kp) return;
+  const bool occ = k < Kop;
+  const int kk = occ ? k : k - Kop;
+  float2 v = make_float2(0.f, 0.f);
+  if (occ ? kk < Ko : kk < Ku) {
+    const double2 d = occ ? d_o[(size_t)f * Ko + kk] : d_u[(size_t)f * Ku + kk];
+    const float sa = scales ? scales[f] : 1.f;
+    v = make_float2((float)d.x * sa, (float)d.y * sa);
+  }
+  dtab[(size_t)f * Kp + k] = v;
+}
+
 template <uint32_t FMT>
 __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, const double2* __restrict__ psi_u,
-                                 int Ku, int n, int Np, int Kop, int Kp, const double2* __restrict__ d_o,
-                                 const double2* __restrict__ d_u, int nf, const float* __restrict__ scales,
-                                 uint16_t* __restrict__ A, size_t aplane, uint16_t* __restrict__ B,
-                                 size_t bplane) {
+                                 int Ku, int n, int Np, int Kop, int Kp, const float2* __restrict__ dtab, int nf,
+                                 const float* __restrict__ scales, uint16_t* __restrict__ A, size_t aplane,
+                                 uint16_t* __restrict__ B, size_t bplane) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (k >= Kp || p >= Np) return;
@@ -124,11 +142,9 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
   for (int f = 0; f < nf; ++f) {
     float ar = 0.f, ai = 0.f;
     if (live) {
-      const double2 d = occ ? d_o[(size_t)f * Ko + kk] : d_u[(size_t)f * Ku + kk];
-      const float sa = scales ? scales[f] : 1.f;
-      const float dr = (float)d.x * sa, di = (float)d.y * sa;
-      ar = cr * dr - ci * di;
-      ai = cr * di + ci * dr;
+      const float2 d = dtab[(size_t)f * Kp + k];
+      ar = cr * d.x - ci * d.y;
+      ai = cr * d.y + ci * d.x;
     }
     const size_t row = (size_t)f * Np + p;
     put_split<FMT>(A + row * ld, k, ar);
@@ -324,11 +340,15 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
                                                        nf, pmax, scales);
       LRS_TRY(after_launch(ctx, "chi0_scales_kernel"));
     }
+    LRS_TRY(ensure(ctx, ctx->ws.denom32, (size_t)nf * Kp));
+    denom32_kernel<<<dim3((Kp + 255) / 256, nf), 256, 0, ctx->stream>>>(
+        ctx->ws.denom_o.ptr, ctx->Ko, ctx->ws.denom_u.ptr, ctx->Ku, Kop, Kp, nf, scales, ctx->ws.denom32.ptr);
+    LRS_TRY(after_launch(ctx, "denom32_kernel"));
     dim3 pg((Kp + 127) / 128, t.np);
     chi0_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(
-        s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku, n, t.np, Kop, Kp, ctx->ws.denom_o.ptr, ctx->ws.denom_u.ptr, nf,
-        scales, ctx->ws.planes_a.ptr + (size_t)t.a_row0 * ld, (size_t)ra * ld,
-        ctx->ws.planes_b.ptr + (size_t)t.b_row0 * ld, (size_t)rb * ld);
+        s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku, n, t.np, Kop, Kp, ctx->ws.denom32.ptr, nf, scales,
+        ctx->ws.planes_a.ptr + (size_t)t.a_row0 * ld, (size_t)ra * ld, ctx->ws.planes_b.ptr + (size_t)t.b_row0 * ld,
+        (size_t)rb * ld);
     LRS_TRY(after_launch(ctx, "chi0_prep_kernel"));
   }
   CUtensorMap ma, mb;
@@ -599,9 +619,13 @@ int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w, const doubl
   LRS_CUDA_TRY(cudaMemsetAsync(ws.gpsi.ptr, 0, (size_t)n * K * sizeof(double2), ctx->stream));
   LRS_CUDA_TRY(cudaMemsetAsync(ws.ge.ptr, 0, (size_t)K * sizeof(double), ctx->stream));
   // operands of the Green's functions (all frequencies) and of the Y/Z products
+  LRS_TRY(ensure(ctx, ws.denom32, (size_t)nf * Kp));
+  denom32_kernel<<<dim3((Kp + 255) / 256, nf), 256, 0, ctx->stream>>>(ws.denom_o.ptr, Ko, ws.denom_u.ptr, Ku, Kop,
+                                                                       Kp, nf, nullptr, ws.denom32.ptr);
+  LRS_TRY(after_launch(ctx, "denom32_kernel"));
   dim3 pg((Kp + 127) / 128, Np);
   chi0_prep_kernel<1><<<pg, 128, 0, ctx->stream>>>(s.psi_o.ptr, Ko, s.psi_u.ptr, Ku, n, Np, Kop, Kp,
-                                                    ws.denom_o.ptr, ws.denom_u.ptr, nf, nullptr, ws.planes_a.ptr,
+                                                    ws.denom32.ptr, nf, nullptr, ws.planes_a.ptr,
                                                     (size_t)nf * Np * ldg, ws.planes_b.ptr, (size_t)Np * ldg);
   LRS_TRY(after_launch(ctx, "chi0_prep_kernel"));
   dim3 tg(Np / 32, std::max(Ko128, Ku128) / 32, 2);
