@@ -231,9 +231,15 @@ __global__ void coeff_prep_kernel(const double2* __restrict__ coeff, int ng, int
   }
 }
 
+// The phase tables in fp32 (converted once: GB300 converts float64 at the FP64 rate).
+__global__ void tab32_kernel(const double2* __restrict__ tab, size_t n, float2* __restrict__ out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)tab[i].x, (float)tab[i].y);
+}
+
 // Projection A operand: e^{i G.R_p} = T1 T2 T3 (times `scale`) -> planes [2][Np][2*NGp].
 template <uint32_t FMT>
-__global__ void phase_prep_kernel(const double2* __restrict__ tab, int npts, int3 nmax, int off1, int off2,
+__global__ void phase_prep_kernel(const float2* __restrict__ tab, int npts, int3 nmax, int off1, int off2,
                                   const int* __restrict__ gvec, int ng, int Np, int NGp, float scale,
                                   uint16_t* __restrict__ A, size_t im_off) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,12 +248,12 @@ __global__ void phase_prep_kernel(const double2* __restrict__ tab, int npts, int
   float re = 0.f, im = 0.f;
   if (g < ng && p < npts) {
     const int w1 = 2 * nmax.x + 1, w2 = 2 * nmax.y + 1, w3 = 2 * nmax.z + 1;
-    const double2 t1 = tab[(size_t)p * w1 + gvec[3 * g] + nmax.x];
-    const double2 t2 = tab[off1 + (size_t)p * w2 + gvec[3 * g + 1] + nmax.y];
-    const double2 t3 = tab[off2 + (size_t)p * w3 + gvec[3 * g + 2] + nmax.z];
-    const float ar = (float)t1.x, ai = (float)t1.y, br = (float)t2.x, bi = (float)t2.y;
+    const float2 t1 = tab[(size_t)p * w1 + gvec[3 * g] + nmax.x];
+    const float2 t2 = tab[off1 + (size_t)p * w2 + gvec[3 * g + 1] + nmax.y];
+    const float2 t3 = tab[off2 + (size_t)p * w3 + gvec[3 * g + 2] + nmax.z];
+    const float ar = t1.x, ai = t1.y, br = t2.x, bi = t2.y;
     const float cr = ar * br - ai * bi, ci = ar * bi + ai * br;
-    const float dr = (float)t3.x, di = (float)t3.y;
+    const float dr = t3.x, di = t3.y;
     re = (cr * dr - ci * di) * scale;
     im = (cr * di + ci * dr) * scale;
   }
@@ -421,8 +427,13 @@ int project_mixed(lrs_ctx* ctx, Site& s) {
   LRS_TRY(phase_setup(ctx, s, &off1, &off2));
   LRS_TRY(ensure(ctx, ctx->ws.proj_a, 2 * (size_t)Np * ld));
   const int* nm = ctx->gmax_idx;
+  const size_t n_tab = (size_t)n * ((2 * nm[0] + 1) + (2 * nm[1] + 1) + (2 * nm[2] + 1));
+  LRS_TRY(ensure(ctx, ctx->ws.phase_tab32, n_tab));
+  tab32_kernel<<<(unsigned)((n_tab + 255) / 256), 256, 0, ctx->stream>>>(ctx->ws.phase_tab.ptr, n_tab,
+                                                                          ctx->ws.phase_tab32.ptr);
+  LRS_TRY(after_launch(ctx, "tab32_kernel"));
   dim3 pg((NGp + 127) / 128, Np);
-  phase_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(ctx->ws.phase_tab.ptr, n, make_int3(nm[0], nm[1], nm[2]),
+  phase_prep_kernel<FMT><<<pg, 128, 0, ctx->stream>>>(ctx->ws.phase_tab32.ptr, n, make_int3(nm[0], nm[1], nm[2]),
                                                        off1, off2, ctx->d_gvec.ptr, ctx->ng, Np, NGp, PHASE_SCALE,
                                                        ctx->ws.proj_a.ptr, (size_t)Np * ld);
   LRS_TRY(after_launch(ctx, "phase_prep_kernel"));

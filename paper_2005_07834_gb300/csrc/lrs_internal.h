@@ -161,6 +161,7 @@ struct Workspace {
   DevBuf<uint16_t> planes_a, planes_b;  // chi0: per-frequency A, frequency-independent B
   DevBuf<float> slab;                   // chi0: [nf][Np][Np] fp32 Re[Go o Gu^T] per frequency
   DevBuf<float2> denom32;               // chi0: [nf][Kp] scaled fp32 denominators of the A planes
+  DevBuf<float2> phase_tab32;           // projection: fp32 copy of the phase tables
   DevBuf<float> tc_scratch;             // chi0: per-CTA parked occupied sums
   DevBuf<double> slab64;                // FP64 chi0: [nf][n][n] per-frequency W_f Re[Go o Gu^T]
   DevBuf<SiteTile> site_tiles;          // multi-site chi0 unit table
