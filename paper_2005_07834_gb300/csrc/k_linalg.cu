@@ -707,16 +707,20 @@ constexpr int GJ_PR = 256 / GJ_NB;       // row groups of the 256-thread pivot a
 // rows of block kp, where the exchange itself writes D_p (read here from D_p,
 // so the gather does not wait for gj_fix_kernel).  Block k of A is rewritten
 // by its own exchange, so the updated values are not stored.
-// GJ_GR rows per CTA, one warp per row (lane = column in the block).
+// GJ_GR rows per CTA, one warp per row (lane = column in the block); the CTAs
+// cover rows row_base + GJ_GR blockIdx.x, and groups starting in [skip_lo,
+// skip_hi) are left out (ranges are multiples of GJ_GR, or end at n).
 constexpr int GJ_GR = 8;
 __global__ void __launch_bounds__(256) gj_gather_kernel(const double* __restrict__ A, int n, int lda, int k0, int kb,
                                                         const double* __restrict__ Dp, const double* __restrict__ Ep,
                                                         int kp0, int kpb, double* __restrict__ C,
                                                         double* __restrict__ E, uint16_t* __restrict__ eplanes,
-                                                        size_t plane_stride, int* __restrict__ eexp) {
+                                                        size_t plane_stride, int* __restrict__ eexp, int row_base,
+                                                        int skip_lo, int skip_hi) {
   __shared__ double dr[GJ_GR][GJ_NB + 1], er[GJ_GR][GJ_NB + 1];   // D_p, E_p rows of this CTA's rows
   __shared__ double dk[GJ_NB][GJ_NB + 1], ek[GJ_NB][GJ_NB + 1];   // D_p, E_p rows of block k
-  const int i0 = blockIdx.x * GJ_GR;
+  const int i0 = row_base + blockIdx.x * GJ_GR;
+  if (i0 >= skip_lo && i0 < skip_hi) return;   // the whole CTA, before any barrier
   const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
   if (Dp) {
     for (int idx = threadIdx.x; idx < GJ_GR * GJ_NB; idx += blockDim.x) {
@@ -826,15 +830,18 @@ __global__ void __launch_bounds__(256) gj_pivot_kernel(const double* __restrict_
   }
 }
 
-// D = C Pinv (n x kb), 8 rows per CTA so that every SM takes part.
+// D = C Pinv (n x kb), 8 rows per CTA so that every SM takes part; rows as in
+// gj_gather_kernel (row_base, groups starting in [skip_lo, skip_hi) left out).
 constexpr int GJ_DR = 8;
 __global__ void __launch_bounds__(256) gj_apply_kernel(const double* __restrict__ C, int n, int kb,
                                                        const double* __restrict__ Pinv, double* __restrict__ D,
                                                        uint16_t* __restrict__ dplanes, size_t plane_stride,
-                                                       int* __restrict__ dexp) {
+                                                       int* __restrict__ dexp, int row_base, int skip_lo,
+                                                       int skip_hi) {
   __shared__ double pv[GJ_NB][GJ_NB + 1];
   __shared__ double cr[GJ_DR][GJ_NB + 1];
-  const int r0 = blockIdx.x * GJ_DR;
+  const int r0 = row_base + blockIdx.x * GJ_DR;
+  if (r0 >= skip_lo && r0 < skip_hi) return;   // the whole CTA, before any barrier
   // zero beyond kb, so that the product can run over all GJ_NB terms
   for (int idx = threadIdx.x; idx < GJ_NB * GJ_NB; idx += blockDim.x) {
     const int i = idx / GJ_NB, j = idx % GJ_NB;
@@ -952,21 +959,32 @@ __global__ void __launch_bounds__(128) gj_update_kernel(double* __restrict__ A, 
   }
 }
 
-// Schedule: the bulk of the trailing update of block k (every tile away from
-// blocks k and k + 1) runs on the context stream while a second, higher
-// priority stream prepares the next panel (gather with the update of block k
-// applied on the fly, pivot inverse, D) in the other of two buffer sets, and
-// a third writes the exchanged block k into A (fix).  The serial pivot inverse
-// (one SM) thereby overlaps the bulk update.  Events: panel k ready -> fix k;
-// panel k + 1 and fix k done -> bulk k + 1; bulk k done -> panel k + 2 (its
-// block and its buffer set are touched by bulk k).
+// Schedule.  Streams: s1 (the context stream) runs the bulk of each trailing
+// update (every tile away from blocks p and p + 1); three side streams of
+// higher priority prepare the panels in two alternating buffer sets.  Panel p
+// on rows R_p = [32 p, 32 p + kb):
+//   s2: gather of rows R_p -> 32 x 32 pivot inverse -> D_p on rows R_{p+1}
+//       (all that the next gather of the diagonal block needs): the chain of
+//       dependent steps, kept as short as possible;
+//   s4: gather of the other rows -> D_p on the other rows;
+//   s3: write-back of the exchanged block p (fix).
+// Events (pairs alternate with the block parity):
+//   gather R_p        <- D_{p-1} on R_p (s2 order), gather rest p-1, bulk p-2, fix p-2 (buffer set);
+//   gather rest p     <- D_{p-1} rest (s4 order), D_{p-1} on R_p, bulk p-2;
+//   D_p on R_{p+1}    <- pivot p (s2 order), gather rest p;
+//   D_p rest          <- gather rest p (s4 order), pivot p;
+//   fix p, bulk p     <- both parts of D_p; bulk p also <- fix p-1.
+// The serial pivot inverse (one SM) thereby overlaps the bulk update and the
+// row-parallel parts of the panels.
 int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
   static_assert(GJ_NB % UT == 0 && GJ_TB >= 1, "a pivot block spans whole update tiles");
+  static_assert(GJ_NB % GJ_GR == 0 && GJ_GR == GJ_DR, "row groups of the gather and apply kernels tile a block");
   if (n <= 0) return LRS_OK;
   const size_t set = 3 * (size_t)n * GJ_NB + GJ_NB * GJ_NB;
   LRS_TRY(ensure(ctx, ctx->ws.gj, 2 * set));
   LRS_TRY(aux_stream_ready(ctx));
-  cudaStream_t s1 = ctx->stream, s2 = ctx->aux_stream, s3 = ctx->aux_stream2;
+  SpdStreams& sp = ctx->spd;
+  cudaStream_t s1 = ctx->stream, s2 = sp.s2, s3 = sp.s3, s4 = sp.s4;
   double *Cb[2], *Eb[2], *Db[2], *Pb[2];
   for (int q = 0; q < 2; ++q) {
     Cb[q] = ctx->ws.gj.ptr + q * set;
@@ -981,6 +999,7 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
                   (ctx->dyson_update == LRS_UPDATE_AUTO && ctx->precision != LRS_FP64);
   const int rows_pad = oz_rows_pad(n);
   const size_t pe = oz_plane_elems(n);
+  const size_t stride = (size_t)rows_pad * 64;
   uint16_t* dpl[2] = {nullptr, nullptr};
   uint16_t* epl[2] = {nullptr, nullptr};
   int* dsc[2] = {nullptr, nullptr};
@@ -999,40 +1018,73 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     // rows beyond n stay zero; rows below n are rewritten by every panel
     LRS_CUDA_TRY(cudaMemsetAsync(ctx->ws.oz_planes.ptr, 0, 4 * pe * sizeof(uint16_t), s1));
   }
-  auto panel = [&](int kb_idx, int q) -> int {
-    const int k0 = kb_idx * GJ_NB, kb = std::min(GJ_NB, n - k0);
-    const size_t stride = (size_t)rows_pad * 64;
-    // the exchange of the previous block (buffer set q ^ 1) is applied to block kb_idx here
-    const int qp = q ^ 1, kp0 = k0 - GJ_NB;
-    const bool prev = kb_idx > 0;
-    // the side-chain kernels carry the highest launch priority, also as nodes of a recorded graph
-    const int pr = ctx->prio_greatest;
+  auto ev = [&](int base, int p) { return sp.ev[base + (p & 1)]; };
+  auto wait = [&](cudaStream_t st, int base, int p) { return cudaStreamWaitEvent(st, ev(base, p), 0); };
+  auto record = [&](cudaStream_t st, int base, int p) { return cudaEventRecord(ev(base, p), st); };
+  const int pr = ctx->prio_greatest;   // side-chain launches: highest priority, also as graph nodes
+  auto rows_of = [&](int p, int& lo, int& hi) {   // rows of block p ([0, 0) beyond the last block)
+    lo = p < nblk ? p * GJ_NB : 0;
+    hi = p < nblk ? std::min(n, lo + GJ_NB) : 0;
+  };
+  auto gather = [&](int p, cudaStream_t st, int row_base, int nrows, int skip_lo, int skip_hi) -> int {
+    const int q = p & 1, qp = q ^ 1, k0 = p * GJ_NB, kb = std::min(GJ_NB, n - k0);
+    const bool prev = p > 0;   // the exchange of block p - 1 is applied to block p on the fly
     const double* dprev = prev ? Db[qp] : nullptr;
     const double* eprev = prev ? Eb[qp] : nullptr;
-    LRS_CUDA_TRY(launch_with_priority(gj_gather_kernel, dim3((n + GJ_GR - 1) / GJ_GR), dim3(256), 0, s2, pr,
-                                      (const double*)A, n, lda, k0, kb, dprev, eprev, kp0, (int)GJ_NB, Cb[q], Eb[q],
-                                      epl[q], stride, esc[q]));
-    LRS_TRY(after_launch(ctx, "gj_gather_kernel"));
-    if (prev) ctx->fp64_flops += 2.0 * n * kb * GJ_NB;
+    LRS_CUDA_TRY(launch_with_priority(gj_gather_kernel, dim3((nrows + GJ_GR - 1) / GJ_GR), dim3(256), 0, st, pr,
+                                      (const double*)A, n, lda, k0, kb, dprev, eprev, k0 - GJ_NB, (int)GJ_NB, Cb[q],
+                                      Eb[q], epl[q], stride, esc[q], row_base, skip_lo, skip_hi));
+    return after_launch(ctx, "gj_gather_kernel");
+  };
+  auto apply = [&](int p, cudaStream_t st, int row_base, int nrows, int skip_lo, int skip_hi) -> int {
+    const int q = p & 1, k0 = p * GJ_NB, kb = std::min(GJ_NB, n - k0);
+    if (nrows <= 0) return LRS_OK;
+    LRS_CUDA_TRY(launch_with_priority(gj_apply_kernel, dim3((nrows + GJ_DR - 1) / GJ_DR), dim3(256), 0, st, pr,
+                                      (const double*)Cb[q], n, kb, (const double*)Pb[q], Db[q], dpl[q], stride,
+                                      dsc[q], row_base, skip_lo, skip_hi));
+    return after_launch(ctx, "gj_apply_kernel");
+  };
+  auto panel = [&](int p) -> int {
+    const int q = p & 1, k0 = p * GJ_NB, kb = std::min(GJ_NB, n - k0);
+    int lo, hi, nlo, nhi;
+    rows_of(p, lo, hi);
+    rows_of(p + 1, nlo, nhi);
+    // s2: the diagonal block and its inverse
+    if (p >= 2) {
+      LRS_CUDA_TRY(wait(s2, SPD_BULK, p - 2));
+      LRS_CUDA_TRY(wait(s2, SPD_FIX, p - 2));
+    }
+    LRS_TRY(gather(p, s2, lo, hi - lo, 0, 0));
     LRS_CUDA_TRY(launch_with_priority(gj_pivot_kernel, dim3(1), dim3(256), 0, s2, pr, (const double*)Cb[q], k0, kb,
                                       Pb[q], status));
     LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
-    LRS_CUDA_TRY(launch_with_priority(gj_apply_kernel, dim3((n + GJ_DR - 1) / GJ_DR), dim3(256), 0, s2, pr,
-                                      (const double*)Cb[q], n, kb, (const double*)Pb[q], Db[q], dpl[q], stride,
-                                      dsc[q]));
-    LRS_TRY(after_launch(ctx, "gj_apply_kernel"));
+    LRS_CUDA_TRY(record(s2, SPD_PIVOT, p));
+    // s4: the other rows of the panel, then their D
+    if (p >= 1) LRS_CUDA_TRY(wait(s4, SPD_ADIAG, p - 1));
+    if (p >= 2) LRS_CUDA_TRY(wait(s4, SPD_BULK, p - 2));
+    LRS_TRY(gather(p, s4, 0, n, lo, hi));
+    LRS_CUDA_TRY(record(s4, SPD_GREST, p));
+    LRS_CUDA_TRY(wait(s4, SPD_PIVOT, p));
+    LRS_TRY(apply(p, s4, 0, n, nlo, nhi));
+    LRS_CUDA_TRY(record(s4, SPD_AREST, p));
+    // s2: D on the rows of the next block
+    LRS_CUDA_TRY(wait(s2, SPD_GREST, p));
+    LRS_TRY(apply(p, s2, nlo, nhi - nlo, 0, 0));
+    LRS_CUDA_TRY(record(s2, SPD_ADIAG, p));
+    if (p > 0) ctx->fp64_flops += 2.0 * n * kb * GJ_NB;
     ctx->fp64_flops += 2.0 * n * kb * kb;
     return LRS_OK;
   };
-  // fork the second stream from the context stream (also inside a graph capture)
-  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fork, s1));
-  LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
-  LRS_TRY(panel(0, 0));
-  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_panel, s2));
+  // fork the side streams from the context stream (also inside a graph capture)
+  LRS_CUDA_TRY(cudaEventRecord(sp.ev[SPD_FORK], s1));
+  for (cudaStream_t st : {s2, s3, s4}) LRS_CUDA_TRY(cudaStreamWaitEvent(st, sp.ev[SPD_FORK], 0));
+  LRS_TRY(panel(0));
   for (int k = 0; k < nblk; ++k) {
     const int q = k & 1, k0 = k * GJ_NB, kb = std::min(GJ_NB, n - k0);
     // bulk of the trailing update on the context stream
-    LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_panel, 0));
+    LRS_CUDA_TRY(wait(s1, SPD_ADIAG, k));
+    LRS_CUDA_TRY(wait(s1, SPD_AREST, k));
+    if (k >= 1) LRS_CUDA_TRY(wait(s1, SPD_FIX, k - 1));   // bulk k updates block k - 1, just written back
     LRS_TRY(stage_begin(ctx, ST_W_MAIN));
     if (tc) {
       LRS_TRY(oz_update(ctx, md[q], me[q], A, n, lda, dsc[q], esc[q], k0, std::min(n, k0 + 2 * GJ_NB), rows_pad,
@@ -1051,30 +1103,21 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
       ++ctx->w_main_launches;
     }
     if (!tc) ctx->fp64_flops += (double)n * n * kb;
-    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_bulk, s1));
-    // exchange of block k on the third stream (after panel k, which s2 has finished
-    // enqueueing), next panel on the second
-    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fork, s2));
-    LRS_CUDA_TRY(cudaStreamWaitEvent(s3, ctx->ev_fork, 0));
-    LRS_CUDA_TRY(launch_with_priority(gj_fix_kernel, dim3(nblk), dim3(256), 0, s3, ctx->prio_greatest, A, n, lda,
-                                      k0, kb, (const double*)Db[q], (const double*)Pb[q]));
+    LRS_CUDA_TRY(record(s1, SPD_BULK, k));
+    // write-back of the exchanged block k on the third stream
+    LRS_CUDA_TRY(wait(s3, SPD_ADIAG, k));
+    LRS_CUDA_TRY(wait(s3, SPD_AREST, k));
+    LRS_CUDA_TRY(launch_with_priority(gj_fix_kernel, dim3(nblk), dim3(256), 0, s3, pr, A, n, lda, k0, kb,
+                                      (const double*)Db[q], (const double*)Pb[q]));
     LRS_TRY(after_launch(ctx, "gj_fix_kernel"));
-    LRS_CUDA_TRY(cudaEventRecord(ctx->ev_fix, s3));
-    if (k + 1 < nblk) {
-      // buffer set q ^ 1 was last read by bulk k - 1, which s2 has waited for
-      LRS_TRY(panel(k + 1, q ^ 1));
-      // bulk k + 1 updates block k, which the exchange has just written
-      LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_fix, 0));
-      LRS_CUDA_TRY(cudaEventRecord(ctx->ev_panel, s2));
-      // block k + 2 and set q are touched by bulk k: wait for it
-      LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_bulk, 0));
-    } else {
-      LRS_CUDA_TRY(cudaStreamWaitEvent(s2, ctx->ev_fix, 0));
-    }
+    LRS_CUDA_TRY(record(s3, SPD_FIX, k));
+    if (k + 1 < nblk) LRS_TRY(panel(k + 1));
   }
-  // join
-  LRS_CUDA_TRY(cudaEventRecord(ctx->ev_join, s2));
-  LRS_CUDA_TRY(cudaStreamWaitEvent(s1, ctx->ev_join, 0));
+  // join the side streams
+  LRS_CUDA_TRY(cudaEventRecord(sp.ev[SPD_JOIN2], s2));
+  LRS_CUDA_TRY(cudaEventRecord(sp.ev[SPD_JOIN3], s3));
+  LRS_CUDA_TRY(cudaEventRecord(sp.ev[SPD_JOIN4], s4));
+  for (int e : {SPD_JOIN2, SPD_JOIN3, SPD_JOIN4}) LRS_CUDA_TRY(cudaStreamWaitEvent(s1, sp.ev[e], 0));
   return LRS_OK;
 }
 

@@ -63,16 +63,27 @@ void dev_free_bytes(lrs_ctx* ctx, void* p, size_t bytes) {
   dev_free_temp(ctx, p, bytes);
 }
 
+static int spd_streams_create(SpdStreams& sp, int priority) {
+  for (cudaStream_t* st : {&sp.s2, &sp.s3, &sp.s4})
+    LRS_CUDA_TRY(cudaStreamCreateWithPriority(st, cudaStreamNonBlocking, priority));
+  for (cudaEvent_t& e : sp.ev) LRS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return LRS_OK;
+}
+
+static void spd_streams_destroy(SpdStreams& sp) {
+  for (cudaEvent_t e : sp.ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : {sp.s2, sp.s3, sp.s4})
+    if (st) cudaStreamDestroy(st);
+  sp = SpdStreams{};
+}
+
 int aux_stream_ready(lrs_ctx* ctx) {
-  if (ctx->aux_stream) return LRS_OK;
+  if (ctx->spd.s2) return LRS_OK;
   int lo = 0, hi = 0;
   LRS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
   ctx->prio_greatest = hi;
-  LRS_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, hi));
-  LRS_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream2, cudaStreamNonBlocking, hi));
-  for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_bulk, &ctx->ev_join, &ctx->ev_fix})
-    LRS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-  return LRS_OK;
+  return spd_streams_create(ctx->spd, hi);
 }
 
 // Lanes 1 .. n - 1 of lrs_solve_w (lane 0 is the context): streams (the first
@@ -86,10 +97,8 @@ static int lanes_ready(lrs_ctx* ctx, int n) {
     ctx->lanes.emplace_back();
     DysonLane& l = ctx->lanes.back();
     LRS_CUDA_TRY(cudaStreamCreateWithPriority(&l.s1, cudaStreamNonBlocking, lo));
-    LRS_CUDA_TRY(cudaStreamCreateWithPriority(&l.s2, cudaStreamNonBlocking, hi));
-    LRS_CUDA_TRY(cudaStreamCreateWithPriority(&l.s3, cudaStreamNonBlocking, hi));
-    for (cudaEvent_t* e : {&l.ev_fork, &l.ev_panel, &l.ev_bulk, &l.ev_join, &l.ev_fix, &l.ev_done})
-      LRS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    LRS_TRY(spd_streams_create(l.spd, hi));
+    LRS_CUDA_TRY(cudaEventCreateWithFlags(&l.ev_done, cudaEventDisableTiming));
   }
   return LRS_OK;
 }
@@ -98,13 +107,7 @@ static int lanes_ready(lrs_ctx* ctx, int n) {
 // (host-side enqueueing of one lane's solves; called again to swap back).
 static void lane_swap(lrs_ctx* ctx, DysonLane& l) {
   std::swap(ctx->stream, l.s1);
-  std::swap(ctx->aux_stream, l.s2);
-  std::swap(ctx->aux_stream2, l.s3);
-  std::swap(ctx->ev_fork, l.ev_fork);
-  std::swap(ctx->ev_panel, l.ev_panel);
-  std::swap(ctx->ev_bulk, l.ev_bulk);
-  std::swap(ctx->ev_join, l.ev_join);
-  std::swap(ctx->ev_fix, l.ev_fix);
+  std::swap(ctx->spd, l.spd);
   Workspace& w = ctx->ws;
   std::swap(w.dyson_a, l.dyson_a);
   std::swap(w.tinv, l.tinv);
@@ -384,15 +387,11 @@ int lrs_destroy(lrs_ctx* ctx) {
   release(ctx, ctx->d_col_o); release(ctx, ctx->d_col_u);
   free_workspace(ctx);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
-  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_panel, ctx->ev_bulk, ctx->ev_join, ctx->ev_fix})
-    if (e) cudaEventDestroy(e);
-  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
-  if (ctx->aux_stream2) cudaStreamDestroy(ctx->aux_stream2);
+  spd_streams_destroy(ctx->spd);
   for (DysonLane& l : ctx->lanes) {
-    for (cudaEvent_t e : {l.ev_fork, l.ev_panel, l.ev_bulk, l.ev_join, l.ev_fix, l.ev_done})
-      if (e) cudaEventDestroy(e);
-    for (cudaStream_t st : {l.s1, l.s2, l.s3})
-      if (st) cudaStreamDestroy(st);
+    spd_streams_destroy(l.spd);
+    if (l.ev_done) cudaEventDestroy(l.ev_done);
+    if (l.s1) cudaStreamDestroy(l.s1);
   }
   if (ctx->ev_lanes) cudaEventDestroy(ctx->ev_lanes);
   for (int s = 0; s < 6; ++s) {

@@ -194,12 +194,24 @@ struct Workspace {
   bool coeff_planes_valid = false;
 };
 
+// Side streams and events of the SPD inverse (spd_inverse, k_linalg.cu): the
+// pivot chain, the write-back of exchanged blocks, the rest of each panel.
+enum SpdEvent : int {
+  SPD_FORK = 0, SPD_JOIN2, SPD_JOIN3, SPD_JOIN4,
+  SPD_PIVOT, SPD_ADIAG = SPD_PIVOT + 2, SPD_GREST = SPD_ADIAG + 2, SPD_AREST = SPD_GREST + 2,
+  SPD_BULK = SPD_AREST + 2, SPD_FIX = SPD_BULK + 2, SPD_EVENTS = SPD_FIX + 2   // pairs alternate by block parity
+};
+struct SpdStreams {
+  cudaStream_t s2 = nullptr, s3 = nullptr, s4 = nullptr;
+  cudaEvent_t ev[SPD_EVENTS] = {};
+};
+
 // Streams, events and Dyson-solve workspace of one lane of lrs_solve_w: the
 // sites of one call are spread over lanes whose solves run concurrently
 // (lane 0 is the context's own stream and workspace).
 struct DysonLane {
-  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_panel = nullptr, ev_bulk = nullptr, ev_join = nullptr, ev_fix = nullptr;
+  cudaStream_t s1 = nullptr;
+  SpdStreams spd;
   cudaEvent_t ev_done = nullptr;
   DevBuf<double> dyson_a, tinv, gj, alda_n;
   DevBuf<int> ipiv, oz_expo, og_expo;
@@ -257,12 +269,9 @@ struct lrs_ctx {
   std::vector<lrs::SiteTile> site_tiles_dev;   // copy of the table last uploaded
   const lrs::SiteTile* site_tiles_dev_ptr = nullptr;
   cudaGraphExec_t graph_exec = nullptr;        // recorded multi-site build
-  // second and third streams of the SPD inverse (higher priority) and their events
-  cudaStream_t aux_stream = nullptr;
-  cudaStream_t aux_stream2 = nullptr;
-  cudaEvent_t ev_fix = nullptr;
+  // side streams of the SPD inverse (higher priority) and their events
+  lrs::SpdStreams spd;
   int prio_greatest = 0;               // numerically smallest (highest) stream priority of the device
-  cudaEvent_t ev_fork = nullptr, ev_panel = nullptr, ev_bulk = nullptr, ev_join = nullptr;
 
   lrs_stats_t stats{};
   double fp64_flops = 0;               // running count of FP64 flop issued by the linear algebra
@@ -280,7 +289,7 @@ namespace lrs {
 
 enum Stage { ST_PROJECT = 0, ST_CHI0 = 1, ST_W = 2, ST_BACKWARD = 3, ST_CHI0_MAIN = 4, ST_W_MAIN = 5 };
 int stage_begin(lrs_ctx* ctx, Stage s);
-// Creates the second stream and its events on first use.
+// Creates the side streams of the SPD inverse and their events on first use.
 int aux_stream_ready(lrs_ctx* ctx);
 int stage_end(lrs_ctx* ctx, Stage s);
 
