@@ -40,3 +40,22 @@ def test_argument_errors_without_device():
     assert lrs.lrs_build_chi0(None, 0, None) == lrs.LRS_ERR_ARG
     assert lrs.lrs_destroy(None) == lrs.LRS_OK
     assert lrs.lrs_version().startswith(b"lrs")
+
+
+def header_constants():
+    src = open(os.path.join(ROOT, "include", "lrs.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(LRS_[A-Z0-9_]+)\s+(-?\d+)\b", src)}
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant of include/lrs.h that the binding names has the header's value
+    (option codes, solver and update modes, lanes, precisions, error codes)."""
+    from paper_2005_07834_gb300 import lrs
+    consts = header_constants()
+    assert {"LRS_OPT_DYSON_LANES", "LRS_OPT_DYSON_UPDATE", "LRS_UPDATE_TC", "LRS_SOLVER_SPD"} <= set(consts)
+    checked = 0
+    for name, value in consts.items():
+        if hasattr(lrs, name):
+            assert getattr(lrs, name) == value, name
+            checked += 1
+    assert checked >= 20
