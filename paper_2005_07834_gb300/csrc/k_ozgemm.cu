@@ -16,8 +16,9 @@
 // Products (oz_gemm_kernel): the 36 slice pairs with t + u <= 7 are issued as
 // bf16 tcgen05 MMAs into eight fp32 accumulators in TMEM, one per level
 // t + u.  Over a K segment of 128 a level sum is an integer of magnitude at
-// most 128 * 8 * 64 * 64 = 2^22, so the tensor cores accumulate it exactly.  The epilogue combines the levels of a segment as 64-bit integers
-// and rounds the product to float64 with integer instructions (oz_combine.cuh);
+// most 128 * 8 * 64 * 64 = 2^22, so the tensor cores accumulate it exactly.
+// The epilogue combines the levels of a segment into one 64-bit integer and
+// rounds the product to float64 with integer instructions (oz_combine.cuh);
 // segments add in float64.  The dropped pairs (t + u >= 8) and the
 // representation errors bound the error by about 2^-54 K |A|row max |B|row max
 // per element, the bound of a float64 dot product of K terms.
