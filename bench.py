@@ -3,10 +3,13 @@
 A step is one pass of the whole hot path over one site with the orbitals
 resident in HBM: projection of the Bloch coefficients onto the site grid,
 frequency denominators, the Green's-function contraction for chi0 with its
-FP64 frequency accumulation, the Coulomb operator and the FP64 LU Dyson solve
-for W.  `value` is site builds per second over all ranks; `e2e` measures the
-same through the C-ABI with host buffers (host->device copy of the
-coefficients and device->host copy of W inside the timed region).
+FP64 frequency accumulation, the Coulomb operator and the Dyson solve for W
+(lm basis: symmetric positive definite form inverted by blocked Gauss-Jordan
+exchange steps, float64-accurate products on the tensor cores in the mixed
+precisions).  `value` is site builds per second over all ranks; `e2e`
+measures the same through the C-ABI with page-locked host buffers
+(host->device copy of the coefficients and device->host copy of W inside the
+timed region).
 
 --impl reference times the FP64 CPU oracle on the host cores instead (rank 0
 only), on a bounded sample of the same workload.
