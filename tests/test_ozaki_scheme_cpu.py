@@ -1,0 +1,162 @@
+"""The float64-accurate tensor-core scheme of the Dyson products, restated on the host
+with exact integers (CPU only).
+
+The kernels (k_ozaki.cu, k_ozgemm.cu, oz_slice.cuh, oz_combine.cuh) cut each row of an
+operand into integer digits after scaling it into (-1/2, 1/2), multiply digit planes on
+the tensor cores into per-level fp32 accumulators, combine the levels into one 64-bit
+integer and round it to float64 with integer instructions.  These tests check the
+arithmetic facts the kernels rely on: the digit ranges (exact in bf16), the level sums
+staying within 2^22 (exact in fp32 and readable by one fp32 add), the 64-bit
+combination not overflowing, the integer rounding equalling IEEE round-to-nearest-even,
+and the result staying within the error bound of a float64 dot product.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+
+def row_scale(row):
+    """e with every |x| < 2^(e-1): from the largest exponent field (frexp gives m = f 2^E, f in [0.5, 1))."""
+    m = max(abs(x) for x in row)
+    if m == 0.0:
+        return -1020
+    _, E = math.frexp(m)
+    return E + 1
+
+
+def fixed56(x, e):
+    """round(x 2^(56 - e)), halves away from zero, exactly (x is a float64)."""
+    num, den = float(x).as_integer_ratio()
+    scaled_num = num * (2 ** (56 - e)) if 56 - e >= 0 else num
+    scaled_den = den if 56 - e >= 0 else den * 2 ** (e - 56)
+    q, r = divmod(abs(scaled_num), scaled_den)
+    if 2 * r >= scaled_den:
+        q += 1
+    return q if scaled_num >= 0 else -q
+
+
+def digits(N, base, count):
+    """Balanced digits of N, least significant first removed: N = sum_t d_t base^(count-1-t)."""
+    half = base // 2
+    out = []
+    for _ in range(count - 1):
+        d = ((N + half) % base) - half
+        out.append(d)
+        N = (N - d) // base
+    out.append(N)
+    return out[::-1]
+
+
+SCHEMES = {
+    # name: (base, digits, kept levels t + u <= L, K of one exact segment, shifts of the 64-bit combination)
+    "update": (256, 7, 6, 32, [40, 32, 24, 16, 8, 0, -8]),
+    "gemm": (128, 8, 7, 128, [42, 35, 28, 21, 14, 7, 0, -7]),
+}
+
+
+def product_by_scheme(a_rows, b_rows, scheme):
+    base, nd, maxlev, _, shifts = SCHEMES[scheme]
+    ea = [row_scale(r) for r in a_rows]
+    eb = [row_scale(r) for r in b_rows]
+    da = [[digits(fixed56(x, ea[i]), base, nd) for x in r] for i, r in enumerate(a_rows)]
+    db = [[digits(fixed56(x, eb[j]), base, nd) for x in r] for j, r in enumerate(b_rows)]
+    out = np.zeros((len(a_rows), len(b_rows)))
+    max_level = 0
+    max_v = 0
+    for i in range(len(a_rows)):
+        for j in range(len(b_rows)):
+            S = [0] * (maxlev + 1)
+            for k in range(len(a_rows[i])):
+                for t in range(nd):
+                    for u in range(nd):
+                        if t + u <= maxlev:
+                            S[t + u] += da[i][k][t] * db[j][k][u]
+            max_level = max(max_level, max(abs(s) for s in S))
+            V = 0
+            for L, s in enumerate(S):
+                V += s << shifts[L] if shifts[L] >= 0 else s >> -shifts[L]   # floor, as the kernels
+            max_v = max(max_v, abs(V))
+            out[i, j] = math.ldexp(float(V), ea[i] + eb[j] - 56)   # int -> float rounds to nearest even
+    return out, ea, eb, max_level, max_v
+
+
+@pytest.mark.parametrize("scheme", ["update", "gemm"])
+def test_digit_ranges_and_reconstruction(scheme):
+    base, nd, *_ = SCHEMES[scheme]
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        row = rng.standard_normal(8) * 10.0 ** rng.uniform(-30, 30, 8)
+        e = row_scale(row)
+        for x in row:
+            N = fixed56(x, e)
+            assert abs(N) <= 2 ** 55
+            d = digits(N, base, nd)
+            assert all(abs(v) <= base // 2 for v in d)              # at most 8 significant bits
+            assert sum(v * base ** (nd - 1 - t) for t, v in enumerate(d)) == N
+            assert abs(N * 2.0 ** (e - 56) - x) <= 2.0 ** (e - 57) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["update", "gemm"])
+def test_level_sums_exact_and_combination_in_range_at_worst_case(scheme):
+    """All digits at their extreme: the level sums reach at most 2^22 and V stays below 2^63."""
+    base, nd, maxlev, K, shifts = SCHEMES[scheme]
+    worst = [base // 2] * nd                                    # |digit| bound
+    S = [sum(worst[t] * worst[L - t] for t in range(L + 1)) * K for L in range(maxlev + 1)]
+    assert max(S) <= 2 ** 22
+    V = sum((s << sh) if sh >= 0 else (s >> -sh) for s, sh in zip(S, shifts))
+    assert V < 2 ** 63
+
+
+def test_magic_number_reads_level_sums_exactly():
+    """S + 1.5 2^23 in fp32, minus the bits of 1.5 2^23, is S for every |S| <= 2^22."""
+    S = np.concatenate([np.arange(-2 ** 22, -2 ** 22 + 5000), np.arange(-3000, 3000),
+                        np.arange(2 ** 22 - 5000, 2 ** 22 + 1),
+                        np.random.default_rng(2).integers(-2 ** 22, 2 ** 22, 200000)]).astype(np.int64)
+    f = S.astype(np.float32) + np.float32(12582912.0)
+    back = f.view(np.int32).astype(np.int64) - 0x4B400000
+    assert np.array_equal(back, S)
+
+
+def test_integer_rounding_equals_ieee_round_to_nearest_even():
+    """The kernels' rounding of a 64-bit integer (leading one, 53 bits, ties to even on the 11
+    dropped bits, exponent added) equals float(v) 2^k."""
+    rng = np.random.default_rng(3)
+
+    def by_bits(v, k):
+        if v == 0:
+            return 0.0
+        a = abs(v)
+        lz = 64 - a.bit_length()
+        m = a << lz
+        mant = m >> 11
+        rem = m & 0x7FF
+        if rem > 0x400 or (rem == 0x400 and (mant & 1)):
+            mant += 1
+        e = 63 - lz + k
+        return math.copysign(math.ldexp(mant, e - 52), v)
+
+    for _ in range(100000):
+        v = int(rng.integers(-2 ** 62, 2 ** 62)) >> int(rng.integers(0, 62))
+        if rng.random() < 0.2:   # ties and near-ties
+            v = (v >> 11 << 11) | (0x400 if rng.random() < 0.5 else 0x3FF)
+        k = int(rng.integers(-300, 300))
+        assert by_bits(v, k) == math.ldexp(float(v), k)
+
+
+@pytest.mark.parametrize("scheme", ["update", "gemm"])
+def test_products_within_a_float64_dot_product_bound(scheme):
+    """Rows with a wide dynamic range: the scheme's product differs from the exact dot product
+    by less than 2^-52 K |a|max |b|max (a float64 dot product's bound is about K 2^-53 of the
+    same)."""
+    K = 32 if scheme == "update" else 40
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((6, K)) * 10.0 ** rng.uniform(-3, 3, (6, K))
+    b = rng.standard_normal((5, K)) * 10.0 ** rng.uniform(-3, 3, (5, K))
+    got, *_ = product_by_scheme(a.tolist(), b.tolist(), scheme)
+    for i in range(a.shape[0]):
+        for j in range(b.shape[0]):
+            exact = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a[i], b[j]))
+            bound = 2.0 ** -52 * K * np.max(np.abs(a[i])) * np.max(np.abs(b[j]))
+            assert abs(Fraction(got[i, j]) - exact) <= Fraction(bound)
