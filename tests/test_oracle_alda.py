@@ -62,3 +62,20 @@ def test_density_integrates_to_the_electron_count():
     omega = abs(np.linalg.det(o.cell))
     total = alda.density(po, wo).sum() * omega / m ** 3
     assert abs(total - 2.0 * np.sum(o.kweights * o.nocc)) < 1e-10
+
+
+def test_exchange_constant_against_the_uniform_gas_values():
+    """Pins the Dirac constant (3/pi)^(1/3) that both the energy and the kernel carry, against
+    textbook values of the uniform electron gas in Hartree atomic units: the exchange energy per
+    electron is -0.458165 / r_s Ha and the exchange potential -0.610887 / r_s Ha, with
+    n = 3 / (4 pi r_s^3).  A wrong constant shared by e_x and f_x passes the second-derivative
+    check but fails these."""
+    for rs in (1.0, 2.0, 5.0):
+        n = 3.0 / (4.0 * np.pi * rs ** 3)
+        eps_x = float(alda.exchange_energy_density(n)) / n
+        assert abs(eps_x - (-0.458165 / rs)) < 1e-6 / rs, (rs, eps_x)
+        h = 1e-4 * n
+        v_x = float(alda.exchange_energy_density(n + h) - alda.exchange_energy_density(n - h)) / (2 * h)
+        assert abs(v_x - (-0.610887 / rs)) < 1e-6 / rs, (rs, v_x)
+        # f_x = dv_x/dn = -(1/3) (3/pi)^(1/3) n^(-2/3) = v_x / (3 n) for the n^(1/3) potential
+        assert abs(float(alda.fx_exchange(n)) - (-0.610887 / rs) / (3.0 * n)) < 1e-6 / (rs * 3.0 * n)
