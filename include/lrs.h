@@ -333,6 +333,27 @@ int lrs_set_site_orbitals(lrs_ctx* ctx, int site, const double* psi);
 int lrs_get_site_orbitals(lrs_ctx* ctx, int site, double* psi);
 
 /*
+ * Device-pointer forms of lrs_set_energies and lrs_set_site_orbitals, for
+ * callers whose energies eps_kb (Eq. (eq-green)) and site-grid orbitals
+ * psi_kb(tau + r_p) (Eq. (bloch)) already live on the GPU, e.g. tensors of a
+ * differentiable program: the values are gathered into the library's column
+ * order by a kernel on the context stream, without a host round trip or a
+ * stream synchronisation.  The caller's buffer must stay valid until that
+ * kernel has run (stream order).  Layouts as in the host forms:
+ *   energies_dev  [nk][nbands] float64 (device)
+ *   psi_dev       [npts][nk*nbands] complex128 interleaved (device)
+ * Values are not inspected on the host: a non-finite energy or orbital shows
+ * up later as LRS_ERR_NUMERIC of lrs_solve_w.  After lrs_set_energies_dev the
+ * host copy of the energies (needed only when lrs_set_frequency_quadrature
+ * derives mu or zeta from them) is read back at that call.  Both invalidate
+ * chi0 and W (all sites for the energies, that site for the orbitals).
+ * Errors: LRS_ERR_ARG (null pointer, site), LRS_ERR_STATE (no orbitals),
+ * LRS_ERR_OOM, LRS_ERR_CUDA.
+ */
+int lrs_set_energies_dev(lrs_ctx* ctx, const double* energies_dev);
+int lrs_set_site_orbitals_dev(lrs_ctx* ctx, int site, const double* psi_dev);
+
+/*
  * Build chi0 on the grids of `nsite` sites (NULL = all), Eq. (chi1) with the
  * Green's functions of Sec. VI.D: per frequency t_i the occupied and
  * unoccupied parts
@@ -398,14 +419,21 @@ int lrs_backward_dev(lrs_ctx* ctx, int site, const double* grad_w_dev,
  *   w_dev [npts][npts]  output W (device, caller-owned)
  *   stream              cudaStream_t of the work (NULL = legacy default stream)
  * Runs on the current device.  Scratch lives in one statically reserved
- * device array of about 2.1 MB (LRS_STATIC_MAX_NPTS^2 doubles plus pivots)
- * that every GPU loading the library holds until exit.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU race, so serialise them.
- * The call waits for its stream to read the pivot status.  No cudaMalloc,
+ * device array of about 2.1 MB (LRS_STATIC_MAX_NPTS^2 doubles plus pivots).
+ * The driver reserves it on a GPU when it loads the library's module that
+ * holds it: under CUDA's default lazy module loading that is the first call
+ * on that device (with CUDA_MODULE_LOADING=EAGER, when the library is loaded);
+ * from then on the GPU holds it until the process exits.  A caller whose own
+ * allocator reserves the GPU's memory should therefore make one call early,
+ * before that reservation.  The first call on a device also looks up that
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  Every call shares the array: calls
+ * that overlap on the GPU race, so serialise them.  The call waits for its
+ * stream to read the pivot status, so a call made while `stream` is being
+ * captured is refused (LRS_ERR_STATE) before any work.  No cudaMalloc,
  * cudaFree or allocating library routine is called.
- * Errors: LRS_ERR_ARG, LRS_ERR_CUDA, LRS_ERR_NUMERIC (zero/non-finite pivot).
+ * Errors: LRS_ERR_ARG, LRS_ERR_STATE, LRS_ERR_CUDA, LRS_ERR_NUMERIC
+ * (zero/non-finite pivot).
  */
 #define LRS_STATIC_MAX_NPTS 512
 int lrs_solve_w_static(int npts, int lmax, const double* pts_dev, const double* wts_dev,

@@ -57,7 +57,11 @@ def green_pair(psi_o, psi_u, e_o, e_u, w_o, w_u, mu, t):
     return g_o, g_u_t
 
 
-def chi0_green(psi_o, psi_u, e_o, e_u, w_o, w_u, mu, t, W, full_g=False):
+def chi0_green(psi_o, psi_u, e_o, e_u, w_o, w_u, mu, t, W, full_g=False, rows=None):
+    """chi0 [npts, npts], or only its rows `rows` (cross terms only): the same sum with the
+    Green's functions evaluated where those rows need them, g(rows, :) and g(:, rows)."""
+    if rows is not None:
+        return _chi0_green_rows(psi_o, psi_u, e_o, e_u, w_o, w_u, mu, t, W, np.asarray(rows))
     npts = psi_o.shape[0]
     acc = np.zeros((npts, npts))
     for ti, wi in zip(t, W):
@@ -69,4 +73,18 @@ def chi0_green(psi_o, psi_u, e_o, e_u, w_o, w_u, mu, t, W, full_g=False):
         else:
             y = g_o * g_u_t                           # g_o(p,p') g_u(p',p)
             acc += wi * (y + y.T).real
+    return (2.0 / np.pi) * acc
+
+
+def _chi0_green_rows(psi_o, psi_u, e_o, e_u, w_o, w_u, mu, t, W, rows):
+    """Rows p in `rows` of (2/pi) sum_i W_i Re[y(p,p') + y(p',p)], y = g_o(p,p') g_u(p',p)."""
+    acc = np.zeros((len(rows), psi_o.shape[0]))
+    for ti, wi in zip(t, W):
+        d_o = w_o / (mu + 1j * ti - e_o)
+        d_u = w_u / (mu + 1j * ti - e_u)
+        g_o_r = (np.conj(psi_o[rows]) * d_o) @ psi_o.T       # g_o(p, p'),  p in rows
+        g_o_c = (np.conj(psi_o) * d_o) @ psi_o[rows].T       # g_o(p', p)
+        g_u_r = (psi_u[rows] * d_u) @ np.conj(psi_u).T       # g_u(p', p)
+        g_u_c = (psi_u * d_u) @ np.conj(psi_u[rows]).T       # g_u(p, p')
+        acc += wi * (g_o_r * g_u_r + (g_o_c * g_u_c).T).real
     return (2.0 / np.pi) * acc

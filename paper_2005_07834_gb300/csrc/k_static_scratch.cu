@@ -7,13 +7,17 @@
 // or an embedded caller with a fixed memory budget fixed at start-up.  For
 // them this entry point takes every input and output from the caller and
 // keeps its scratch (LU matrix, pivots, status words, point radii) in one
-// file-scope __device__ array of fixed size, reserved on every GPU that loads
-// the library until the process exits.
+// file-scope __device__ array of fixed size.  The array is reserved on a GPU
+// when the driver loads this file's module there: with CUDA's default lazy
+// module loading that is the first call on that device (at library load with
+// CUDA_MODULE_LOADING=EAGER); it is then held until the process exits.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents; the status words are cleared at the start of each call.  Calls
 // that overlap on the GPU (two streams, or two host threads) race on it and
-// must be serialised by the caller.
+// must be serialised by the caller.  Each call waits for its stream (it reads
+// the pivot status back), so a call on a stream that is being captured is
+// refused before any work.
 #include <mutex>
 
 #include "lrs_internal.h"
@@ -74,6 +78,10 @@ extern "C" int lrs_solve_w_static(int npts, int lmax, const double* pts_dev, con
                      npts, LRS_STATIC_MAX_NPTS);
   if (lmax < 0 || lmax > 64) return set_error(LRS_ERR_ARG, "lmax = %d out of [0,64]", lmax);
   if (!pts_dev || !wts_dev || !chi0_dev || !w_dev) return set_error(LRS_ERR_ARG, "null device pointer");
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  LRS_CUDA_TRY(cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &capture));
+  if (capture != cudaStreamCaptureStatusNone)
+    return set_error(LRS_ERR_STATE, "lrs_solve_w_static waits for its stream and cannot run while it is captured");
   int device = -1;
   LRS_CUDA_TRY(cudaGetDevice(&device));
   if (device < 0 || device >= kMaxDevices) return set_error(LRS_ERR_ARG, "device %d not supported", device);

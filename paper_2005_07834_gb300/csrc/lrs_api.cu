@@ -266,6 +266,42 @@ __global__ void gamma_real_check_kernel(const double2* __restrict__ c, const int
   }
 }
 
+// Public-order energies [nk][nb] -> the per-column arrays of the occupied and unoccupied sets.
+__global__ void gather_energies_kernel(const double* __restrict__ e, const int* __restrict__ col_o,
+                                       const int* __restrict__ col_u, int Ko, int Ku, double* __restrict__ eo,
+                                       double* __restrict__ eu) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < Ko) eo[j] = e[col_o[j]];
+  else if (j < Ko + Ku) eu[j - Ko] = e[col_u[j - Ko]];
+}
+
+// Public-order site orbitals [npts][ncol] -> psi_o [npts][Ko], psi_u [npts][Ku].
+__global__ void gather_psi_kernel(const double2* __restrict__ psi, int npts, int ncol, const int* __restrict__ col_o,
+                                  const int* __restrict__ col_u, int Ko, int Ku, double2* __restrict__ po,
+                                  double2* __restrict__ pu) {
+  const size_t total = (size_t)npts * (Ko + Ku);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = i / (Ko + Ku);
+    const int j = (int)(i % (Ko + Ku));
+    if (j < Ko) po[p * Ko + j] = psi[p * ncol + col_o[j]];
+    else pu[p * Ku + (j - Ko)] = psi[p * ncol + col_u[j - Ko]];
+  }
+}
+
+// After lrs_set_energies_dev the host copy of the energies is rebuilt from the
+// per-column device arrays the first time host code needs it.
+static int host_energies(lrs_ctx* ctx) {
+  if (!ctx->energies_on_device_only) return LRS_OK;
+  std::vector<double> eo(ctx->Ko), eu(ctx->Ku);
+  LRS_CUDA_TRY(cudaMemcpyAsync(eo.data(), ctx->e_o.ptr, ctx->Ko * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaMemcpyAsync(eu.data(), ctx->e_u.ptr, ctx->Ku * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  for (int j = 0; j < ctx->Ko; ++j) ctx->energies[ctx->col_o[j]] = eo[j];
+  for (int j = 0; j < ctx->Ku; ++j) ctx->energies[ctx->col_u[j]] = eu[j];
+  ctx->energies_on_device_only = false;
+  return LRS_OK;
+}
+
 static int check_site(lrs_ctx* ctx, int site) {
   if (site < 0 || site >= (int)ctx->sites.size())
     return set_error(LRS_ERR_ARG, "site %d out of range (have %zu)", site, ctx->sites.size());
@@ -504,6 +540,7 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   ctx->kpts.assign(kpts, kpts + 3 * nk);
   ctx->kw.assign(kweights, kweights + nk);
   ctx->energies.assign(energies, energies + (size_t)nk * nbands);
+  ctx->energies_on_device_only = false;
   ctx->gvec.assign(gvec, gvec + 3 * (size_t)ng);
   ctx->ws.fft_plan_ok = false;   // the FFT index tables follow the G set
   std::vector<int> partner;
@@ -617,6 +654,11 @@ int lrs_set_frequency_quadrature(lrs_ctx* ctx, int nf, double mu, double zeta, d
   if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
   if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
   if (nf < 1 || nf > 128) return set_error(LRS_ERR_ARG, "nf = %d out of [1,128]", nf);
+  {
+    DeviceGuard g(ctx->device);
+    if (g.rc) return g.rc;
+    LRS_TRY(host_energies(ctx));
+  }
   if (std::isnan(mu)) {
     double top = -1e300, bottom = 1e300;
     for (int k = 0; k < ctx->nk; ++k)
@@ -852,6 +894,7 @@ int lrs_set_energies(lrs_ctx* ctx, const double* energies) {
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
   ctx->energies.assign(energies, energies + ne);
+  ctx->energies_on_device_only = false;
   std::vector<double> eo(ctx->Ko), eu(ctx->Ku);
   for (int j = 0; j < ctx->Ko; ++j) eo[j] = energies[ctx->col_o[j]];
   for (int j = 0; j < ctx->Ku; ++j) eu[j] = energies[ctx->col_u[j]];
@@ -882,6 +925,43 @@ int lrs_set_site_orbitals(lrs_ctx* ctx, int site, const double* psi) {
   LRS_CUDA_TRY(cudaMemcpyAsync(s.psi_o.ptr, o.data(), o.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
   LRS_CUDA_TRY(cudaMemcpyAsync(s.psi_u.ptr, u.data(), u.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  s.has_psi = true;
+  s.has_chi0 = s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_set_energies_dev(lrs_ctx* ctx, const double* energies_dev) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  if (!energies_dev) return set_error(LRS_ERR_ARG, "energies_dev is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  const int K = ctx->Ko + ctx->Ku;
+  gather_energies_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(energies_dev, ctx->d_col_o.ptr, ctx->d_col_u.ptr,
+                                                                   ctx->Ko, ctx->Ku, ctx->e_o.ptr, ctx->e_u.ptr);
+  LRS_TRY(after_launch(ctx, "gather_energies_kernel"));
+  ctx->energies_on_device_only = true;
+  for (auto& s : ctx->sites) s.has_chi0 = s.has_w = false;
+  return LRS_OK;
+}
+
+int lrs_set_site_orbitals_dev(lrs_ctx* ctx, int site, const double* psi_dev) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  if (!ctx->has_orb) return set_error(LRS_ERR_STATE, "load orbitals first");
+  LRS_TRY(check_site(ctx, site));
+  if (!psi_dev) return set_error(LRS_ERR_ARG, "psi_dev is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  Site& s = ctx->sites[site];
+  LRS_TRY(alloc_psi(ctx, s));
+  const size_t total = (size_t)s.npts * (ctx->Ko + ctx->Ku);
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+  gather_psi_kernel<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const double2*>(psi_dev), s.npts,
+                                                     ctx->nk * ctx->nb, ctx->d_col_o.ptr, ctx->d_col_u.ptr, ctx->Ko,
+                                                     ctx->Ku, s.psi_o.ptr, s.psi_u.ptr);
+  LRS_TRY(after_launch(ctx, "gather_psi_kernel"));
   s.has_psi = true;
   s.has_chi0 = s.has_w = false;
   return LRS_OK;

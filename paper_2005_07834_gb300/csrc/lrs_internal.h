@@ -248,6 +248,7 @@ struct lrs_ctx {
   std::vector<int> nocc;
   double cell[9], recip[9], omega = 0;
   std::vector<double> kpts, kw, energies;
+  bool energies_on_device_only = false;  // set by lrs_set_energies_dev: host copy read back when needed
   std::vector<int> gvec;
   int gmax_idx[3] = {0, 0, 0};
   lrs::DevBuf<double2> coeff;          // [nk][ng][nb]

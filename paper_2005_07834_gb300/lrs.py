@@ -32,6 +32,7 @@ LRS_FXC_NONE, LRS_FXC_USER, LRS_FXC_ALDA_X = 0, 1, 2
 LRS_OPT_REAL_ORBITALS, LRS_REAL_AUTO, LRS_REAL_OFF = 8, 0, 1
 LRS_OPT_DYSON_UPDATE, LRS_UPDATE_AUTO, LRS_UPDATE_FP64, LRS_UPDATE_TC = 9, 0, 1, 2
 LRS_OPT_DYSON_LANES = 10
+LRS_STATIC_MAX_NPTS = 512
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
 
@@ -75,6 +76,8 @@ _SIGS = {
     "lrs_get_fft_grid": (C.c_int, [_P, _IP]),
     "lrs_set_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_site_orbitals": (C.c_int, [_P, C.c_int, _DP]),
+    "lrs_set_energies_dev": (C.c_int, [_P, _P]),
+    "lrs_set_site_orbitals_dev": (C.c_int, [_P, C.c_int, _P]),
     "lrs_build_chi0": (C.c_int, [_P, C.c_int, _IP]),
     "lrs_solve_w": (C.c_int, [_P, C.c_int, _IP]),
     "lrs_get_chi0": (C.c_int, [_P, C.c_int, _DP]),
@@ -134,6 +137,7 @@ class Screening:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(lrs_create(C.byref(self.ctx), int(device), prec, _P(stream or 0)), "lrs_create")
         self.precision = prec
+        self.stream = int(stream or 0)
         self.npts = []
         self.nk = self.nb = 0
 
@@ -157,6 +161,7 @@ class Screening:
 
     def set_stream(self, stream):
         _check(lrs_set_stream(self.ctx, _P(stream or 0)), "lrs_set_stream")
+        self.stream = int(stream or 0)
 
     def set_option(self, option, value):
         _check(lrs_set_option(self.ctx, int(option), int(value)), "lrs_set_option")
@@ -273,6 +278,14 @@ class Screening:
         psi, view = _c128_view(psi)
         assert psi.shape == (self.npts[site], self.nk * self.nb)
         _check(lrs_set_site_orbitals(self.ctx, int(site), _dp(view)), "lrs_set_site_orbitals")
+
+    def set_energies_dev(self, energies_ptr):
+        """Energies [nk][nb] float64 from device memory (stream-ordered on the context stream)."""
+        _check(lrs_set_energies_dev(self.ctx, _P(energies_ptr)), "lrs_set_energies_dev")
+
+    def set_site_orbitals_dev(self, site, psi_ptr):
+        """Site orbitals [npts][nk*nb] complex128 from device memory (stream-ordered)."""
+        _check(lrs_set_site_orbitals_dev(self.ctx, int(site), _P(psi_ptr)), "lrs_set_site_orbitals_dev")
 
     def get_site_orbitals(self, site):
         out = np.empty((self.npts[site], self.nk * self.nb), np.complex128)

@@ -22,3 +22,13 @@ class Reference:
         self.chi0 = ochi0.chi0_pairs(*pr.args(), pr.t, pr.W)
         self.v = ocoul.coulomb_multipole(pr.site.pts, pr.site.lmax)
         self.w = odys.screened_interaction(self.v, self.chi0, pr.site.wts)
+
+
+def max_rel(a, b):
+    """Element-wise error scaled by the reference's largest element: max |a - b| / max |b|."""
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def row_rel(a, b):
+    """Largest relative Frobenius error over the rows of a [rows, n] block."""
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))

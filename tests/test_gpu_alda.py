@@ -7,7 +7,7 @@ import pytest
 
 from oracle import alda as oalda, induced as oind
 from paper_2005_07834_gb300 import synth
-from tests.gpu_util import Reference, rel_fro
+from tests.gpu_util import Reference, max_rel, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -68,9 +68,12 @@ def test_user_kernel_and_mixed_context(lrs, case):
     scr.set_fxc(0, lrs.LRS_FXC_USER, f)
     assert np.array_equal(scr.get_fxc(0), f)
     scr.solve_w()
-    err = rel_fro(scr.get_w(0), oalda.screened_interaction_alda(ref.chi0, ref.v, f, s.wts))
-    print(f"bf16x3, caller kernel: W~ vs oracle {err:.2e}")
-    assert err < 1e-5
+    w_ref = oalda.screened_interaction_alda(ref.chi0, ref.v, f, s.wts)
+    w = scr.get_w(0)
+    err = rel_fro(w, w_ref)
+    print(f"bf16x3, caller kernel: W~ vs oracle {err:.2e} (max {max_rel(w, w_ref):.2e}, "
+          f"W~ - v {rel_fro(w - ref.v, w_ref - ref.v):.2e})")
+    assert err < 1e-5 and max_rel(w, w_ref) < 1e-5 and rel_fro(w - ref.v, w_ref - ref.v) < 1e-5
     scr.close()
 
 

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import grad as ograd
 from paper_2005_07834_gb300 import synth
-from tests.gpu_util import Reference, public_psi, rel_fro
+from tests.gpu_util import Reference, public_psi, max_rel, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -138,26 +138,73 @@ def test_backward_central_differences(lrs, case):
     scr.close()
 
 
-def test_autograd_function(lrs, case):
+@pytest.mark.parametrize("own_stream", [False, True])
+def test_autograd_function(lrs, case, own_stream):
+    """Leaf tensors on the GPU: forward (device setters), loss and backward never leave device
+    memory; the library runs on torch's current stream or on a stream of its own."""
     import torch
     from paper_2005_07834_gb300.autograd import screened_interaction
 
     wl, ref, q = case
-    scr = lrs.Screening(0, "fp64", torch.cuda.current_stream().cuda_stream)
+    side = torch.cuda.Stream() if own_stream else torch.cuda.current_stream()
+    scr = lrs.Screening(0, "fp64", side.cuda_stream)
     scr.load(wl.orbitals)
     scr.set_sites(wl.sites)
     scr.set_frequency_quadrature(wl.nfreq, mu=ref.pr.mu, zeta=ref.pr.zeta)
-    e = torch.tensor(wl.orbitals.energies, dtype=torch.float64, requires_grad=True)
-    psi = torch.tensor(public_psi(ref.pr), dtype=torch.complex128, requires_grad=True)
+    e = torch.tensor(wl.orbitals.energies, dtype=torch.float64, device="cuda", requires_grad=True)
+    psi = torch.tensor(public_psi(ref.pr), dtype=torch.complex128, device="cuda", requires_grad=True)
     qt = torch.tensor(q, dtype=torch.float64, device="cuda")
     w = screened_interaction(e, psi, scr, 0)
     loss = qt @ w @ qt
     loss.backward()
+    assert e.grad.is_cuda and psi.grad.is_cuda
     assert rel_fro(w.detach().cpu().numpy(), ref.w) < 1e-10
     oe, op = oracle_grads(ref, gamma_w=np.outer(q, q))
-    assert rel_fro(e.grad.numpy(), oe) < 1e-9
-    assert rel_fro(psi.grad.numpy(), op) < 1e-9
+    assert rel_fro(e.grad.cpu().numpy(), oe) < 1e-9
+    assert rel_fro(psi.grad.cpu().numpy(), op) < 1e-9
+    # a scissor shift through the device setter: the forward sees the new energies
+    shifted = e.detach().clone()
+    shifted[:, :] += torch.tensor(np.where(np.arange(wl.orbitals.nbands)[None, :] >= wl.orbitals.nocc[:, None],
+                                           0.05, 0.0), device="cuda")
+    w2 = screened_interaction(shifted, psi.detach(), scr, 0)
+    torch.cuda.synchronize()
+    assert rel_fro(w2.cpu().numpy(), ref.w) > 1e-6
     scr.close()
+
+
+def test_device_setters_match_host_setters(lrs, case):
+    """lrs_set_energies_dev / lrs_set_site_orbitals_dev give chi0 and W bit-identical to the host
+    setters, and the quadrature rule reads the energies set on the device."""
+    import torch
+    wl, ref, q = case
+    o = wl.orbitals
+    e_new = o.energies + np.where(np.arange(o.nbands)[None, :] >= o.nocc[:, None], 0.03, -0.02)
+    res = []
+    for dev in (False, True):
+        scr = lrs.Screening(0, "fp64", torch.cuda.current_stream().cuda_stream)
+        scr.load(o)
+        scr.set_sites(wl.sites)
+        if dev:
+            e_t = torch.tensor(e_new, dtype=torch.float64, device="cuda")
+            p_t = torch.tensor(public_psi(ref.pr), dtype=torch.complex128, device="cuda")
+            scr.set_energies_dev(e_t.data_ptr())
+            scr.set_site_orbitals_dev(0, p_t.data_ptr())
+        else:
+            scr.set_energies(e_new)
+            scr.set_site_orbitals(0, public_psi(ref.pr))
+        mu, zeta = scr.set_frequency_quadrature(wl.nfreq)
+        scr.build_chi0()
+        scr.solve_w()
+        res.append((mu, zeta, scr.get_chi0(0), scr.get_w(0)))
+        scr.close()
+    assert res[0][0] == res[1][0] and res[0][1] == res[1][1]
+    assert np.array_equal(res[0][2], res[1][2]) and np.array_equal(res[0][3], res[1][3])
+    with pytest.raises(lrs.LrsError):
+        scr = lrs.Screening(0, "fp64")
+        try:
+            scr.set_energies_dev(0)
+        finally:
+            scr.close()
 
 
 def test_mixed_adjoint_on_tensor_cores(lrs, case):
@@ -173,6 +220,8 @@ def test_mixed_adjoint_on_tensor_cores(lrs, case):
     ge, gp = scr.backward(0, grad_w=np.outer(q, q))
     oe, op = oracle_grads(ref, gamma_w=np.outer(q, q))
     err_e, err_p = rel_fro(ge, oe), rel_fro(gp, op)
-    print(f"mixed adjoint vs oracle gradient: energies {err_e:.2e}, orbitals {err_p:.2e}")
+    print(f"mixed adjoint vs oracle gradient: energies {err_e:.2e} (max {max_rel(ge, oe):.2e}), "
+          f"orbitals {err_p:.2e} (max {max_rel(gp, op):.2e})")
     assert err_e < 1e-5 and err_p < 1e-5   # mixed-path tolerance (measured 1.4e-6, 1.9e-6)
+    assert max_rel(ge, oe) < 1e-5 and max_rel(gp, op) < 1e-5
     scr.close()

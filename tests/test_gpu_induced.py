@@ -7,7 +7,7 @@ import pytest
 
 from oracle import induced as oind
 from paper_2005_07834_gb300 import synth
-from tests.gpu_util import Reference, rel_fro
+from tests.gpu_util import Reference, max_rel, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,9 @@ def test_induced_matches_oracle(lrs, case260, precision, tol):
         for q, rs in ((-1.0, 1.5), (1.0, 3.0)):
             rho, vind, grid = scr.induced_potential(0, q, rs, lresp)
             _, orho, ovind = oind.induced_potential(ref.chi0, s.pts, s.wts, s.nrad, s.nang, q, rs, lresp)
-            e = (rel_fro(rho, orho), rel_fro(vind, ovind), rel_fro(grid, oind.on_grid(ovind, s.pts, s.nang)))
+            ogrid = oind.on_grid(ovind, s.pts, s.nang)
+            e = (rel_fro(rho, orho), rel_fro(vind, ovind), rel_fro(grid, ogrid),
+                 max_rel(rho, orho), max_rel(vind, ovind), max_rel(grid, ogrid))
             print(f"{precision} l_resp {lresp} q {q} R_S {rs}: rho {e[0]:.1e} v_ind {e[1]:.1e} grid {e[2]:.1e}")
             assert max(e) < tol
     scr.close()

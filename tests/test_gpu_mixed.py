@@ -1,12 +1,13 @@
 """Mixed-precision (bf16x3 tensor-core) path vs the FP64 oracle through the C-ABI.
 
-Tolerance: 1e-5 relative Frobenius for chi0 and W (measured ~1e-7 and ~1e-9).
+Tolerance: 1e-5, both relative Frobenius and element-wise (max |d| / max |ref|), for psi,
+chi0, W and W - v.
 """
 import numpy as np
 import pytest
 
 from paper_2005_07834_gb300 import synth
-from tests.gpu_util import Reference, public_psi, rel_fro
+from tests.gpu_util import Reference, max_rel, public_psi, rel_fro
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -37,6 +38,7 @@ def test_mixed_projection(lrs, cfg_260):
     psi = scr.get_site_orbitals(0)
     err = rel_fro(psi, public_psi(cfg_260.pr))
     assert err < TOL, err
+    assert max_rel(psi, public_psi(cfg_260.pr)) < TOL
     scr.close()
 
 
@@ -47,6 +49,7 @@ def test_mixed_chi0_from_exact_orbitals(lrs, cfg_260):
     scr.synchronize()
     chi = scr.get_chi0(0)
     assert rel_fro(chi, cfg_260.chi0) < TOL
+    assert max_rel(chi, cfg_260.chi0) < TOL
     assert np.array_equal(chi, chi.T)
     scr.close()
 
@@ -57,10 +60,13 @@ def test_mixed_full_build(lrs, cfg_260):
     scr.project()
     scr.build_chi0()
     scr.solve_w()
-    assert rel_fro(scr.get_chi0(0), ref.chi0) < TOL
+    chi = scr.get_chi0(0)
     w = scr.get_w(0)
-    assert rel_fro(w, ref.w) < TOL
-    assert rel_fro(w - ref.v, ref.w - ref.v) < 1e-3
+    e = {"chi0": (rel_fro(chi, ref.chi0), max_rel(chi, ref.chi0)), "w": (rel_fro(w, ref.w), max_rel(w, ref.w)),
+         "w-v": (rel_fro(w - ref.v, ref.w - ref.v), max_rel(w - ref.v, ref.w - ref.v))}
+    print("bf16x3 260-point site (fro, max):", {k: (f"{a:.2e}", f"{b:.2e}") for k, (a, b) in e.items()})
+    for k, (a, b) in e.items():
+        assert a < TOL and b < TOL, (k, a, b)
     scr.close()
 
 
@@ -73,6 +79,8 @@ def test_mixed_ragged_multisite(lrs):
     scr.solve_w()
     for i in range(2):
         ref = Reference(wl, site=i)
-        assert rel_fro(scr.get_chi0(i), ref.chi0) < TOL
-        assert rel_fro(scr.get_w(i), ref.w) < TOL
+        chi, w = scr.get_chi0(i), scr.get_w(i)
+        assert rel_fro(chi, ref.chi0) < TOL and max_rel(chi, ref.chi0) < TOL
+        assert rel_fro(w, ref.w) < TOL and max_rel(w, ref.w) < TOL
+        assert rel_fro(w - ref.v, ref.w - ref.v) < TOL and max_rel(w - ref.v, ref.w - ref.v) < TOL
     scr.close()

@@ -153,6 +153,21 @@ def test_pair_and_green_routes_agree(tiny8):
     assert np.max(np.abs(c - a[rows])) < 1e-14 * np.max(np.abs(a))
 
 
+def test_green_route_rows_match_the_pair_sum(tiny8):
+    """The row-restricted Green's-function route (used on the large site grids, where the full
+    matrix is too costly for every check) against the independent pair sum, rows in any order,
+    repeated and at both ends."""
+    pr = tiny8
+    npts = pr.po.shape[0]
+    rows = [npts - 1, 0, 7, 7, 3]
+    a = chi0.chi0_pairs(*pr.args(), pr.t, pr.W, rows=rows)
+    b = chi0.chi0_green(*pr.args(), pr.t, pr.W, rows=rows)
+    assert b.shape == (len(rows), npts)
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
+    full = chi0.chi0_green(*pr.args(), pr.t, pr.W)
+    assert np.max(np.abs(full[rows] - b)) < 1e-14 * np.max(np.abs(full))
+
+
 def test_chi0_invariants(tiny8):
     pr = tiny8
     for kw in (dict(exact=True), dict(t=pr.t, W=pr.W)):
