@@ -11,8 +11,21 @@ measures the same through the C-ABI with page-locked host buffers
 (host->device copy of the coefficients and device->host copy of W inside the
 timed region).
 
+After the timed region (default 3520-point site):
+  plain_fp64          the same build on the plain FP64 path, and the mixed path's
+                      chi0, W and W - v errors against it;
+  backward            the adjoint of L = q^T W q on this site (device buffers,
+                      tensor roofline) and on the 260-point differentiation case;
+  workloads           the 64-site workload (graph replay, rooflines, mixed vs
+                      plain FP64 on a seeded sample of sites, oracle on the two
+                      smallest sites);
+  cpu_baseline        the FP64 oracle on the host cores on a bounded sample of the
+                      build, whose outputs (chi0 rows, dense LU on each path's chi0)
+                      give accuracy_vs_oracle.
+
 --impl reference times the FP64 CPU oracle on the host cores instead (rank 0
-only), on a bounded sample of the same workload.
+only), each step a bounded sample of the same workload; its `ms_per_step` is
+the sample's wall time and `value` the throughput scaled from it.
 """
 import argparse
 import json
@@ -164,35 +177,160 @@ def dist_setup():
     return world, rank, local
 
 
-def make_workload(name):
+def make_workload(name, nfreq=0):
+    """The named synthetic workload; nfreq > 0 replaces its frequency count (smaller profiler captures)."""
+    import dataclasses
     from paper_2005_07834_gb300 import synth
-    return getattr(synth, WORKLOADS[name])()
+    wl = getattr(synth, WORKLOADS[name])()
+    return dataclasses.replace(wl, nfreq=nfreq) if nfreq else wl
 
 
-# ----------------------------------------------------------------------------- reference arm
+# ----------------------------------------------------------------------------- shared descriptions
 
-def oracle_build_sample(wl, kfrac_k=1, nfreq_sample=2):
-    """Times the FP64 oracle on one site: projection on `kfrac_k` of the k-points,
-    chi0 by the Green's-function route on `nfreq_sample` of the frequencies, and
-    the full Dyson solve; returns the time of one whole build scaled from it."""
+DTYPE = {"fp64": "f64",
+         "bf16x3": "bf16x3 chi0/adjoint + fp16x3 projection, f32 accumulate, f64 denominators/frequency sum/Dyson",
+         "fp16x3": "fp16x3, f32 accumulate, f64 denominators/frequency sum/Dyson"}
+DYSON_SAMPLE_SITES = 4      # sites of the 64-site workload rebuilt by the plain FP64 path for the error report
+ORACLE_ROWS = 48            # chi0 rows the oracle evaluates on the single-site workloads
+
+
+def workload_config(name, wl, args):
+    """The `config` object of both arms: names the workload and its sizes (no precision: `dtype`
+    and `precision` say how each arm computes)."""
+    o = wl.orbitals
+    K = o.nk * o.nbands
+    if name in MULTI_SITE:
+        sizes = [s.npts for s in wl.sites]
+        return {"workload": name, "sites": len(sizes), "npts_min": min(sizes), "npts_max": max(sizes),
+                "npts_sum": sum(sizes), "K": K, "nfreq": wl.nfreq, "ng": o.ng, "projection": args.projection,
+                "graph": "one CUDA graph replay per step", "l2": "inputs larger than L2"}
+    s = wl.sites[0]
+    return {"workload": name, "npts": s.npts, "K": K, "nfreq": wl.nfreq, "ng": o.ng, "replicas_per_gpu": 1,
+            "projection": args.projection, "real_orbitals": name.startswith("gamma"),
+            "l2": "inputs larger than L2 (coefficients %d MB, orbitals %d MB)" % (
+                o.coeff.nbytes >> 20, (s.npts * K * 16) >> 20)}
+
+
+def errors(a, ref):
+    """Relative Frobenius and element-wise (max |d| / max |ref|) error."""
+    d = a - ref
+    return {"fro": float(np.linalg.norm(d) / np.linalg.norm(ref)), "max": float(np.max(np.abs(d)) / np.max(np.abs(ref)))}
+
+
+def matrix_errors(chi, w, v, chi_ref, w_ref):
+    return {"chi0": errors(chi, chi_ref), "w": errors(w, w_ref), "w_minus_v": errors(w - v, w_ref - v)}
+
+
+# ----------------------------------------------------------------------------- CPU legs (FP64 oracle)
+
+def oracle_reference_sample(wl):
+    """One step of the reference arm: the FP64 oracle on one site, on a bounded sample of the
+    build - projection of the first k-point (its orbitals stand in for the other k-points'), the
+    Green's-function chi0 on the first frequency over all rows, and the full dense Dyson LU on that
+    chi0 (each frequency term is negative semidefinite, so the solve is a representative one).
+    Returns the measured seconds and the seconds of one whole build scaled from them
+    (projection x nk, chi0 x nfreq, LU x 1)."""
     from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
     o, s = wl.orbitals, wl.sites[0]
     t0 = time.perf_counter()
-    psi_k = oproj.project_direct(o.cell, o.kpts[:kfrac_k], o.gvec, o.coeff[:kfrac_k], s.center, s.pts)
-    t_proj = (time.perf_counter() - t0) * o.nk / kfrac_k
-    # orbitals of the remaining k-points are not timed: reuse the sampled ones
-    psi = np.concatenate([psi_k] * (o.nk // kfrac_k), axis=1)
+    psi_k = oproj.project_direct(o.cell, o.kpts[:1], o.gvec, o.coeff[:1], s.center, s.pts)
+    t_proj = time.perf_counter() - t0
+    psi = np.concatenate([psi_k] * o.nk, axis=1)
     po, pu, eo, eu, wo, wu = oproj.split_occupied(psi, o.energies, o.nocc, o.kweights)
     mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
     t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
     t0 = time.perf_counter()
-    chi = ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t[:nfreq_sample], W[:nfreq_sample])
-    t_chi = (time.perf_counter() - t0) * wl.nfreq / nfreq_sample
+    chi = ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t[:1], W[:1])
+    t_chi = time.perf_counter() - t0
     t0 = time.perf_counter()
     v = ocoul.coulomb_multipole(s.pts, s.lmax)
     odys.screened_interaction(v, chi, s.wts)
     t_w = time.perf_counter() - t0
-    return t_proj + t_chi + t_w, {"t_project_s": t_proj, "t_chi0_s": t_chi, "t_w_s": t_w}
+    measured = t_proj + t_chi + t_w
+    scaled = t_proj * o.nk + t_chi * wl.nfreq + t_w
+    return measured, scaled, {"t_project_s": t_proj, "t_chi0_s": t_chi, "t_w_s": t_w,
+                              "scale_project": o.nk, "scale_chi0": wl.nfreq, "scale_w": 1}
+
+
+def oracle_single_site_leg(wl, results):
+    """cpu_baseline leg of the single-site workloads: the FP64 oracle on the host cores on a bounded
+    sample of one build, timed, whose outputs double as the accuracy reference:
+      * orbitals on every site point for every k-point by the direct sum (Sec. VI.B method 1), timed;
+      * chi0 by the Green's-function route over all rows on the first frequency, timed (x nfreq);
+      * v and the dense LU of (I - v Q chi0 Q) W = v on the library's chi0, timed;
+      * chi0 on ORACLE_ROWS seeded rows at every frequency (not timed): the accuracy reference.
+    `results` maps a path name to (chi0, W, v) from the library; each is compared with the oracle:
+    its chi0 rows element-wise and by row norms, and its W and W - v with the oracle's dense LU applied
+    to that path's own chi0 (the Dyson route, the rounding of chi0 taken out).  The mixed path is
+    also compared with the plain one.  Returns (cpu_baseline dict, accuracy dict)."""
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
+    o, s = wl.orbitals, wl.sites[0]
+    rows = np.sort(np.random.default_rng(3).choice(s.npts, ORACLE_ROWS, replace=False))
+    t0 = time.perf_counter()
+    psi = oproj.project_direct(o.cell, o.kpts, o.gvec, o.coeff, s.center, s.pts)
+    t_proj = time.perf_counter() - t0
+    po, pu, eo, eu, wo, wu = oproj.split_occupied(psi, o.energies, o.nocc, o.kweights)
+    mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
+    t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
+    t0 = time.perf_counter()
+    ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t[:1], W[:1])
+    t_chi1 = time.perf_counter() - t0
+    first = next(iter(results))
+    t0 = time.perf_counter()
+    v = ocoul.coulomb_multipole(s.pts, s.lmax)
+    w_first = odys.screened_interaction(v, results[first][0], s.wts)
+    t_w = time.perf_counter() - t0
+    t_build = t_proj + t_chi1 * wl.nfreq + t_w
+    chi_rows = ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t, W, rows=rows)
+    acc = {"reference": "FP64 oracle on the host cores: orbitals by the direct sum on every point, chi0 on "
+                        f"{len(rows)} seeded rows (Green's-function route), W by a dense LU on each path's own chi0",
+           "rows": int(len(rows))}
+    for name, (chi, w, v_lib) in results.items():
+        w_lu = w_first if name == first else odys.screened_interaction(v, chi, s.wts)
+        acc[name] = {"chi0_rows": errors(chi[rows], chi_rows),
+                     "chi0_rows_max_row_fro": float(np.max(np.linalg.norm(chi[rows] - chi_rows, axis=1)
+                                                           / np.linalg.norm(chi_rows, axis=1))),
+                     "v": errors(v_lib, v), "dyson_w": errors(w, w_lu), "dyson_w_minus_v": errors(w - v, w_lu - v)}
+    if "mixed" in results and "fp64" in results:
+        cm, wm, _ = results["mixed"]
+        cp, wp, _ = results["fp64"]
+        acc["mixed_vs_fp64_gpu"] = {"chi0": errors(cm, cp), "w": errors(wm, wp), "w_minus_v": errors(wm - v, wp - v)}
+    cpu = {"value": 1.0 / t_build, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"one site: orbitals on all {s.npts} points for all {o.nk} k-points, chi0 over all rows on 1 "
+                     f"of {wl.nfreq} frequencies (x {wl.nfreq}), full Dyson LU",
+           "parts_s": {"t_project_s": t_proj, "t_chi0_one_frequency_s": t_chi1, "t_w_s": t_w},
+           "measured_s": t_proj + t_chi1 + t_w}
+    return cpu, acc
+
+
+def oracle_multisite_leg(wl, sites, lib):
+    """cpu_baseline leg of the multi-site workloads: the whole FP64 oracle build (direct-sum
+    orbitals, Green's-function chi0, dense LU) of the given sites, timed and scaled to every site by
+    the algorithmic cost 8 N^2 K nf + 14/3 N^3; `lib` maps a site to the mixed path's (chi0, W, v)
+    for the accuracy report."""
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
+    o = wl.orbitals
+    K = o.nk * o.nbands
+    mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
+    t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
+    acc, t_all = {}, 0.0
+    for i in sites:
+        s = wl.sites[i]
+        t0 = time.perf_counter()
+        psi = oproj.project_direct(o.cell, o.kpts, o.gvec, o.coeff, s.center, s.pts)
+        po, pu, eo, eu, wo, wu = oproj.split_occupied(psi, o.energies, o.nocc, o.kweights)
+        chi = ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t, W)
+        v = ocoul.coulomb_multipole(s.pts, s.lmax)
+        w = odys.screened_interaction(v, chi, s.wts)
+        t_all += time.perf_counter() - t0
+        c, g, _ = lib[i]
+        acc[str(i)] = {"npts": s.npts, **matrix_errors(c, g, v, chi, w)}
+    scale = sum(site_cost(s, K, wl.nfreq) for s in wl.sites) / sum(site_cost(wl.sites[i], K, wl.nfreq)
+                                                                   for i in sites)
+    cpu = {"value": len(wl.sites) / (t_all * scale), "unit": "site builds/s", "cores": os.cpu_count(),
+           "kind": "oracle", "sample": f"sites {list(sites)} built whole by the oracle ({t_all:.2f} s), scaled to all "
+                                       f"{len(wl.sites)} sites by 8 N^2 K nf + 14/3 N^3 (x{scale:.1f})"}
+    return cpu, acc
 
 
 def run_reference(args):
@@ -201,30 +339,292 @@ def run_reference(args):
         return
     wl = make_workload(args.workload)
     cores = os.cpu_count()
-    sample = (f"one site of {args.workload}: projection timed on 1 of {wl.orbitals.nk} k-points, chi0 "
-              f"(Green's-function route) on 2 of {wl.nfreq} frequencies, full Dyson LU; scaled to one build")
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle_build_sample(wl)
-    times = []
-    parts = None
+    if args.workload in MULTI_SITE:
+        # the smallest site, the oracle's whole build, scaled by the algorithmic cost
+        o = wl.orbitals
+        K = o.nk * o.nbands
+        small = min(range(len(wl.sites)), key=lambda i: wl.sites[i].npts)
+        sub = type(wl)(wl.name, o, [wl.sites[small]], wl.nfreq, wl.fft_grid)
+        work = site_cost(wl.sites[small], K, wl.nfreq) / sum(site_cost(s, K, wl.nfreq) for s in wl.sites)
+
+        def one_step():
+            m, scaled, parts = oracle_reference_sample(sub)
+            return m, scaled / work, parts
+        sample = (f"site {small} ({wl.sites[small].npts} points) of {args.workload}: projection of 1 of {o.nk} "
+                  f"k-points, chi0 on 1 of {wl.nfreq} frequencies (all rows), full Dyson LU; scaled to that site "
+                  "(x nk, x nfreq) and to all sites by 8 N^2 K nf + 14/3 N^3")
+        unit = "site builds/s"
+        per_build = len(wl.sites)
+    else:
+        def one_step():
+            return oracle_reference_sample(wl)
+        sample = (f"one site of {args.workload}: projection of 1 of {wl.orbitals.nk} k-points, chi0 "
+                  f"(Green's-function route) on 1 of {wl.nfreq} frequencies over all rows, full Dyson LU; "
+                  "scaled to one build (x nk, x nfreq, x 1)")
+        unit = "builds/s"
+        per_build = 1
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    measured, scaled, parts = [], [], None
     for _ in range(args.steps):
-        t, parts = oracle_build_sample(wl)
-        times.append(t)
-    ms = 1e3 * statistics.mean(times)
-    value = 1e3 / ms
-    line = {"impl": "reference", "metric": "site chi0+W builds/s", "value": value, "unit": "builds/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        m, sc, parts = one_step()
+        measured.append(m)
+        scaled.append(sc)
+    ms_sample = 1e3 * statistics.mean(measured)
+    s_build = statistics.mean(scaled)
+    value = per_build / s_build
+    line = {"impl": "reference", "metric": "site chi0+W builds/s", "value": value, "unit": unit,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            # wall time of one step as run (the bounded sample); `value` comes from the scaled time
+            "ms_per_step": ms_sample,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded generator)",
-            "config": {"workload": args.workload, "precision": "fp64-oracle-cpu"},
-            "cpu_baseline": {"value": value, "unit": "builds/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": value, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "precision": "fp64 oracle on the host cores", "data": "synthetic (seeded generator)",
+            "config": workload_config(args.workload, wl, args),
+            "sample_ms_per_step": ms_sample, "scaled_s_per_build": s_build,
+            "scale_factor": s_build * 1e3 / ms_sample,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "parts_s": parts}
     print(json.dumps(line), flush=True)
 
 
-# ----------------------------------------------------------------------------- our arm
+# ----------------------------------------------------------------------------- GPU legs
+
+def timed_on(stream, fn, warmup, steps):
+    """Median device time (ms) of fn() by CUDA events on `stream`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms))
+
+
+def backward_leg(lrs, scr, stream, s, K, nf, peaks, precision, real=False):
+    """Adjoint of L = q^T W q (q seeded N(0,1)) for one site, device buffers, event-timed: the
+    Green's functions recomputed per frequency (8 N^2 K) and the four H psi products (16 N^2 K)."""
+    import torch
+    n = s.npts
+    from paper_2005_07834_gb300 import synth
+    q = torch.tensor(synth.loss_weights(n, seed=2), dtype=torch.float64, device="cuda")
+    gw = torch.outer(q, q).contiguous()
+    ge = torch.empty(K, dtype=torch.float64, device="cuda")
+    gp = torch.empty((n, K), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    ms = timed_on(stream, lambda: scr.backward_dev(0, gw.data_ptr(), 0, ge.data_ptr(), gp.data_ptr()), 1, 3)
+    st = scr.stats()
+    flop = (12.0 if real else 24.0) * n * n * K * nf
+    out = {"ms": ms, "ms_library": st["ms_backward"], "flop": flop,
+           "achieved_tflops": flop / (ms * 1e-3) / 1e12, "device_bytes_peak": st["device_bytes_peak"],
+           "flop_model": "per frequency: G recompute 8 N^2 K + four H psi products 16 N^2 K (complex)"}
+    if precision == "fp64":
+        out.update({"bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "peak_source": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2.07 GHz"})
+    else:
+        pk = peaks["bf16_tflops_sustained"]
+        out.update({"bound": "tensor", "peak": pk, "unit": "TFLOP/s",
+                    "peak_source": f"bf16 sustained, {peaks['source']}",
+                    "issued_frac": 3 * out["achieved_tflops"] / pk})
+    out["frac"] = out["achieved_tflops"] / out["peak"]
+    return out
+
+
+def config4_backward(lrs, stream):
+    """Differentiation workload: 260-point site, FP64 context, L = q^T W q; microseconds per
+    forward build and per backward (device buffers, event-timed medians)."""
+    import torch
+    from paper_2005_07834_gb300 import synth
+    wl = synth.single_site_260()
+    o, s = wl.orbitals, wl.sites[0]
+    scr = lrs.Screening(0, "fp64", stream.cuda_stream)
+    scr.load(o)
+    scr.set_sites([s])
+    scr.set_frequency_quadrature(wl.nfreq)
+
+    def fwd():
+        scr.project()
+        scr.build_chi0()
+        scr.solve_w()
+    ms_f = timed_on(stream, fwd, 3, 20)
+    q = torch.tensor(synth.loss_weights(s.npts, seed=2), dtype=torch.float64, device="cuda")
+    gw = torch.outer(q, q).contiguous()
+    K = o.nk * o.nbands
+    ge = torch.empty(K, dtype=torch.float64, device="cuda")
+    gp = torch.empty((s.npts, K), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    ms_b = timed_on(stream, lambda: scr.backward_dev(0, gw.data_ptr(), 0, ge.data_ptr(), gp.data_ptr()), 3, 20)
+    scr.close()
+    return {"workload": "single-site-260 (differentiation)", "precision": "fp64", "us_forward": 1e3 * ms_f,
+            "us_backward": 1e3 * ms_b, "loss": "q^T W q, q ~ N(0,1) seed 2"}
+
+
+def gpu_path(lrs, precision, stream, wl, sites, pmode):
+    """A context with the workload's orbitals and `sites` built once (projection, chi0, W)."""
+    scr = lrs.Screening(0, precision, stream.cuda_stream)
+    scr.load(wl.orbitals)
+    scr.set_sites(sites)
+    scr.set_frequency_quadrature(wl.nfreq)
+    scr.set_fft_grid(*wl.fft_grid)
+    scr.project(mode=pmode)
+    scr.build_chi0()
+    scr.solve_w()
+    scr.synchronize()
+    return scr
+
+
+def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True, oracle_sites=0):
+    """Graph-replayed build of every site of a multi-site workload: site builds/s, both rooflines,
+    the eager stage split, and (compare) the mixed path against the plain FP64 path on a seeded sample
+    of sites, and (oracle_sites > 0) against the FP64 oracle on the smallest sites."""
+    import torch
+    o = wl.orbitals
+    K = o.nk * o.nbands
+    pmode = proj_mode(lrs, args)
+    scr = lrs.Screening(0, args.precision, stream.cuda_stream)
+    scr.load(o)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(wl.nfreq)
+    scr.set_fft_grid(*wl.fft_grid)
+    scr.set_option(lrs.LRS_OPT_GRAPH_PROJECTION, pmode)
+    if args.dyson_lanes:
+        scr.set_option(lrs.LRS_OPT_DYSON_LANES, args.dyson_lanes)
+    tuned = None
+    if args.precision != "fp64":
+        scr.project(mode=pmode)
+        tuned = scr.autotune()
+    scr.graph_capture()
+    scr.synchronize()
+    for _ in range(warmup):
+        scr.graph_launch()
+    scr.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        scr.graph_launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    scr.synchronize()   # raises if a device-side wait timed out during the replays
+    ms = e0.elapsed_time(e1) / steps
+    # stage split of one eager build (event-timed inside the library); its kernel count is the
+    # count of one replay (the graph records the same launches)
+    launches0 = scr.stats()["kernel_launches"]
+    scr.project(mode=pmode)
+    scr.build_chi0()
+    scr.solve_w()
+    st = scr.stats()
+    launches_per_build = st["kernel_launches"] - launches0
+    flop_chi0 = sum(8.0 * s.npts ** 2 * K * wl.nfreq for s in wl.sites)
+    flop_all = sum(site_cost(s, K, wl.nfreq) for s in wl.sites)
+    main_ms = st["ms_chi0_main"]
+    pk = peaks["bf16_tflops_sustained"]
+    roof = {"bound": "tensor", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+            "peak_source": f"bf16 sustained, {peaks['source']}",
+            "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk, "traffic": None,
+            "traffic_source": "not captured for this workload",
+            "kernel": "zgemm_tc_kernel<chi0> (all sites, one launch per workspace group)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    st["dyson_update_tc"] = args.precision != "fp64"
+    roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"),
+                            peaks["hbm_gbs"])
+    dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
+    out = {"value": len(wl.sites) * 1e3 / ms, "unit": "site builds/s", "ms_per_step": ms, "steps": steps,
+           "warmup": warmup, "tflops": flop_all / (ms * 1e-3) / 1e12, "autotuned": tuned,
+           "dyson_lanes": args.dyson_lanes or 2, "config": workload_config(args.workload, wl, args),
+           "stage_ms_eager": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
+                              "w": st["ms_w"]},
+           "roofline": roof_w if dominant_w else roof,
+           "roofline_chi0" if dominant_w else "roofline_dyson": roof if dominant_w else roof_w,
+           "clocks": clocks, "device_bytes_peak": st["device_bytes_peak"],
+           "gpu_launches": int(launches_per_build) * steps,
+           "gpu_launches_note": "kernels of one eager build x replays (a replay launches the recorded kernels)"}
+    mixed = {}
+    if compare and args.precision != "fp64":
+        rng = np.random.default_rng(5)
+        order = sorted(range(len(wl.sites)), key=lambda i: wl.sites[i].npts)
+        pick = sorted({order[0], order[-1], *rng.choice(order[1:-1], DYSON_SAMPLE_SITES - 2, replace=False)})
+        for i in set(pick) | set(order[:oracle_sites]):
+            mixed[i] = (scr.get_chi0(i), scr.get_w(i), scr.get_v(i))
+        plain = gpu_path(lrs, "fp64", stream, wl, [wl.sites[i] for i in pick], pmode)
+        ms_plain = timed_on(stream, lambda: (plain.build_chi0(), plain.solve_w()), 0, 1)
+        cmp = {}
+        for j, i in enumerate(pick):
+            c, w, v = mixed[i]
+            cmp[str(i)] = {"npts": wl.sites[i].npts,
+                           **matrix_errors(c, w, v, plain.get_chi0(j), plain.get_w(j))}
+        plain.close()
+        t_mixed = st["ms_chi0"] + st["ms_w"]    # eager, all sites
+        frac = sum(site_cost(wl.sites[i], K, wl.nfreq) for i in pick) / flop_all
+        out["mixed_vs_fp64_plain"] = {
+            "sites": cmp, "reference": "plain FP64 GPU path (chi0 on the FP64 pipe, Dyson with float64 FMAs)",
+            "fp64_plain_ms_sample_chi0_w": ms_plain,
+            "fp64_plain_site_builds_per_s_est": len(pick) / (ms_plain * 1e-3),
+            "mixed_eager_site_builds_per_s": len(wl.sites) / (t_mixed * 1e-3),
+            "note": f"plain FP64 timed on the sampled sites ({frac:.3f} of the workload's algorithmic flop)"}
+    scr.close()
+    return out, mixed
+
+
+def run_multisite_line(args):
+    """--workload batched-64-sites / large-cell-16-sites: one JSON line for the multi-site build."""
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2005_07834_gb300 import lrs
+    t_gen = time.perf_counter()
+    wl = make_workload(args.workload)
+    t_gen = time.perf_counter() - t_gen
+    o = wl.orbitals
+    K = o.nk * o.nbands
+    nsites_total = len(wl.sites)
+    if world > 1:
+        # sites are independent: each rank builds its own share (no data-path collective)
+        from paper_2005_07834_gb300 import sharding
+        mine = sharding.shard_sites(wl.sites, K, wl.nfreq, rank, world)
+        wl = type(wl)(wl.name, o, [wl.sites[i] for i in mine], wl.nfreq, wl.fft_grid)
+    stream = torch.cuda.Stream()
+    peaks = load_peaks()
+    if world > 1:
+        torch.distributed.barrier()
+    res, mixed = multisite_measure(args, lrs, wl, stream, args.steps, args.warmup, peaks,
+                                   compare=(rank == 0 and not args.no_fp64_compare),
+                                   oracle_sites=0 if args.no_cpu_baseline else 2)
+    ms = res["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank == 0:
+        cpu, acc = None, None
+        if not args.no_cpu_baseline and mixed:
+            small = sorted(range(len(wl.sites)), key=lambda i: wl.sites[i].npts)[:2]
+            cpu, acc = oracle_multisite_leg(wl, small, mixed)
+        line = {"metric": "site chi0+W builds/s", "value": nsites_total * 1e3 / ms, "unit": "site builds/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[args.precision], "precision": args.precision,
+                "data": "synthetic (seeded generator; no DFT orbitals)", **{k: v for k, v in res.items()
+                                                                              if k not in ("value", "ms_per_step",
+                                                                                           "steps", "warmup")},
+                "cpu_baseline": cpu, "accuracy_vs_oracle": acc, "e2e": None, "generation_s": t_gen}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
 
 def run_ours(args):
     import torch
@@ -235,7 +635,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2005_07834_gb300 import lrs
 
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.nfreq)
     o, s = wl.orbitals, wl.sites[0]
     stream = torch.cuda.Stream()
     scr = lrs.Screening(local, args.precision, stream.cuda_stream)
@@ -262,7 +662,6 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    chi_main_ms, chi_ms, w_ms, proj_ms = [], [], [], []
     barrier()
     sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -320,8 +719,9 @@ def run_ours(args):
 
     peaks = load_peaks()
     n, K, nf = s.npts, o.nk * o.nbands, wl.nfreq
+    real = bool(scr.orbitals_are_real())
     # complex x complex products: 8 flop per multiply-add; Gamma-point real orbitals make B real (4)
-    flop_chi0 = (4.0 if scr.orbitals_are_real() else 8.0) * n * n * K * nf
+    flop_chi0 = (4.0 if real else 8.0) * n * n * K * nf
     main_ms = st["ms_chi0_main"]
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
@@ -331,65 +731,77 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": pk,
                 "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {peaks['source']}",
                 "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk}
+        if clocks.get("sm_mhz") and peaks.get("clocks_under_load", {}).get("sm_mhz_median"):
+            # the sustained peak was taken at the clock the driver saw under its GEMM loop; the burst
+            # peak scaled to this run's median SM clock is the tighter denominator when they differ
+            burst_here = peaks["bf16_tflops"] * clocks["sm_mhz"] / peaks.get("sm_max_mhz", 2070.0)
+            roof["frac_of_burst_at_sampled_clock"] = roof["achieved"] / burst_here
     roof["frac"] = roof["achieved"] / roof["peak"]
     version = lrs.lrs_version().decode()
-    roof["traffic"] = CHI0_TRAFFIC.get((args.workload, args.precision, kernel_revision(version, "chi0-tc")))
+    rev = kernel_revision(version, "chi0-tc")
+    roof["traffic"] = CHI0_TRAFFIC.get((args.workload, args.precision, rev))
+    roof["traffic_source"] = (f"stored ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of kernel "
+                              f"revision chi0-tc {rev}" if roof["traffic"] else
+                              "no ncu capture of this kernel revision on this workload")
     roof["kernel"] = "chi0_fp64_kernel" if args.precision == "fp64" else "zgemm_tc_kernel<chi0>"
     roof["library"] = version
-    # FP64 Dyson: its dominant kernel is the trailing update of the SPD inverse (one launch per
-    # pivot block), timed per launch with CUDA events on its stream inside the library; algorithmic
-    # flop per launch = 2 kb x the lower-triangle elements it updates
+    # the SPD inverse's trailing update (one launch per pivot block), timed per launch with CUDA
+    # events on its stream inside the library
     st["dyson_update_tc"] = args.precision != "fp64"   # LRS_UPDATE_AUTO: tensor cores in the mixed precisions
     roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"), peaks["hbm_gbs"])
-    # the roofline object describes the kernel that dominates the step; the other is kept beside it
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
 
-    # the plain FP64 path on the same workload, one untimed-warm step (for "mixed vs FP64 plain")
-    plain = None
+    chi_mixed, w_mixed, v_lib = scr.get_chi0(0), scr.get_w(0), scr.get_v(0)
+    # the plain FP64 path on the same workload, one step (for "mixed vs FP64 plain")
+    plain, results = None, {("mixed" if args.precision != "fp64" else "fp64"): (chi_mixed, w_mixed, v_lib)}
     if rank == 0 and args.precision != "fp64" and not args.no_fp64_compare:
         scr3 = lrs.Screening(local, "fp64", stream.cuda_stream)
         scr3.load(o)
         scr3.set_sites([s])
         scr3.set_frequency_quadrature(wl.nfreq)
-        torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
         scr3.set_fft_grid(*wl.fft_grid)
-        scr3.project(mode=pmode)
-        scr3.build_chi0()
-        scr3.solve_w()
-        p1.record(stream)
         torch.cuda.synchronize()
+        plain_ms = timed_on(stream, lambda: (scr3.project(mode=pmode), scr3.build_chi0(), scr3.solve_w()), 0, 1)
         st3 = scr3.stats()
-        plain_ms = p0.elapsed_time(p1)
         chi_plain, w_plain = scr3.get_chi0(0), scr3.get_w(0)
         scr3.close()
-        chi_mixed, w_mixed = scr.get_chi0(0), scr.get_w(0)
+        results["fp64"] = (chi_plain, w_plain, v_lib)
         plain = {"builds_per_s": 1e3 / plain_ms, "ms_per_step": plain_ms,
                  "stage_ms": {"project": st3["ms_project"], "chi0": st3["ms_chi0"], "w": st3["ms_w"]},
                  "mixed_vs_plain_speedup": plain_ms / ms,
-                 "mixed_rel_err_chi0": float(np.linalg.norm(chi_mixed - chi_plain) / np.linalg.norm(chi_plain)),
-                 "mixed_rel_err_w": float(np.linalg.norm(w_mixed - w_plain) / np.linalg.norm(w_plain))}
+                 "mixed_vs_plain": {"chi0": errors(chi_mixed, chi_plain), "w": errors(w_mixed, w_plain),
+                                    "w_minus_v": errors(w_mixed - v_lib, w_plain - v_lib)}}
+
+    backward = None
+    if rank == 0 and not args.no_backward:
+        backward = {"workload": args.workload, "precision": args.precision,
+                    **backward_leg(lrs, scr, stream, s, K, nf, peaks, args.precision, real)}
+        backward["differentiation_260"] = config4_backward(lrs, stream)
+    scr.close()
+
+    workloads = None
+    if rank == 0 and args.workloads:
+        workloads = {}
+        for name in args.workloads.split(","):
+            sub = argparse.Namespace(**{**vars(args), "workload": name})
+            wl2 = make_workload(name)
+            res, mixed = multisite_measure(sub, lrs, wl2, stream, 5, 2, peaks, compare=True,
+                                           oracle_sites=0 if args.no_cpu_baseline else 2)
+            if not args.no_cpu_baseline and mixed:
+                small = sorted(range(len(wl2.sites)), key=lambda i: wl2.sites[i].npts)[:2]
+                res["cpu_baseline"], res["accuracy_vs_oracle"] = oracle_multisite_leg(wl2, small, mixed)
+            workloads[name] = res
 
     if rank == 0:
-        cpu = None
+        cpu, acc = None, None
         if not args.no_cpu_baseline:
-            t_cpu, parts = oracle_build_sample(wl)
-            cpu = {"value": 1.0 / t_cpu, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": f"one site: projection on 1 of {o.nk} k-points, chi0 (Green's-function route) on 2 "
-                             f"of {nf} frequencies, full Dyson LU; scaled to one build", "parts_s": parts}
+            cpu, acc = oracle_single_site_leg(wl, results)
         line = {
             "metric": "site chi0+W builds/s", "value": value, "unit": "builds/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "bf16x3": "bf16x3/f32acc/f64", "fp16x3": "fp16x3/f32acc/f64"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "precision": args.precision,
             "data": "synthetic (seeded generator; no DFT orbitals)",
-            "config": {"workload": args.workload, "npts": n, "K": K, "nfreq": nf, "ng": o.ng,
-                       "precision": args.precision, "replicas_per_gpu": 1, "projection": args.projection,
-                       "real_orbitals": bool(scr.orbitals_are_real()),
-                       "l2": "inputs larger than L2 (coefficients %d MB, orbitals %d MB)" % (
-                           o.coeff.nbytes >> 20, (n * K * 16) >> 20)},
+            "config": workload_config(args.workload, wl, args),
             "tflops": (flop_chi0 + 14.0 / 3.0 * n ** 3) / (ms * 1e-3) / 1e12,
             "stage_ms": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
                          "w": st["ms_w"]},
@@ -399,11 +811,11 @@ def run_ours(args):
                             "tflops_executed": st["flop_w_executed"] / (st["ms_w"] * 1e-3) / 1e12,
                             "frac_fp64_peak": st["flop_w_executed"] / (st["ms_w"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                             "flop_full_grid_formula": st["flop_w"]},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "cpu_baseline": cpu, "accuracy_vs_oracle": acc, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "device_bytes_peak": st["device_bytes_peak"], "plain_fp64": plain,
+            "backward": backward, "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
-    scr.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -412,126 +824,6 @@ def site_cost(s, K, nf):
     """Algorithmic flop of one site build: 8 N^2 K nf (chi0) + 14/3 N^3 (Dyson)."""
     n = s.npts
     return 8.0 * n * n * K * nf + 14.0 / 3.0 * n ** 3
-
-
-def run_ours_multisite(args):
-    """All sites of the workload per step: one CUDA-graph replay of projection,
-    chi0 (one persistent tensor-core launch over every site) and the Dyson solves."""
-    import torch
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2005_07834_gb300 import lrs
-
-    t_gen = time.perf_counter()
-    wl = make_workload(args.workload)
-    t_gen = time.perf_counter() - t_gen
-    o = wl.orbitals
-    K = o.nk * o.nbands
-    nsites_total = len(wl.sites)
-    if world > 1:
-        # sites are independent: each rank builds its own share (no data-path collective)
-        from paper_2005_07834_gb300 import sharding
-        mine = sharding.shard_sites(wl.sites, K, wl.nfreq, rank, world)
-        wl = type(wl)(wl.name, o, [wl.sites[i] for i in mine], wl.nfreq, wl.fft_grid)
-    stream = torch.cuda.Stream()
-    scr = lrs.Screening(local, args.precision, stream.cuda_stream)
-    scr.load(o)
-    scr.set_sites(wl.sites)
-    scr.set_frequency_quadrature(wl.nfreq)
-    tuned = None
-    pmode = proj_mode(lrs, args)
-    scr.set_fft_grid(*wl.fft_grid)
-    scr.set_option(lrs.LRS_OPT_GRAPH_PROJECTION, pmode)
-    if args.dyson_lanes:
-        scr.set_option(lrs.LRS_OPT_DYSON_LANES, args.dyson_lanes)
-    if args.precision != "fp64":
-        scr.project(mode=pmode)
-        tuned = scr.autotune()
-    scr.graph_capture()
-    scr.synchronize()
-    for _ in range(args.warmup):
-        scr.graph_launch()
-    scr.synchronize()
-    sampler = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        scr.graph_launch()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    scr.synchronize()   # raises if a device-side wait timed out during the replays
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    nsites = len(wl.sites)
-    value = nsites_total * 1e3 / ms
-    # stage split of one eager build (event-timed inside the library)
-    scr.project(mode=pmode)
-    scr.build_chi0()
-    scr.solve_w()
-    st = scr.stats()
-    flop_chi0 = sum(8.0 * s.npts ** 2 * K * wl.nfreq for s in wl.sites)
-    flop_all = sum(site_cost(s, K, wl.nfreq) for s in wl.sites)
-    peaks = load_peaks()
-    main_ms = st["ms_chi0_main"]
-    pk = peaks["bf16_tflops_sustained"]
-    roof = {"bound": "tensor", "achieved": flop_chi0 / (main_ms * 1e-3) / 1e12, "peak": pk, "unit": "TFLOP/s",
-            "peak_source": f"bf16 sustained, {peaks['source']}",
-            "issued_frac": 3 * flop_chi0 / (main_ms * 1e-3) / 1e12 / pk, "traffic": None,
-            "kernel": "zgemm_tc_kernel<chi0> (all sites, one launch per workspace group)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    st["dyson_update_tc"] = args.precision != "fp64"
-    roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"), peaks["hbm_gbs"])
-    dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
-    if rank == 0:
-        cpu = None
-        if not args.no_cpu_baseline:
-            # the oracle on the smallest site, scaled to all sites by the algorithmic cost
-            small = min(range(nsites), key=lambda i: wl.sites[i].npts)
-            sub = type(wl)(wl.name, o, [wl.sites[small]], wl.nfreq)
-            t_cpu, parts = oracle_build_sample(sub)
-            scale = flop_all / site_cost(wl.sites[small], K, wl.nfreq)
-            cpu = {"value": nsites / (t_cpu * scale), "unit": "site builds/s", "cores": os.cpu_count(),
-                   "kind": "oracle",
-                   "sample": f"site {small} ({wl.sites[small].npts} points): projection on 1 of {o.nk} k-points, "
-                             f"chi0 on 2 of {wl.nfreq} frequencies, full LU; scaled to all {nsites} sites by "
-                             "8 N^2 K nf + 14/3 N^3", "parts_s": parts}
-        sizes = [s.npts for s in wl.sites]
-        line = {
-            "metric": "site chi0+W builds/s", "value": value, "unit": "site builds/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "bf16x3": "bf16x3/f32acc/f64", "fp16x3": "fp16x3/f32acc/f64"}[args.precision],
-            "data": "synthetic (seeded generator; no DFT orbitals)",
-            "config": {"workload": args.workload, "sites": nsites, "npts_min": min(sizes), "npts_max": max(sizes),
-                       "npts_sum": sum(sizes), "K": K, "nfreq": wl.nfreq, "ng": o.ng, "precision": args.precision,
-                       "projection": args.projection,
-                       "graph": "one CUDA graph replay per step", "autotuned": tuned,
-                       "dyson_lanes": args.dyson_lanes or 2,
-                       "l2": "inputs larger than L2"},
-            "tflops": flop_all / (ms * 1e-3) / 1e12,
-            "stage_ms_eager": {"project": st["ms_project"], "chi0": st["ms_chi0"], "chi0_main": main_ms,
-                               "w": st["ms_w"]},
-            "roofline": roof_w if dominant_w else roof,
-            "roofline_chi0" if dominant_w else "roofline_dyson": roof if dominant_w else roof_w,
-            "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
-            "device_bytes_peak": st["device_bytes_peak"], "generation_s": t_gen,
-        }
-        print(json.dumps(line), flush=True)
-    scr.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
 
 
 def run_rows(args):
@@ -650,6 +942,13 @@ def main():
                     help="concurrent Dyson solves of the multi-site workloads (0: the library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-backward", action="store_true",
+                    help="skip the adjoint timings (this workload and the 260-point differentiation case)")
+    ap.add_argument("--nfreq", type=int, default=0,
+                    help="replace the workload's frequency count (0: keep it); for small profiler captures only")
+    ap.add_argument("--workloads", default="batched-64-sites",
+                    help="comma-separated multi-site workloads measured after a single-site run and reported "
+                         "in its `workloads` object ('' for none)")
     ap.add_argument("--rows", action="store_true",
                     help="time each next-row operation (FFT projection, induced response, ALDA, augmentation, "
                          "Gamma point) on the 3520-point site instead of the build")
@@ -659,7 +958,7 @@ def main():
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload in MULTI_SITE:
-        run_ours_multisite(args)
+        run_multisite_line(args)
     else:
         run_ours(args)
 

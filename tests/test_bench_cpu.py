@@ -40,3 +40,37 @@ def test_peaks_have_every_denominator():
     for key in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "source"):
         assert key in peaks
     assert peaks["hbm_gbs"] > 1000 and peaks["bf16_tflops_sustained"] > 100
+
+
+def test_both_arms_name_the_same_config():
+    import argparse
+    from paper_2005_07834_gb300 import synth
+    args = argparse.Namespace(projection="exact")
+    wl = synth.single_site_260()
+    a = bench.workload_config("single-site-260", wl, args)
+    assert a == bench.workload_config("single-site-260", wl, args)
+    assert "precision" not in a and a["npts"] == 260 and a["K"] == 256
+
+
+def test_oracle_leg_reports_errors_of_each_path():
+    """The cpu_baseline leg's accuracy report, fed the oracle's own chi0 (perturbed by a known
+    relative amount) as a library result: errors of that size come back, and the Dyson check of an
+    exact W is at rounding level."""
+    import numpy as np
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys
+    from paper_2005_07834_gb300 import synth
+    from tests.oracle_problem import OracleProblem
+    wl = synth.single_site_260()
+    pr = OracleProblem(wl)
+    chi = ochi0.chi0_green(*pr.args(), pr.t, pr.W)
+    v = ocoul.coulomb_multipole(pr.site.pts, pr.site.lmax)
+    bad = chi * (1.0 + 1e-6)
+    res = {"mixed": (bad, odys.screened_interaction(v, bad, pr.site.wts), v),
+           "fp64": (chi, odys.screened_interaction(v, chi, pr.site.wts), v)}
+    cpu, acc = bench.oracle_single_site_leg(wl, res)
+    assert cpu["value"] > 0 and cpu["cores"] >= 1
+    assert abs(acc["mixed"]["chi0_rows"]["fro"] - 1e-6) < 1e-9
+    assert acc["fp64"]["chi0_rows"]["fro"] < 1e-13
+    for name in ("mixed", "fp64"):
+        assert acc[name]["dyson_w"]["fro"] < 1e-13 and acc[name]["v"]["fro"] < 1e-14
+    assert abs(acc["mixed_vs_fp64_gpu"]["chi0"]["fro"] - 1e-6) < 1e-9
