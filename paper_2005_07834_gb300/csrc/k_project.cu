@@ -7,6 +7,8 @@
 // L1/L2 while the contraction tiles are staged in shared memory.
 #include <cmath>
 
+#include <algorithm>
+
 #include "lrs_internal.h"
 
 namespace lrs {
@@ -53,12 +55,24 @@ constexpr int PT = 64;   // points per tile
 constexpr int BT = 64;   // bands per tile
 constexpr int GK = 16;   // plane waves per chunk
 
-// One k-point: psi[p][b] for a 64 x 64 tile, complex FP64, 4x4 outputs per thread.
+// Column offsets of the k-points of one launch (blockIdx.z = k - k0).
+constexpr int PROJ_KMAX = 64;
+struct ProjK {
+  int k0;
+  int nocc[PROJ_KMAX], oofs[PROJ_KMAX], uofs[PROJ_KMAX];
+};
+
+// psi[p][b] of k-point k0 + blockIdx.z for a 64 x 64 tile, complex FP64, 4x4 outputs per thread
+// (every k-point of a launch at once, so that small sites still fill the GPU).
 __global__ void __launch_bounds__(256) project_fp64_kernel(
     const double2* __restrict__ tab, int npts, int3 nmax, int off1, int off2,
-    const int* __restrict__ gvec, int ng, const double2* __restrict__ coeff_k, int nb,
-    const double2* __restrict__ kph, int nocc, double2* __restrict__ psi_o, int Ko, int oofs,
-    double2* __restrict__ psi_u, int Ku, int uofs) {
+    const int* __restrict__ gvec, int ng, const double2* __restrict__ coeff, int nb,
+    const double2* __restrict__ kphase, const ProjK pk, double2* __restrict__ psi_o, int Ko,
+    double2* __restrict__ psi_u, int Ku) {
+  const int kz = blockIdx.z, k = pk.k0 + kz;
+  const double2* __restrict__ coeff_k = coeff + (size_t)k * ng * nb;
+  const double2* __restrict__ kph = kphase + (size_t)k * npts;
+  const int nocc = pk.nocc[kz], oofs = pk.oofs[kz], uofs = pk.uofs[kz];
   __shared__ double2 As[GK][PT + 1];
   __shared__ double2 Bs[GK][BT + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -155,16 +169,22 @@ int project_fp64(lrs_ctx* ctx, Site& s) {
   LRS_TRY(phase_setup(ctx, s, &off1, &off2));
   const int* nm = ctx->gmax_idx;
   int oofs = 0, uofs = 0;
-  for (int k = 0; k < ctx->nk; ++k) {
-    dim3 grid((ctx->nb + BT - 1) / BT, (s.npts + PT - 1) / PT);
+  for (int k0 = 0; k0 < ctx->nk; k0 += PROJ_KMAX) {
+    const int nks = std::min(PROJ_KMAX, ctx->nk - k0);
+    ProjK pk;
+    pk.k0 = k0;
+    for (int j = 0; j < nks; ++j) {
+      pk.nocc[j] = ctx->nocc[k0 + j];
+      pk.oofs[j] = oofs;
+      pk.uofs[j] = uofs;
+      oofs += ctx->nocc[k0 + j];
+      uofs += ctx->nb - ctx->nocc[k0 + j];
+    }
+    dim3 grid((ctx->nb + BT - 1) / BT, (s.npts + PT - 1) / PT, nks);
     project_fp64_kernel<<<grid, 256, 0, ctx->stream>>>(
         ctx->ws.phase_tab.ptr, s.npts, make_int3(nm[0], nm[1], nm[2]), off1, off2, ctx->d_gvec.ptr,
-        ctx->ng, ctx->coeff.ptr + (size_t)k * ctx->ng * ctx->nb, ctx->nb,
-        ctx->ws.kphase.ptr + (size_t)k * s.npts, ctx->nocc[k], s.psi_o.ptr, ctx->Ko, oofs,
-        s.psi_u.ptr, ctx->Ku, uofs);
+        ctx->ng, ctx->coeff.ptr, ctx->nb, ctx->ws.kphase.ptr, pk, s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku);
     LRS_TRY(after_launch(ctx, "project_fp64_kernel"));
-    oofs += ctx->nocc[k];
-    uofs += ctx->nb - ctx->nocc[k];
   }
   return LRS_OK;
 }

@@ -565,43 +565,53 @@ __global__ void hprep_kernel(const float2* __restrict__ go, const float2* __rest
   }
 }
 
-__device__ __forceinline__ double2 zmul64(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
 // Same update as the float64 adjoint's grad_accum_kernel, from fp32 Y, Z.
+constexpr int GA32_ROWS = 256;
 template <bool kOcc>
-__global__ void grad_accum32_kernel(const double2* __restrict__ psi, const float2* __restrict__ Y,
-                                    const float2* __restrict__ Z, const double2* __restrict__ d,
-                                    const double* __restrict__ w, int n, int K, double2* __restrict__ gpsi,
-                                    double* __restrict__ ge) {
-  const int b = blockIdx.x;
-  const double2 db = d[b];
-  double er = 0.0, ei = 0.0;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const size_t ix = (size_t)p * K + b;
-    const float2 yf = Y[ix], zf = Z[ix];
-    const double2 y = make_double2(yf.x, yf.y), z = make_double2(zf.x, zf.y), ps = psi[ix];
-    const double2 dy = zmul64(db, y), dz = zmul64(db, z);
-    double2 g = gpsi[ix];
-    g.x += dy.x + dz.x;
-    g.y += kOcc ? (dy.y - dz.y) : (-dy.y + dz.y);
-    gpsi[ix] = g;
-    const double2 t = kOcc ? zmul64(make_double2(ps.x, -ps.y), y) : zmul64(ps, y);
-    er += t.x;
-    ei += t.y;
+__global__ void __launch_bounds__(256) grad_accum32_kernel(const double2* __restrict__ psi,
+                                                           const float2* __restrict__ Y,
+                                                           const float2* __restrict__ Z,
+                                                           const double2* __restrict__ d, int n, int K,
+                                                           double2* __restrict__ gpsi, double2* __restrict__ part) {
+  // 32 columns per CTA (one per lane: coalesced rows), GA32_ROWS rows in eight row groups.
+  // The products with d and psi are formed in fp32 (Y and Z are fp32 tensor-core results);
+  // each element's contribution is added to the float64 gradient once per frequency, and the
+  // column sums of the energy gradient leave the CTA as float64 partial sums.
+  __shared__ double2 red[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int b = blockIdx.x * 32 + tx;
+  const int p0 = blockIdx.y * GA32_ROWS;
+  float er = 0.f, ei = 0.f;
+  if (b < K) {
+    const double2 dd = d[b];
+    const float dx = (float)dd.x, dy = (float)dd.y;
+    const int p1 = min(n, p0 + GA32_ROWS);
+    for (int p = p0 + ty; p < p1; p += 8) {
+      const size_t ix = (size_t)p * K + b;
+      const float2 y = Y[ix], z = Z[ix];
+      const double2 ps = psi[ix];
+      const float sx = y.x + z.x, sy = y.y + z.y;                       // y + z
+      const float tx_ = kOcc ? y.x - z.x : z.x - y.x, ty_ = kOcc ? y.y - z.y : z.y - y.y;
+      double2 g = gpsi[ix];
+      g.x += (double)fmaf(dx, sx, -dy * sy);                           // Re d (y + z)
+      g.y += (double)fmaf(dx, ty_, dy * tx_);                          // Im d (y -+ z)
+      gpsi[ix] = g;
+      const float px = (float)ps.x, py = (float)ps.y;
+      if (kOcc) {                                                       // conj(psi) y
+        er += fmaf(px, y.x, py * y.y);
+        ei += fmaf(px, y.y, -py * y.x);
+      } else {                                                          // psi y
+        er += fmaf(px, y.x, -py * y.y);
+        ei += fmaf(px, y.y, py * y.x);
+      }
+    }
   }
-  __shared__ double sr[32], si[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    er += __shfl_down_sync(0xffffffffu, er, o);
-    ei += __shfl_down_sync(0xffffffffu, ei, o);
-  }
-  if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = er; si[threadIdx.x >> 5] = ei; }
+  red[ty][tx] = make_double2((double)er, (double)ei);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { er += sr[i]; ei += si[i]; }
-    const double2 d2 = zmul64(db, db);
-    ge[b] += (er * d2.x - ei * d2.y) / w[b];
+  if (ty == 0 && b < K) {
+    double2 s = red[0][tx];
+    for (int r = 1; r < 8; ++r) { s.x += red[r][tx].x; s.y += red[r][tx].y; }
+    part[(size_t)blockIdx.y * K + b] = s;
   }
 }
 
@@ -625,6 +635,8 @@ int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w, const doubl
   LRS_TRY(ensure(ctx, ws.yz32, 2 * (size_t)n * K));
   LRS_TRY(ensure(ctx, ws.gpsi, (size_t)n * K));
   LRS_TRY(ensure(ctx, ws.ge, (size_t)K));
+  const int chunks = (n + GA32_ROWS - 1) / GA32_ROWS;
+  LRS_TRY(ensure(ctx, ws.gpart, (size_t)chunks * K));
   LRS_TRY(ensure(ctx, ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * 128));
   LRS_TRY(ensure(ctx, ws.adj_tiles, (size_t)nf + 4));
   LRS_CUDA_TRY(cudaMemsetAsync(ws.gpsi.ptr, 0, (size_t)n * K * sizeof(double2), ctx->stream));
@@ -718,13 +730,14 @@ int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w, const doubl
     LRS_TRY((launch_tc<128, 1, 1, ZStore>(ctx, ma_h, mb_t, sy, zst, "zgemm_tc_kernel<adjoint>")));
     const double2* dof = ws.denom_o.ptr + (size_t)f * Ko;
     const double2* duf = ws.denom_u.ptr + (size_t)f * Ku;
-    grad_accum32_kernel<true><<<Ko, 256, 0, ctx->stream>>>(s.psi_o.ptr, Y + yoff[0], Y + yoff[1], dof, ctx->w_o.ptr,
-                                                           n, Ko, ws.gpsi.ptr, ws.ge.ptr);
+    grad_accum32_kernel<true><<<dim3((Ko + 31) / 32, chunks), 256, 0, ctx->stream>>>(
+        s.psi_o.ptr, Y + yoff[0], Y + yoff[1], dof, n, Ko, ws.gpsi.ptr, ws.gpart.ptr);
     LRS_TRY(after_launch(ctx, "grad_accum32_kernel"));
-    grad_accum32_kernel<false><<<Ku, 256, 0, ctx->stream>>>(s.psi_u.ptr, Y + yoff[2], Y + yoff[3], duf,
-                                                            ctx->w_u.ptr, n, Ku, ws.gpsi.ptr + (size_t)n * Ko,
-                                                            ws.ge.ptr + Ko);
+    LRS_TRY(grad_energy(ctx, ws.gpart.ptr, chunks, dof, ctx->w_o.ptr, Ko, ws.ge.ptr));
+    grad_accum32_kernel<false><<<dim3((Ku + 31) / 32, chunks), 256, 0, ctx->stream>>>(
+        s.psi_u.ptr, Y + yoff[2], Y + yoff[3], duf, n, Ku, ws.gpsi.ptr + (size_t)n * Ko, ws.gpart.ptr);
     LRS_TRY(after_launch(ctx, "grad_accum32_kernel"));
+    LRS_TRY(grad_energy(ctx, ws.gpart.ptr, chunks, duf, ctx->w_u.ptr, Ku, ws.ge.ptr + Ko));
   }
   return scatter_gradients(ctx, n, ws.gpsi.ptr, ws.gpsi.ptr + (size_t)n * Ko, ws.ge.ptr, grad_e, grad_psi);
 }

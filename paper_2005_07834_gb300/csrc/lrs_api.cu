@@ -348,7 +348,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.denom_o); release(ctx, w.denom_u); release(ctx, w.dyson_a); release(ctx, w.ipiv); release(ctx, w.tinv);
   release(ctx, w.status); release(ctx, w.phase_tab); release(ctx, w.kphase); release(ctx, w.ru);
   release(ctx, w.gamma_s); release(ctx, w.gbuf_o); release(ctx, w.gbuf_u); release(ctx, w.ybuf);
-  release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.tmp_nn);
+  release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.gpart); release(ctx, w.tmp_nn);
   release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.denom32); release(ctx, w.phase_tab32); release(ctx, w.tc_scratch); release(ctx, w.slab64);
   release(ctx, w.site_tiles);
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);

@@ -156,6 +156,7 @@ struct Workspace {
   DevBuf<double2> ybuf;               // [n][K]
   DevBuf<double> ge;                  // [K]
   DevBuf<double2> gpsi;               // [n][K]
+  DevBuf<double2> gpart;              // [row chunks][K] partial column sums of the energy gradient
   DevBuf<double> tmp_nn;              // [n][n]
   // mixed precision (bf16 hi/lo operand planes)
   DevBuf<uint16_t> planes_a, planes_b;  // chi0: per-frequency A, frequency-independent B
@@ -386,6 +387,9 @@ int backward_site(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double*
 int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev,
                         double* grad_e_dev, double2* grad_psi_dev);
 int gamma_s_build(lrs_ctx* ctx, Site& s, const double* grad_w_dev, const double* grad_chi0_dev);
+// ge[b] += Re[e_b d_b^2 / w_b], e_b the sum over `chunks` row chunks of part[chunk][b] (fixed order).
+int grad_energy(lrs_ctx* ctx, const double2* part, int chunks, const double2* d, const double* w, int K,
+                double* ge);
 int scatter_gradients(lrs_ctx* ctx, int n, const double2* gpo, const double2* gpu, const double* ge,
                       double* grad_e, double2* grad_psi);
 
