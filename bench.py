@@ -71,21 +71,36 @@ DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"):
                  ("single-site-3520", "r4"): 28.52e6}
 
 
-def dyson_roofline(st, workload=None, version=None, hbm_gbs=None):
-    """The SPD inverse's trailing update.  On the FP64 pipe (FP64 context) it is bound by the
-    FP64 FMA rate.  On the tensor cores its float64 work is one subtraction per element and its
-    algorithmic traffic one read and one write of each updated element of C (16 bytes; the
-    library counts 2 kb flop per updated element, kb = 32), so it is reported against the HBM
-    copy bandwidth, with the FP64-equivalent rate beside it."""
+def dyson_roofline(st, workload=None, version=None, hbm_gbs=None, bf16_tflops=None):
+    """The SPD inverse's trailing updates.  On the FP64 pipe (FP64 context) they are bound by the
+    FP64 FMA rate.  On the tensor cores their float64 work is one subtraction per element and their
+    algorithmic traffic one read and one write of each updated element (16 bytes; the library
+    reports the elements rewritten).  With 32-wide pivot blocks (28 slice products over K = 32 per
+    element) that traffic bounds the update, so it is reported against the HBM copy bandwidth;
+    with 128-wide blocks (36 slice products over K = 128 per element, the float64-accurate GEMM)
+    the issued tensor work does, so it is reported against the bf16 peak.  The FP64-equivalent rate
+    is given beside either."""
     if not st.get("w_main_launches"):
         return None
     ms = st["ms_w_main"]
     tc = st.get("dyson_update_tc", False)
     fp64_eq = st["flop_w_main"] / (ms * 1e-3) / 1e12
+    elems = st.get("w_main_elements") or st["flop_w_main"] / (2.0 * 32)
+    kb = st["flop_w_main"] / (2.0 * elems)
     common = {"launches": st["w_main_launches"], "avg_launch_us": 1e3 * ms / st["w_main_launches"],
-              "traffic": DYSON_TRAFFIC.get((workload, version))}
-    if tc and hbm_gbs:
-        algo_bytes = st["flop_w_main"] / (2.0 * 32) * 16.0
+              "pivot_block": round(kb), "traffic": DYSON_TRAFFIC.get((workload, version))}
+    algo_bytes = 16.0 * elems
+    if tc and kb > 64 and bf16_tflops:
+        issued = 36 * 2.0 * kb * elems
+        r = {"bound": "tensor",
+             "kernel": "oz_gemm_kernel (rank-128 trailing update, float64-accurate bf16 slices on tcgen05)",
+             "achieved": issued / (ms * 1e-3) / 1e12, "peak": bf16_tflops, "unit": "TFLOP/s",
+             "peak_source": "bf16 burst, measured (36 slice products per K element issued)",
+             "hbm_gbs_algorithmic": algo_bytes / (ms * 1e-3) / 1e9,
+             "algorithmic_bytes_per_launch": algo_bytes / st["w_main_launches"],
+             "fp64_equivalent_tflops": fp64_eq, "fp64_equivalent_vs_fp64_fma_peak": fp64_eq / FP64_PEAK_TFLOPS,
+             **common}
+    elif tc and hbm_gbs:
         r = {"bound": "hbm",
              "kernel": "oz_update_kernel (SPD-inverse trailing update, float64-accurate bf16 slices on tcgen05)",
              "achieved": algo_bytes / (ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
@@ -333,6 +348,51 @@ def oracle_multisite_leg(wl, sites, lib):
     return cpu, acc
 
 
+def oracle_sampled_sites_leg(wl, lib, rows=16, points=64):
+    """cpu_baseline leg of workloads whose sites are too large for a whole oracle build on the host
+    (the 9312-point sites of the large cell: the direct-sum projection alone is 8 N N_G K ~ 4e13 flop
+    per site).  Per site, timed, on the library's own intermediate results:
+      * orbitals by the direct sum on `points` seeded grid points, every band and k-point, against the
+        library's projection;
+      * chi0 on `rows` seeded rows by the Green's-function route, every frequency, from the library's
+        orbitals (isolates the mixed-precision contraction);
+      * v and the dense LU of (I - v Q chi0 Q) W = v on the library's chi0 (isolates the Dyson route).
+    The measured time is scaled to a whole build of every site (projection x N / points, chi0 rows x
+    N / 2 rows, LU x 1, then x sites) for the cpu_baseline value."""
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
+    o = wl.orbitals
+    mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
+    t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
+    acc, t_scaled = {}, 0.0
+    for i, (chi, w, v_lib, psi_lib) in lib.items():
+        s = wl.sites[i]
+        rng = np.random.default_rng(17 + i)
+        pts = np.sort(rng.choice(s.npts, points, replace=False))
+        rws = np.sort(rng.choice(s.npts, rows, replace=False))
+        t0 = time.perf_counter()
+        psi = oproj.project_direct(o.cell, o.kpts, o.gvec, o.coeff, s.center, s.pts[pts]).reshape(points, -1)
+        t_p = time.perf_counter() - t0
+        po, pu, eo, eu, wo, wu = oproj.split_occupied(psi_lib.reshape(s.npts, o.nk, o.nbands), o.energies, o.nocc,
+                                                      o.kweights)
+        t0 = time.perf_counter()
+        chi_rows = ochi0.chi0_green(po, pu, eo, eu, wo, wu, mu, t, W, rows=rws)
+        t_c = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        v = ocoul.coulomb_multipole(s.pts, s.lmax)
+        w_lu = odys.screened_interaction(v, chi, s.wts)
+        t_w = time.perf_counter() - t0
+        t_scaled += t_p * s.npts / points + t_c * s.npts / (2.0 * rows) + t_w
+        acc[str(i)] = {"npts": s.npts, "psi_sampled_points": errors(psi_lib[pts], psi),
+                       "chi0_rows_from_library_psi": errors(chi[rws], chi_rows), "v": errors(v_lib, v),
+                       "dyson_w": errors(w, w_lu), "dyson_w_minus_v": errors(w - v, w_lu - v),
+                       "oracle_s": {"project_sampled": t_p, "chi0_rows": t_c, "dense_lu": t_w}}
+    scale = len(wl.sites) / len(lib)
+    cpu = {"value": len(wl.sites) / (t_scaled * scale), "unit": "site builds/s", "cores": os.cpu_count(),
+           "kind": "oracle", "sample": f"sites {sorted(lib)}: direct-sum orbitals on {points} points, chi0 on {rows} "
+                                       "rows, dense Dyson LU; scaled to whole builds of every site"}
+    return cpu, acc
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -479,10 +539,11 @@ def gpu_path(lrs, precision, stream, wl, sites, pmode):
     return scr
 
 
-def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True, oracle_sites=0):
+def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True, oracle_sites=0, keep_psi=()):
     """Graph-replayed build of every site of a multi-site workload: site builds/s, both rooflines,
     the eager stage split, and (compare) the mixed path against the plain FP64 path on a seeded sample
-    of sites, and (oracle_sites > 0) against the FP64 oracle on the smallest sites."""
+    of sites, and (oracle_sites > 0) against the FP64 oracle on the smallest sites.  The mixed
+    results of the sites in `keep_psi` (orbitals included) are returned for sampled oracle checks."""
     import torch
     o = wl.orbitals
     K = o.nk * o.nbands
@@ -495,6 +556,8 @@ def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True,
     scr.set_option(lrs.LRS_OPT_GRAPH_PROJECTION, pmode)
     if args.dyson_lanes:
         scr.set_option(lrs.LRS_OPT_DYSON_LANES, args.dyson_lanes)
+    if args.dyson_panel:
+        scr.set_option(lrs.LRS_OPT_DYSON_PANEL, args.dyson_panel)
     tuned = None
     if args.precision != "fp64":
         scr.project(mode=pmode)
@@ -537,7 +600,7 @@ def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True,
     roof["frac"] = roof["achieved"] / roof["peak"]
     st["dyson_update_tc"] = args.precision != "fp64"
     roof_w = dyson_roofline(st, args.workload, kernel_revision(lrs.lrs_version().decode(), "dyson-gj"),
-                            peaks["hbm_gbs"])
+                            peaks["hbm_gbs"], peaks["bf16_tflops"])
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
     out = {"value": len(wl.sites) * 1e3 / ms, "unit": "site builds/s", "ms_per_step": ms, "steps": steps,
            "warmup": warmup, "tflops": flop_all / (ms * 1e-3) / 1e12, "autotuned": tuned,
@@ -550,6 +613,8 @@ def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True,
            "gpu_launches": int(launches_per_build) * steps,
            "gpu_launches_note": "kernels of one eager build x replays (a replay launches the recorded kernels)"}
     mixed = {}
+    for i in keep_psi:
+        mixed[i] = (scr.get_chi0(i), scr.get_w(i), scr.get_v(i), scr.get_site_orbitals(i))
     if compare and args.precision != "fp64":
         rng = np.random.default_rng(5)
         order = sorted(range(len(wl.sites)), key=lambda i: wl.sites[i].npts)
@@ -600,9 +665,27 @@ def run_multisite_line(args):
     peaks = load_peaks()
     if world > 1:
         torch.distributed.barrier()
+    large = max(s.npts for s in wl.sites) * K > 2e7     # whole oracle or FP64 builds take minutes per site
+    keep = (0, 1) if (large and rank == 0 and not args.no_cpu_baseline) else ()
     res, mixed = multisite_measure(args, lrs, wl, stream, args.steps, args.warmup, peaks,
-                                   compare=(rank == 0 and not args.no_fp64_compare),
-                                   oracle_sites=0 if args.no_cpu_baseline else 2)
+                                   compare=(rank == 0 and not args.no_fp64_compare and not large),
+                                   oracle_sites=0 if (args.no_cpu_baseline or large) else 2, keep_psi=keep)
+    if large:
+        res["mixed_vs_fp64_plain"] = ("not run: a plain FP64 build of one site is 8 N^2 K nf = %.0f TFLOP on the "
+                                      "FP64 pipe; accuracy comes from the sampled oracle checks" % (
+                                          8.0 * wl.sites[0].npts ** 2 * K * wl.nfreq / 1e12))
+    backward = None
+    if rank == 0 and not args.no_backward and large:
+        one = lrs.Screening(0, args.precision, stream.cuda_stream)
+        one.load(o)
+        one.set_sites(wl.sites[:1])
+        one.set_frequency_quadrature(wl.nfreq)
+        one.set_fft_grid(*wl.fft_grid)
+        one.project(mode=proj_mode(lrs, args))
+        one.build_chi0()
+        one.solve_w()
+        backward = {"site": 0, **backward_leg(lrs, one, stream, wl.sites[0], K, wl.nfreq, peaks, args.precision)}
+        one.close()
     ms = res["ms_per_step"]
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -610,9 +693,11 @@ def run_multisite_line(args):
         ms = float(t.item())
     if rank == 0:
         cpu, acc = None, None
-        if not args.no_cpu_baseline and mixed:
+        if not args.no_cpu_baseline and mixed and large:
+            cpu, acc = oracle_sampled_sites_leg(wl, {i: mixed[i] for i in keep})
+        elif not args.no_cpu_baseline and mixed:
             small = sorted(range(len(wl.sites)), key=lambda i: wl.sites[i].npts)[:2]
-            cpu, acc = oracle_multisite_leg(wl, small, mixed)
+            cpu, acc = oracle_multisite_leg(wl, small, {i: mixed[i][:3] for i in small})
         line = {"metric": "site chi0+W builds/s", "value": nsites_total * 1e3 / ms, "unit": "site builds/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -620,7 +705,8 @@ def run_multisite_line(args):
                 "data": "synthetic (seeded generator; no DFT orbitals)", **{k: v for k, v in res.items()
                                                                               if k not in ("value", "ms_per_step",
                                                                                            "steps", "warmup")},
-                "cpu_baseline": cpu, "accuracy_vs_oracle": acc, "e2e": None, "generation_s": t_gen}
+                "cpu_baseline": cpu, "accuracy_vs_oracle": acc, "e2e": None, "generation_s": t_gen,
+                "backward": backward}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -645,6 +731,8 @@ def run_ours(args):
 
     pmode = proj_mode(lrs, args)
     scr.set_fft_grid(*wl.fft_grid)
+    if args.dyson_panel:
+        scr.set_option(lrs.LRS_OPT_DYSON_PANEL, args.dyson_panel)
 
     def step():
         scr.project(mode=pmode)
@@ -748,7 +836,8 @@ def run_ours(args):
     # the SPD inverse's trailing update (one launch per pivot block), timed per launch with CUDA
     # events on its stream inside the library
     st["dyson_update_tc"] = args.precision != "fp64"   # LRS_UPDATE_AUTO: tensor cores in the mixed precisions
-    roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"), peaks["hbm_gbs"])
+    roof_w = dyson_roofline(st, args.workload, kernel_revision(version, "dyson-gj"), peaks["hbm_gbs"],
+                            peaks["bf16_tflops"])
     dominant_w = roof_w is not None and st["ms_w_main"] > main_ms
 
     chi_mixed, w_mixed, v_lib = scr.get_chi0(0), scr.get_w(0), scr.get_v(0)
@@ -940,6 +1029,8 @@ def main():
                     help="Sec. VI.B method 1 (direct sum) or method 2 (FFT + cubic Lagrange on the workload's grid)")
     ap.add_argument("--dyson-lanes", type=int, default=0,
                     help="concurrent Dyson solves of the multi-site workloads (0: the library default)")
+    ap.add_argument("--dyson-panel", type=int, default=0, choices=[0, 32, 128],
+                    help="pivot-block width of the lm-basis SPD inverse (0: the library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true",

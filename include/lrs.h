@@ -77,6 +77,7 @@ extern "C" {
 #define LRS_OPT_REAL_ORBITALS    8  /* value: LRS_REAL_AUTO (default) or LRS_REAL_OFF */
 #define LRS_OPT_DYSON_UPDATE     9  /* value: LRS_UPDATE_AUTO (default), LRS_UPDATE_FP64 or LRS_UPDATE_TC */
 #define LRS_OPT_DYSON_LANES     10  /* value: 1..8 concurrent Dyson solves in one lrs_solve_w call (default 2) */
+#define LRS_OPT_DYSON_PANEL     11  /* value: 0 (auto), 32 or 128: pivot-block width of the lm-basis SPD inverse */
 #define LRS_UPDATE_AUTO   0   /* tensor cores in the mixed precisions, the FP64 pipe in LRS_FP64 */
 #define LRS_UPDATE_FP64   1   /* trailing update of the SPD inverse with float64 FMAs */
 #define LRS_UPDATE_TC     2   /* float64-accurate update from exact bf16 slices on the tensor cores */
@@ -101,6 +102,7 @@ typedef struct lrs_stats_t {
   double ms_w_main;       /* device time of the SPD-inverse trailing-update launches of the last lrs_solve_w */
   double flop_w_main;     /* their algorithmic flop: 2 kb x (lower-triangle elements updated), summed */
   int64_t w_main_launches;/* how many such launches */
+  double w_main_elements; /* lower-triangle elements they rewrote, summed over the launches */
 } lrs_stats_t;
 
 /* Last error message of the calling thread ("" if none). */
@@ -145,6 +147,14 @@ int lrs_set_stream(lrs_ctx* ctx, void* stream);
  * accumulated per level exactly in fp32 and combined in float64 - an error
  * bound of about 6e-16 of |D|max |E|max per element, as for a float64 dot
  * product of 32 terms.
+ * LRS_OPT_DYSON_PANEL sets the width of the pivot blocks the SPD inverse
+ * exchanges at a time: 32, or 128 - the 128 x 128 pivot block inverted by the
+ * 32-wide steps, then D = C P and the rank-128 trailing update float64-accurate
+ * on the tensor cores (eight exact bf16 slices per row), so that the trailing
+ * matrix is rewritten once per 128 pivots.  Exchanging a block at once equals
+ * exchanging its parts in turn.  0 (default) and 32 take the 32-wide exchange,
+ * whose trailing updates overlap the serial pivot chain (measured faster on
+ * the 3520-point and 64-site workloads).
  * LRS_OPT_DYSON_LANES sets how many sites of one lrs_solve_w call are solved
  * concurrently, each on its own streams and workspace (sites are dealt to the
  * lanes by decreasing cost); a single site's serial pivot chain then overlaps

@@ -245,7 +245,11 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
     LRS_TRY(after_launch(ctx, "lm_left_kernel"));
     lm_right_kernel<false><<<g, 128, 0, ctx->stream>>>(B, s.fl.ptr, nrad, L2, -1.0, 1.0, Z);
     LRS_TRY(after_launch(ctx, "lm_right_kernel"));
-    LRS_TRY(spd_inverse(ctx, Z, r, r, ctx->ws.status.ptr));
+    // 128-wide pivot blocks on request (LRS_OPT_DYSON_PANEL); the default keeps the 32-wide
+    // exchange, whose trailing update overlaps the pivot chain
+    const bool blocked = ctx->dyson_panel == SPD_OUTER_BLOCK;
+    if (blocked) LRS_TRY(spd_inverse_blocked(ctx, Z, r, r, ctx->ws.status.ptr));
+    else LRS_TRY(spd_inverse(ctx, Z, r, r, ctx->ws.status.ptr));
     lm_left_kernel<false, true><<<g, 128, 0, ctx->stream>>>(Z, s.fl.ptr, nrad, L2, 1.0, 0.0, X);
     LRS_TRY(after_launch(ctx, "lm_left_kernel"));
     lm_right_kernel<true><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, Z);

@@ -1085,7 +1085,9 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
     LRS_CUDA_TRY(wait(s1, SPD_ADIAG, k));
     LRS_CUDA_TRY(wait(s1, SPD_AREST, k));
     if (k >= 1) LRS_CUDA_TRY(wait(s1, SPD_FIX, k - 1));   // bulk k updates block k - 1, just written back
-    LRS_TRY(stage_begin(ctx, ST_W_MAIN));
+    // the trailing updates of an inverse nested in the blocked one are not its main updates
+    const bool main = !ctx->spd_inner;
+    if (main) LRS_TRY(stage_begin(ctx, ST_W_MAIN));
     if (tc) {
       LRS_TRY(oz_update(ctx, md[q], me[q], A, n, lda, dsc[q], esc[q], k0, std::min(n, k0 + 2 * GJ_NB), rows_pad,
                         s1));
@@ -1093,13 +1095,14 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
       gj_update_kernel<<<(unsigned)(nt * (nt + 1) / 2), 128, 0, s1>>>(A, n, lda, kb, k, Db[q], Eb[q]);
       LRS_TRY(after_launch(ctx, "gj_update_kernel"));
     }
-    LRS_TRY(stage_end(ctx, ST_W_MAIN));
-    {
+    if (main) LRS_TRY(stage_end(ctx, ST_W_MAIN));
+    if (main) {
       // lower-triangle elements outside the rows and columns of blocks k and k + 1
       const double b0 = k0, b1 = std::min(n, k0 + 2 * GJ_NB), nn = n;
       const double rows_in = (b1 * (b1 + 1) - b0 * (b0 + 1)) / 2.0;   // sum of (i + 1), i in [b0, b1)
       const double elems = nn * (nn + 1) / 2.0 - rows_in - (b1 - b0) * (nn - b1);
       ctx->w_main_flop += 2.0 * kb * elems;
+      ctx->w_main_elems += elems;
       ++ctx->w_main_launches;
     }
     if (!tc) ctx->fp64_flops += (double)n * n * kb;

@@ -112,6 +112,7 @@ static void lane_swap(lrs_ctx* ctx, DysonLane& l) {
   std::swap(w.dyson_a, l.dyson_a);
   std::swap(w.tinv, l.tinv);
   std::swap(w.gj, l.gj);
+  std::swap(w.gjb, l.gjb);
   std::swap(w.alda_n, l.alda_n);
   std::swap(w.ipiv, l.ipiv);
   std::swap(w.oz_expo, l.oz_expo);
@@ -122,7 +123,7 @@ static void lane_swap(lrs_ctx* ctx, DysonLane& l) {
 }
 
 static void release_lane_buffers(lrs_ctx* ctx, DysonLane& l) {
-  release(ctx, l.dyson_a); release(ctx, l.tinv); release(ctx, l.gj); release(ctx, l.alda_n);
+  release(ctx, l.dyson_a); release(ctx, l.tinv); release(ctx, l.gj); release(ctx, l.gjb); release(ctx, l.alda_n);
   release(ctx, l.ipiv); release(ctx, l.oz_expo); release(ctx, l.og_expo);
   release(ctx, l.oz_planes); release(ctx, l.og_planes); release(ctx, l.ru);
 }
@@ -354,6 +355,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
+  release(ctx, w.gjb);
   release(ctx, w.oz_planes); release(ctx, w.oz_expo); release(ctx, w.og_planes); release(ctx, w.og_expo);
   release(ctx, w.fft_grid); release(ctx, w.fft_index); release(ctx, w.fft_tw);
   release(ctx, w.induced);
@@ -373,7 +375,7 @@ const char* lrs_last_error(void) { return g_last_error.c_str(); }
 
 // The chi0 tensor-core kernel revision lets measurements quote profiler
 // counters only for the kernel version they were taken on.
-const char* lrs_version(void) { return "lrs 0.4 (sm_103a) chi0-tc r1 dyson-gj r4"; }
+const char* lrs_version(void) { return "lrs 0.5 (sm_103a) chi0-tc r1 dyson-gj r5"; }
 
 int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   clear_error();
@@ -446,6 +448,11 @@ int lrs_set_option(lrs_ctx* ctx, int option, int value) {
       if (value != LRS_DYSON_AUTO && value != LRS_DYSON_FULL && value != LRS_DYSON_LM)
         return set_error(LRS_ERR_ARG, "unknown Dyson basis %d", value);
       ctx->dyson_basis = value;
+      return LRS_OK;
+    case LRS_OPT_DYSON_PANEL:
+      if (value != 0 && value != 32 && value != SPD_OUTER_BLOCK)
+        return set_error(LRS_ERR_ARG, "Dyson pivot-block width %d: 0 (auto), 32 or %d", value, SPD_OUTER_BLOCK);
+      ctx->dyson_panel = value;
       return LRS_OK;
     case LRS_OPT_DYSON_LANES:
       if (value < 1 || value > 8) return set_error(LRS_ERR_ARG, "Dyson lanes %d out of [1, 8]", value);
@@ -1049,6 +1056,7 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   double flop = 0;
   const double fp64_before = ctx->fp64_flops;
   ctx->w_main_flop = 0;
+  ctx->w_main_elems = 0;
   ctx->w_main_launches = 0;
   const int nl = std::min<int>(ctx->dyson_lanes, (int)list.size());
   if (nl <= 1) {
@@ -1105,6 +1113,7 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   ctx->stats.flop_w = flop;
   ctx->stats.flop_w_executed = ctx->fp64_flops - fp64_before;
   ctx->stats.flop_w_main = ctx->w_main_flop;
+  ctx->stats.w_main_elements = ctx->w_main_elems;
   ctx->stats.w_main_launches = ctx->w_main_launches;
   if (ctx->capturing) return LRS_OK;   // checked after each replay by lrs_graph_launch's caller
   // zero pivots / non-finite values are reported through the status word

@@ -173,6 +173,7 @@ struct Workspace {
   DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
+  DevBuf<double> gjb;                   // blocked SPD inverse: C, E, D [n][128] and the pivot block
   DevBuf<uint16_t> oz_planes;           // SPD inverse on tensor cores: slice planes of D, E (two sets)
   DevBuf<int> oz_expo;                  // and their row exponents
   DevBuf<uint16_t> og_planes;           // float64-accurate tensor-core GEMM: slice planes of both operands
@@ -214,7 +215,7 @@ struct DysonLane {
   cudaStream_t s1 = nullptr;
   SpdStreams spd;
   cudaEvent_t ev_done = nullptr;
-  DevBuf<double> dyson_a, tinv, gj, alda_n;
+  DevBuf<double> dyson_a, tinv, gj, gjb, alda_n;
   DevBuf<int> ipiv, oz_expo, og_expo;
   DevBuf<uint16_t> oz_planes, og_planes;
   DevBuf<RadialUnit> ru;
@@ -278,6 +279,9 @@ struct lrs_ctx {
   lrs_stats_t stats{};
   double fp64_flops = 0;               // running count of FP64 flop issued by the linear algebra
   double w_main_flop = 0;              // algorithmic flop of the SPD-inverse bulk updates of the last solve
+  double w_main_elems = 0;             // lower-triangle elements those updates rewrote (summed over launches)
+  bool spd_inner = false;              // an spd_inverse inside the blocked one: its updates are not "main"
+  int dyson_panel = 0;                 // LRS_OPT_DYSON_PANEL: 0 auto, 32 or SPD_OUTER_BLOCK
   int64_t w_main_launches = 0;
   // stage timing: event pairs of the stage's intervals since its last reset
   // (the main chi0 kernel runs once per workspace group of one build)
@@ -361,6 +365,10 @@ int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double 
 // In-place inverse of an SPD matrix; lower triangle in and out.  status[0] = 2
 // (status[1] = column) on a pivot that is not positive and finite.
 int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status);
+// The same inverse with SPD_OUTER_BLOCK-wide pivot blocks (k_spd_blocked.cu): the 32-wide inverse
+// of each pivot block, then D = C P and the trailing update on the float64-accurate tensor-core GEMM.
+constexpr int SPD_OUTER_BLOCK = 128;
+int spd_inverse_blocked(lrs_ctx* ctx, double* A, int n, int lda, int* status);
 
 // lm-basis Dyson on product grids (k_dyson_lm.cu)
 int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts_host);

@@ -32,6 +32,7 @@ LRS_FXC_NONE, LRS_FXC_USER, LRS_FXC_ALDA_X = 0, 1, 2
 LRS_OPT_REAL_ORBITALS, LRS_REAL_AUTO, LRS_REAL_OFF = 8, 0, 1
 LRS_OPT_DYSON_UPDATE, LRS_UPDATE_AUTO, LRS_UPDATE_FP64, LRS_UPDATE_TC = 9, 0, 1, 2
 LRS_OPT_DYSON_LANES = 10
+LRS_OPT_DYSON_PANEL = 11
 LRS_STATIC_MAX_NPTS = 512
 PRECISIONS = {"fp64": LRS_FP64, "bf16x3": LRS_MIXED_BF16X3, "fp16x3": LRS_MIXED_FP16X3}
 
@@ -41,7 +42,8 @@ class lrs_stats_t(C.Structure):
                 ("ms_backward", C.c_double), ("ms_chi0_main", C.c_double), ("flop_chi0", C.c_double),
                 ("flop_w", C.c_double), ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
                 ("device_bytes_peak", C.c_int64), ("status_word", C.c_int), ("flop_w_executed", C.c_double),
-                ("ms_w_main", C.c_double), ("flop_w_main", C.c_double), ("w_main_launches", C.c_int64)]
+                ("ms_w_main", C.c_double), ("flop_w_main", C.c_double), ("w_main_launches", C.c_int64),
+                ("w_main_elements", C.c_double)]
 
 
 if not os.path.exists(LIB_PATH):

@@ -74,3 +74,37 @@ def test_oracle_leg_reports_errors_of_each_path():
     for name in ("mixed", "fp64"):
         assert acc[name]["dyson_w"]["fro"] < 1e-13 and acc[name]["v"]["fro"] < 1e-14
     assert abs(acc["mixed_vs_fp64_gpu"]["chi0"]["fro"] - 1e-6) < 1e-9
+
+
+def test_sampled_oracle_leg_on_library_like_results():
+    """The sampled checks of large sites, fed the oracle's own orbitals, chi0 and W (chi0 perturbed by
+    a known relative amount): the projection and Dyson checks are at rounding level, the chi0 rows
+    report the perturbation."""
+    import numpy as np
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys
+    from paper_2005_07834_gb300 import synth
+    from tests.oracle_problem import OracleProblem
+    wl = synth.single_site_260()
+    pr = OracleProblem(wl)
+    chi = ochi0.chi0_green(*pr.args(), pr.t, pr.W) * (1.0 + 2e-6)
+    v = ocoul.coulomb_multipole(pr.site.pts, pr.site.lmax)
+    w = odys.screened_interaction(v, chi, pr.site.wts)
+    psi = pr.psi.reshape(pr.site.npts, -1)
+    cpu, acc = bench.oracle_sampled_sites_leg(wl, {0: (chi, w, v, psi)}, rows=8, points=16)
+    a = acc["0"]
+    assert a["psi_sampled_points"]["fro"] < 1e-13
+    assert abs(a["chi0_rows_from_library_psi"]["fro"] - 2e-6) < 1e-9
+    assert a["dyson_w"]["fro"] < 1e-13 and a["v"]["fro"] < 1e-14
+    assert cpu["value"] > 0
+
+
+def test_blocked_update_is_reported_against_the_tensor_peak():
+    """128-wide pivot blocks: the library reports 2 kb flop per rewritten element with kb = 128; the
+    bench counts 36 slice products per K element issued and reports against the bf16 peak."""
+    elems, launches, ms = 3.2e6, 20, 1.0
+    st = {"w_main_launches": launches, "ms_w_main": ms, "flop_w_main": 2.0 * 128 * elems * launches,
+          "w_main_elements": elems * launches, "dyson_update_tc": True}
+    r = bench.dyson_roofline(st, "x", "r5", hbm_gbs=6700.0, bf16_tflops=1900.0)
+    assert r["bound"] == "tensor" and r["pivot_block"] == 128
+    assert abs(r["achieved"] - 36 * 2.0 * 128 * elems * launches / (ms * 1e-3) / 1e12) < 1e-6
+    assert abs(r["hbm_gbs_algorithmic"] - 16.0 * elems * launches / (ms * 1e-3) / 1e9) < 1e-6

@@ -236,3 +236,37 @@ def test_tensor_core_basis_change_over_several_k_segments(lrs):
         print(f"{name}: tensor-core vs float64 arithmetic, W - v: {err:.2e}")
         assert err < 1e-12
     scr.close()
+
+
+def test_128_wide_pivot_blocks_match_32_wide(lrs):
+    """The SPD inverse exchanging 128-wide pivot blocks (each inverted by 32-wide steps, then
+    D = C P and the rank-128 trailing update on the float64-accurate tensor-core GEMM) against the
+    32-wide exchange, from the same chi0 on the 48 x 110 site (r = 3888: 30 full blocks and a
+    ragged one of 48) and on a 7 x 110 site (r = 567: four full blocks and one of 55): W - v agrees to
+    1e-12; the blocked solve rewrites the trailing matrix once per 128 pivots."""
+    wl = synth.single_site_260()
+    for nrad in (48, 7):
+        wl.sites = [synth.site_grid(wl.sites[0].center, nrad, 110, 4.0)]
+        scr = lrs.Screening(0, "bf16x3")
+        scr.load(wl.orbitals)
+        scr.set_sites(wl.sites)
+        scr.set_frequency_quadrature(8)
+        scr.project()
+        scr.build_chi0()
+        ws, launches = [], []
+        for panel in (32, 128, 0):
+            scr.set_option(lrs.LRS_OPT_DYSON_PANEL, panel)
+            scr.solve_w()
+            ws.append(scr.get_w(0))
+            launches.append(scr.stats()["w_main_launches"])
+        v = scr.get_v(0)
+        r = nrad * 81
+        err = rel_fro(ws[1] - v, ws[0] - v)
+        print(f"r = {r}: 128- vs 32-wide pivot blocks, W - v: {err:.2e}; update launches {launches}")
+        assert err < 1e-12
+        assert np.array_equal(ws[0], ws[2])               # the default takes 32-wide blocks
+        assert launches[1] == (r + 127) // 128 and launches[0] == (r + 31) // 32
+        with pytest.raises(lrs.LrsError) as e:
+            scr.set_option(lrs.LRS_OPT_DYSON_PANEL, 64)
+        assert e.value.code == lrs.LRS_ERR_ARG
+        scr.close()
