@@ -372,9 +372,14 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
   sh.nsites = ns;
   // Gamma-point real orbitals: B = [psi_o | conj psi_u] is real
   sh.real_b = ctx->real_orbitals && ctx->real_mode == LRS_REAL_AUTO ? 1 : 0;
+  // short K (each contraction at most two accumulation segments long): both contractions of a
+  // unit accumulate whole in their own TMEM set and the epilogue multiplies them straight from
+  // TMEM, with no folding of segments and no parking of the occupied sums
+  const bool direct = sh.nchunk0 <= 2 * sh.seg && sh.nchunk - sh.nchunk0 <= 2 * sh.seg;
   Chi0Store epi{ctx->ws.slab.ptr, ctx->ws.tc_scratch.ptr, 0, TN};
   LRS_TRY(stage_begin(ctx, ST_CHI0_MAIN));
-  LRS_TRY((launch_tc<TN, 2, FMT, Chi0Store>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0>")));
+  if (direct) LRS_TRY((launch_tc<TN, 2, FMT, Chi0Store, true>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0, short K>")));
+  else LRS_TRY((launch_tc<TN, 2, FMT, Chi0Store>(ctx, ma, mb, sh, epi, "zgemm_tc_kernel<chi0>")));
   LRS_TRY(stage_end(ctx, ST_CHI0_MAIN));
   for (int i = 0; i < ns; ++i) {
     Site& s = ctx->sites[list[i]];

@@ -145,7 +145,7 @@ __host__ __device__ constexpr int tc_smem_bytes() {
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int TN, int NPHASE, uint32_t FMT, class Epi>
+template <int TN, int NPHASE, uint32_t FMT, class Epi, bool DIRECT = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     zgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const TcShape sh, const Epi epi, int* status) {
@@ -218,6 +218,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
     producer_done:;
+    }
+  } else if (DIRECT && warp == 1) {
+    // ------------------------------------------------ MMA issue, short K: Go whole into set 0, Gu^T into set 1
+    if (lane == 0) {
+      constexpr uint32_t ID_POS = idesc_f16(TILE_M, TN, FMT, false);
+      constexpr uint32_t ID_NEG = idesc_f16(TILE_M, TN, FMT, true);
+      int stage = 0;
+      uint32_t phase = 0, unit_phase = 0;
+      const bool real_b = sh.real_b != 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        // both sets free: the epilogue has read the previous unit
+        if (!mbar_wait(&acce_bar[0], unit_phase ^ 1u, &abort_flag)) {
+          abort_flag = 1;
+          atomicCAS(status, 0, TC_TIMEOUT_MMA);
+          break;
+        }
+        tc_fence_after();
+        for (int c = 0; c < sh.nchunk; ++c) {
+          if (!mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+            abort_flag = 1;
+            atomicCAS(status, 0, TC_TIMEOUT_MMA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int set = c < sh.nchunk0 ? 0 : 1;
+          const int cl = set ? c - sh.nchunk0 : c;              // chunk within its contraction
+          const uint32_t dre = tbase + set * SET_COLS, dim = dre + TN;
+          const uint32_t s = smem_base + stage * STAGE_BYTES;
+          const uint32_t aR = s, aI = s + TILE_BYTES, bR = s + 2 * TILE_BYTES, bI = bR + B_TILE;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;
+            const uint32_t a0 = (cl == 0 && ks == 0) ? 0u : 1u;
+            if (real_b) {
+              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
+              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
+              mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, a0);
+              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
+            } else {
+              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
+              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
+              mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
+              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + hi), ID_NEG, 1u);
+              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + lo), ID_NEG, 1u);
+              mma_f16(dre, sw128_desc(aI + lo), sw128_desc(bI + hi), ID_NEG, 1u);
+              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + hi), ID_POS, a0);
+              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + lo), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aR + lo), sw128_desc(bI + hi), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
+              mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
+            }
+          }
+          mma_commit(&empty_bar[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(&accf_bar[1]);   // completes once every product of the unit has landed
+        unit_phase ^= 1u;
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issue
@@ -296,6 +360,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (set == 0) set_phase ^= 1u;
         }
       }
+    }
+  } else if (DIRECT) {
+    // ------------------------------------------------ epilogue, short K: both contractions read from TMEM
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+    const int lrow = quarter * 32 + lane, lcol0 = half * COLS;
+    uint32_t unit_phase = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      const Unit x = decode_unit<TN>(sh, sh.sites, sh.nsites, u);
+      int got = 1;
+      if (lane == 0) got = mbar_wait(&accf_bar[1], unit_phase, &abort_flag) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      __syncwarp();
+      if (!got) {
+        if (lane == 0) {
+          abort_flag = 1;
+          atomicCAS(status, 0, TC_TIMEOUT_EPILOGUE);
+        }
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tb = tbase + lane_off + lcol0;
+#pragma unroll 1
+      for (int j = 0; j < COLS / 16; ++j) {
+        float gr[16], gi[16], ur[16], ui[16];
+        tmem_ld16(tb + 16 * j, gr);                     // Go re, im (set 0)
+        tmem_ld16(tb + TN + 16 * j, gi);
+        tmem_ld16(tb + SET_COLS + 16 * j, ur);          // Gu^T re, im (set 1)
+        tmem_ld16(tb + SET_COLS + TN + 16 * j, ui);
+        tmem_ld_wait();
+        epi.store_direct16(gr, gi, ur, ui, x, x.tm * TILE_M + lrow, x.tn * TN + lcol0 + 16 * j);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[0]);
+      unit_phase ^= 1u;
     }
   } else {
     // ------------------------------------------------ epilogue (warps 2..9)
@@ -377,12 +478,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-template <int TN, int NPHASE, uint32_t FMT, class Epi>
+template <int TN, int NPHASE, uint32_t FMT, class Epi, bool DIRECT = false>
 int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const TcShape& sh, const Epi& epi,
               const char* name) {
+  static_assert(!DIRECT || (NPHASE == 2 && Epi::kDirect), "short-K mode: two contractions, chi0 epilogue");
   constexpr int smem = tc_smem_bytes<TN>();
   if (!ctx->capturing)
-    LRS_CUDA_TRY(cudaFuncSetAttribute(zgemm_tc_kernel<TN, NPHASE, FMT, Epi>,
+    LRS_CUDA_TRY(cudaFuncSetAttribute(zgemm_tc_kernel<TN, NPHASE, FMT, Epi, DIRECT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int grid = std::min(sh.units, ctx->num_sms);
   if (grid <= 0) return LRS_OK;
@@ -399,7 +501,7 @@ int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const 
   attr[0].val.priority = ctx->prio_greatest;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, zgemm_tc_kernel<TN, NPHASE, FMT, Epi>, ma, mb, sh, epi,
+  cudaError_t e = cudaLaunchKernelEx(&cfg, zgemm_tc_kernel<TN, NPHASE, FMT, Epi, DIRECT>, ma, mb, sh, epi,
                                      ctx->ws.status.ptr + 8);
   if (e != cudaSuccess) return set_error(LRS_ERR_CUDA, "%s launch: %s", name, cudaGetErrorString(e));
   return after_launch(ctx, name);
@@ -411,9 +513,24 @@ int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const 
 // [2][128][tile_n] fp32, L2 resident) while the unoccupied sums accumulate in
 // registers; each thread reads back only what it wrote.
 struct Chi0Store {
+  static constexpr bool kDirect = true;
   float* slab;      // [batches][ld][ld]
   float* scratch;   // [gridDim.x][2][128][tile_n]
   int ld, tile_n;
+  // Short K: both contractions of 16 columns of this thread's row, read straight from TMEM.
+  __device__ void store_direct16(const float (&gr)[16], const float (&gi)[16], const float (&ur)[16],
+                                 const float (&ui)[16], const Unit& x, int row, int col) const {
+    float* dst = slab + x.slab0 + ((size_t)x.b * x.ld + row) * x.ld + col;
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      float4 v;
+      v.x = fmaf(-gi[i + 0], ui[i + 0], gr[i + 0] * ur[i + 0]);
+      v.y = fmaf(-gi[i + 1], ui[i + 1], gr[i + 1] * ur[i + 1]);
+      v.z = fmaf(-gi[i + 2], ui[i + 2], gr[i + 2] * ur[i + 2]);
+      v.w = fmaf(-gi[i + 3], ui[i + 3], gr[i + 3] * ur[i + 3]);
+      *reinterpret_cast<float4*>(dst + i) = v;
+    }
+  }
   template <int COLS>
   __device__ void save_phase0(const float (&s)[2][COLS], int lrow, int lcol0) const {
     float* base = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
@@ -445,6 +562,9 @@ struct Chi0Store {
 // Adjoint: the Green's functions themselves, Go and Gu^T of one frequency,
 // as complex fp32 [np][np] (ld = unit.ld).
 struct GStore {
+  static constexpr bool kDirect = false;
+  __device__ void store_direct16(const float (&)[16], const float (&)[16], const float (&)[16], const float (&)[16],
+                                 const Unit&, int, int) const {}
   float2* go;
   float2* gu;
   float* scratch;   // [gridDim.x][2][128][tile_n]
@@ -477,6 +597,9 @@ struct GStore {
 // Adjoint: a plain complex product D (fp32 re, im) into out + unit.slab0,
 // rows < m_valid, columns < n_valid.
 struct ZStore {
+  static constexpr bool kDirect = false;
+  __device__ void store_direct16(const float (&)[16], const float (&)[16], const float (&)[16], const float (&)[16],
+                                 const Unit&, int, int) const {}
   float2* out;
   template <int COLS>
   __device__ void save_phase0(const float (&)[2][COLS], int, int) const {}
@@ -495,6 +618,9 @@ struct ZStore {
 // projection: psi(p, b) = e^{ik.R_p}/sqrt(Omega) * unscale * D(p, b), scattered
 // into the occupied / unoccupied orbital blocks.
 struct ProjStore {
+  static constexpr bool kDirect = false;
+  __device__ void store_direct16(const float (&)[16], const float (&)[16], const float (&)[16], const float (&)[16],
+                                 const Unit&, int, int) const {}
   const double2* kph;     // [nk][npts]
   const float* unscale;   // device scalar
   int npts, nb;
