@@ -223,10 +223,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         tmem_ld_wait();
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const long long V = ((long long)oz_level_int(a[0][c]) << 40) + ((long long)oz_level_int(a[1][c]) << 32) +
-                              ((long long)oz_level_int(a[2][c]) << 24) + ((long long)oz_level_int(a[3][c]) << 16) +
-                              ((long long)oz_level_int(a[4][c]) << 8) + (long long)oz_level_int(a[5][c]) +
-                              (long long)(oz_level_int(a[6][c]) >> 8);
+          // |S_L| < 2^22: pairs of levels combine exactly in int32 before one 64-bit assembly
+          const int t3 = (oz_level_int(a[0][c]) << 8) + oz_level_int(a[1][c]);
+          const int t2 = (oz_level_int(a[2][c]) << 8) + oz_level_int(a[3][c]);
+          const int t1 = (oz_level_int(a[4][c]) << 8) + oz_level_int(a[5][c]) + (oz_level_int(a[6][c]) >> 8);
+          const long long V = ((long long)t3 << 32) + ((long long)t2 << 16) + (long long)t1;
           const int fj = __shfl_sync(0xffffffffu, fj_lane, ch * 8 + c);
           double* q = stg + lane * OZ_STG_LD + ch * 8 + c;
           // entries of the stage outside the update hold stale values and are not written back

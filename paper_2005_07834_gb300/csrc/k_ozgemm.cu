@@ -369,10 +369,11 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
             // V = sum_L S_L 2^(42 - 7 L) with floor(S_7 / 2^7) (|V| < 2^62; the floor drops
             // less than 2^-56 of the row scales' product), rounded to float64 with integer
             // instructions
-            const long long V = ((long long)oz_level_int(a[0][c]) << 42) + ((long long)oz_level_int(a[1][c]) << 35) +
-                                ((long long)oz_level_int(a[2][c]) << 28) + ((long long)oz_level_int(a[3][c]) << 21) +
-                                ((long long)oz_level_int(a[4][c]) << 14) + ((long long)oz_level_int(a[5][c]) << 7) +
-                                (long long)oz_level_int(a[6][c]) + (long long)(oz_level_int(a[7][c]) >> 7);
+            const int ta = (oz_level_int(a[1][c]) << 7) + oz_level_int(a[2][c]);
+            const int tb = (oz_level_int(a[3][c]) << 7) + oz_level_int(a[4][c]);
+            const int tc = (oz_level_int(a[5][c]) << 7) + oz_level_int(a[6][c]) + (oz_level_int(a[7][c]) >> 7);
+            const long long V = ((long long)oz_level_int(a[0][c]) << 42) + ((long long)ta << 28) +
+                                ((long long)tb << 14) + (long long)tc;
             const int j = col0 + ch * 8 + c;
             const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
             stg[lane * 9 + c] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)

@@ -160,3 +160,31 @@ def test_products_within_a_float64_dot_product_bound(scheme):
             exact = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a[i], b[j]))
             bound = 2.0 ** -52 * K * np.max(np.abs(a[i])) * np.max(np.abs(b[j]))
             assert abs(Fraction(got[i, j]) - exact) <= Fraction(bound)
+
+
+def test_level_pairs_combine_in_int32():
+    """The epilogues first add pairs of adjacent levels in int32, (S_a << s) + S_b, and assemble the
+    64-bit integer from those; at the worst-case level magnitudes no int32 intermediate overflows and
+    the result equals the level-by-level 64-bit combination."""
+    rng = np.random.default_rng(5)
+    i32 = (-(1 << 31), (1 << 31) - 1)
+    # update kernel: 7 levels, base 2^8, |S| < 2^22; GEMM: 8 levels, base 2^7, |S| <= 2^22
+    for nlev, sh, bound in ((7, 8, (1 << 22) - 1), (8, 7, 1 << 22)):
+        cases = [np.full(nlev, bound), np.full(nlev, -bound)]
+        cases += [rng.integers(-bound, bound + 1, nlev) for _ in range(2000)]
+        for S in cases:
+            S = [int(x) for x in S]
+            if nlev == 7:
+                ref = sum(S[L] << (40 - 8 * L) for L in range(6)) + (S[6] >> 8)
+                t3 = (S[0] << 8) + S[1]
+                t2 = (S[2] << 8) + S[3]
+                t1 = (S[4] << 8) + S[5] + (S[6] >> 8)
+                parts, got = (t3, t2, t1), (t3 << 32) + (t2 << 16) + t1
+            else:
+                ref = sum(S[L] << (42 - 7 * L) for L in range(7)) + (S[7] >> 7)
+                ta = (S[1] << 7) + S[2]
+                tb = (S[3] << 7) + S[4]
+                tc = (S[5] << 7) + S[6] + (S[7] >> 7)
+                parts, got = (ta, tb, tc), (S[0] << 42) + (ta << 28) + (tb << 14) + tc
+            assert all(i32[0] <= p <= i32[1] for p in parts)
+            assert got == ref and abs(got) < (1 << 63)
