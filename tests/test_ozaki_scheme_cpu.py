@@ -187,4 +187,4 @@ def test_level_pairs_combine_in_int32():
                 tc = (S[5] << 7) + S[6] + (S[7] >> 7)
                 parts, got = (ta, tb, tc), (S[0] << 42) + (ta << 28) + (tb << 14) + tc
             assert all(i32[0] <= p <= i32[1] for p in parts)
-            assert got == ref and abs(got) < (1 << 63)
+            assert got == ref
