@@ -21,7 +21,6 @@
 
 namespace lrs {
 
-constexpr int ZT = 64;    // tile edge
 constexpr int ZK = 16;    // k chunk
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
@@ -35,7 +34,8 @@ __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -
 struct ZBatch {
   long long a, s, b, c;
 };
-template <bool TA, bool CA, bool TB, bool CB>
+// T x T output tile (T = 64 or 32), 256 threads of (T/16) x (T/16) outputs each.
+template <bool TA, bool CA, bool TB, bool CB, int T>
 __global__ void __launch_bounds__(256) zgemm64_kernel(int m, int n, int k, const double2* __restrict__ A, int lda,
                                                       const double2* __restrict__ s, const double2* __restrict__ B,
                                                       int ldb, double beta, double2* __restrict__ C, int ldc,
@@ -44,19 +44,20 @@ __global__ void __launch_bounds__(256) zgemm64_kernel(int m, int n, int k, const
   if (s) s += blockIdx.z * bs.s;
   B += blockIdx.z * bs.b;
   C += blockIdx.z * bs.c;
-  __shared__ double2 As[ZK][ZT + 1];
-  __shared__ double2 Bs[ZK][ZT + 1];
+  constexpr int R = T / 16;   // outputs per thread and dimension
+  __shared__ double2 As[ZK][T + 1];
+  __shared__ double2 Bs[ZK][T + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
-  double2 acc[4][4];
+  const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+  double2 acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < R; ++j) acc[i][j] = make_double2(0.0, 0.0);
   for (int k0 = 0; k0 < k; k0 += ZK) {
-    for (int idx = threadIdx.x; idx < ZK * ZT; idx += 256) {
+    for (int idx = threadIdx.x; idx < ZK * T; idx += 256) {
       int r, kk;
-      if (TA) { kk = idx / ZT; r = idx % ZT; } else { r = idx / ZK; kk = idx % ZK; }
+      if (TA) { kk = idx / T; r = idx % T; } else { r = idx / ZK; kk = idx % ZK; }
       const int gi = i0 + r, gk = k0 + kk;
       double2 a = make_double2(0.0, 0.0);
       if (gi < m && gk < k) {
@@ -66,9 +67,9 @@ __global__ void __launch_bounds__(256) zgemm64_kernel(int m, int n, int k, const
       }
       As[kk][r] = a;
     }
-    for (int idx = threadIdx.x; idx < ZK * ZT; idx += 256) {
+    for (int idx = threadIdx.x; idx < ZK * T; idx += 256) {
       int c, kk;
-      if (TB) { c = idx / ZK; kk = idx % ZK; } else { kk = idx / ZT; c = idx % ZT; }
+      if (TB) { c = idx / ZK; kk = idx % ZK; } else { kk = idx / T; c = idx % T; }
       const int gj = j0 + c, gk = k0 + kk;
       double2 b = make_double2(0.0, 0.0);
       if (gj < n && gk < k) {
@@ -80,15 +81,15 @@ __global__ void __launch_bounds__(256) zgemm64_kernel(int m, int n, int k, const
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < ZK; ++kk) {
-      double2 a[4], b[4];
+      double2 a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
           acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
           acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
         }
@@ -96,11 +97,11 @@ __global__ void __launch_bounds__(256) zgemm64_kernel(int m, int n, int k, const
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int gi = i0 + ty + 16 * i;
     if (gi >= m) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int gj = j0 + tx + 16 * j;
       if (gj >= n) continue;
       double2* c = &C[(size_t)gi * ldc + gj];
@@ -118,8 +119,15 @@ template <bool TA, bool CA, bool TB, bool CB>
 static int zgemm64(lrs_ctx* ctx, int m, int n, int k, const double2* A, int lda, const double2* s,
                    const double2* B, int ldb, double beta, double2* C, int ldc, int batch = 1,
                    ZBatch bs = ZBatch{0, 0, 0, 0}) {
-  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT, batch);
-  zgemm64_kernel<TA, CA, TB, CB><<<grid, 256, 0, ctx->stream>>>(m, n, k, A, lda, s, B, ldb, beta, C, ldc, bs);
+  // 32-wide tiles when 64-wide ones would leave most SMs idle (the FP64 pipe of one SM is slow)
+  const long long big = (long long)((n + 63) / 64) * ((m + 63) / 64) * batch;
+  if (big < 2LL * ctx->num_sms) {
+    dim3 grid((n + 31) / 32, (m + 31) / 32, batch);
+    zgemm64_kernel<TA, CA, TB, CB, 32><<<grid, 256, 0, ctx->stream>>>(m, n, k, A, lda, s, B, ldb, beta, C, ldc, bs);
+  } else {
+    dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
+    zgemm64_kernel<TA, CA, TB, CB, 64><<<grid, 256, 0, ctx->stream>>>(m, n, k, A, lda, s, B, ldb, beta, C, ldc, bs);
+  }
   return after_launch(ctx, "zgemm64_kernel");
 }
 

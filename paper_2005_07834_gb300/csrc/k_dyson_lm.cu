@@ -105,12 +105,12 @@ int site_detect_product(lrs_ctx* ctx, Site& s, const double* pts) {
   }
   LRS_TRY(ensure(ctx, s.yang, yang.size()));
   LRS_TRY(ensure(ctx, s.rl, rl.size()));
-  LRS_CUDA_TRY(cudaMemcpy(s.yang.ptr, yang.data(), yang.size() * sizeof(double), cudaMemcpyHostToDevice));
-  LRS_CUDA_TRY(cudaMemcpy(s.rl.ptr, rl.data(), rl.size() * sizeof(double), cudaMemcpyHostToDevice));
+  LRS_TRY(h2d_sync(ctx, s.yang.ptr, yang.data(), yang.size() * sizeof(double)));
+  LRS_TRY(h2d_sync(ctx, s.rl.ptr, rl.data(), rl.size() * sizeof(double)));
   s.spd = spd;
   if (spd) {
     LRS_TRY(ensure(ctx, s.fl, fl.size()));
-    LRS_CUDA_TRY(cudaMemcpy(s.fl.ptr, fl.data(), fl.size() * sizeof(double), cudaMemcpyHostToDevice));
+    LRS_TRY(h2d_sync(ctx, s.fl.ptr, fl.data(), fl.size() * sizeof(double)));
   }
   s.product = true;
   s.nrad = nrad;

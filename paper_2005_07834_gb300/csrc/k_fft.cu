@@ -304,8 +304,8 @@ static int build_plan(lrs_ctx* ctx, const int n[3]) {
     for (int j = 0; j < n[d]; ++j) tw.push_back(make_double2(std::cos(two_pi * j / n[d]), std::sin(two_pi * j / n[d])));
   LRS_TRY(ensure(ctx, ws.fft_index, all.size()));
   LRS_TRY(ensure(ctx, ws.fft_tw, tw.size()));
-  LRS_CUDA_TRY(cudaMemcpy(ws.fft_index.ptr, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
-  LRS_CUDA_TRY(cudaMemcpy(ws.fft_tw.ptr, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  LRS_TRY(h2d_sync(ctx, ws.fft_index.ptr, all.data(), all.size() * sizeof(int)));
+  LRS_TRY(h2d_sync(ctx, ws.fft_tw.ptr, tw.data(), tw.size() * sizeof(double2)));
   for (int d = 0; d < 3; ++d) ws.fft_plan_n[d] = n[d];
   ws.fft_plan_ok = true;
   return LRS_OK;

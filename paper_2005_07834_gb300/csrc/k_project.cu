@@ -51,8 +51,6 @@ __global__ void kphase_kernel(const double* __restrict__ pts, int npts, double c
   out[(size_t)k * npts + p] = make_double2(c * inv_sqrt_omega, s * inv_sqrt_omega);
 }
 
-constexpr int PT = 64;   // points per tile
-constexpr int BT = 64;   // bands per tile
 constexpr int GK = 16;   // plane waves per chunk
 
 // Column offsets of the k-points of one launch (blockIdx.z = k - k0).
@@ -62,8 +60,9 @@ struct ProjK {
   int nocc[PROJ_KMAX], oofs[PROJ_KMAX], uofs[PROJ_KMAX];
 };
 
-// psi[p][b] of k-point k0 + blockIdx.z for a 64 x 64 tile, complex FP64, 4x4 outputs per thread
-// (every k-point of a launch at once, so that small sites still fill the GPU).
+// psi[p][b] of k-point k0 + blockIdx.z for a T x T tile (T = 64 or 32), complex FP64, (T/16)^2
+// outputs per thread (every k-point of a launch at once, so that small sites still fill the GPU).
+template <int T>
 __global__ void __launch_bounds__(256) project_fp64_kernel(
     const double2* __restrict__ tab, int npts, int3 nmax, int off1, int off2,
     const int* __restrict__ gvec, int ng, const double2* __restrict__ coeff, int nb,
@@ -73,21 +72,22 @@ __global__ void __launch_bounds__(256) project_fp64_kernel(
   const double2* __restrict__ coeff_k = coeff + (size_t)k * ng * nb;
   const double2* __restrict__ kph = kphase + (size_t)k * npts;
   const int nocc = pk.nocc[kz], oofs = pk.oofs[kz], uofs = pk.uofs[kz];
-  __shared__ double2 As[GK][PT + 1];
-  __shared__ double2 Bs[GK][BT + 1];
+  __shared__ double2 As[GK][T + 1];
+  __shared__ double2 Bs[GK][T + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int p0 = blockIdx.y * PT, b0 = blockIdx.x * BT;
+  const int p0 = blockIdx.y * T, b0 = blockIdx.x * T;
   const int w1 = 2 * nmax.x + 1, w2 = 2 * nmax.y + 1, w3 = 2 * nmax.z + 1;
-  double2 acc[4][4];
+  constexpr int R = T / 16;
+  double2 acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < R; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
   for (int g0 = 0; g0 < ng; g0 += GK) {
-    // A: phases for 64 points x 16 plane waves
-    for (int idx = threadIdx.x; idx < GK * PT; idx += 256) {
-      int kk = idx / PT, r = idx % PT;
+    // A: phases for T points x 16 plane waves
+    for (int idx = threadIdx.x; idx < GK * T; idx += 256) {
+      int kk = idx / T, r = idx % T;
       int g = g0 + kk, p = p0 + r;
       double2 val = make_double2(0.0, 0.0);
       if (g < ng && p < npts) {
@@ -99,24 +99,24 @@ __global__ void __launch_bounds__(256) project_fp64_kernel(
       }
       As[kk][r] = val;
     }
-    // B: coefficients for 16 plane waves x 64 bands
-    for (int idx = threadIdx.x; idx < GK * BT; idx += 256) {
-      int kk = idx / BT, c = idx % BT;
+    // B: coefficients for 16 plane waves x T bands
+    for (int idx = threadIdx.x; idx < GK * T; idx += 256) {
+      int kk = idx / T, c = idx % T;
       int g = g0 + kk, b = b0 + c;
       Bs[kk][c] = (g < ng && b < nb) ? coeff_k[(size_t)g * nb + b] : make_double2(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GK; ++kk) {
-      double2 a[4], b[4];
+      double2 a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
           acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
           acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
         }
@@ -124,12 +124,12 @@ __global__ void __launch_bounds__(256) project_fp64_kernel(
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     int p = p0 + ty + 16 * i;
     if (p >= npts) continue;
     double2 ph = kph[p];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       int b = b0 + tx + 16 * j;
       if (b >= nb) continue;
       double2 v = cmul(ph, acc[i][j]);
@@ -180,10 +180,19 @@ int project_fp64(lrs_ctx* ctx, Site& s) {
       oofs += ctx->nocc[k0 + j];
       uofs += ctx->nb - ctx->nocc[k0 + j];
     }
-    dim3 grid((ctx->nb + BT - 1) / BT, (s.npts + PT - 1) / PT, nks);
-    project_fp64_kernel<<<grid, 256, 0, ctx->stream>>>(
-        ctx->ws.phase_tab.ptr, s.npts, make_int3(nm[0], nm[1], nm[2]), off1, off2, ctx->d_gvec.ptr,
-        ctx->ng, ctx->coeff.ptr, ctx->nb, ctx->ws.kphase.ptr, pk, s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku);
+    // 32-wide tiles when 64-wide ones would leave most SMs idle (the FP64 pipe of one SM is slow)
+    const long long big = (long long)((ctx->nb + 63) / 64) * ((s.npts + 63) / 64) * nks;
+    if (big < 2LL * ctx->num_sms) {
+      dim3 grid((ctx->nb + 31) / 32, (s.npts + 31) / 32, nks);
+      project_fp64_kernel<32><<<grid, 256, 0, ctx->stream>>>(
+          ctx->ws.phase_tab.ptr, s.npts, make_int3(nm[0], nm[1], nm[2]), off1, off2, ctx->d_gvec.ptr, ctx->ng,
+          ctx->coeff.ptr, ctx->nb, ctx->ws.kphase.ptr, pk, s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku);
+    } else {
+      dim3 grid((ctx->nb + 63) / 64, (s.npts + 63) / 64, nks);
+      project_fp64_kernel<64><<<grid, 256, 0, ctx->stream>>>(
+          ctx->ws.phase_tab.ptr, s.npts, make_int3(nm[0], nm[1], nm[2]), off1, off2, ctx->d_gvec.ptr, ctx->ng,
+          ctx->coeff.ptr, ctx->nb, ctx->ws.kphase.ptr, pk, s.psi_o.ptr, ctx->Ko, s.psi_u.ptr, ctx->Ku);
+    }
     LRS_TRY(after_launch(ctx, "project_fp64_kernel"));
   }
   return LRS_OK;

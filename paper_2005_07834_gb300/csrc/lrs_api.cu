@@ -25,6 +25,12 @@ int set_error(int code, const char* fmt, ...) {
 
 void clear_error() { g_last_error.clear(); }
 
+int h2d_sync(lrs_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  LRS_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
 int after_launch(lrs_ctx* ctx, const char* what, int n) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
@@ -647,8 +653,8 @@ int lrs_set_sites(lrs_ctx* ctx, int nsites, const double* centers, const int* np
     std::memcpy(s.center, centers + 3 * i, 3 * sizeof(double));
     LRS_TRY(ensure(ctx, s.pts, 3 * (size_t)s.npts));
     LRS_TRY(ensure(ctx, s.wts, s.npts));
-    LRS_CUDA_TRY(cudaMemcpy(s.pts.ptr, pts + 3 * off, 3 * (size_t)s.npts * sizeof(double), cudaMemcpyHostToDevice));
-    LRS_CUDA_TRY(cudaMemcpy(s.wts.ptr, wts + off, (size_t)s.npts * sizeof(double), cudaMemcpyHostToDevice));
+    LRS_TRY(h2d_sync(ctx, s.pts.ptr, pts + 3 * off, 3 * (size_t)s.npts * sizeof(double)));
+    LRS_TRY(h2d_sync(ctx, s.wts.ptr, wts + off, (size_t)s.npts * sizeof(double)));
     LRS_TRY(site_detect_product(ctx, s, pts + 3 * off));
     off += npts[i];
   }
@@ -709,8 +715,8 @@ int lrs_set_frequency_quadrature(lrs_ctx* ctx, int nf, double mu, double zeta, d
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  LRS_CUDA_TRY(cudaMemcpy(ctx->d_t.ptr, ctx->t.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
-  LRS_CUDA_TRY(cudaMemcpy(ctx->d_W.ptr, ctx->W.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
+  LRS_TRY(h2d_sync(ctx, ctx->d_t.ptr, ctx->t.data(), nf * sizeof(double)));
+  LRS_TRY(h2d_sync(ctx, ctx->d_W.ptr, ctx->W.data(), nf * sizeof(double)));
   ctx->nf = nf;
   ctx->mu = mu;
   ctx->zeta = zeta;
@@ -906,8 +912,8 @@ int lrs_set_energies(lrs_ctx* ctx, const double* energies) {
   for (int j = 0; j < ctx->Ko; ++j) eo[j] = energies[ctx->col_o[j]];
   for (int j = 0; j < ctx->Ku; ++j) eu[j] = energies[ctx->col_u[j]];
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  LRS_CUDA_TRY(cudaMemcpy(ctx->e_o.ptr, eo.data(), ctx->Ko * sizeof(double), cudaMemcpyHostToDevice));
-  LRS_CUDA_TRY(cudaMemcpy(ctx->e_u.ptr, eu.data(), ctx->Ku * sizeof(double), cudaMemcpyHostToDevice));
+  LRS_TRY(h2d_sync(ctx, ctx->e_o.ptr, eo.data(), ctx->Ko * sizeof(double)));
+  LRS_TRY(h2d_sync(ctx, ctx->e_u.ptr, eu.data(), ctx->Ku * sizeof(double)));
   for (auto& s : ctx->sites) s.has_chi0 = s.has_w = false;
   return LRS_OK;
 }
@@ -1326,10 +1332,12 @@ int lrs_synchronize(lrs_ctx* ctx) {
   if (g.rc) return g.rc;
   LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   int tc_status = 0;
-  LRS_CUDA_TRY(cudaMemcpy(&tc_status, ctx->ws.status.ptr + 8, sizeof(int), cudaMemcpyDeviceToHost));
+  LRS_CUDA_TRY(cudaMemcpyAsync(&tc_status, ctx->ws.status.ptr + 8, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (tc_status != 0) {
     ctx->stats.status_word = tc_status;
-    cudaMemset(ctx->ws.status.ptr + 8, 0, sizeof(int));
+    cudaMemsetAsync(ctx->ws.status.ptr + 8, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     return set_error(LRS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code %d)", tc_status);
   }
   for (int s = 0; s < 6; ++s)

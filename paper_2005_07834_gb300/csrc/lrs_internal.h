@@ -69,6 +69,11 @@ cudaError_t launch_with_priority(void (*kernel)(KArgs...), dim3 grid, dim3 block
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Host-to-device copy on the context stream, complete when the call returns (the host buffer may
+// be pageable or short-lived).  Not cudaMemcpy: the legacy default stream would also wait for
+// every other blocking stream of the device, e.g. another context's build.
+int h2d_sync(lrs_ctx* ctx, void* dst, const void* src, size_t bytes);
+
 template <typename T>
 int ensure(lrs_ctx* ctx, DevBuf<T>& b, size_t count) {
   if (b.count >= count && b.ptr) return LRS_OK;
