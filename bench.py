@@ -68,7 +68,7 @@ MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 
 # (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per launch of the update kernel
 DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"): 28.5e6,
-                 ("single-site-3520", "r4"): 28.52e6}
+                 ("single-site-3520", "r4"): 28.52e6, ("single-site-3520", "r5"): 28.52e6}
 
 
 def dyson_roofline(st, workload=None, version=None, hbm_gbs=None, bf16_tflops=None):
