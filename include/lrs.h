@@ -79,8 +79,8 @@ extern "C" {
 #define LRS_OPT_DYSON_LANES     10  /* value: 1..8 concurrent Dyson solves in one lrs_solve_w call (default 2) */
 #define LRS_OPT_DYSON_PANEL     11  /* value: 0 (auto), 32 or 128: pivot-block width of the lm-basis SPD inverse */
 #define LRS_UPDATE_AUTO   0   /* tensor cores in the mixed precisions, the FP64 pipe in LRS_FP64 */
-#define LRS_UPDATE_FP64   1   /* trailing update of the SPD inverse with float64 FMAs */
-#define LRS_UPDATE_TC     2   /* float64-accurate update from exact bf16 slices on the tensor cores */
+#define LRS_UPDATE_FP64   1   /* lm-basis Dyson products (basis changes, radial blocks, SPD updates) with float64 FMAs */
+#define LRS_UPDATE_TC     2   /* the same products float64-accurate from exact bf16 slices on the tensor cores */
 #define LRS_REAL_AUTO     0   /* Gamma-point real orbitals (Sec. VI.F) use real-operand tensor-core contractions */
 #define LRS_REAL_OFF      1   /* always the complex contractions */
 
@@ -146,7 +146,10 @@ int lrs_set_stream(lrs_ctx* ctx, void* stream);
  * seven exact bf16 slices per row (power-of-two row scales), 28 slice products
  * accumulated per level exactly in fp32 and combined in float64 - an error
  * bound of about 6e-16 of |D|max |E|max per element, as for a float64 dot
- * product of 32 terms.
+ * product of 32 terms.  The same switch moves the basis changes (Y^T Q chi0 Q Y,
+ * Y Z Y^T) and the four radial-block products of the SPD form (F^T X F and
+ * F M^-1 F^T, one GEMM per lm over the radial index) between the two
+ * arithmetics; on the tensor cores they use eight slices per row.
  * LRS_OPT_DYSON_PANEL sets the width of the pivot blocks the SPD inverse
  * exchanges at a time: 32, or 128 - the 128 x 128 pivot block inverted by the
  * 32-wide steps, then D = C P and the rank-128 trailing update float64-accurate

@@ -239,15 +239,54 @@ int dyson_solve_lm(lrs_ctx* ctx, Site& s) {
     LRS_TRY(dgemm_batched(ctx, true, false, r, L2, nang, 1.0, T, r, (long long)nang * r, s.wts.ptr, nang, Yang,
                           L2, 0, nullptr, 0.0, X, r, L2, nrad));
   dim3 g((r + 127) / 128, r);
-  if (use_spd) {
+  // 128-wide pivot blocks on request (LRS_OPT_DYSON_PANEL); the default keeps the 32-wide
+  // exchange, whose trailing update overlaps the pivot chain
+  const bool blocked = ctx->dyson_panel == SPD_OUTER_BLOCK;
+  if (use_spd && tc) {
+    // The same four radial-block products as below, each a GEMM over the radial index per lm
+    // (rows c, columns j, contraction j'), float64-accurate on the tensor cores.  With
+    // Fh = blockdiag_lm F_l (Fh[(j', lm), (j, lm)] = F_l[j'][j]):
+    //   B = X Fh,  M = I - B^T Fh = I - Fh^T X Fh,  Y = M^-1 Fh^T,  Z = Y^T Fh^T = Fh M^-1 Fh^T.
+    // A product whose operand is a symmetric matrix S reads S[(j', lm), c] for S[c, (j', lm)]
+    // (consecutive c, consecutive words); M and Z are symmetric, so they are stored at the
+    // transposed position, again with consecutive c in consecutive words.
+    const long long R = r, LR = (long long)L2 * r;
+    const OzOperand Fjpj{s.fl.ptr, 1, nrad, (long long)nrad * nrad, true};    // (j, j') -> F_l[j'][j]
+    const OzOperand Fjjp{s.fl.ptr, nrad, 1, (long long)nrad * nrad, true};    // (j, j') -> F_l[j][j']
+    OzStore to_rows;           // [c][(j, lm)]: row c, column j L2 + lm
+    to_rows.rs = R;
+    to_rows.cs = L2;
+    to_rows.sb = 1;
+    to_rows.batch_fastest = true;   // entries lm, lm + 1, ... fill the same sectors together
+    OzStore to_cols = to_rows;      // [(j, lm)][c]
+    to_cols.rs = 1;
+    to_cols.cs = LR;
+    to_cols.sb = R;
+    to_cols.batch_fastest = false;
+    LRS_TRY(mirror_lower(ctx, X, r, r));
+    to_rows.c = B;
+    LRS_TRY(oz_gemm_strided(ctx, r, nrad, nrad, L2, OzOperand{X, 1, LR, R, false}, nullptr, 0, Fjpj, to_rows));
+    OzStore m = to_cols;
+    m.c = Z;
+    m.alpha = -1.0;
+    m.dI = 1;                  // diagonal: c == j L2 + lm
+    m.dJ = -L2;
+    m.dB = -1;
+    m.dadd = 1.0;
+    LRS_TRY(oz_gemm_strided(ctx, r, nrad, nrad, L2, OzOperand{B, 1, LR, R, false}, nullptr, 0, Fjpj, m));
+    if (blocked) LRS_TRY(spd_inverse_blocked(ctx, Z, r, r, ctx->ws.status.ptr));
+    else LRS_TRY(spd_inverse(ctx, Z, r, r, ctx->ws.status.ptr));
+    LRS_TRY(mirror_lower(ctx, Z, r, r));
+    to_rows.c = X;
+    LRS_TRY(oz_gemm_strided(ctx, r, nrad, nrad, L2, OzOperand{Z, 1, LR, R, false}, nullptr, 0, Fjjp, to_rows));
+    to_cols.c = Z;
+    LRS_TRY(oz_gemm_strided(ctx, r, nrad, nrad, L2, OzOperand{X, 1, LR, R, false}, nullptr, 0, Fjjp, to_cols));
+  } else if (use_spd) {
     // M = I - F^T X F (in Z), inverted in place; Z = F M^-1 F^T
     lm_left_kernel<true, true><<<g, 128, 0, ctx->stream>>>(X, s.fl.ptr, nrad, L2, 1.0, 0.0, B);
     LRS_TRY(after_launch(ctx, "lm_left_kernel"));
     lm_right_kernel<false><<<g, 128, 0, ctx->stream>>>(B, s.fl.ptr, nrad, L2, -1.0, 1.0, Z);
     LRS_TRY(after_launch(ctx, "lm_right_kernel"));
-    // 128-wide pivot blocks on request (LRS_OPT_DYSON_PANEL); the default keeps the 32-wide
-    // exchange, whose trailing update overlaps the pivot chain
-    const bool blocked = ctx->dyson_panel == SPD_OUTER_BLOCK;
     if (blocked) LRS_TRY(spd_inverse_blocked(ctx, Z, r, r, ctx->ws.status.ptr));
     else LRS_TRY(spd_inverse(ctx, Z, r, r, ctx->ws.status.ptr));
     lm_left_kernel<false, true><<<g, 128, 0, ctx->stream>>>(Z, s.fl.ptr, nrad, L2, 1.0, 0.0, X);

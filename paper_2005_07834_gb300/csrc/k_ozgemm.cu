@@ -1,7 +1,9 @@
 // Float64-accurate batched GEMM on the tensor cores,
 //   C_b = alpha op(A_b) diag(ks_b) op(B_b) + beta C_b,
 // for the basis changes of the lm-basis Dyson solve (Sec. VI.E: T = chi0 Q Y,
-// X = Y^T Q T, U = Y Z, W = U Y^T, one batch entry per radial shell).
+// X = Y^T Q T, U = Y Z, W = U Y^T, one batch entry per radial shell) and the
+// radial-block products of its SPD form (F^T X F, F M^-1 F^T: one batch entry
+// per lm, operands and results addressed through arbitrary strides).
 //
 // Packing (oz_pack_kernel): every row of op(A) diag(ks) and of op(B)^T is
 // scaled by a power of two, x = 2^e a with |a| < 1/2 (e from the largest
@@ -57,16 +59,16 @@ constexpr int OG_BAD_EXP = 1 << 20;            // row exponent of a row holding 
 static_assert(OG_SMEM <= 227 * 1024, "shared memory of one CTA");
 
 // ---------------------------------------------------------------- slicing
-// Operand X (rows x k, logical) with X[i][kk] = (trans ? x[kk ld + i] : x[i ld + kk]) ks[kk]
+// Operand X (rows x k, logical) with X[i][kk] = x[i si + kk sk] ks[kk]
 // into planes[b][q][kc][rows_pad][64] and expo[b][rows_pad].  One CTA: 32 rows, all of K,
 // read through 32 x 32 shared-memory tiles so that both layouts are read coalesced.
 struct OgPack {
   const double* x;
-  int ld;
+  long long si, sk;        // element (i, kk) of batch b at x + b stride + i si + kk sk
   long long stride;
   const double* ks;
   long long stride_ks;
-  int trans;
+  int trans;               // the tile is walked with i fastest (si is the short stride)
   int rows, k, rows_pad, nchunks;
   uint16_t* planes;
   int* expo;
@@ -80,7 +82,7 @@ __device__ __forceinline__ void og_load_tile(const OgPack& p, const double* x, c
     const int i = i0 + ii, k = k0 + kk;
     double v = 0.0;
     if (i < p.rows && k < p.k) {
-      v = p.trans ? x[(size_t)k * p.ld + i] : x[(size_t)i * p.ld + k];
+      v = x[i * p.si + k * p.sk];
       if (ks) v *= ks[k];
     }
     t[kk][ii] = v;
@@ -171,27 +173,49 @@ __global__ void __launch_bounds__(256) oz_pack_kernel(const OgPack p) {
 // ---------------------------------------------------------------- products
 struct OgGemm {
   double* C;
-  int ldc;
+  long long rs, cs;        // element (i, j) of C_b at C + b stride_c + i rs + j cs
   long long stride_c;
   int m, n;
   double alpha, beta;
+  int dI, dJ, dB;          // dadd is added where i dI + j dJ + b dB == 0 (a diagonal)
+  double dadd;
   const int* ea;           // [a batches][a_rows_pad]
   const int* eb;           // [b batches][b_rows_pad]
   int a_shared, b_shared;  // one packed operand serves every batch entry
+  int b_sqrt;              // B of batch entry b is packed batch floor(sqrt(b))
   int a_rows_pad, b_rows_pad, nchunks;
   int row_tiles, col_tiles, batch;
+  int batch_fastest;       // units run batch entry fastest (neighbouring entries write neighbouring words)
   int lower_col;           // > 0: C_b is column block b * lower_col of a symmetric matrix (lower tiles only)
 };
 
 __device__ __forceinline__ bool og_decode(const OgGemm& p, int u, int& b, int& bi, int& bj) {
   const int per = p.row_tiles * p.col_tiles;
-  b = u / per;
-  const int rem = u - b * per;
+  int rem;
+  if (p.batch_fastest) {
+    rem = u / p.batch;
+    b = u - rem * p.batch;
+  } else {
+    b = u / per;
+    rem = u - b * per;
+  }
   bi = rem / p.col_tiles;
   bj = rem - bi * p.col_tiles;
   return p.lower_col <= 0 || bi * OG_TM + OG_TM - 1 >= b * p.lower_col + bj * OG_TN;
 }
 
+__device__ __forceinline__ int og_b_batch(const OgGemm& p, int b) {
+  if (p.b_shared) return 0;
+  if (!p.b_sqrt) return b;
+  int l = (int)sqrtf((float)b);
+  while (l * l > b) --l;
+  while ((l + 1) * (l + 1) <= b) ++l;
+  return l;
+}
+
+// ROWWISE: C is row-major (cs == 1) and a warp stores 4 rows x 8 columns per step; otherwise each
+// lane stores its own row (consecutive words when rs == 1).
+template <bool ROWWISE>
 __global__ void __launch_bounds__(OG_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const OgGemm p, int* status) {
@@ -239,7 +263,7 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
       for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
         int b, bi, bj;
         if (!og_decode(p, u, b, bi, bj)) continue;
-        const int ab = p.a_shared ? 0 : b, bb = p.b_shared ? 0 : b;
+        const int ab = p.a_shared ? 0 : b, bb = og_b_batch(p, b);
         for (int kc = 0; kc < p.nchunks; ++kc) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) {
             abort_flag = 1;
@@ -329,7 +353,7 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
     for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
       int b, bi, bj;
       if (!og_decode(p, u, b, bi, bj)) continue;
-      const int ab = p.a_shared ? 0 : b, bb = p.b_shared ? 0 : b;
+      const int ab = p.a_shared ? 0 : b, bb = og_b_batch(p, b);
       double* C = p.C + p.stride_c * b;
       const int row0 = bi * OG_TM + quarter * 32;
       const int col0 = bj * OG_TN + half * 32;
@@ -349,15 +373,18 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
         tc_fence_after();
         const bool read_c = sg > 0 || p.beta != 0.0;
         const double cscale = sg > 0 ? 1.0 : p.beta;
+        constexpr bool rowwise = ROWWISE;
 #pragma unroll 1
         for (int ch = 0; ch < 4; ++ch) {
+          if (col0 + ch * 8 >= p.n) break;       // warp-uniform: nothing to store past column n
           double cv[8];
           bool ok[8];
 #pragma unroll
           for (int it = 0; it < 8; ++it) {
-            const int i = row0 + it * 4 + (lane >> 3), j = col0 + ch * 8 + (lane & 7);
+            const int i = rowwise ? row0 + it * 4 + (lane >> 3) : row0 + lane;
+            const int j = rowwise ? col0 + ch * 8 + (lane & 7) : col0 + ch * 8 + it;
             ok[it] = i < p.m && j < p.n;
-            cv[it] = (ok[it] && read_c) ? C[(size_t)i * p.ldc + j] : 0.0;
+            cv[it] = (ok[it] && read_c) ? C[i * p.rs + j * p.cs] : 0.0;
           }
           float a[OG_LEVELS][8];
 #pragma unroll
@@ -383,11 +410,14 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
           __syncwarp();
 #pragma unroll
           for (int it = 0; it < 8; ++it) {
-            const int r = it * 4 + (lane >> 3), c = lane & 7;
+            const int r = rowwise ? it * 4 + (lane >> 3) : lane, c = rowwise ? lane & 7 : it;
             if (ok[it]) {
+              const int i = row0 + r, j = col0 + ch * 8 + c;
               double v = stg[r * 9 + c];
               if (p.alpha != 1.0) v *= p.alpha;
-              C[(size_t)(row0 + r) * p.ldc + col0 + ch * 8 + c] = read_c ? fma(cscale, cv[it], v) : v;
+              if (read_c) v = fma(cscale, cv[it], v);
+              if (sg == 0 && p.dadd != 0.0 && i * p.dI + j * p.dJ + b * p.dB == 0) v += p.dadd;
+              C[i * p.rs + j * p.cs] = v;
             }
           }
           __syncwarp();
@@ -414,15 +444,17 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
   }
 }
 
-static int og_pack(lrs_ctx* ctx, const double* x, int ld, long long stride, const double* ks, long long stride_ks,
-                   bool trans, int rows, int k, int rows_pad, int nchunks, int batches, uint16_t* planes, int* expo) {
+static int og_pack(lrs_ctx* ctx, const double* x, long long si, long long sk, long long stride, const double* ks,
+                   long long stride_ks, int rows, int k, int rows_pad, int nchunks, int batches, uint16_t* planes,
+                   int* expo) {
   OgPack p;
   p.x = x;
-  p.ld = ld;
+  p.si = si;
+  p.sk = sk;
   p.stride = stride;
   p.ks = ks;
   p.stride_ks = stride_ks;
-  p.trans = trans ? 1 : 0;
+  p.trans = (si < sk) ? 1 : 0;
   p.rows = rows;
   p.k = k;
   p.rows_pad = rows_pad;
@@ -433,20 +465,23 @@ static int og_pack(lrs_ctx* ctx, const double* x, int ld, long long stride, cons
   return after_launch(ctx, "oz_pack_kernel");
 }
 
-int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
-                    long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
-                    long long stride_b, double beta, double* c, int ldc, long long stride_c, int batch,
-                    int lower_col) {
+int oz_gemm_strided(lrs_ctx* ctx, int m, int n, int k, int batch, const OzOperand& a, const double* ks,
+                    long long stride_ks, const OzOperand& b, const OzStore& c) {
   if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
-  if (k <= 0)   // C = beta C: nothing for the tensor cores to do
-    return dgemm_batched(ctx, ta, tb, m, n, 0, alpha, a, lda, stride_a, ks, stride_ks, b, ldb, stride_b, nullptr,
-                         beta, c, ldc, stride_c, batch);
+  if (k <= 0) return set_error(LRS_ERR_ARG, "oz_gemm_strided: empty contraction");
+  if (a.sqrt_batch) return set_error(LRS_ERR_ARG, "oz_gemm_strided: sqrt batch mapping is for B only");
   const int nchunks = (k + 31) / 32;
   const int a_rows_pad = (m + OG_TM - 1) / OG_TM * OG_TM;
   const int b_rows_pad = (n + OG_TN - 1) / OG_TN * OG_TN;
-  const bool a_shared = stride_a == 0 && (ks == nullptr || stride_ks == 0);
-  const bool b_shared = stride_b == 0;
-  const int a_batches = a_shared ? 1 : batch, b_batches = b_shared ? 1 : batch;
+  const bool a_shared = a.sb == 0 && (ks == nullptr || stride_ks == 0);
+  const bool b_shared = b.sb == 0;
+  int b_distinct = batch;
+  if (b.sqrt_batch) {
+    int l = 0;
+    while ((l + 1) * (l + 1) <= batch - 1) ++l;
+    b_distinct = l + 1;
+  }
+  const int a_batches = a_shared ? 1 : batch, b_batches = b_shared ? 1 : b_distinct;
   const size_t a_elems = (size_t)a_batches * OG_PLANES * nchunks * a_rows_pad * 64;
   const size_t b_elems = (size_t)b_batches * OG_PLANES * nchunks * b_rows_pad * 64;
   LRS_TRY(ensure(ctx, ctx->ws.og_planes, a_elems + b_elems));
@@ -455,39 +490,74 @@ int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double 
   uint16_t* pb = pa + a_elems;
   int* xa = ctx->ws.og_expo.ptr;
   int* xb = xa + (size_t)a_batches * a_rows_pad;
-  // op(A) diag(ks): rows i, K index kk; op(B)^T: rows j (output columns), K index kk
-  LRS_TRY(og_pack(ctx, a, lda, a_shared ? 0 : stride_a, ks, a_shared ? 0 : stride_ks, ta, m, k, a_rows_pad, nchunks,
+  // A diag(ks): rows i, K index kk; B: rows j (output columns), K index kk
+  LRS_TRY(og_pack(ctx, a.x, a.si, a.sk, a_shared ? 0 : a.sb, ks, a_shared ? 0 : stride_ks, m, k, a_rows_pad, nchunks,
                   a_batches, pa, xa));
-  LRS_TRY(og_pack(ctx, b, ldb, b_shared ? 0 : stride_b, nullptr, 0, !tb, n, k, b_rows_pad, nchunks, b_batches, pb,
+  LRS_TRY(og_pack(ctx, b.x, b.si, b.sk, b_shared ? 0 : b.sb, nullptr, 0, n, k, b_rows_pad, nchunks, b_batches, pb,
                   xb));
   CUtensorMap ma, mb;
   LRS_TRY(make_operand_map(&ma, pa, 64, (uint64_t)a_batches * OG_PLANES * nchunks * a_rows_pad, OG_TM));
   LRS_TRY(make_operand_map(&mb, pb, 64, (uint64_t)b_batches * OG_PLANES * nchunks * b_rows_pad, OG_TN));
   OgGemm p;
-  p.C = c;
-  p.ldc = ldc;
-  p.stride_c = stride_c;
+  p.C = c.c;
+  p.rs = c.rs;
+  p.cs = c.cs;
+  p.stride_c = c.sb;
   p.m = m;
   p.n = n;
-  p.alpha = alpha;
-  p.beta = beta;
+  p.alpha = c.alpha;
+  p.beta = c.beta;
+  p.dI = c.dI;
+  p.dJ = c.dJ;
+  p.dB = c.dB;
+  p.dadd = c.dadd;
   p.ea = xa;
   p.eb = xb;
   p.a_shared = a_shared ? 1 : 0;
   p.b_shared = b_shared ? 1 : 0;
+  p.b_sqrt = (b.sqrt_batch && !b_shared) ? 1 : 0;
   p.a_rows_pad = a_rows_pad;
   p.b_rows_pad = b_rows_pad;
   p.nchunks = nchunks;
   p.row_tiles = a_rows_pad / OG_TM;
   p.col_tiles = b_rows_pad / OG_TN;
   p.batch = batch;
-  p.lower_col = lower_col;
-  if (!ctx->capturing)
-    LRS_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OG_SMEM));
+  p.batch_fastest = c.batch_fastest ? 1 : 0;
+  p.lower_col = c.lower_col;
   const long long units = (long long)batch * p.row_tiles * p.col_tiles;
   const int grid = (int)std::min<long long>(units, ctx->num_sms);
-  oz_gemm_kernel<<<grid, OG_THREADS, OG_SMEM, ctx->stream>>>(ma, mb, p, ctx->ws.status.ptr + 8);
+  if (c.cs == 1) {
+    if (!ctx->capturing)
+      LRS_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OG_SMEM));
+    oz_gemm_kernel<true><<<grid, OG_THREADS, OG_SMEM, ctx->stream>>>(ma, mb, p, ctx->ws.status.ptr + 8);
+  } else {
+    if (!ctx->capturing)
+      LRS_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OG_SMEM));
+    oz_gemm_kernel<false><<<grid, OG_THREADS, OG_SMEM, ctx->stream>>>(ma, mb, p, ctx->ws.status.ptr + 8);
+  }
   return after_launch(ctx, "oz_gemm_kernel");
+}
+
+int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* a, int lda,
+                    long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
+                    long long stride_b, double beta, double* c, int ldc, long long stride_c, int batch,
+                    int lower_col) {
+  if (m <= 0 || n <= 0 || batch <= 0) return LRS_OK;
+  if (k <= 0)   // C = beta C: nothing for the tensor cores to do
+    return dgemm_batched(ctx, ta, tb, m, n, 0, alpha, a, lda, stride_a, ks, stride_ks, b, ldb, stride_b, nullptr,
+                         beta, c, ldc, stride_c, batch);
+  // op(A)[i][kk] and op(B)^T[j][kk] = op(B)[kk][j]
+  const OzOperand A{a, ta ? 1 : (long long)lda, ta ? (long long)lda : 1, stride_a, false};
+  const OzOperand B{b, tb ? (long long)ldb : 1, tb ? 1 : (long long)ldb, stride_b, false};
+  OzStore C;
+  C.c = c;
+  C.rs = ldc;
+  C.cs = 1;
+  C.sb = stride_c;
+  C.alpha = alpha;
+  C.beta = beta;
+  C.lower_col = lower_col;
+  return oz_gemm_strided(ctx, m, n, k, batch, A, ks, stride_ks, B, C);
 }
 
 }  // namespace lrs

@@ -156,9 +156,13 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
 // The result is symmetric: one CTA per pair of 32 x 32 tiles (bi <= bj) reads tiles (bi, bj) and
 // (bj, bi) of every frequency once, accumulates their symmetric sum once and writes both output
 // tiles (the transposed one through shared memory), so that each slab element is read once and
-// each float64 accumulation is done once.
+// each float64 accumulation is done once.  With sym, X_f is itself symmetric (real orbitals:
+// both Green's functions are symmetric in r, r') and only the tiles reaching its lower triangle
+// were computed: X_f + X_f^T = 2 X_f is read from the lower element of each pair (the tile
+// (bj, bi), and within a diagonal tile whichever of the two elements lies on or below the
+// diagonal), so that chi0 comes out exactly symmetric.
 __global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf, const double* __restrict__ Wf,
-                                   const float* __restrict__ scales, int n, double* __restrict__ chi0) {
+                                   const float* __restrict__ scales, int n, int sym, double* __restrict__ chi0) {
   __shared__ float t[32][33];
   __shared__ double o[32][33];
   const int bi = blockIdx.y, bj = blockIdx.x;
@@ -172,7 +176,7 @@ __global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int n
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       t[ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
-      direct[i] = s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
+      direct[i] = (sym && bi != bj) ? 0.f : s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
     }
     __syncthreads();
     double w = Wf[f];
@@ -181,7 +185,11 @@ __global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int n
       w /= sc * sc;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] = fma(w, (double)(direct[i] + t[tx][ty + 8 * i]), acc[i]);
+    for (int i = 0; i < 4; ++i) {
+      // output element (r, q) = (r0 + ty + 8 i, c0 + tx); t holds X_f(q, r), direct X_f(r, q)
+      const float lower = (c0 + tx >= r0 + ty + 8 * i) ? t[tx][ty + 8 * i] : direct[i];
+      acc[i] = fma(w, sym ? 2.0 * (double)lower : (double)(direct[i] + t[tx][ty + 8 * i]), acc[i]);
+    }
     __syncthreads();
   }
   const double c = 0.63661977236758134308;   // 2/pi
@@ -287,6 +295,10 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
   const int Kop = round_up(ctx->Ko, 32), Kup = round_up(ctx->Ku, 32), Kp = Kop + Kup;
   const size_t ld = 2 * (size_t)Kp;
   const int ns = (int)list.size();
+  // Gamma-point real orbitals: B = [psi_o | conj psi_u] is real, both Green's functions are
+  // symmetric in (r, r'), and so is each frequency's product: only the tiles that reach the
+  // lower triangle are computed
+  const bool real = ctx->real_orbitals && ctx->real_mode == LRS_REAL_AUTO;
   std::vector<SiteTile> table(ns);
   long long ra = 0, rb = 0, slab = 0, units = 0;
   for (int i = 0; i < ns; ++i) {
@@ -302,7 +314,8 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
     t.a_row0 = (int)ra;
     t.b_row0 = (int)rb;
     t.slab0 = slab;
-    units += (long long)t.m_tiles * t.n_tiles * nf;
+    const long long q = TILE_M / TN;
+    units += (real ? q * t.m_tiles * (t.m_tiles + 1) / 2 : (long long)t.m_tiles * t.n_tiles) * nf;
     ra += (long long)nf * np;
     rb += np;
     slab += (long long)nf * np * np;
@@ -370,8 +383,8 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
   sh.units = (int)units;
   sh.sites = ctx->ws.site_tiles.ptr + toff;
   sh.nsites = ns;
-  // Gamma-point real orbitals: B = [psi_o | conj psi_u] is real
-  sh.real_b = ctx->real_orbitals && ctx->real_mode == LRS_REAL_AUTO ? 1 : 0;
+  sh.real_b = real ? 1 : 0;
+  sh.tri = real ? 1 : 0;
   // short K (each contraction at most two accumulation segments long): both contractions of a
   // unit accumulate whole in their own TMEM set and the epilogue multiplies them straight from
   // TMEM, with no folding of segments and no parking of the occupied sums
@@ -387,7 +400,7 @@ static int chi0_mixed_t(lrs_ctx* ctx, const std::vector<int>& list, int toff) {
     dim3 rg(t.np / 32, t.np / 32);
     chi0_reduce_kernel<<<rg, dim3(32, 8), 0, ctx->stream>>>(ctx->ws.slab.ptr + t.slab0, t.np, nf, ctx->d_W.ptr,
                                                             FMT == 0 ? ctx->ws.scales.ptr + sstride * i : nullptr,
-                                                            s.npts, s.chi0.ptr);
+                                                            s.npts, real ? 1 : 0, s.chi0.ptr);
     LRS_TRY(after_launch(ctx, "chi0_reduce_kernel"));
   }
   return LRS_OK;

@@ -366,6 +366,28 @@ int oz_gemm_batched(lrs_ctx* ctx, bool ta, bool tb, int m, int n, int k, double 
                     long long stride_a, const double* ks, long long stride_ks, const double* b, int ldb,
                     long long stride_b, double beta, double* c, int ldc, long long stride_c, int batch,
                     int lower_col);
+// The same GEMM on strided operands: for batch entries b < batch, i < m, j < n,
+//   C[b c.sb + i c.rs + j c.cs] = c.alpha sum_kk A(b, i, kk) ks_b[kk] B(b, j, kk) + c.beta C[...]
+//                                 + c.dadd [i c.dI + j c.dJ + b c.dB == 0],
+// A(b, i, kk) = a.x[b a.sb + i a.si + kk a.sk] and B(b, j, kk) = b.x[b' b.sb + j b.si + kk b.sk]
+// with b' = floor(sqrt(b)) when b.sqrt_batch (one radial factor per l serving its 2l + 1 lm
+// entries), else b' = b.  A stride of 0 shares one operand between all entries.
+struct OzOperand {
+  const double* x;
+  long long si, sk, sb;
+  bool sqrt_batch;
+};
+struct OzStore {
+  double* c = nullptr;
+  long long rs = 0, cs = 1, sb = 0;
+  double alpha = 1.0, beta = 0.0;
+  int dI = 0, dJ = 0, dB = 0;
+  double dadd = 0.0;
+  bool batch_fastest = false;
+  int lower_col = 0;
+};
+int oz_gemm_strided(lrs_ctx* ctx, int m, int n, int k, int batch, const OzOperand& a, const double* ks,
+                    long long stride_ks, const OzOperand& b, const OzStore& c);
 
 // In-place inverse of an SPD matrix; lower triangle in and out.  status[0] = 2
 // (status[1] = column) on a pivot that is not positive and finite.

@@ -50,6 +50,7 @@ struct TcShape {
   const struct SiteTile* sites;   // multi-site table (NULL: one problem)
   int nsites;
   int real_b;        // 1: B is real (its imaginary planes are neither loaded nor multiplied)
+  int tri;           // 1 (site-table launches): only the tiles that reach the lower triangle of each output
 };
 
 struct Unit {
@@ -79,8 +80,19 @@ __device__ __forceinline__ Unit decode_unit(const TcShape& sh, const SiteTile* _
     const int lu = u - st.unit0;
     x.b = lu % sh.batches;
     const int t = lu / sh.batches;
-    x.tm = t / st.n_tiles;
-    x.tn = t % st.n_tiles;
+    if (sh.tri) {
+      // row tile tm holds the q (tm + 1) column tiles that reach the diagonal; it starts at
+      // unit q tm (tm + 1) / 2
+      constexpr int q = TILE_M / TN;
+      int tm = (int)((sqrtf(8.f * (float)t / q + 1.f) - 1.f) * 0.5f);
+      while (tm > 0 && q * tm * (tm + 1) / 2 > t) --tm;
+      while (q * (tm + 1) * (tm + 2) / 2 <= t) ++tm;
+      x.tm = tm;
+      x.tn = t - q * tm * (tm + 1) / 2;
+    } else {
+      x.tm = t / st.n_tiles;
+      x.tn = t % st.n_tiles;
+    }
     x.ya = st.a_row0 + x.b * st.np + x.tm * TILE_M;
     x.yb = st.b_row0 + x.tn * TN;
     x.site = lo;
@@ -142,6 +154,43 @@ __host__ __device__ constexpr int tc_stages() {
 template <int TN>
 __host__ __device__ constexpr int tc_smem_bytes() {
   return tc_stages<TN>() * tc_stage_bytes<TN>() + 1024;
+}
+
+// One K16 step of a complex product D = A B^T from hi/lo split planes (offsets hi, lo within
+// the 128-byte rows):  Re += Ar Br - Ai Bi, Im += Ar Bi + Ai Br, each real product as the three
+// split terms hi hi + hi lo + lo hi.  The two products of one A hi tile into the same accumulator
+// are issued back to back with A kept in the collector buffer (8 reads of A instead of 12); the
+// minus sign of Ai Bi is the A negation bit.  a0 = 0 starts both accumulators.
+template <uint32_t FMT, int TN>
+__device__ __forceinline__ void cplx_products(uint32_t dre, uint32_t dim, uint32_t aR, uint32_t aI, uint32_t bR,
+                                              uint32_t bI, uint32_t hi, uint32_t lo, uint32_t a0) {
+  constexpr uint32_t P = idesc_f16(TILE_M, TN, FMT, false);
+  constexpr uint32_t N = idesc_f16(TILE_M, TN, FMT, true);
+  mma_f16a<A_FILL>(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), P, a0);
+  mma_f16a<A_LAST>(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), P, 1u);
+  mma_f16a<A_ONCE>(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), P, 1u);
+  mma_f16a<A_FILL>(dre, sw128_desc(aI + hi), sw128_desc(bI + hi), N, 1u);
+  mma_f16a<A_LAST>(dre, sw128_desc(aI + hi), sw128_desc(bI + lo), N, 1u);
+  mma_f16a<A_ONCE>(dre, sw128_desc(aI + lo), sw128_desc(bI + hi), N, 1u);
+  mma_f16a<A_FILL>(dim, sw128_desc(aR + hi), sw128_desc(bI + hi), P, a0);
+  mma_f16a<A_LAST>(dim, sw128_desc(aR + hi), sw128_desc(bI + lo), P, 1u);
+  mma_f16a<A_ONCE>(dim, sw128_desc(aR + lo), sw128_desc(bI + hi), P, 1u);
+  mma_f16a<A_FILL>(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), P, 1u);
+  mma_f16a<A_LAST>(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), P, 1u);
+  mma_f16a<A_ONCE>(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), P, 1u);
+}
+
+// The same step with B real: Re += Ar Br, Im += Ai Br.
+template <uint32_t FMT, int TN>
+__device__ __forceinline__ void cplx_products_real_b(uint32_t dre, uint32_t dim, uint32_t aR, uint32_t aI,
+                                                     uint32_t bR, uint32_t hi, uint32_t lo, uint32_t a0) {
+  constexpr uint32_t P = idesc_f16(TILE_M, TN, FMT, false);
+  mma_f16a<A_FILL>(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), P, a0);
+  mma_f16a<A_LAST>(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), P, 1u);
+  mma_f16a<A_ONCE>(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), P, 1u);
+  mma_f16a<A_FILL>(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), P, a0);
+  mma_f16a<A_LAST>(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), P, 1u);
+  mma_f16a<A_ONCE>(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), P, 1u);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -222,8 +271,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (DIRECT && warp == 1) {
     // ------------------------------------------------ MMA issue, short K: Go whole into set 0, Gu^T into set 1
     if (lane == 0) {
-      constexpr uint32_t ID_POS = idesc_f16(TILE_M, TN, FMT, false);
-      constexpr uint32_t ID_NEG = idesc_f16(TILE_M, TN, FMT, true);
       int stage = 0;
       uint32_t phase = 0, unit_phase = 0;
       const bool real_b = sh.real_b != 0;
@@ -251,29 +298,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t aR = s, aI = s + TILE_BYTES, bR = s + 2 * TILE_BYTES, bI = bR + B_TILE;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;
             const uint32_t a0 = (cl == 0 && ks == 0) ? 0u : 1u;
-            if (real_b) {
-              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
-              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
-              mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, a0);
-              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
-            } else {
-              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
-              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
-              mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
-              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + hi), ID_NEG, 1u);
-              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + lo), ID_NEG, 1u);
-              mma_f16(dre, sw128_desc(aI + lo), sw128_desc(bI + hi), ID_NEG, 1u);
-              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + hi), ID_POS, a0);
-              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + lo), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aR + lo), sw128_desc(bI + hi), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
-            }
+            if (real_b) cplx_products_real_b<FMT, TN>(dre, dim, aR, aI, bR, 32 * ks, 64 + 32 * ks, a0);
+            else cplx_products<FMT, TN>(dre, dim, aR, aI, bR, bI, 32 * ks, 64 + 32 * ks, a0);
           }
           mma_commit(&empty_bar[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -286,8 +313,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issue
     if (lane == 0) {
-      constexpr uint32_t ID_POS = idesc_f16(TILE_M, TN, FMT, false);
-      constexpr uint32_t ID_NEG = idesc_f16(TILE_M, TN, FMT, true);
       int stage = 0, set = 0;
       uint32_t phase = 0, set_phase = 0;
       const int nseg = plan.count();
@@ -317,39 +342,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t s = smem_base + stage * STAGE_BYTES;
             const uint32_t aR = s, aI = s + TILE_BYTES, bR = s + 2 * TILE_BYTES, bI = bR + B_TILE;
-            if (real_b) {
-              // real B (Gamma-point real orbitals): Re = Ar Br, Im = Ai Br
-#pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;
-                const uint32_t a0 = (c == 0 && ks == 0) ? 0u : 1u;
-                mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
-                mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
-                mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
-                mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, a0);
-                mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
-                mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
-              }
-              mma_commit(&empty_bar[stage]);
-              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-              continue;
-            }
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-              const uint32_t hi = 32 * ks, lo = 64 + 32 * ks;
               const uint32_t a0 = (c == 0 && ks == 0) ? 0u : 1u;
-              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + hi), ID_POS, a0);
-              mma_f16(dre, sw128_desc(aR + hi), sw128_desc(bR + lo), ID_POS, 1u);
-              mma_f16(dre, sw128_desc(aR + lo), sw128_desc(bR + hi), ID_POS, 1u);
-              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + hi), ID_NEG, 1u);
-              mma_f16(dre, sw128_desc(aI + hi), sw128_desc(bI + lo), ID_NEG, 1u);
-              mma_f16(dre, sw128_desc(aI + lo), sw128_desc(bI + hi), ID_NEG, 1u);
-              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + hi), ID_POS, a0);
-              mma_f16(dim, sw128_desc(aR + hi), sw128_desc(bI + lo), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aR + lo), sw128_desc(bI + hi), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + hi), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + hi), sw128_desc(bR + lo), ID_POS, 1u);
-              mma_f16(dim, sw128_desc(aI + lo), sw128_desc(bR + hi), ID_POS, 1u);
+              // real B (Gamma-point real orbitals): Re = Ar Br, Im = Ai Br
+              if (real_b) cplx_products_real_b<FMT, TN>(dre, dim, aR, aI, bR, 32 * ks, 64 + 32 * ks, a0);
+              else cplx_products<FMT, TN>(dre, dim, aR, aI, bR, bI, 32 * ks, 64 + 32 * ks, a0);
             }
             mma_commit(&empty_bar[stage]);
             if (++stage == STAGES) { stage = 0; phase ^= 1u; }

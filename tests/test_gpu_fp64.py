@@ -4,7 +4,7 @@ import pytest
 
 from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys
 from paper_2005_07834_gb300 import synth
-from tests.gpu_util import Reference, public_psi, rel_fro
+from tests.gpu_util import max_rel, Reference, public_psi, rel_fro
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -235,6 +235,43 @@ def test_tensor_core_basis_change_over_several_k_segments(lrs):
         err = rel_fro(b - v, a - v)
         print(f"{name}: tensor-core vs float64 arithmetic, W - v: {err:.2e}")
         assert err < 1e-12
+    scr.close()
+
+
+@pytest.mark.parametrize("nrad,nang", [(70, 14), (130, 6)])
+def test_tensor_core_radial_products_over_several_tiles(lrs, nrad, nang):
+    """The four radial-block products around the SPD inverse (M = I - F^T X F, Z = F M^-1 F^T)
+    as per-lm GEMMs on the tensor cores: 70 shells x 14 directions (r = 630; 70 output columns
+    span two tiles, K = 70 three chunks with a ragged one) and 130 shells x 6 directions (r = 520;
+    K = 130 two exactly accumulated segments, so the identity of M is added once).  Tensor-core vs
+    float64-FMA arithmetic from the same chi0: W - v agrees to 1e-12 (Frobenius), and element by
+    element the tensor-core route is within twice the float64 route's own distance from the dense
+    float64 LU of the same Dyson equation."""
+    wl = synth.single_site_260()
+    wl.sites = [synth.site_grid(wl.sites[0].center, nrad, nang, 4.0)]
+    scr = lrs.Screening(0, "bf16x3")
+    scr.load(wl.orbitals)
+    scr.set_sites(wl.sites)
+    scr.set_frequency_quadrature(8)
+    scr.project()
+    scr.build_chi0()
+    scr.set_option(lrs.LRS_OPT_DYSON_SOLVER, lrs.LRS_SOLVER_SPD)
+    ws = []
+    for mode in (lrs.LRS_UPDATE_FP64, lrs.LRS_UPDATE_TC):
+        scr.set_option(lrs.LRS_OPT_DYSON_UPDATE, mode)
+        scr.solve_w()
+        ws.append(scr.get_w(0))
+    v = scr.get_v(0)
+    err = rel_fro(ws[1] - v, ws[0] - v)
+    # element-wise, both routes against the dense float64 LU of the full-grid Dyson equation on the
+    # same chi0: M = I - F^T X F has condition number up to |C| |X|, which scales rounding in
+    # single elements of either route alike
+    ref = odys.screened_interaction(v, scr.get_chi0(0), wl.sites[0].wts)
+    e64, etc = max_rel(ws[0] - v, ref - v), max_rel(ws[1] - v, ref - v)
+    print(f"{nrad} x {nang}: tensor-core vs float64 radial products, W - v: {err:.2e}; max element against "
+          f"the dense LU: float64 route {e64:.2e}, tensor-core route {etc:.2e}")
+    assert err < 1e-12
+    assert etc < 2.0 * e64 + 1e-13
     scr.close()
 
 
