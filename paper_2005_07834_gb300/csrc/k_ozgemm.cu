@@ -109,10 +109,12 @@ __device__ __forceinline__ void og_put_digits(double v, int e, uint16_t* base, s
 }
 
 // One CTA: 32 rows (warp w holds rows w, w + 8, w + 16, w + 24, lane = K index within a chunk).
-// Up to OG_HOLD chunks stay in registers between the row scale and the digits; longer rows are
-// read twice (the second time from L2).
-constexpr int OG_HOLD = 8;
-__global__ void __launch_bounds__(256) oz_pack_kernel(const OgPack p) {
+// Up to HOLD chunks stay in registers between the row scale and the digits; longer rows are
+// read twice (the second time from L2).  HOLD follows K (2 or 4 chunks; 1 = read twice), so
+// that few registers are held and several CTAs reside on an SM to cover the memory latency.
+template <int HOLD>
+__global__ void __launch_bounds__(256, HOLD <= 2 ? 4 : 3) oz_pack_kernel(const OgPack p) {
+  constexpr int OG_HOLD = HOLD;
   __shared__ double t[32][33];
   const int b = blockIdx.y;
   const double* x = p.x + p.stride * b;
@@ -177,7 +179,10 @@ struct OgGemm {
   long long stride_c;
   int m, n;
   double alpha, beta;
-  int dI, dJ, dB;          // dadd is added where i dI + j dJ + b dB == 0 (a diagonal)
+  int alpha_mode;          // 0: alpha = 1, 1: alpha = -1 (a sign flip), 2: a float64 product
+  int beta_zero;           // beta == 0: C is not read in the first segment
+  int dI, dJ, dB;          // dadd is added where i dI + j dJ + b dB == 0 (a diagonal), if has_diag
+  int has_diag;
   double dadd;
   const int* ea;           // [a batches][a_rows_pad]
   const int* eb;           // [b batches][b_rows_pad]
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const bool read_c = sg > 0 || p.beta != 0.0;
+        const bool read_c = sg > 0 || !p.beta_zero;
         const double cscale = sg > 0 ? 1.0 : p.beta;
         constexpr bool rowwise = ROWWISE;
 #pragma unroll 1
@@ -414,9 +419,10 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
             if (ok[it]) {
               const int i = row0 + r, j = col0 + ch * 8 + c;
               double v = stg[r * 9 + c];
-              if (p.alpha != 1.0) v *= p.alpha;
+              if (p.alpha_mode == 1) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+              else if (p.alpha_mode == 2) v *= p.alpha;
               if (read_c) v = fma(cscale, cv[it], v);
-              if (sg == 0 && p.dadd != 0.0 && i * p.dI + j * p.dJ + b * p.dB == 0) v += p.dadd;
+              if (p.has_diag && sg == 0 && i * p.dI + j * p.dJ + b * p.dB == 0) v += p.dadd;
               C[i * p.rs + j * p.cs] = v;
             }
           }
@@ -461,7 +467,10 @@ static int og_pack(lrs_ctx* ctx, const double* x, long long si, long long sk, lo
   p.nchunks = nchunks;
   p.planes = planes;
   p.expo = expo;
-  oz_pack_kernel<<<dim3(rows_pad / 32, batches), 256, 0, ctx->stream>>>(p);
+  const dim3 grid(rows_pad / 32, batches);
+  if (nchunks <= 2) oz_pack_kernel<2><<<grid, 256, 0, ctx->stream>>>(p);
+  else if (nchunks <= 4) oz_pack_kernel<4><<<grid, 256, 0, ctx->stream>>>(p);
+  else oz_pack_kernel<1><<<grid, 256, 0, ctx->stream>>>(p);
   return after_launch(ctx, "oz_pack_kernel");
 }
 
@@ -507,9 +516,12 @@ int oz_gemm_strided(lrs_ctx* ctx, int m, int n, int k, int batch, const OzOperan
   p.n = n;
   p.alpha = c.alpha;
   p.beta = c.beta;
+  p.alpha_mode = c.alpha == 1.0 ? 0 : (c.alpha == -1.0 ? 1 : 2);
+  p.beta_zero = c.beta == 0.0 ? 1 : 0;
   p.dI = c.dI;
   p.dJ = c.dJ;
   p.dB = c.dB;
+  p.has_diag = c.dadd != 0.0 ? 1 : 0;
   p.dadd = c.dadd;
   p.ea = xa;
   p.eb = xb;

@@ -161,34 +161,53 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
 // were computed: X_f + X_f^T = 2 X_f is read from the lower element of each pair (the tile
 // (bj, bi), and within a diagonal tile whichever of the two elements lies on or below the
 // diagonal), so that chi0 comes out exactly symmetric.
-__global__ void chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf, const double* __restrict__ Wf,
-                                   const float* __restrict__ scales, int n, int sym, double* __restrict__ chi0) {
-  __shared__ float t[32][33];
+__global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf,
+                                                          const double* __restrict__ Wf,
+                                                          const float* __restrict__ scales, int n, int sym,
+                                                          double* __restrict__ chi0) {
+  __shared__ float t[2][32][33];
   __shared__ double o[32][33];
+  __shared__ double wsm[128];   // per-frequency weights W_f / (scales[f] scales[nf])^2 (x 2 with sym)
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bi > bj) return;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int tid = ty * 32 + tx;
   const int r0 = bi * 32, c0 = bj * 32;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int f = 0; f < nf; ++f) {
-    const float* s = slab + (size_t)f * Np * Np;
-    float direct[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      t[ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
-      direct[i] = (sym && bi != bj) ? 0.f : s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
-    }
-    __syncthreads();
+  for (int f = tid; f < nf; f += 256) {
     double w = Wf[f];
     if (scales) {
       const double sc = (double)scales[f] * (double)scales[nf];
       w /= sc * sc;
     }
+    wsm[f] = sym ? 2.0 * w : w;
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  // two frequencies per pair of barriers: both tiles of both are in flight at once
+  for (int f = 0; f < nf; f += 2) {
+    const int nb = min(2, nf - f);
+    float direct[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      // output element (r, q) = (r0 + ty + 8 i, c0 + tx); t holds X_f(q, r), direct X_f(r, q)
-      const float lower = (c0 + tx >= r0 + ty + 8 * i) ? t[tx][ty + 8 * i] : direct[i];
-      acc[i] = fma(w, sym ? 2.0 * (double)lower : (double)(direct[i] + t[tx][ty + 8 * i]), acc[i]);
+    for (int h = 0; h < 2; ++h) {
+      if (h >= nb) break;
+      const float* s = slab + (size_t)(f + h) * Np * Np;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        t[h][ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
+        direct[h][i] = (sym && bi != bj) ? 0.f : s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= nb) break;
+      const double w = wsm[f + h];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        // output element (r, q) = (r0 + ty + 8 i, c0 + tx); t holds X_f(q, r), direct X_f(r, q)
+        const float tq = t[h][tx][ty + 8 * i];
+        const float v = sym ? ((c0 + tx >= r0 + ty + 8 * i) ? tq : direct[h][i]) : direct[h][i] + tq;
+        acc[i] = fma(w, (double)v, acc[i]);
+      }
     }
     __syncthreads();
   }

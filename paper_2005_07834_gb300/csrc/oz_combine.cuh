@@ -57,6 +57,10 @@ __device__ __forceinline__ int oz_level_int(float s) {
   return __float_as_int(s + 12582912.0f) - 0x4B400000;
 }
 
+// Out-of-range results of oz_i64_times_pow2, kept out of line so that its float64
+// instructions are not issued (predicated off) on the common path.
+static __device__ __noinline__ double oz_i64_times_pow2_slow(long long v, int k) { return ldexp((double)v, k); }
+
 // v 2^k rounded to the nearest float64 (ties to even) from the bits of v:
 // find the leading one, keep 53 bits, round on the 11 dropped bits and add
 // the exponent.  Results outside the normal range take a float64 path
@@ -76,7 +80,7 @@ __device__ __forceinline__ double oz_i64_times_pow2(long long v, int k) {
     // to 2^53 adds another and leaves a zero fraction, as it should
     return __longlong_as_double((long long)(sign | ((((unsigned long long)(e + 1022)) << 52) + mant)));
   }
-  return ldexp((double)v, k);
+  return oz_i64_times_pow2_slow(v, k);
 }
 
 }  // namespace lrs
