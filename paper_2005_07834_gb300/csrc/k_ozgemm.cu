@@ -26,7 +26,7 @@
 // per element, the bound of a float64 dot product of K terms.
 //
 // Tiles of 128 x 64 outputs, one persistent CTA per SM: a TMA producer warp,
-// an MMA-issuing warp and eight epilogue warps; two pipeline stages of one K
+// an MMA-issuing warp and sixteen epilogue warps; two pipeline stages of one K
 // chunk (four A and four B planes, 96 KB) each.
 #include <cuda_bf16.h>
 
@@ -49,10 +49,12 @@ constexpr int OG_B_PLANE = OG_TN * 128;
 constexpr int OG_STAGE = OG_PLANES * (OG_A_PLANE + OG_B_PLANE);
 constexpr int OG_STAGES = 2;
 constexpr int OG_SEG = 4;                      // K chunks of 32 per exact accumulation segment
-constexpr int OG_EPI_WARPS = 8;
-constexpr int OG_STAGE_EPI = OG_EPI_WARPS * 32 * 9 * 8;   // per-warp [32][9] float64 staging
+constexpr int OG_EPI_WARPS = 16;               // four per TMEM lane quarter, 16 columns each
+constexpr int OG_EPI_COLS = OG_TN / (OG_EPI_WARPS / 4);
+constexpr int OG_STG_LD = 33;                  // per-warp [8 columns][33] float64 staging
+constexpr int OG_STAGE_EPI = OG_EPI_WARPS * 8 * OG_STG_LD * 8;
 constexpr int OG_SMEM = OG_STAGES * OG_STAGE + OG_STAGE_EPI + 1024;
-constexpr int OG_THREADS = 320;
+constexpr int OG_THREADS = 64 + 32 * OG_EPI_WARPS;   // producer, MMA issuer, epilogue warps
 constexpr int OG_TMEM_COLS = 512;              // 8 levels x 64 columns
 constexpr int OG_BAD_EXP = 1 << 20;            // row exponent of a row holding a NaN or an infinity
 
@@ -346,13 +348,16 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
     // Level sums S_0 .. S_7 (integers of magnitude at most 2^22 in fp32, read as int32 by one
     // fp32 add each) are combined into one 64-bit integer V, the segment's product being
     // 2^(e_i + f_j - 56) V, rounded to float64 with integer instructions: with alpha = 1 and
-    // beta = 0 the epilogue issues no float64 operation.  Each warp stages 32 rows x 8 columns in shared memory and
-    // writes them row-wise (coalesced).
+    // beta = 0 the epilogue issues no float64 operation.  Sixteen warps, four per TMEM lane
+    // quarter with 16 columns each (two steps of 8), keep enough independent work in flight to
+    // cover the latency of these integer chains.  Each step is staged in shared memory and, for
+    // row-major C, written row-wise (coalesced).
+    const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int cg = ew >> 2;                      // column group of OG_EPI_COLS
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
     double* stg = reinterpret_cast<double*>(og_smem_raw + (smem_base - smem_u32(og_smem_raw)) +
-                                            OG_STAGES * OG_STAGE) + (warp - 2) * 32 * 9;
+                                            OG_STAGES * OG_STAGE) + ew * 8 * OG_STG_LD;
     uint32_t acc_phase = 0;
     bool stop = false;
     for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
@@ -361,7 +366,7 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
       const int ab = p.a_shared ? 0 : b, bb = og_b_batch(p, b);
       double* C = p.C + p.stride_c * b;
       const int row0 = bi * OG_TM + quarter * 32;
-      const int col0 = bj * OG_TN + half * 32;
+      const int col0 = bj * OG_TN + cg * OG_EPI_COLS;
       const int ei = p.ea[(size_t)ab * p.a_rows_pad + row0 + lane];   // padded rows hold 0
       for (int sg = 0; sg < nseg; ++sg) {
         int got = 1;
@@ -380,20 +385,12 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
         const double cscale = sg > 0 ? 1.0 : p.beta;
         constexpr bool rowwise = ROWWISE;
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = 0; ch < OG_EPI_COLS / 8; ++ch) {
           if (col0 + ch * 8 >= p.n) break;       // warp-uniform: nothing to store past column n
-          double cv[8];
-          bool ok[8];
-#pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            const int i = rowwise ? row0 + it * 4 + (lane >> 3) : row0 + lane;
-            const int j = rowwise ? col0 + ch * 8 + (lane & 7) : col0 + ch * 8 + it;
-            ok[it] = i < p.m && j < p.n;
-            cv[it] = (ok[it] && read_c) ? C[i * p.rs + j * p.cs] : 0.0;
-          }
           float a[OG_LEVELS][8];
 #pragma unroll
-          for (int lv = 0; lv < OG_LEVELS; ++lv) tmem_ld8(tbase + lane_off + lv * OG_TN + half * 32 + ch * 8, a[lv]);
+          for (int lv = 0; lv < OG_LEVELS; ++lv)
+            tmem_ld8(tbase + lane_off + lv * OG_TN + cg * OG_EPI_COLS + ch * 8, a[lv]);
           tmem_ld_wait();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
@@ -408,20 +405,20 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
                                 ((long long)tb << 14) + (long long)tc;
             const int j = col0 + ch * 8 + c;
             const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
-            stg[lane * 9 + c] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
-                                    ? __longlong_as_double(0x7ff8000000000000ll)   // NaN, as in float64
-                                    : oz_i64_times_pow2(V, ei + fj - 56);
+            stg[c * OG_STG_LD + lane] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
+                                            ? __longlong_as_double(0x7ff8000000000000ll)   // NaN, as in float64
+                                            : oz_i64_times_pow2(V, ei + fj - 56);
           }
           __syncwarp();
 #pragma unroll
           for (int it = 0; it < 8; ++it) {
             const int r = rowwise ? it * 4 + (lane >> 3) : lane, c = rowwise ? lane & 7 : it;
-            if (ok[it]) {
-              const int i = row0 + r, j = col0 + ch * 8 + c;
-              double v = stg[r * 9 + c];
+            const int i = row0 + r, j = col0 + ch * 8 + c;
+            if (i < p.m && j < p.n) {
+              double v = stg[c * OG_STG_LD + r];
               if (p.alpha_mode == 1) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
               else if (p.alpha_mode == 2) v *= p.alpha;
-              if (read_c) v = fma(cscale, cv[it], v);
+              if (read_c) v = fma(cscale, C[i * p.rs + j * p.cs], v);
               if (p.has_diag && sg == 0 && i * p.dI + j * p.dJ + b * p.dB == 0) v += p.dadd;
               C[i * p.rs + j * p.cs] = v;
             }

@@ -161,6 +161,25 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
 // were computed: X_f + X_f^T = 2 X_f is read from the lower element of each pair (the tile
 // (bj, bi), and within a diagonal tile whichever of the two elements lies on or below the
 // diagonal), so that chi0 comes out exactly symmetric.
+// fp32 -> float64 (exact) with integer instructions and selects only: GB300 converts to float64
+// on its float64 pipe (2 per SM per clock), which this sum needs for its FMAs.  Normal values
+// rebias the exponent by 1023 - 127 and move the fraction up by 29 bits; subnormal ones
+// (m 2^-149) are normalised at their leading one; zeros, infinities and NaNs keep their class.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  const int p = 31 - __clz(m | 1u);   // leading one of a subnormal fraction
+  const unsigned long long sub =
+      ((unsigned long long)(p + 874) << 52) | ((unsigned long long)((m << (23 - p)) & 0x7FFFFFu) << 29);
+  const unsigned long long nrm = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  const unsigned long long special = (0x7FFull << 52) | ((unsigned long long)m << 29);
+  unsigned long long r = e == 0xFFu ? special : nrm;
+  r = e == 0u ? (m == 0u ? 0ull : sub) : r;
+  return __longlong_as_double((long long)(sign | r));
+}
+
 __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf,
                                                           const double* __restrict__ Wf,
                                                           const float* __restrict__ scales, int n, int sym,
@@ -206,7 +225,7 @@ __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restric
         // output element (r, q) = (r0 + ty + 8 i, c0 + tx); t holds X_f(q, r), direct X_f(r, q)
         const float tq = t[h][tx][ty + 8 * i];
         const float v = sym ? ((c0 + tx >= r0 + ty + 8 * i) ? tq : direct[h][i]) : direct[h][i] + tq;
-        acc[i] = fma(w, (double)v, acc[i]);
+        acc[i] = fma(w, f32_to_f64_exact(v), acc[i]);
       }
     }
     __syncthreads();
