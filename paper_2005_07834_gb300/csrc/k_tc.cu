@@ -161,25 +161,6 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
 // were computed: X_f + X_f^T = 2 X_f is read from the lower element of each pair (the tile
 // (bj, bi), and within a diagonal tile whichever of the two elements lies on or below the
 // diagonal), so that chi0 comes out exactly symmetric.
-// fp32 -> float64 (exact) with integer instructions and selects only: GB300 converts to float64
-// on its float64 pipe (2 per SM per clock), which this sum needs for its FMAs.  Normal values
-// rebias the exponent by 1023 - 127 and move the fraction up by 29 bits; subnormal ones
-// (m 2^-149) are normalised at their leading one; zeros, infinities and NaNs keep their class.
-__device__ __forceinline__ double f32_to_f64_exact(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned e = (u >> 23) & 0xFFu;
-  const unsigned m = u & 0x7FFFFFu;
-  const int p = 31 - __clz(m | 1u);   // leading one of a subnormal fraction
-  const unsigned long long sub =
-      ((unsigned long long)(p + 874) << 52) | ((unsigned long long)((m << (23 - p)) & 0x7FFFFFu) << 29);
-  const unsigned long long nrm = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
-  const unsigned long long special = (0x7FFull << 52) | ((unsigned long long)m << 29);
-  unsigned long long r = e == 0xFFu ? special : nrm;
-  r = e == 0u ? (m == 0u ? 0ull : sub) : r;
-  return __longlong_as_double((long long)(sign | r));
-}
-
 __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf,
                                                           const double* __restrict__ Wf,
                                                           const float* __restrict__ scales, int n, int sym,
@@ -621,10 +602,18 @@ __global__ void hprep_kernel(const float2* __restrict__ go, const float2* __rest
   }
 }
 
+// psi (float64 complex) -> fp32 complex, once per adjoint.
+__global__ void psi_to_f32_kernel(const double2* __restrict__ psi, size_t count, float2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = psi[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
 // Same update as the float64 adjoint's grad_accum_kernel, from fp32 Y, Z.
 constexpr int GA32_ROWS = 256;
 template <bool kOcc>
-__global__ void __launch_bounds__(256) grad_accum32_kernel(const double2* __restrict__ psi,
+__global__ void __launch_bounds__(256) grad_accum32_kernel(const float2* __restrict__ psi,
                                                            const float2* __restrict__ Y,
                                                            const float2* __restrict__ Z,
                                                            const double2* __restrict__ d, int n, int K,
@@ -632,7 +621,9 @@ __global__ void __launch_bounds__(256) grad_accum32_kernel(const double2* __rest
   // 32 columns per CTA (one per lane: coalesced rows), GA32_ROWS rows in eight row groups.
   // The products with d and psi are formed in fp32 (Y and Z are fp32 tensor-core results);
   // each element's contribution is added to the float64 gradient once per frequency, and the
-  // column sums of the energy gradient leave the CTA as float64 partial sums.
+  // column sums of the energy gradient leave the CTA as float64 partial sums.  psi arrives as
+  // fp32 (converted once per adjoint) and the fp32 terms are widened with integer instructions:
+  // GB300 converts between fp32 and float64 on its float64 pipe, which the sums already use.
   __shared__ double2 red[8][32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int b = blockIdx.x * 32 + tx;
@@ -645,14 +636,14 @@ __global__ void __launch_bounds__(256) grad_accum32_kernel(const double2* __rest
     for (int p = p0 + ty; p < p1; p += 8) {
       const size_t ix = (size_t)p * K + b;
       const float2 y = Y[ix], z = Z[ix];
-      const double2 ps = psi[ix];
+      const float2 ps = psi[ix];
       const float sx = y.x + z.x, sy = y.y + z.y;                       // y + z
       const float tx_ = kOcc ? y.x - z.x : z.x - y.x, ty_ = kOcc ? y.y - z.y : z.y - y.y;
       double2 g = gpsi[ix];
-      g.x += (double)fmaf(dx, sx, -dy * sy);                           // Re d (y + z)
-      g.y += (double)fmaf(dx, ty_, dy * tx_);                          // Im d (y -+ z)
+      g.x += f32_to_f64_exact(fmaf(dx, sx, -dy * sy));                 // Re d (y + z)
+      g.y += f32_to_f64_exact(fmaf(dx, ty_, dy * tx_));                // Im d (y -+ z)
       gpsi[ix] = g;
-      const float px = (float)ps.x, py = (float)ps.y;
+      const float px = ps.x, py = ps.y;
       if (kOcc) {                                                       // conj(psi) y
         er += fmaf(px, y.x, py * y.y);
         ei += fmaf(px, y.y, -py * y.x);
@@ -690,12 +681,19 @@ int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w, const doubl
   LRS_TRY(ensure(ctx, ws.g32, 2 * (size_t)Np * Np));
   LRS_TRY(ensure(ctx, ws.yz32, 2 * (size_t)n * K));
   LRS_TRY(ensure(ctx, ws.gpsi, (size_t)n * K));
+  LRS_TRY(ensure(ctx, ws.psi32, (size_t)n * K));
   LRS_TRY(ensure(ctx, ws.ge, (size_t)K));
   const int chunks = (n + GA32_ROWS - 1) / GA32_ROWS;
   LRS_TRY(ensure(ctx, ws.gpart, (size_t)chunks * K));
   LRS_TRY(ensure(ctx, ws.tc_scratch, (size_t)ctx->num_sms * 2 * TILE_M * 128));
   LRS_TRY(ensure(ctx, ws.adj_tiles, (size_t)nf + 4));
   LRS_CUDA_TRY(cudaMemsetAsync(ws.gpsi.ptr, 0, (size_t)n * K * sizeof(double2), ctx->stream));
+  float2* psi32_o = ws.psi32.ptr;
+  float2* psi32_u = ws.psi32.ptr + (size_t)n * Ko;
+  psi_to_f32_kernel<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(s.psi_o.ptr, (size_t)n * Ko, psi32_o);
+  LRS_TRY(after_launch(ctx, "psi_to_f32_kernel"));
+  psi_to_f32_kernel<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(s.psi_u.ptr, (size_t)n * Ku, psi32_u);
+  LRS_TRY(after_launch(ctx, "psi_to_f32_kernel"));
   LRS_CUDA_TRY(cudaMemsetAsync(ws.ge.ptr, 0, (size_t)K * sizeof(double), ctx->stream));
   // operands of the Green's functions (all frequencies) and of the Y/Z products
   LRS_TRY(ensure(ctx, ws.denom32, (size_t)nf * Kp));
@@ -787,11 +785,11 @@ int backward_site_mixed(lrs_ctx* ctx, Site& s, const double* grad_w, const doubl
     const double2* dof = ws.denom_o.ptr + (size_t)f * Ko;
     const double2* duf = ws.denom_u.ptr + (size_t)f * Ku;
     grad_accum32_kernel<true><<<dim3((Ko + 31) / 32, chunks), 256, 0, ctx->stream>>>(
-        s.psi_o.ptr, Y + yoff[0], Y + yoff[1], dof, n, Ko, ws.gpsi.ptr, ws.gpart.ptr);
+        psi32_o, Y + yoff[0], Y + yoff[1], dof, n, Ko, ws.gpsi.ptr, ws.gpart.ptr);
     LRS_TRY(after_launch(ctx, "grad_accum32_kernel"));
     LRS_TRY(grad_energy(ctx, ws.gpart.ptr, chunks, dof, ctx->w_o.ptr, Ko, ws.ge.ptr));
     grad_accum32_kernel<false><<<dim3((Ku + 31) / 32, chunks), 256, 0, ctx->stream>>>(
-        s.psi_u.ptr, Y + yoff[2], Y + yoff[3], duf, n, Ku, ws.gpsi.ptr + (size_t)n * Ko, ws.gpart.ptr);
+        psi32_u, Y + yoff[2], Y + yoff[3], duf, n, Ku, ws.gpsi.ptr + (size_t)n * Ko, ws.gpart.ptr);
     LRS_TRY(after_launch(ctx, "grad_accum32_kernel"));
     LRS_TRY(grad_energy(ctx, ws.gpart.ptr, chunks, duf, ctx->w_u.ptr, Ku, ws.ge.ptr + Ko));
   }

@@ -358,7 +358,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.ge); release(ctx, w.gpsi); release(ctx, w.gpart); release(ctx, w.tmp_nn);
   release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.denom32); release(ctx, w.phase_tab32); release(ctx, w.tc_scratch); release(ctx, w.slab64);
   release(ctx, w.site_tiles);
-  release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32);
+  release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32); release(ctx, w.psi32);
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
   release(ctx, w.gjb);

@@ -264,6 +264,25 @@ __device__ __forceinline__ float pow2_scale(float amax) {
   return exp2f(floorf(log2f(16384.f / amax)));
 }
 
+// fp32 -> float64 (exact) with integer instructions and selects only: GB300 converts to float64
+// on its float64 pipe (2 per SM per clock), which this sum needs for its FMAs.  Normal values
+// rebias the exponent by 1023 - 127 and move the fraction up by 29 bits; subnormal ones
+// (m 2^-149) are normalised at their leading one; zeros, infinities and NaNs keep their class.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  const int p = 31 - __clz(m | 1u);   // leading one of a subnormal fraction
+  const unsigned long long sub =
+      ((unsigned long long)(p + 874) << 52) | ((unsigned long long)((m << (23 - p)) & 0x7FFFFFu) << 29);
+  const unsigned long long nrm = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  const unsigned long long special = (0x7FFull << 52) | ((unsigned long long)m << 29);
+  unsigned long long r = e == 0xFFu ? special : nrm;
+  r = e == 0u ? (m == 0u ? 0ull : sub) : r;
+  return __longlong_as_double((long long)(sign | r));
+}
+
 }  // namespace tc
 
 // Host: encodes a 2-D bf16 tensor map [rows][cols] with a 64 x 128 box and

@@ -643,7 +643,8 @@ struct ProjStore {
       const int band = col0 + i;
       if (band >= nb) continue;
       const float a = s[0][i], c = s[1][i];
-      const double2 v = make_double2((double)(pr * a - pi * c), (double)(pr * c + pi * a));
+      // widened with integer instructions (GB300 converts on its float64 pipe)
+      const double2 v = make_double2(f32_to_f64_exact(pr * a - pi * c), f32_to_f64_exact(pr * c + pi * a));
       if (band < no) psi_o[(size_t)row * Ko + oofs[k] + band] = v;
       else psi_u[(size_t)row * Ku + uofs[k] + band - no] = v;
     }
