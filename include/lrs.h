@@ -76,7 +76,7 @@ extern "C" {
 #define LRS_OPT_GRAPH_PROJECTION 7  /* value: LRS_PROJ_EXACT (default) or LRS_PROJ_FFT_LAGRANGE3, recorded by lrs_graph_capture */
 #define LRS_OPT_REAL_ORBITALS    8  /* value: LRS_REAL_AUTO (default) or LRS_REAL_OFF */
 #define LRS_OPT_DYSON_UPDATE     9  /* value: LRS_UPDATE_AUTO (default), LRS_UPDATE_FP64 or LRS_UPDATE_TC */
-#define LRS_OPT_DYSON_LANES     10  /* value: 1..8 concurrent Dyson solves in one lrs_solve_w call (default 2) */
+#define LRS_OPT_DYSON_LANES     10  /* value: 1..8 concurrent Dyson solves in one lrs_solve_w call (default 4) */
 #define LRS_OPT_DYSON_PANEL     11  /* value: 0 (auto), 32 or 128: pivot-block width of the lm-basis SPD inverse */
 #define LRS_UPDATE_AUTO   0   /* tensor cores in the mixed precisions, the FP64 pipe in LRS_FP64 */
 #define LRS_UPDATE_FP64   1   /* lm-basis Dyson products (basis changes, radial blocks, SPD updates) with float64 FMAs */

@@ -11,7 +11,9 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "lrs_internal.h"
 #include "oz_slice.cuh"
@@ -461,9 +463,10 @@ static int launch_panel_cluster(lrs_ctx* ctx, double* A, int n, int j0, int jb, 
   const int rows = (m + PANEL_CS - 1) / PANEL_CS;
   const size_t smem = (size_t)rows * NB * sizeof(double);
   if (smem > 200 * 1024) return LRS_OK;   // taller panels: single-CTA kernel
-  static bool configured = false, usable = true;
-  if (!configured) {
-    configured = true;
+  // configured once, also when contexts on several host threads get here together
+  static std::atomic<bool> usable{true};
+  static std::once_flag configured;
+  std::call_once(configured, [] {
     if (cudaFuncSetAttribute(lu_panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess ||
         cudaFuncSetAttribute(lu_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
@@ -471,7 +474,7 @@ static int launch_panel_cluster(lrs_ctx* ctx, double* A, int n, int j0, int jb, 
       cudaGetLastError();
       usable = false;
     }
-  }
+  });
   if (!usable) return LRS_OK;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(PANEL_CS);

@@ -189,11 +189,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int col0 = bj * OZ_TN + cg * OZ_EPI_COLS;
       const int j = col0 + wc;
       const bool col_ok = j < p.n && !(j >= p.x0 && j < p.x1);
+      // rows r of this warp's 32 that this lane's column takes: inside the matrix, outside the
+      // pivot blocks [x0, x1), and on or below the diagonal (row0 + r >= j)
+      const int my_i = row0 + lane;
+      const unsigned rows_in = __ballot_sync(0xffffffffu, my_i < p.n && !(my_i >= p.x0 && my_i < p.x1));
+      const int rmin = j - row0;
+      const unsigned lower = rmin <= 0 ? 0xffffffffu : (rmin >= 32 ? 0u : (0xffffffffu << rmin));
+      const unsigned take = col_ok ? (rows_in & lower) : 0u;
 #pragma unroll 4
       for (int r = wr; r < 32; r += 2) {
-        const int i = row0 + r;
-        if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1))
-          cp_async8(stg_s + (uint32_t)(r * OZ_STG_LD + wc) * 8u, p.C + (size_t)i * p.ldc + j);
+        if ((take >> r) & 1u)
+          cp_async8(stg_s + (uint32_t)(r * OZ_STG_LD + wc) * 8u, p.C + (size_t)(row0 + r) * p.ldc + j);
       }
       cp_async_commit();
       // the row scale of this lane's TMEM row and the column scales of the 16 columns
@@ -224,9 +230,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           // |S_L| < 2^22: pairs of levels combine exactly in int32 before one 64-bit assembly
-          const int t3 = (oz_level_int(a[0][c]) << 8) + oz_level_int(a[1][c]);
-          const int t2 = (oz_level_int(a[2][c]) << 8) + oz_level_int(a[3][c]);
-          const int t1 = (oz_level_int(a[4][c]) << 8) + oz_level_int(a[5][c]) + (oz_level_int(a[6][c]) >> 8);
+          const int t3 = oz_pair<8>(oz_level_bits(a[0][c]), oz_level_bits(a[1][c]));
+          const int t2 = oz_pair<8>(oz_level_bits(a[2][c]), oz_level_bits(a[3][c]));
+          const int t1 = oz_pair<8>(oz_level_bits(a[4][c]), oz_level_bits(a[5][c])) +
+                         oz_level_shr<8>(oz_level_bits(a[6][c]));
           const long long V = ((long long)t3 << 32) + ((long long)t2 << 16) + (long long)t1;
           const int fj = __shfl_sync(0xffffffffu, fj_lane, ch * 8 + c);
           double* q = stg + lane * OZ_STG_LD + ch * 8 + c;
@@ -241,9 +248,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       acc_phase ^= 1u;
 #pragma unroll 4
       for (int r = wr; r < 32; r += 2) {
-        const int i = row0 + r;
-        if (col_ok && i < p.n && j <= i && !(i >= p.x0 && i < p.x1))
-          p.C[(size_t)i * p.ldc + j] = stg[r * OZ_STG_LD + wc];
+        if ((take >> r) & 1u) p.C[(size_t)(row0 + r) * p.ldc + j] = stg[r * OZ_STG_LD + wc];
       }
       __syncwarp();
     }

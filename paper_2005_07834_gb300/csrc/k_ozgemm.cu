@@ -398,9 +398,10 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
             // V = sum_L S_L 2^(42 - 7 L) with floor(S_7 / 2^7) (|V| < 2^62; the floor drops
             // less than 2^-56 of the row scales' product), rounded to float64 with integer
             // instructions
-            const int ta = (oz_level_int(a[1][c]) << 7) + oz_level_int(a[2][c]);
-            const int tb = (oz_level_int(a[3][c]) << 7) + oz_level_int(a[4][c]);
-            const int tc = (oz_level_int(a[5][c]) << 7) + oz_level_int(a[6][c]) + (oz_level_int(a[7][c]) >> 7);
+            const int ta = oz_pair<7>(oz_level_bits(a[1][c]), oz_level_bits(a[2][c]));
+            const int tb = oz_pair<7>(oz_level_bits(a[3][c]), oz_level_bits(a[4][c]));
+            const int tc = oz_pair<7>(oz_level_bits(a[5][c]), oz_level_bits(a[6][c])) +
+                           oz_level_shr<7>(oz_level_bits(a[7][c]));
             const long long V = ((long long)oz_level_int(a[0][c]) << 42) + ((long long)ta << 28) +
                                 ((long long)tb << 14) + (long long)tc;
             const int j = col0 + ch * 8 + c;

@@ -23,15 +23,16 @@
 namespace lrs {
 
 int make_operand_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (a function-local static is initialised once even when contexts on several
+  // host threads get here together)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-      return set_error(LRS_ERR_CUDA, "cuTensorMapEncodeTiled not available from the driver");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return set_error(LRS_ERR_CUDA, "cuTensorMapEncodeTiled not available from the driver");
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (cols * 2) % 16 != 0 || cols % 64 != 0 || rows % 128 != 0)
     return set_error(LRS_ERR_ARG, "operand map: misaligned base or shape (%llu x %llu)",
                      (unsigned long long)rows, (unsigned long long)cols);

@@ -642,12 +642,20 @@ int lrs_set_sites(lrs_ctx* ctx, int nsites, const double* centers, const int* np
   DeviceGuard g(ctx->device);
   if (g.rc) return g.rc;
   cudaStreamSynchronize(ctx->stream);
-  for (auto& s : ctx->sites) free_site(ctx, s);
-  ctx->sites.clear();
+  // A recorded build refers to the previous sites.  The device buffers of the sites that remain
+  // are kept and regrown only when too small: cudaFree waits for the whole device, which would
+  // stall the work other contexts have in flight.
+  drop_graph(ctx);
+  for (size_t i = nsites; i < ctx->sites.size(); ++i) free_site(ctx, ctx->sites[i]);
   ctx->sites.resize(nsites);
   off = 0;
   for (int i = 0; i < nsites; ++i) {
     Site& s = ctx->sites[i];
+    s.has_v = s.has_psi = s.has_chi0 = s.has_w = false;
+    s.spd = false;
+    s.product = false;
+    s.fxc_kind = LRS_FXC_NONE;
+    s.nrad = s.nang = 0;
     s.npts = npts[i];
     s.lmax = lmax[i];
     std::memcpy(s.center, centers + 3 * i, 3 * sizeof(double));

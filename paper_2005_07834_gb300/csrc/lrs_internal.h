@@ -246,7 +246,7 @@ struct lrs_ctx {
   int real_mode = LRS_REAL_AUTO;       // use the real-orbital contractions when the orbitals are real
   double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
-  int dyson_lanes = 2;                 // concurrent Dyson solves of one lrs_solve_w call
+  int dyson_lanes = 4;                 // concurrent Dyson solves of one lrs_solve_w call
   std::vector<lrs::DysonLane> lanes;   // lanes 1.. (lane 0 is the context itself)
   cudaEvent_t ev_lanes = nullptr;      // fork of the lanes from the context stream
 

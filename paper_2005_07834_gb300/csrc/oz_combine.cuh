@@ -57,6 +57,24 @@ __device__ __forceinline__ int oz_level_int(float s) {
   return __float_as_int(s + 12582912.0f) - 0x4B400000;
 }
 
+// The same without removing the bias: the bit pattern S + OZ_LEVEL_BIAS.  Combinations of
+// several levels remove the bias once (below); the bias is a multiple of 2^22.
+constexpr unsigned OZ_LEVEL_BIAS = 0x4B400000u;
+__device__ __forceinline__ unsigned oz_level_bits(float s) { return __float_as_uint(s + 12582912.0f); }
+
+// (S_a 2^W) + S_b from the biased bit patterns, in 32-bit arithmetic that wraps modulo 2^32:
+// exact whenever the result fits in an int32.
+template <int W>
+__device__ __forceinline__ int oz_pair(unsigned ba, unsigned bb) {
+  return (int)((ba << W) + bb - ((OZ_LEVEL_BIAS << W) + OZ_LEVEL_BIAS));
+}
+
+// floor(S / 2^W) from the biased bit pattern (W <= 22, so the bias divides exactly).
+template <int W>
+__device__ __forceinline__ int oz_level_shr(unsigned b) {
+  return (int)(b >> W) - (int)(OZ_LEVEL_BIAS >> W);
+}
+
 // Out-of-range results of oz_i64_times_pow2, kept out of line so that its float64
 // instructions are not issued (predicated off) on the common path.
 static __device__ __noinline__ double oz_i64_times_pow2_slow(long long v, int k) { return ldexp((double)v, k); }

@@ -188,3 +188,29 @@ def test_level_pairs_combine_in_int32():
                 parts, got = (ta, tb, tc), (S[0] << 42) + (ta << 28) + (tb << 14) + tc
             assert all(i32[0] <= p <= i32[1] for p in parts)
             assert got == ref
+
+
+def test_level_pairs_from_biased_bit_patterns():
+    """The epilogues read each level sum as the bit pattern b = S + 0x4B400000 of the fp32 value
+    S + 1.5 2^23 and remove the bias once per pair: (b_a << w) + b_b - ((bias << w) + bias) in
+    32-bit arithmetic that wraps modulo 2^32 equals (S_a << w) + S_b, and (b >> w) - (bias >> w)
+    equals floor(S / 2^w), for |S| <= 2^22 and w = 7, 8 (the bias is a multiple of 2^22)."""
+    bias = 0x4B400000
+    rng = np.random.default_rng(6)
+    m32 = (1 << 32) - 1
+
+    def as_i32(x):
+        x &= m32
+        return x - (1 << 32) if x >> 31 else x
+
+    for w in (7, 8):
+        cases = [((1 << 22), (1 << 22)), (-(1 << 22), -(1 << 22)), ((1 << 22), -(1 << 22)), (0, 0)]
+        cases += [tuple(int(v) for v in rng.integers(-(1 << 22), (1 << 22) + 1, 2)) for _ in range(5000)]
+        for sa, sb in cases:
+            # the fp32 value S + 1.5 2^23 has the bit pattern S + bias (consecutive integers)
+            ba = int(np.float32(sa + 12582912.0).view(np.uint32))
+            bb = int(np.float32(sb + 12582912.0).view(np.uint32))
+            assert ba == sa + bias and bb == sb + bias
+            pair = as_i32(((ba << w) & m32) + bb - (((bias << w) & m32) + bias))
+            assert pair == (sa << w) + sb
+            assert (ba >> w) - (bias >> w) == sa >> w
