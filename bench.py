@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one chi0 launch, from one ncu capture
 # (profiles/ncu_chi0_single-site-3520_bf16x3.md), valid only for the kernel revision named.
-CHI0_TRAFFIC = {("single-site-3520", "bf16x3", "r1"): 23.26e9}
+CHI0_TRAFFIC = {("single-site-3520", "bf16x3", "r1"): 23.26e9, ("single-site-3520", "bf16x3", "r2"): 20.77e9}
 
 
 def kernel_revision(version, name):
@@ -68,7 +68,8 @@ MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 
 # (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per launch of the update kernel
 DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"): 28.5e6,
-                 ("single-site-3520", "r4"): 28.52e6, ("single-site-3520", "r5"): 28.52e6}
+                 ("single-site-3520", "r4"): 28.52e6, ("single-site-3520", "r5"): 28.52e6,
+                 ("single-site-3520", "r6"): 28.51e6}
 
 
 def dyson_roofline(st, workload=None, version=None, hbm_gbs=None, bf16_tflops=None):
@@ -192,12 +193,17 @@ def dist_setup():
     return world, rank, local
 
 
-def make_workload(name, nfreq=0):
-    """The named synthetic workload; nfreq > 0 replaces its frequency count (smaller profiler captures)."""
+def make_workload(name, nfreq=0, sites=None):
+    """The named synthetic workload; nfreq > 0 replaces its frequency count and `sites` (indices)
+    keeps a subset of a multi-site workload's sites (smaller profiler captures)."""
     import dataclasses
     from paper_2005_07834_gb300 import synth
     wl = getattr(synth, WORKLOADS[name])()
-    return dataclasses.replace(wl, nfreq=nfreq) if nfreq else wl
+    if nfreq:
+        wl = dataclasses.replace(wl, nfreq=nfreq)
+    if sites:
+        wl = dataclasses.replace(wl, sites=[wl.sites[i] for i in sites])
+    return wl
 
 
 # ----------------------------------------------------------------------------- shared descriptions
@@ -216,9 +222,12 @@ def workload_config(name, wl, args):
     K = o.nk * o.nbands
     if name in MULTI_SITE:
         sizes = [s.npts for s in wl.sites]
-        return {"workload": name, "sites": len(sizes), "npts_min": min(sizes), "npts_max": max(sizes),
-                "npts_sum": sum(sizes), "K": K, "nfreq": wl.nfreq, "ng": o.ng, "projection": args.projection,
-                "graph": "one CUDA graph replay per step", "l2": "inputs larger than L2"}
+        cfg = {"workload": name, "sites": len(sizes), "npts_min": min(sizes), "npts_max": max(sizes),
+               "npts_sum": sum(sizes), "K": K, "nfreq": wl.nfreq, "ng": o.ng, "projection": args.projection,
+               "graph": "one CUDA graph replay per step", "l2": "inputs larger than L2"}
+        if getattr(args, "sites", None):
+            cfg["site_subset"] = list(args.sites)   # a profiling run, not the named workload
+        return cfg
     s = wl.sites[0]
     return {"workload": name, "npts": s.npts, "K": K, "nfreq": wl.nfreq, "ng": o.ng, "replicas_per_gpu": 1,
             "projection": args.projection, "real_orbitals": name.startswith("gamma"),
@@ -651,7 +660,7 @@ def run_multisite_line(args):
     torch.cuda.set_device(local)
     from paper_2005_07834_gb300 import lrs
     t_gen = time.perf_counter()
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.nfreq, args.sites)
     t_gen = time.perf_counter() - t_gen
     o = wl.orbitals
     K = o.nk * o.nbands
@@ -761,22 +770,36 @@ def e2e_measure(lrs, torch, wl, pmode, precision, device, reps):
     serial_s = (time.perf_counter() - t0) / reps
     # two contexts, each driven by its own host thread over every other step: while one thread
     # waits in solve_w (it reads the Dyson status, so it returns when W is done) or copies W back,
-    # the other copies its step's inputs and queues its projection, chi0 and Dyson solve
+    # the other copies its step's inputs and queues its projection, chi0 and Dyson solve.  Step i
+    # copies its inputs only once step i - 1 has been queued, so that the copies always overlap
+    # queued device work (two threads copying at once would leave the GPU without work).
     import threading
     torch.cuda.synchronize()
     errors = []
+    queued = [0]
+    turn = threading.Condition()
 
     def drive(ci):
         c = ctxs[ci]
         try:
             torch.cuda.set_device(device)
-            for _ in range(ci, reps, 2):
+            for i in range(ci, reps, 2):
+                with turn:
+                    if not turn.wait_for(lambda: queued[0] >= i or errors, timeout=120.0):
+                        raise RuntimeError("e2e: the other context's step was not queued")
+                if errors:
+                    return
                 prepare(c)
                 launch(c)
+                with turn:
+                    queued[0] = i + 1
+                    turn.notify_all()
                 c.solve_w()
                 c.get_w(0, out=w_host[ci])
         except Exception as ex:   # re-raised on the main thread
-            errors.append(ex)
+            with turn:
+                errors.append(ex)
+                turn.notify_all()
 
     threads = [threading.Thread(target=drive, args=(ci,)) for ci in range(2)]
     t0 = time.perf_counter()
@@ -793,8 +816,8 @@ def e2e_measure(lrs, torch, wl, pmode, precision, device, reps):
             "steps": reps, "contexts": 2, "one_context_value": 1.0 / serial_s,
             "method": "page-locked host buffers; every step loads coefficients, energies, k-points and the site "
                       "grid and reads W back; two contexts on two streams, each driven by its own host thread, "
-                      "take every other step, so that one step's copies and queued kernels overlap the other's "
-                      "build and read-back"}
+                      "take every other step; a step copies its inputs once the previous step is queued, so "
+                      "that its copies overlap device work"}
 
 
 def run_ours(args):
@@ -1099,6 +1122,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true",
                     help="skip the adjoint timings (this workload and the 260-point differentiation case)")
+    ap.add_argument("--sites", type=lambda t: [int(x) for x in t.split(",") if x], default=None,
+                    help="comma-separated site indices: build only these sites of a multi-site workload "
+                         "(profiler captures; not a bench line of the named workload)")
     ap.add_argument("--nfreq", type=int, default=0,
                     help="replace the workload's frequency count (0: keep it); for small profiler captures only")
     ap.add_argument("--workloads", default="batched-64-sites",
