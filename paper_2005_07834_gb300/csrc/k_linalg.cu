@@ -1062,9 +1062,14 @@ int spd_inverse(lrs_ctx* ctx, double* A, int n, int lda, int* status) {
                                       Pb[q], status));
     LRS_TRY(after_launch(ctx, "gj_pivot_kernel"));
     LRS_CUDA_TRY(record(s2, SPD_PIVOT, p));
-    // s4: the other rows of the panel, then their D
+    // s4: the other rows of the panel, then their D.  The rows of block p - 2 read stored
+    // (j, i), j in block p, from the column block that the exchange write-back of p - 2
+    // (gj_fix_kernel on s3) rewrites: wait for it too
     if (p >= 1) LRS_CUDA_TRY(wait(s4, SPD_ADIAG, p - 1));
-    if (p >= 2) LRS_CUDA_TRY(wait(s4, SPD_BULK, p - 2));
+    if (p >= 2) {
+      LRS_CUDA_TRY(wait(s4, SPD_BULK, p - 2));
+      LRS_CUDA_TRY(wait(s4, SPD_FIX, p - 2));
+    }
     LRS_TRY(gather(p, s4, 0, n, lo, hi));
     LRS_CUDA_TRY(record(s4, SPD_GREST, p));
     LRS_CUDA_TRY(wait(s4, SPD_PIVOT, p));

@@ -130,3 +130,29 @@ def test_concurrent_dyson_lanes_match_one_lane(lrs, workload, lanes):
         scr.set_option(lrs.LRS_OPT_DYSON_LANES, 9)
     assert e.value.code == lrs.LRS_ERR_ARG
     scr.close()
+
+
+def test_four_lanes_on_large_sites_match_one_lane(lrs):
+    """Four sites of the 64-site workload (800 to 9118 points, r up to 6768) solved on four
+    concurrent lanes, whose side streams then compete for the GPU: W bit for bit equal to one
+    lane.  (Before the gather of a panel's other rows waited for the exchange write-back of the
+    block two steps back, this case read stale values under contention: W - v off by 6e-5.)"""
+    from paper_2005_07834_gb300 import synth as _synth
+    wl = _synth.batched_64_sites()
+    sites = [wl.sites[i] for i in (4, 5, 17, 59)]
+    scr = lrs.Screening(0, "bf16x3")
+    scr.load(wl.orbitals)
+    scr.set_sites(sites)
+    scr.set_frequency_quadrature(wl.nfreq)
+    scr.project()
+    scr.build_chi0()
+    scr.set_option(lrs.LRS_OPT_DYSON_LANES, 1)
+    scr.solve_w()
+    one = [scr.get_w(i) for i in range(4)]
+    for lanes in (4, 3, 2):
+        scr.set_option(lrs.LRS_OPT_DYSON_LANES, lanes)
+        for _ in range(2):
+            scr.solve_w()
+            for i in range(4):
+                assert np.array_equal(scr.get_w(i), one[i]), (lanes, i)
+    scr.close()
