@@ -725,10 +725,9 @@ def e2e_measure(lrs, torch, wl, pmode, precision, device, reps):
     """Site builds per second through the C-ABI from page-locked host buffers: every step loads the
     coefficients, energies, k-points and the site grid (host -> device), projects, builds chi0 and W
     and reads W back into host memory (device -> host).  Two contexts on two streams take the steps
-    in turn, each driven by its own host thread, so that one step's host -> device copy and kernels
-    overlap the other step's build (a caller with a stream of builds would do the same); the
-    one-context figure without any overlap is reported beside it.  One untimed step per context
-    first (allocations)."""
+    in turn, so that one step's host -> device copy and queued kernels overlap the other step's
+    build (a caller with a stream of builds would do the same); the one-context figure without any
+    overlap is reported beside it.  One untimed step per context first (allocations)."""
     import dataclasses
     o, s = wl.orbitals, wl.sites[0]
     h2d = o.coeff.nbytes + o.energies.nbytes + o.kpts.nbytes + o.kweights.nbytes + o.gvec.nbytes + \
@@ -768,56 +767,32 @@ def e2e_measure(lrs, torch, wl, pmode, precision, device, reps):
         ctxs[0].solve_w()
         ctxs[0].get_w(0, out=w_host[0])
     serial_s = (time.perf_counter() - t0) / reps
-    # two contexts, each driven by its own host thread over every other step: while one thread
-    # waits in solve_w (it reads the Dyson status, so it returns when W is done) or copies W back,
-    # the other copies its step's inputs and queues its projection, chi0 and Dyson solve.  Step i
-    # copies its inputs only once step i - 1 has been queued, so that the copies always overlap
-    # queued device work (two threads copying at once would leave the GPU without work).
-    import threading
+    # two contexts on two streams, one host thread: step i + 1's inputs are copied and its
+    # projection, chi0 and Dyson solve queued (lrs_solve_w_async) while step i runs; then step
+    # i's status is read (lrs_synchronize) and W copied back
     torch.cuda.synchronize()
-    errors = []
-    queued = [0]
-    turn = threading.Condition()
-
-    def drive(ci):
-        c = ctxs[ci]
-        try:
-            torch.cuda.set_device(device)
-            for i in range(ci, reps, 2):
-                with turn:
-                    if not turn.wait_for(lambda: queued[0] >= i or errors, timeout=120.0):
-                        raise RuntimeError("e2e: the other context's step was not queued")
-                if errors:
-                    return
-                prepare(c)
-                launch(c)
-                with turn:
-                    queued[0] = i + 1
-                    turn.notify_all()
-                c.solve_w()
-                c.get_w(0, out=w_host[ci])
-        except Exception as ex:   # re-raised on the main thread
-            with turn:
-                errors.append(ex)
-                turn.notify_all()
-
-    threads = [threading.Thread(target=drive, args=(ci,)) for ci in range(2)]
     t0 = time.perf_counter()
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
+    prepare(ctxs[0])
+    launch(ctxs[0])
+    ctxs[0].solve_w_async()
+    for i in range(reps):
+        c = ctxs[i % 2]
+        if i + 1 < reps:
+            nxt = ctxs[(i + 1) % 2]   # its previous step (i - 1) has been read back
+            prepare(nxt)
+            launch(nxt)
+            nxt.solve_w_async()
+        c.synchronize()
+        c.get_w(0, out=w_host[i % 2])
     e2e_s = (time.perf_counter() - t0) / reps
-    if errors:
-        raise errors[0]
     for c in ctxs:
         c.close()
     return {"value": 1.0 / e2e_s, "unit": "builds/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "steps": reps, "contexts": 2, "one_context_value": 1.0 / serial_s,
             "method": "page-locked host buffers; every step loads coefficients, energies, k-points and the site "
-                      "grid and reads W back; two contexts on two streams, each driven by its own host thread, "
-                      "take every other step; a step copies its inputs once the previous step is queued, so "
-                      "that its copies overlap device work"}
+                      "grid and reads W back; two contexts on two streams take the steps in turn from one "
+                      "host thread: the next step's inputs are copied and its projection, chi0 and Dyson "
+                      "solve queued (lrs_solve_w_async) while the current step runs"}
 
 
 def run_ours(args):
@@ -884,7 +859,7 @@ def run_ours(args):
     e2e = None
     if rank == 0 and not args.no_e2e:
         e2e = e2e_measure(lrs, torch, wl, pmode, args.precision, local,
-                          reps=1 if args.precision == "fp64" else max(3, min(args.steps, 10)))
+                          reps=1 if args.precision == "fp64" else max(3, min(2 * args.steps, 20)))
 
     peaks = load_peaks()
     n, K, nf = s.npts, o.nk * o.nbands, wl.nfreq

@@ -390,6 +390,20 @@ int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites);
  */
 int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites);
 
+/*
+ * The same solves queued on the context stream without waiting for them
+ * (Sec. VI.E, as lrs_solve_w): the call returns once the work is queued, so
+ * that one host thread can keep the next build in flight.  W of those sites
+ * may be read at once (lrs_get_w copies in stream order, after the solve).
+ * Device-side failures (a zero, non-positive or non-finite pivot; a
+ * tensor-core kernel that gave up a bounded wait) are reported by the next
+ * lrs_synchronize or lrs_solve_w on the context, which then marks W of the
+ * queued sites missing; lrs_set_sites forgets the queued sites (call
+ * lrs_synchronize first to see their status).
+ * Errors (at queueing): LRS_ERR_STATE (no chi0), LRS_ERR_ARG, LRS_ERR_OOM.
+ */
+int lrs_solve_w_async(lrs_ctx* ctx, int nsite, const int* sites);
+
 /* Copy chi0, W or v of one site ([npts][npts] float64) to host memory. */
 int lrs_get_chi0(lrs_ctx* ctx, int site, double* out);
 int lrs_get_w(lrs_ctx* ctx, int site, double* out);
@@ -479,7 +493,9 @@ int lrs_graph_launch(lrs_ctx* ctx);
  */
 int lrs_autotune(lrs_ctx* ctx, int nsite, const int* sites, int* tile_n, int* segment, double* ms_best);
 
-/* Wait for the context stream; fold device timings into the stats. */
+/* Wait for the context stream; fold device timings into the stats; report the
+ * status of solves queued by lrs_solve_w_async (LRS_ERR_NUMERIC,
+ * LRS_ERR_TIMEOUT). */
 int lrs_synchronize(lrs_ctx* ctx);
 
 /* Statistics of the context (synchronises the stream first). */

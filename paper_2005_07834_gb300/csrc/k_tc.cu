@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restric
                                                           const double* __restrict__ Wf,
                                                           const float* __restrict__ scales, int n, int sym,
                                                           double* __restrict__ chi0) {
-  __shared__ float t[2][32][33];
+  constexpr int FB = 4;          // frequencies per pair of barriers: all their tiles in flight at once
+  __shared__ float t[FB][32][33];
   __shared__ double o[32][33];
   __shared__ double wsm[128];   // per-frequency weights W_f / (scales[f] scales[nf])^2 (x 2 with sym)
   const int bi = blockIdx.y, bj = blockIdx.x;
@@ -183,12 +184,11 @@ __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restric
     wsm[f] = sym ? 2.0 * w : w;
   }
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  // two frequencies per pair of barriers: both tiles of both are in flight at once
-  for (int f = 0; f < nf; f += 2) {
-    const int nb = min(2, nf - f);
-    float direct[2][4];
+  for (int f = 0; f < nf; f += FB) {
+    const int nb = min(FB, nf - f);
+    float direct[FB][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < FB; ++h) {
       if (h >= nb) break;
       const float* s = slab + (size_t)(f + h) * Np * Np;
 #pragma unroll
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restric
     }
     __syncthreads();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < FB; ++h) {
       if (h >= nb) break;
       const double w = wsm[f + h];
 #pragma unroll

@@ -381,7 +381,7 @@ const char* lrs_last_error(void) { return g_last_error.c_str(); }
 
 // The chi0 tensor-core kernel revision lets measurements quote profiler
 // counters only for the kernel version they were taken on.
-const char* lrs_version(void) { return "lrs 0.5 (sm_103a) chi0-tc r2 dyson-gj r6"; }
+const char* lrs_version(void) { return "lrs 0.6 (sm_103a) chi0-tc r2 dyson-gj r6"; }
 
 int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   clear_error();
@@ -646,6 +646,7 @@ int lrs_set_sites(lrs_ctx* ctx, int nsites, const double* centers, const int* np
   // are kept and regrown only when too small: cudaFree waits for the whole device, which would
   // stall the work other contexts have in flight.
   drop_graph(ctx);
+  ctx->w_pending.clear();   // queued solves refer to the previous sites (their status words stay)
   for (size_t i = nsites; i < ctx->sites.size(); ++i) free_site(ctx, ctx->sites[i]);
   ctx->sites.resize(nsites);
   off = 0;
@@ -1057,12 +1058,8 @@ int lrs_build_chi0(lrs_ctx* ctx, int nsite, const int* sites) {
   return LRS_OK;
 }
 
-int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
-  clear_error();
-  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
-  DeviceGuard g(ctx->device);
-  if (g.rc) return g.rc;
-  std::vector<int> list;
+// lrs_solve_w up to the device-side status check: queues the solves of the listed sites.
+static int solve_w_queue(lrs_ctx* ctx, int nsite, const int* sites, std::vector<int>& list) {
   LRS_TRY(site_list(ctx, nsite, sites, list));
   for (int i : list)
     if (!ctx->sites[i].has_chi0) return set_error(LRS_ERR_STATE, "site %d has no chi0", i);
@@ -1129,6 +1126,13 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
   ctx->stats.flop_w_main = ctx->w_main_flop;
   ctx->stats.w_main_elements = ctx->w_main_elems;
   ctx->stats.w_main_launches = ctx->w_main_launches;
+  return LRS_OK;
+}
+
+// The status words of queued solves of `list` (waits for the context stream): a tensor-core
+// kernel that gave up a bounded wait, or a zero / non-positive / non-finite pivot (the sites'
+// W are then marked missing).
+static int solve_w_status(lrs_ctx* ctx, const std::vector<int>& list) {
   if (ctx->capturing) return LRS_OK;   // checked after each replay by lrs_graph_launch's caller
   // zero pivots / non-finite values are reported through the status word
   int status[16] = {0};
@@ -1146,6 +1150,30 @@ int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
                      status[0] == 2 ? "SPD inverse" : "LU", status[0] == 2 ? "non-positive or non-finite"
                      : "zero or non-finite", status[0], status[1]);
   }
+  return LRS_OK;
+}
+
+int lrs_solve_w(lrs_ctx* ctx, int nsite, const int* sites) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  std::vector<int> list;
+  LRS_TRY(solve_w_queue(ctx, nsite, sites, list));
+  // solves queued earlier by lrs_solve_w_async share the status words
+  list.insert(list.end(), ctx->w_pending.begin(), ctx->w_pending.end());
+  ctx->w_pending.clear();
+  return solve_w_status(ctx, list);
+}
+
+int lrs_solve_w_async(lrs_ctx* ctx, int nsite, const int* sites) {
+  clear_error();
+  if (!ctx) return set_error(LRS_ERR_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (g.rc) return g.rc;
+  std::vector<int> list;
+  LRS_TRY(solve_w_queue(ctx, nsite, sites, list));
+  if (!ctx->capturing) ctx->w_pending.insert(ctx->w_pending.end(), list.begin(), list.end());
   return LRS_OK;
 }
 
@@ -1347,6 +1375,11 @@ int lrs_synchronize(lrs_ctx* ctx) {
     cudaMemsetAsync(ctx->ws.status.ptr + 8, 0, sizeof(int), ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     return set_error(LRS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code %d)", tc_status);
+  }
+  if (!ctx->w_pending.empty()) {
+    const std::vector<int> list = std::move(ctx->w_pending);
+    ctx->w_pending.clear();
+    LRS_TRY(solve_w_status(ctx, list));
   }
   for (int s = 0; s < 6; ++s)
     if (ctx->ev_pending[s]) {

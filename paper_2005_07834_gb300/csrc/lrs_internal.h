@@ -247,6 +247,7 @@ struct lrs_ctx {
   double workspace_budget = 48e9;      // bytes of chi0 operand planes + slabs per launch
   bool capturing = false;              // a CUDA graph is being recorded on the stream
   int dyson_lanes = 4;                 // concurrent Dyson solves of one lrs_solve_w call
+  std::vector<int> w_pending;          // sites of queued lrs_solve_w_async calls (status not read yet)
   std::vector<lrs::DysonLane> lanes;   // lanes 1.. (lane 0 is the context itself)
   cudaEvent_t ev_lanes = nullptr;      // fork of the lanes from the context stream
 

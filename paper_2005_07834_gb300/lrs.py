@@ -82,6 +82,7 @@ _SIGS = {
     "lrs_set_site_orbitals_dev": (C.c_int, [_P, C.c_int, _P]),
     "lrs_build_chi0": (C.c_int, [_P, C.c_int, _IP]),
     "lrs_solve_w": (C.c_int, [_P, C.c_int, _IP]),
+    "lrs_solve_w_async": (C.c_int, [_P, C.c_int, _IP]),
     "lrs_get_chi0": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_w": (C.c_int, [_P, C.c_int, _DP]),
     "lrs_get_v": (C.c_int, [_P, C.c_int, _DP]),
@@ -301,6 +302,10 @@ class Screening:
     def solve_w(self, sites=None):
         n, p, _keep = self._sites(sites)
         _check(lrs_solve_w(self.ctx, n, p), "lrs_solve_w")
+
+    def solve_w_async(self, sites=None):
+        n, p, _keep = self._sites(sites)
+        _check(lrs_solve_w_async(self.ctx, n, p), "lrs_solve_w_async")
 
     def _get(self, fn, site, name, out=None):
         n = self.npts[site]

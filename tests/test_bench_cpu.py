@@ -108,3 +108,17 @@ def test_blocked_update_is_reported_against_the_tensor_peak():
     assert r["bound"] == "tensor" and r["pivot_block"] == 128
     assert abs(r["achieved"] - 36 * 2.0 * 128 * elems * launches / (ms * 1e-3) / 1e12) < 1e-6
     assert abs(r["hbm_gbs_algorithmic"] - 16.0 * elems * launches / (ms * 1e-3) / 1e9) < 1e-6
+
+
+def test_site_subset_of_a_multi_site_workload():
+    """--sites keeps the named sites of a multi-site workload (profiling runs) and the bench line's
+    config says so."""
+    import argparse
+    import bench
+    wl = bench.make_workload("batched-64-sites", 0, [2, 5])
+    full = bench.make_workload("batched-64-sites")
+    assert len(wl.sites) == 2
+    assert wl.sites[0].npts == full.sites[2].npts and wl.sites[1].npts == full.sites[5].npts
+    args = argparse.Namespace(projection="exact", sites=[2, 5])
+    cfg = bench.workload_config("batched-64-sites", wl, args)
+    assert cfg["sites"] == 2 and cfg["site_subset"] == [2, 5]

@@ -62,3 +62,43 @@ def test_two_threads_and_reused_site_buffers(lrs):
         assert [i for i, _ in out[t]] == order[t]
         for i, w in out[t]:
             assert np.array_equal(w, ref[i]), (t, i)
+
+
+def test_queued_solves_match_waiting_ones(lrs):
+    """lrs_solve_w_async queues the Dyson solves and returns; W read afterwards (stream order)
+    equals lrs_solve_w's bit for bit, also with two contexts whose builds are queued one behind
+    the other from one host thread (the end-to-end pipeline); lrs_synchronize reads the status."""
+    wl = synth.single_site_260()
+    c = wl.sites[0].center
+    sites = [wl.sites[0], synth.site_grid(c, 20, 26, 4.0)]
+    scr = lrs.Screening(0, "bf16x3")
+    scr.load(wl.orbitals)
+    ref = [build(scr, wl, s) for s in sites]
+    scr.set_sites([sites[0]])
+    scr.set_frequency_quadrature(wl.nfreq)
+    scr.project()
+    scr.build_chi0()
+    scr.solve_w_async()
+    assert np.array_equal(scr.get_w(0), ref[0])
+    scr.synchronize()
+    scr.close()
+    ctxs = [lrs.Screening(0, "bf16x3") for _ in range(2)]
+    order = [0, 1, 1, 0, 0, 1]
+
+    def queue(c, i):
+        c.load(wl.orbitals)
+        c.set_sites([sites[i]])
+        c.set_frequency_quadrature(wl.nfreq)
+        c.project()
+        c.build_chi0()
+        c.solve_w_async()
+
+    queue(ctxs[0], order[0])
+    for k, i in enumerate(order):
+        cur = ctxs[k % 2]
+        if k + 1 < len(order):
+            queue(ctxs[(k + 1) % 2], order[k + 1])
+        cur.synchronize()
+        assert np.array_equal(cur.get_w(0), ref[i]), k
+    for c_ in ctxs:
+        c_.close()
