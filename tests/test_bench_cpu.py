@@ -122,3 +122,12 @@ def test_site_subset_of_a_multi_site_workload():
     args = argparse.Namespace(projection="exact", sites=[2, 5])
     cfg = bench.workload_config("batched-64-sites", wl, args)
     assert cfg["sites"] == 2 and cfg["site_subset"] == [2, 5]
+
+
+def test_bench_line_is_strict_json():
+    """A non-finite float anywhere in the line (a failed sub-measurement) is printed as null."""
+    import json
+    import bench
+    line = {"value": 1.0, "a": {"b": [float("nan"), 2.0, float("inf")]}, "c": None}
+    out = json.loads(json.dumps(bench.strict_json(line), allow_nan=False))
+    assert out == {"value": 1.0, "a": {"b": [None, 2.0, None]}, "c": None}
