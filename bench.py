@@ -288,7 +288,7 @@ def oracle_reference_sample(wl):
                               "scale_project": o.nk, "scale_chi0": wl.nfreq, "scale_w": 1}
 
 
-def oracle_single_site_leg(wl, results):
+def oracle_single_site_leg(wl, results, config1=None):
     """cpu_baseline leg of the single-site workloads: the FP64 oracle on the host cores on a bounded
     sample of one build, timed, whose outputs double as the accuracy reference:
       * orbitals on every site point for every k-point by the direct sum (Sec. VI.B method 1), timed;
@@ -298,7 +298,10 @@ def oracle_single_site_leg(wl, results):
     `results` maps a path name to (chi0, W, v) from the library; each is compared with the oracle:
     its chi0 rows element-wise and by row norms, and its W and W - v with the oracle's dense LU applied
     to that path's own chi0 (the Dyson route, the rounding of chi0 taken out).  The mixed path is
-    also compared with the plain one.  Returns (cpu_baseline dict, accuracy dict)."""
+    also compared with the plain one.  `config1` is the plain FP64 build (chi0, W, v) of the
+    260-point site, compared whole with the oracle at the quadrature (kappa_N) and with the exact
+    frequency integral (kappa_exact: the quadrature error itself).  Returns (cpu_baseline dict,
+    accuracy dict)."""
     from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
     o, s = wl.orbitals, wl.sites[0]
     rows = np.sort(np.random.default_rng(3).choice(s.npts, ORACLE_ROWS, replace=False))
@@ -331,12 +334,35 @@ def oracle_single_site_leg(wl, results):
         cm, wm, _ = results["mixed"]
         cp, wp, _ = results["fp64"]
         acc["mixed_vs_fp64_gpu"] = {"chi0": errors(cm, cp), "w": errors(wm, wp), "w_minus_v": errors(wm - v, wp - v)}
+    if config1 is not None:
+        acc["plain_fp64_260_points"] = config1_vs_kappa(config1)
     cpu = {"value": 1.0 / t_build, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
            "sample": f"one site: orbitals on all {s.npts} points for all {o.nk} k-points, chi0 over all rows on 1 "
                      f"of {wl.nfreq} frequencies (x {wl.nfreq}), full Dyson LU",
            "parts_s": {"t_project_s": t_proj, "t_chi0_one_frequency_s": t_chi1, "t_w_s": t_w},
            "measured_s": t_proj + t_chi1 + t_w}
     return cpu, acc
+
+
+def config1_vs_kappa(built):
+    """The plain FP64 build of the 260-point site against the pair-sum oracle with the quadrature
+    kernel kappa_N (the method's own result) and with kappa_exact (the exact frequency integral)."""
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
+    from paper_2005_07834_gb300 import synth
+    wl = synth.single_site_260()
+    o, s = wl.orbitals, wl.sites[0]
+    psi = oproj.project_direct(o.cell, o.kpts, o.gvec, o.coeff, s.center, s.pts)
+    po, pu, eo, eu, wo, wu = oproj.split_occupied(psi, o.energies, o.nocc, o.kweights)
+    mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
+    t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
+    v = ocoul.coulomb_multipole(s.pts, s.lmax)
+    chi, w, _ = built
+    out = {"reference": "pair-sum oracle (Eq. chi1) on the whole 260-point site, 12 frequencies"}
+    for name, exact in (("vs_kappa_N", False), ("vs_kappa_exact", True)):
+        c = ochi0.chi0_pairs(po, pu, eo, eu, wo, wu, mu, t, W, exact=exact)
+        wr = odys.screened_interaction(v, c, s.wts)
+        out[name] = {"chi0": errors(chi, c), "w": errors(w, wr), "w_minus_v": errors(w - v, wr - v)}
+    return out
 
 
 def oracle_multisite_leg(wl, sites, lib):
@@ -520,7 +546,7 @@ def backward_leg(lrs, scr, stream, s, K, nf, peaks, precision, real=False):
 def config4_backward(lrs, stream):
     """Differentiation workload: 260-point site, FP64 context, L = q^T W q; microseconds per
     forward build (eager and replayed from a recorded CUDA graph) and per backward (device
-    buffers, event-timed medians)."""
+    buffers, event-timed medians).  Also returns the build's (chi0, W, v) for the oracle leg."""
     import torch
     from paper_2005_07834_gb300 import synth
     wl = synth.single_site_260()
@@ -535,6 +561,7 @@ def config4_backward(lrs, stream):
         scr.build_chi0()
         scr.solve_w()
     ms_f = timed_on(stream, fwd, 3, 20)
+    built = (scr.get_chi0(0), scr.get_w(0), scr.get_v(0))   # for the oracle leg (kappa_N and exact)
     # the same build recorded once as a CUDA graph and replayed (this size is launch-bound)
     try:
         scr.graph_capture()
@@ -558,7 +585,7 @@ def config4_backward(lrs, stream):
             "builds_per_s_graph_replay": 1e3 / ms_g if ms_g else None,
             "graph_error": graph_error,
             "us_backward": 1e3 * ms_b, "loss": "q^T W q, q ~ N(0,1) seed 2",
-            "timing": "median of 20 after 3 warm-ups, CUDA events on the context stream"}
+            "timing": "median of 20 after 3 warm-ups, CUDA events on the context stream"}, built
 
 
 def gpu_path(lrs, precision, stream, wl, sites, pmode):
@@ -948,11 +975,11 @@ def run_ours(args):
                  "mixed_vs_plain": {"chi0": errors(chi_mixed, chi_plain), "w": errors(w_mixed, w_plain),
                                     "w_minus_v": errors(w_mixed - v_lib, w_plain - v_lib)}}
 
-    backward = None
+    backward, config1 = None, None
     if rank == 0 and not args.no_backward:
         backward = {"workload": args.workload, "precision": args.precision,
                     **backward_leg(lrs, scr, stream, s, K, nf, peaks, args.precision, real)}
-        backward["differentiation_260"] = config4_backward(lrs, stream)
+        backward["differentiation_260"], config1 = config4_backward(lrs, stream)
     scr.close()
 
     workloads = None
@@ -971,7 +998,7 @@ def run_ours(args):
     if rank == 0:
         cpu, acc = None, None
         if not args.no_cpu_baseline:
-            cpu, acc = oracle_single_site_leg(wl, results)
+            cpu, acc = oracle_single_site_leg(wl, results, config1)
         line = {
             "metric": "site chi0+W builds/s", "value": value, "unit": "builds/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

@@ -131,3 +131,23 @@ def test_bench_line_is_strict_json():
     line = {"value": 1.0, "a": {"b": [float("nan"), 2.0, float("inf")]}, "c": None}
     out = json.loads(json.dumps(bench.strict_json(line), allow_nan=False))
     assert out == {"value": 1.0, "a": {"b": [None, 2.0, None]}, "c": None}
+
+
+def test_config1_against_both_kernels():
+    """The bench's report of the 260-point plain build against the pair-sum oracle: fed the
+    oracle's own kappa_N build it reads zero against kappa_N and the quadrature error (about
+    4e-8 at 12 frequencies) against kappa_exact."""
+    import bench
+    from oracle import chi0 as ochi0, coulomb as ocoul, dyson as odys, projection as oproj, quadrature as oquad
+    from paper_2005_07834_gb300 import synth
+    wl = synth.single_site_260()
+    o, s = wl.orbitals, wl.sites[0]
+    psi = oproj.project_direct(o.cell, o.kpts, o.gvec, o.coeff, s.center, s.pts)
+    po, pu, eo, eu, wo, wu = oproj.split_occupied(psi, o.energies, o.nocc, o.kweights)
+    mu = oquad.chemical_potential_midgap(o.energies, o.nocc)
+    t, W = oquad.frequency_grid(wl.nfreq, oquad.zeta_rule(o.energies, mu))
+    v = ocoul.coulomb_multipole(s.pts, s.lmax)
+    c = ochi0.chi0_pairs(po, pu, eo, eu, wo, wu, mu, t, W)
+    out = bench.config1_vs_kappa((c, odys.screened_interaction(v, c, s.wts), v))
+    assert out["vs_kappa_N"]["chi0"]["fro"] < 1e-14 and out["vs_kappa_N"]["w"]["fro"] < 1e-14
+    assert 1e-9 < out["vs_kappa_exact"]["chi0"]["fro"] < 1e-6
