@@ -82,6 +82,10 @@ MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"): 28.5e6,
                  ("single-site-3520", "r4"): 28.52e6, ("single-site-3520", "r5"): 28.52e6,
                  ("single-site-3520", "r6"): 28.51e6}
+# Multi-site workloads (launches of many sizes): DRAM bytes per rewritten element of one ncu capture
+# on the workload's largest site (r = 6768, block 100: 187.27 MB read + 119.26 MB written for
+# 22,475,160 elements), applied to the average launch; valid only for the revision named.
+DYSON_TRAFFIC_PER_ELEMENT = {("batched-64-sites", "r6"): (187.27e6 + 119.26e6) / 22475160}
 
 
 def dyson_roofline(st, workload=None, version=None, hbm_gbs=None, bf16_tflops=None):
@@ -100,8 +104,15 @@ def dyson_roofline(st, workload=None, version=None, hbm_gbs=None, bf16_tflops=No
     fp64_eq = st["flop_w_main"] / (ms * 1e-3) / 1e12
     elems = st.get("w_main_elements") or st["flop_w_main"] / (2.0 * 32)
     kb = st["flop_w_main"] / (2.0 * elems)
+    traffic = DYSON_TRAFFIC.get((workload, version))
+    per_elem = DYSON_TRAFFIC_PER_ELEMENT.get((workload, version))
+    if traffic is None and per_elem is not None:
+        traffic = per_elem * elems / st["w_main_launches"]
     common = {"launches": st["w_main_launches"], "avg_launch_us": 1e3 * ms / st["w_main_launches"],
-              "pivot_block": round(kb), "traffic": DYSON_TRAFFIC.get((workload, version))}
+              "pivot_block": round(kb), "traffic": traffic}
+    if per_elem is not None and (workload, version) not in DYSON_TRAFFIC:
+        common["traffic_source"] = ("ncu DRAM bytes per rewritten element on the workload's largest site "
+                                    f"({per_elem:.2f} B), times the average launch's elements")
     algo_bytes = 16.0 * elems
     if tc and kb > 64 and bf16_tflops:
         issued = 36 * 2.0 * kb * elems

@@ -151,3 +151,16 @@ def test_config1_against_both_kernels():
     out = bench.config1_vs_kappa((c, odys.screened_interaction(v, c, s.wts), v))
     assert out["vs_kappa_N"]["chi0"]["fro"] < 1e-14 and out["vs_kappa_N"]["w"]["fro"] < 1e-14
     assert 1e-9 < out["vs_kappa_exact"]["chi0"]["fro"] < 1e-6
+
+
+def test_multisite_update_traffic_from_bytes_per_element():
+    """For the 64-site workload the update's DRAM traffic is the measured bytes per rewritten
+    element of the largest site's capture times the average launch's elements."""
+    import bench
+    per = bench.DYSON_TRAFFIC_PER_ELEMENT[("batched-64-sites", "r6")]
+    st = {"w_main_launches": 4, "ms_w_main": 0.4, "flop_w_main": 2.0 * 32 * 8.0e6,
+          "w_main_elements": 8.0e6, "dyson_update_tc": True}
+    r = bench.dyson_roofline(st, "batched-64-sites", "r6", 6758.5, 1871.0)
+    assert abs(r["traffic"] - per * 2.0e6) < 1.0 and "traffic_source" in r
+    assert 13.0 < per < 14.0
+    assert bench.dyson_roofline(st, "batched-64-sites", "r5", 6758.5, 1871.0)["traffic"] is None
