@@ -156,23 +156,25 @@ __global__ void chi0_prep_kernel(const double2* __restrict__ psi_o, int Ko, cons
 // chi0 = (2/pi) sum_f W_f (X_f + X_f^T) / (scales[f] scales[nf])^2, float64 accumulation.
 // The result is symmetric: one CTA per pair of 32 x 32 tiles (bi <= bj) reads tiles (bi, bj) and
 // (bj, bi) of every frequency once, accumulates their symmetric sum once and writes both output
-// tiles (the transposed one through shared memory), so that each slab element is read once and
-// each float64 accumulation is done once.  With sym, X_f is itself symmetric (real orbitals:
-// both Green's functions are symmetric in r, r') and only the tiles reaching its lower triangle
-// were computed: X_f + X_f^T = 2 X_f is read from the lower element of each pair (the tile
-// (bj, bi), and within a diagonal tile whichever of the two elements lies on or below the
-// diagonal), so that chi0 comes out exactly symmetric.
+// tiles through shared memory (coalesced rows), so that each slab element is read once and each
+// float64 accumulation is done once.  The slabs are in the chi0 kernel's layout (slab_index:
+// 128-row bands stored as [column / 4][row][4]); thread (w, lane) reads row lane of a block as
+// the float4 of columns 4 w .. 4 w + 3, so that a warp reads 512 consecutive bytes.  With sym,
+// X_f is itself symmetric (real orbitals: both Green's functions are symmetric in r, r') and only
+// the tiles reaching its lower triangle were computed: X_f + X_f^T = 2 X_f is read from the lower
+// element of each pair (the tile (bj, bi), and within a diagonal tile whichever of the two
+// elements lies on or below the diagonal), so that chi0 comes out exactly symmetric.
 __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restrict__ slab, int Np, int nf,
                                                           const double* __restrict__ Wf,
                                                           const float* __restrict__ scales, int n, int sym,
                                                           double* __restrict__ chi0) {
   constexpr int FB = 4;          // frequencies per pair of barriers: all their tiles in flight at once
-  __shared__ float t[FB][32][33];
+  __shared__ float tb[FB][32][33];   // tb[h][a][b] = X_f(c0 + b, r0 + a) of frequency f + h
   __shared__ double o[32][33];
   __shared__ double wsm[128];   // per-frequency weights W_f / (scales[f] scales[nf])^2 (x 2 with sym)
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bi > bj) return;
-  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8: lane, and the column group of 4
   const int tid = ty * 32 + tx;
   const int r0 = bi * 32, c0 = bj * 32;
   for (int f = tid; f < nf; f += 256) {
@@ -183,45 +185,51 @@ __global__ void __launch_bounds__(256) chi0_reduce_kernel(const float* __restric
     }
     wsm[f] = sym ? 2.0 * w : w;
   }
+  // this thread's outputs: row R = r0 + tx, columns q = c0 + 4 ty + j
+  const bool need_direct = !(sym && bi != bj);
+  const size_t off_direct = slab_index(Np, r0 + tx, c0 + 4 * ty);
+  const size_t off_trans = slab_index(Np, c0 + tx, r0 + 4 * ty);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int f = 0; f < nf; f += FB) {
     const int nb = min(FB, nf - f);
-    float direct[FB][4];
+    float4 direct[FB];
 #pragma unroll
     for (int h = 0; h < FB; ++h) {
       if (h >= nb) break;
       const float* s = slab + (size_t)(f + h) * Np * Np;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        t[h][ty + 8 * i][tx] = s[(size_t)(c0 + ty + 8 * i) * Np + r0 + tx];
-        direct[h][i] = (sym && bi != bj) ? 0.f : s[(size_t)(r0 + ty + 8 * i) * Np + c0 + tx];
-      }
+      const float4 tv = *reinterpret_cast<const float4*>(s + off_trans);   // X(c0 + tx, r0 + 4 ty + j)
+      tb[h][4 * ty + 0][tx] = tv.x;
+      tb[h][4 * ty + 1][tx] = tv.y;
+      tb[h][4 * ty + 2][tx] = tv.z;
+      tb[h][4 * ty + 3][tx] = tv.w;
+      direct[h] = need_direct ? *reinterpret_cast<const float4*>(s + off_direct) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll
     for (int h = 0; h < FB; ++h) {
       if (h >= nb) break;
       const double w = wsm[f + h];
+      const float d[4] = {direct[h].x, direct[h].y, direct[h].z, direct[h].w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        // output element (r, q) = (r0 + ty + 8 i, c0 + tx); t holds X_f(q, r), direct X_f(r, q)
-        const float tq = t[h][tx][ty + 8 * i];
-        const float v = sym ? ((c0 + tx >= r0 + ty + 8 * i) ? tq : direct[h][i]) : direct[h][i] + tq;
-        acc[i] = fma(w, f32_to_f64_exact(v), acc[i]);
+      for (int j = 0; j < 4; ++j) {
+        // output (R, q) = (r0 + tx, c0 + 4 ty + j): tb holds X_f(q, R), d X_f(R, q)
+        const float tq = tb[h][tx][4 * ty + j];
+        const float v = sym ? ((c0 + 4 * ty + j >= r0 + tx) ? tq : d[j]) : d[j] + tq;
+        acc[j] = fma(w, f32_to_f64_exact(v), acc[j]);
       }
     }
     __syncthreads();
   }
   const double c = 0.63661977236758134308;   // 2/pi
 #pragma unroll
+  for (int j = 0; j < 4; ++j) o[tx][4 * ty + j] = c * acc[j];
+  __syncthreads();
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = r0 + ty + 8 * i, q = c0 + tx;
-    const double v = c * acc[i];
-    if (r < n && q < n) chi0[(size_t)r * n + q] = v;
-    o[ty + 8 * i][tx] = v;
+    if (r < n && q < n) chi0[(size_t)r * n + q] = o[ty + 8 * i][tx];
   }
   if (bi == bj) return;
-  __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = c0 + ty + 8 * i, q = r0 + tx;   // output tile (bj, bi): element (q', r') of o transposed

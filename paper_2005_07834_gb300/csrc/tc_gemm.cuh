@@ -505,8 +505,25 @@ int launch_tc(lrs_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const 
   return after_launch(ctx, name);
 }
 
+// Index of element (row, col) in one frequency's fp32 slab of a site padded to Np (a multiple of
+// 128): each 128-row band is stored as [col / 4][row % 128][4], so that a warp writing (or
+// reading) one float4 of columns for 32 consecutive rows covers 512 consecutive bytes.
+__host__ __device__ __forceinline__ size_t slab_index(int Np, int row, int col) {
+  return (size_t)(row >> 7) * 128 * Np + (size_t)(col >> 2) * 512 + (size_t)(row & 127) * 4 + (col & 3);
+}
+
 // ---------------------------------------------------------------- epilogue stores
-// chi0: X = Re[Go o Gu^T] of one frequency into its fp32 slab.
+// Slot of a parked value in a CTA's scratch ([2][128][2 COLS] floats): the 256 epilogue threads
+// (row lrow of the tile, column half lcol0 / COLS) keep their float4 chunks interleaved, chunk c
+// of part p of thread t at ((p COLS / 4 + c) 256 + t) float4s, so that a warp's 32 lanes touch
+// 512 consecutive bytes per access; each thread reads back only what it wrote.
+template <int COLS>
+__device__ __forceinline__ float* park_slot(float* scratch, int lrow, int lcol0, int part, int i) {
+  const int t = lrow + (lcol0 / COLS) * 128;
+  return scratch + (size_t)blockIdx.x * 2 * 128 * (2 * COLS) +
+         ((size_t)(part * (COLS / 4) + (i >> 2)) * 256 + t) * 4;
+}
+// chi0: X = Re[Go o Gu^T] of one frequency into its fp32 slab (layout of slab_index).
 // The occupied sums Go of a unit are parked in `scratch` (per CTA
 // [2][128][tile_n] fp32, L2 resident) while the unoccupied sums accumulate in
 // registers; each thread reads back only what it wrote.
@@ -518,7 +535,7 @@ struct Chi0Store {
   // Short K: both contractions of 16 columns of this thread's row, read straight from TMEM.
   __device__ void store_direct16(const float (&gr)[16], const float (&gi)[16], const float (&ur)[16],
                                  const float (&ui)[16], const Unit& x, int row, int col) const {
-    float* dst = slab + x.slab0 + ((size_t)x.b * x.ld + row) * x.ld + col;
+    float* plane = slab + x.slab0 + (size_t)x.b * x.ld * x.ld;
 #pragma unroll
     for (int i = 0; i < 16; i += 4) {
       float4 v;
@@ -526,33 +543,31 @@ struct Chi0Store {
       v.y = fmaf(-gi[i + 1], ui[i + 1], gr[i + 1] * ur[i + 1]);
       v.z = fmaf(-gi[i + 2], ui[i + 2], gr[i + 2] * ur[i + 2]);
       v.w = fmaf(-gi[i + 3], ui[i + 3], gr[i + 3] * ur[i + 3]);
-      *reinterpret_cast<float4*>(dst + i) = v;
+      *reinterpret_cast<float4*>(plane + slab_index(x.ld, row, col + i)) = v;
     }
   }
   template <int COLS>
   __device__ void save_phase0(const float (&s)[2][COLS], int lrow, int lcol0) const {
-    float* base = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
 #pragma unroll
     for (int part = 0; part < 2; ++part)
 #pragma unroll
       for (int i = 0; i < COLS; i += 4)
-        *reinterpret_cast<float4*>(base + (size_t)part * 128 * tile_n + i) =
+        *reinterpret_cast<float4*>(park_slot<COLS>(scratch, lrow, lcol0, part, i)) =
             make_float4(s[part][i], s[part][i + 1], s[part][i + 2], s[part][i + 3]);
   }
   template <int COLS>
   __device__ void store(const float (&s)[2][COLS], const Unit& x, int row, int lrow, int col0, int lcol0) const {
-    const float* go = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
-    float* dst = slab + x.slab0 + ((size_t)x.b * x.ld + row) * x.ld + col0;
+    float* plane = slab + x.slab0 + (size_t)x.b * x.ld * x.ld;
 #pragma unroll
     for (int i = 0; i < COLS; i += 4) {
-      const float4 r = *reinterpret_cast<const float4*>(go + i);
-      const float4 m = *reinterpret_cast<const float4*>(go + (size_t)128 * tile_n + i);
+      const float4 r = *reinterpret_cast<const float4*>(park_slot<COLS>(scratch, lrow, lcol0, 0, i));
+      const float4 m = *reinterpret_cast<const float4*>(park_slot<COLS>(scratch, lrow, lcol0, 1, i));
       float4 v;
       v.x = fmaf(-m.x, s[1][i + 0], r.x * s[0][i + 0]);
       v.y = fmaf(-m.y, s[1][i + 1], r.y * s[0][i + 1]);
       v.z = fmaf(-m.z, s[1][i + 2], r.z * s[0][i + 2]);
       v.w = fmaf(-m.w, s[1][i + 3], r.w * s[0][i + 3]);
-      *reinterpret_cast<float4*>(dst + i) = v;
+      *reinterpret_cast<float4*>(plane + slab_index(x.ld, row, col0 + i)) = v;
     }
   }
 };
@@ -569,23 +584,23 @@ struct GStore {
   int tile_n;
   template <int COLS>
   __device__ void save_phase0(const float (&s)[2][COLS], int lrow, int lcol0) const {
-    float* base = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
 #pragma unroll
     for (int part = 0; part < 2; ++part)
 #pragma unroll
       for (int i = 0; i < COLS; i += 4)
-        *reinterpret_cast<float4*>(base + (size_t)part * 128 * tile_n + i) =
+        *reinterpret_cast<float4*>(park_slot<COLS>(scratch, lrow, lcol0, part, i)) =
             make_float4(s[part][i], s[part][i + 1], s[part][i + 2], s[part][i + 3]);
   }
   template <int COLS>
   __device__ void store(const float (&s)[2][COLS], const Unit& x, int row, int lrow, int col0, int lcol0) const {
-    const float* g0 = scratch + (size_t)blockIdx.x * 2 * 128 * tile_n + (size_t)lrow * tile_n + lcol0;
     float2* po = go + x.slab0 + (size_t)row * x.ld + col0;
     float2* pu = gu + x.slab0 + (size_t)row * x.ld + col0;
 #pragma unroll
     for (int i = 0; i < COLS; i += 2) {
-      const float2 r = *reinterpret_cast<const float2*>(g0 + i);
-      const float2 m = *reinterpret_cast<const float2*>(g0 + (size_t)128 * tile_n + i);
+      const float* g0 = park_slot<COLS>(scratch, lrow, lcol0, 0, i & ~3) + (i & 3);
+      const float* g1 = park_slot<COLS>(scratch, lrow, lcol0, 1, i & ~3) + (i & 3);
+      const float2 r = *reinterpret_cast<const float2*>(g0);
+      const float2 m = *reinterpret_cast<const float2*>(g1);
       *reinterpret_cast<float4*>(po + i) = make_float4(r.x, m.x, r.y, m.y);
       *reinterpret_cast<float4*>(pu + i) = make_float4(s[0][i], s[1][i], s[0][i + 1], s[1][i + 1]);
     }
