@@ -16,9 +16,18 @@
 // runs at tensor-core speed instead of the 2 DFMA per SM per clock of the
 // float64 pipe.
 //
-// Tiles of 128 x 64 elements of the lower triangle; elements in the rows or
-// columns of the excluded pivot blocks (the side stream of the SPD inverse
-// updates those) are left untouched.
+// Tiles of 64 rows x 128 columns of C, transposed on the tensor cores: the MMA's M
+// side (the 128 TMEM lanes) runs along the columns j (rows of E) and its N side (64
+// TMEM columns per level) along the rows i (rows of D).  A warp's 32 lanes then hold
+// 32 consecutive columns of one row of the row-major C and read and write it in
+// 256-byte lines, with no staging of the result.  Every level accumulator starts with
+// one product of constant tiles (1.0 times 1.5 2^19 over K = 16), so it holds the level
+// sum plus 1.5 2^23 and its bits are read directly as a biased integer.  The epilogue
+// packs the seven levels of its elements into 64-bit integers and releases TMEM before
+// rounding them, so the next tile's MMAs run under the rounding and the float64
+// subtractions.  Elements in the rows or columns of the excluded pivot blocks (the
+// side stream of the SPD inverse updates those) and above the diagonal are left
+// untouched.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -34,54 +43,122 @@ using namespace tc;
 constexpr int OZ_SLICES = OZ_SLICE_COUNT;
 constexpr int OZ_PLANES = OZ_PLANE_COUNT;      // two slices per 128-byte row (the last half of plane 3 is zero)
 constexpr int OZ_LEVELS = 7;                   // t + u = 2 .. 8
-constexpr int OZ_TM = 128, OZ_TN = 64;
-constexpr int OZ_A_PLANE = OZ_TM * 128;        // bytes of one A plane tile
-constexpr int OZ_B_PLANE = OZ_TN * 128;
+constexpr int OZ_TJ = 128, OZ_TI = 64;         // columns (MMA M, TMEM lanes) and rows (MMA N) of a tile
+constexpr int OZ_A_PLANE = OZ_TJ * 128;        // bytes of one E plane tile (the A operand)
+constexpr int OZ_B_PLANE = OZ_TI * 128;        // bytes of one D plane tile (the B operand)
 constexpr int OZ_STAGE = OZ_PLANES * (OZ_A_PLANE + OZ_B_PLANE);
-constexpr int OZ_STAGES = 1;
-constexpr int OZ_EPI_WARPS = 16;               // four per TMEM lane quarter, 16 columns each
-constexpr int OZ_EPI_COLS = OZ_TN / (OZ_EPI_WARPS / 4);
-constexpr int OZ_STG_LD = OZ_EPI_COLS + 1;      // padded row of a warp's staging tile
-constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * 32 * OZ_STG_LD * 8;   // per-warp [32][17] float64 staging of C
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + OZ_STAGE_EPI + 1024;
+constexpr int OZ_BIAS = OZ_A_PLANE + OZ_B_PLANE;   // the constant tiles of the bias product
+constexpr int OZ_EPI_WARPS = 16;               // four per TMEM lane quarter
+constexpr int OZ_EPI_ROWS = OZ_TI / (OZ_EPI_WARPS / 4);   // 16 rows of C per warp
+constexpr int OZ_HALF = OZ_EPI_ROWS / 2;       // C is fetched in two halves of 8 rows
+constexpr int OZ_STAGE_EPI = OZ_EPI_WARPS * OZ_EPI_ROWS * 32 * 8;   // per-warp [16][32] float64 copy of C
+constexpr int OZ_SMEM = OZ_STAGE + OZ_BIAS + OZ_STAGE_EPI + 1024;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;   // producer, MMA issuer, epilogue warps
 constexpr int OZ_TMEM_COLS = 512;              // 7 levels x 64 columns used
+constexpr uint32_t OZ_BF16_ONE2 = 0x3F803F80u;     // two bf16 1.0
+constexpr uint32_t OZ_BF16_BIAS2 = 0x49404940u;    // two bf16 1.5 2^19 (16 of them sum to 1.5 2^23)
 
 struct OzUpdate {
   double* C;
   int n, ldc;
-  const int* ed;        // row exponents of D (output rows)
-  const int* ee;        // row exponents of E (output columns)
+  const int* ed;        // row exponents of D (rows i of C)
+  const int* ee;        // row exponents of E (columns j of C)
   int x0, x1;           // rows / columns in [x0, x1) are left to the side stream
-  int row_tiles, col_tiles;
-  int a_plane_rows, b_plane_rows;   // padded rows of one plane (row offset between planes)
+  int ti_tiles, tj_tiles;             // tiles of 64 rows, of 128 columns
+  int d_plane_rows, e_plane_rows;     // padded rows of one plane (row offset between planes)
 };
 
-__device__ __forceinline__ bool oz_decode(const OzUpdate& p, int u, int& bi, int& bj) {
-  bi = u / p.col_tiles;
-  bj = u % p.col_tiles;
-  return bj * OZ_TN <= bi * OZ_TM + OZ_TM - 1;   // tile reaches the lower triangle
+__device__ __forceinline__ bool oz_decode(const OzUpdate& p, int u, int& ti, int& tj) {
+  ti = u / p.tj_tiles;
+  tj = u % p.tj_tiles;
+  return tj * OZ_TJ <= ti * OZ_TI + OZ_TI - 1;   // the tile reaches the lower triangle
+}
+
+// The first unit at or after u, stepping by the grid, whose tile reaches the lower
+// triangle; `units` when none is left.
+__device__ __forceinline__ int oz_next(const OzUpdate& p, int u, int units, int& ti, int& tj) {
+  for (; u < units; u += gridDim.x)
+    if (oz_decode(p, u, ti, tj)) return u;
+  return units;
+}
+
+// An epilogue warp's share of a tile: its lane's column j, the first of its 16 rows, and
+// which rows this lane's element takes (inside the matrix, outside the pivot blocks, on
+// or below the diagonal).  Warp-collective (a ballot).
+struct OzRows {
+  double* at;          // C at (row i0, column j); dereferenced only where `take` says so
+  int i0, j;
+  unsigned take;       // bit c: row i0 + c
+};
+
+__device__ __forceinline__ OzRows oz_rows(const OzUpdate& p, int ti, int tj, int quarter, int cg, int lane) {
+  OzRows r;
+  r.i0 = ti * OZ_TI + cg * OZ_EPI_ROWS;
+  r.j = tj * OZ_TJ + quarter * 32 + lane;
+  const int i = r.i0 + lane;
+  const unsigned rows_in =
+      __ballot_sync(0xffffffffu, lane < OZ_EPI_ROWS && i < p.n && !(i >= p.x0 && i < p.x1)) & 0xFFFFu;
+  const int rmin = r.j - r.i0;   // rows c >= rmin are on or below the diagonal
+  const unsigned lower = rmin <= 0 ? 0xFFFFu : (rmin >= OZ_EPI_ROWS ? 0u : ((0xFFFFu << rmin) & 0xFFFFu));
+  const bool col_ok = r.j < p.n && !(r.j >= p.x0 && r.j < p.x1);
+  r.take = col_ok ? (rows_in & lower) : 0u;
+  r.at = p.C + ((size_t)r.i0 * p.ldc + r.j);
+  return r;
+}
+
+// Copies rows [8H, 8H + 8) of the warp's share of C into its stage (one copy group).
+template <int H>
+__device__ __forceinline__ void oz_fetch(const OzRows& r, int ldc, uint32_t stg_s, int lane) {
+#pragma unroll
+  for (int c = H * OZ_HALF; c < (H + 1) * OZ_HALF; ++c)
+    if ((r.take >> c) & 1u) cp_async8(stg_s + (uint32_t)(c * 32 + lane) * 8u, r.at + (size_t)c * ldc);
+  cp_async_commit();
+}
+
+// C - 2^(e_i + f_j - 56) V for rows [8H, 8H + 8): rounds each V to float64, subtracts it
+// from the staged C and writes the row back.  Returns the rows whose product leaves the
+// directly assembled exponent range (left unwritten here).
+template <int H>
+__device__ __forceinline__ unsigned oz_finish(const OzRows& r, int ldc, const double* stg,
+                                              const long long (&V)[OZ_EPI_ROWS], int ei_lane, int fjm, int lane) {
+  unsigned bad = 0u;
+#pragma unroll
+  for (int c = H * OZ_HALF; c < (H + 1) * OZ_HALF; ++c) {
+    const int k = __shfl_sync(0xffffffffu, ei_lane, c) + fjm;
+    bool ok;
+    const double prod = oz_round_pow2(V[c], k, ok);
+    const double x = stg[c * 32 + lane];   // stale where this lane's element is not taken
+    if ((r.take >> c) & 1u) {
+      if (ok) r.at[(size_t)c * ldc] = x - prod;
+      else bad |= 1u << c;
+    }
+  }
+  return bad;
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_update_kernel(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmE,
                      const OzUpdate p, int* status) {
-  __shared__ __align__(8) uint64_t full_bar[OZ_STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[OZ_STAGES];
+  __shared__ __align__(8) uint64_t full_bar;
+  __shared__ __align__(8) uint64_t empty_bar;
   __shared__ __align__(8) uint64_t accf_bar;
   __shared__ __align__(8) uint64_t acce_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   extern __shared__ uint8_t oz_smem_raw[];
   const uint32_t smem_base = (smem_u32(oz_smem_raw) + 1023u) & ~1023u;
+  uint8_t* const smem = oz_smem_raw + (smem_base - smem_u32(oz_smem_raw));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int units = p.row_tiles * p.col_tiles;
+  const int units = p.ti_tiles * p.tj_tiles;
 
+  // the constant tiles of the bias product, written once and handed to the tensor cores
+  uint32_t* const bias_w = reinterpret_cast<uint32_t*>(smem + OZ_STAGE);
+  for (int w = threadIdx.x; w < OZ_BIAS / 4; w += blockDim.x)
+    bias_w[w] = w < OZ_A_PLANE / 4 ? OZ_BF16_ONE2 : OZ_BF16_BIAS2;
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < OZ_STAGES; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
+    mbar_init(&full_bar, 1);
+    mbar_init(&empty_bar, 1);
     mbar_init(&accf_bar, 1);
     mbar_init(&acce_bar, OZ_EPI_WARPS);
     abort_flag = 0;
@@ -103,114 +180,92 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------ TMA producer: all slice planes of a tile
     if (lane == 0) {
-      int stage = 0;
       uint32_t phase = 0;
-      for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        int bi, bj;
-        if (!oz_decode(p, u, bi, bj)) continue;
-        if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) {
+      int ti, tj;
+      for (int u = oz_next(p, blockIdx.x, units, ti, tj); u < units; u = oz_next(p, u + gridDim.x, units, ti, tj)) {
+        if (!mbar_wait(&empty_bar, phase ^ 1u, &abort_flag)) {
           abort_flag = 1;
           atomicCAS(status, 0, TC_TIMEOUT_PRODUCER);
           break;
         }
-        mbar_arrive_expect_tx(&full_bar[stage], OZ_STAGE);
-        const uint32_t s = smem_base + stage * OZ_STAGE;
+        mbar_arrive_expect_tx(&full_bar, OZ_STAGE);
         for (int q = 0; q < OZ_PLANES; ++q) {
-          tma_load_2d(s + q * OZ_A_PLANE, &tmD, &full_bar[stage], 0, q * p.a_plane_rows + bi * OZ_TM);
-          tma_load_2d(s + OZ_PLANES * OZ_A_PLANE + q * OZ_B_PLANE, &tmE, &full_bar[stage], 0,
-                      q * p.b_plane_rows + bj * OZ_TN);
+          tma_load_2d(smem_base + q * OZ_A_PLANE, &tmE, &full_bar, 0, q * p.e_plane_rows + tj * OZ_TJ);
+          tma_load_2d(smem_base + OZ_PLANES * OZ_A_PLANE + q * OZ_B_PLANE, &tmD, &full_bar, 0,
+                      q * p.d_plane_rows + ti * OZ_TI);
         }
-        if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
+        phase ^= 1u;
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------ MMA issue: 28 slice pairs x 2 K16 steps
+    // ------------------------------------------------ MMA issue: 7 bias products, then 28 slice pairs x 2 K16 steps
     if (lane == 0) {
-      constexpr uint32_t ID = idesc_f16(OZ_TM, OZ_TN, 1, false);
-      int stage = 0;
+      constexpr uint32_t ID = idesc_f16(OZ_TJ, OZ_TI, 1, false);
+      const uint32_t sa = smem_base, sb = smem_base + OZ_PLANES * OZ_A_PLANE;
+      const uint64_t bias_a = sw128_desc(smem_base + OZ_STAGE), bias_b = sw128_desc(smem_base + OZ_STAGE + OZ_A_PLANE);
       uint32_t phase = 0, acc_phase = 0;
-      for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        int bi, bj;
-        if (!oz_decode(p, u, bi, bj)) continue;
-        if (!mbar_wait(&acce_bar, acc_phase ^ 1u, &abort_flag) || !mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+      int ti, tj;
+      for (int u = oz_next(p, blockIdx.x, units, ti, tj); u < units; u = oz_next(p, u + gridDim.x, units, ti, tj)) {
+        if (!mbar_wait(&acce_bar, acc_phase ^ 1u, &abort_flag) || !mbar_wait(&full_bar, phase, &abort_flag)) {
           abort_flag = 1;
           atomicCAS(status, 0, TC_TIMEOUT_MMA);
           break;
         }
         tc_fence_after();
-        const uint32_t s = smem_base + stage * OZ_STAGE;
-        const uint32_t sa = s, sb = s + OZ_PLANES * OZ_A_PLANE;
+#pragma unroll
+        for (int L = 0; L < OZ_LEVELS; ++L) mma_f16(tbase + L * OZ_TI, bias_a, bias_b, ID, 0u);
 #pragma unroll
         for (int t = 0; t < OZ_SLICES; ++t) {
 #pragma unroll
           for (int v = 0; v < OZ_SLICES; ++v) {
             if (t + v > OZ_SLICES - 1) continue;                 // keep t + u <= 8 (1-based)
-            const uint32_t d = tbase + (t + v) * OZ_TN;
+            const uint32_t d = tbase + (t + v) * OZ_TI;
             const uint32_t ao = sa + (t >> 1) * OZ_A_PLANE + (t & 1) * 64;
             const uint32_t bo = sb + (v >> 1) * OZ_B_PLANE + (v & 1) * 64;
-            // pairs are issued t-major, so (0, level) is the first product into each level
-            const uint32_t first = (t == 0) ? 0u : 1u;
-            mma_f16(d, sw128_desc(ao), sw128_desc(bo), ID, first);
+            mma_f16(d, sw128_desc(ao), sw128_desc(bo), ID, 1u);
             mma_f16(d, sw128_desc(ao + 32), sw128_desc(bo + 32), ID, 1u);
           }
         }
-        mma_commit(&empty_bar[stage]);
+        mma_commit(&empty_bar);
         mma_commit(&accf_bar);
-        if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
+        phase ^= 1u;
         acc_phase ^= 1u;
       }
     }
   } else {
     // ------------------------------------------------ epilogue: combine the levels, C -= D E^T
-    // Each warp owns 32 rows (its TMEM lane quarter) x 16 columns of the tile.  Its
-    // share of C is copied into a [32][17] shared-memory stage (cp.async) before the
-    // accumulators are ready, so the memory latency overlaps the MMAs.  Level sums S_L
-    // (integers of magnitude below 2^22 in fp32, read as int32 by one fp32 add each)
-    // are combined into one 64-bit integer in units of 2^-56 of the scaled product,
+    // Each warp owns 32 columns (its TMEM lane quarter) x 16 rows of the tile.  Its share
+    // of C is copied into a [16][32] stage in two halves of 8 rows, each half of the next
+    // tile as soon as this tile's half has been consumed, so the copies run under the
+    // MMAs and the rounding.  The biased level sums b_L = S_L + 1.5 2^23 are combined
+    // into one 64-bit integer in units of 2^-56 of the scaled product,
     //   V = S_0 2^40 + S_1 2^32 + S_2 2^24 + S_3 2^16 + S_4 2^8 + S_5 + floor(S_6 / 2^8)
-    // (|V| < 2^60; the floor drops less than 2^-56 of the row scales' product), so
-    // the product is 2^(e_i + f_j - 56) V, rounded to float64 with integer
-    // instructions and subtracted from the staged C (the only float64 operation per
-    // element).  TMEM is then released to the next tile's MMAs, and the stage is
-    // written back, two rows of 16 columns per instruction.
+    // (|V| < 2^60; the floor drops less than 2^-56 of the row scales' product), after
+    // which TMEM goes back to the MMAs.  The product 2^(e_i + f_j - 56) V is rounded to
+    // float64 with integer instructions and subtracted from C (the only float64
+    // operation per element).
     const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int cg = ew >> 2;                      // column group of 16
+    const int cg = ew >> 2;                      // group of 16 rows
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-    double* stg = reinterpret_cast<double*>(oz_smem_raw + (smem_base - smem_u32(oz_smem_raw)) +
-                                            OZ_STAGES * OZ_STAGE) + ew * 32 * OZ_STG_LD;
-    const uint32_t stg_s = smem_u32(stg);
-    const int wc = lane & 15, wr = lane >> 4;    // this lane's column and row parity when C moves
+    const double* stg = reinterpret_cast<const double*>(smem + OZ_STAGE + OZ_BIAS) + ew * OZ_EPI_ROWS * 32;
+    const uint32_t stg_s = smem_base + OZ_STAGE + OZ_BIAS + ew * OZ_EPI_ROWS * 32 * 8;
     uint32_t acc_phase = 0;
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
-      int bi, bj;
-      if (!oz_decode(p, u, bi, bj)) continue;
-      const int row0 = bi * OZ_TM + quarter * 32;
-      const int col0 = bj * OZ_TN + cg * OZ_EPI_COLS;
-      const int j = col0 + wc;
-      const bool col_ok = j < p.n && !(j >= p.x0 && j < p.x1);
-      // rows r of this warp's 32 that this lane's column takes: inside the matrix, outside the
-      // pivot blocks [x0, x1), and on or below the diagonal (row0 + r >= j)
-      const int my_i = row0 + lane;
-      const unsigned rows_in = __ballot_sync(0xffffffffu, my_i < p.n && !(my_i >= p.x0 && my_i < p.x1));
-      const int rmin = j - row0;
-      const unsigned lower = rmin <= 0 ? 0xffffffffu : (rmin >= 32 ? 0u : (0xffffffffu << rmin));
-      const unsigned take = col_ok ? (rows_in & lower) : 0u;
-#pragma unroll 4
-      for (int r = wr; r < 32; r += 2) {
-        if ((take >> r) & 1u)
-          cp_async8(stg_s + (uint32_t)(r * OZ_STG_LD + wc) * 8u, p.C + (size_t)(row0 + r) * p.ldc + j);
-      }
-      cp_async_commit();
-      // the row scale of this lane's TMEM row and the column scales of the 16 columns
-      const int my_row = row0 + lane;
-      const int ei = my_row < p.n ? p.ed[my_row] : 0;
-      const int fj_lane = (col0 + wc) < p.n ? p.ee[col0 + wc] : 0;
+    int ti, tj;
+    int u = oz_next(p, blockIdx.x, units, ti, tj);
+    OzRows cur;
+    cur.take = 0u;
+    if (u < units) cur = oz_rows(p, ti, tj, quarter, cg, lane);
+    oz_fetch<0>(cur, p.ldc, stg_s, lane);
+    oz_fetch<1>(cur, p.ldc, stg_s, lane);
+    while (u < units) {
+      // the column scale of this lane and the row scales of the warp's 16 rows
+      const int fjm = (cur.j < p.n ? p.ee[cur.j] : 0) - 56;
+      const int ei_lane = (lane < OZ_EPI_ROWS && cur.i0 + lane < p.n) ? p.ed[cur.i0 + lane] : 0;
       int got = 1;
       if (lane == 0) got = mbar_wait(&accf_bar, acc_phase, &abort_flag) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) {
-        cp_async_wait_all();
         if (lane == 0) {
           abort_flag = 1;
           atomicCAS(status, 0, TC_TIMEOUT_EPILOGUE);
@@ -218,27 +273,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         break;
       }
       tc_fence_after();
-      cp_async_wait_all();
-      __syncwarp();
+      long long V[OZ_EPI_ROWS];
 #pragma unroll
-      for (int ch = 0; ch < OZ_EPI_COLS / 8; ++ch) {
-        float a[OZ_LEVELS][8];
+      for (int q = 0; q < OZ_EPI_ROWS / 4; ++q) {
+        float a[OZ_LEVELS][4];
 #pragma unroll
         for (int lv = 0; lv < OZ_LEVELS; ++lv)
-          tmem_ld8(tbase + lane_off + lv * OZ_TN + cg * OZ_EPI_COLS + ch * 8, a[lv]);
+          tmem_ld4(tbase + lane_off + lv * OZ_TI + cg * OZ_EPI_ROWS + q * 4, a[lv]);
         tmem_ld_wait();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < 4; ++c) {
           // |S_L| < 2^22: pairs of levels combine exactly in int32 before one 64-bit assembly
-          const int t3 = oz_pair<8>(oz_level_bits(a[0][c]), oz_level_bits(a[1][c]));
-          const int t2 = oz_pair<8>(oz_level_bits(a[2][c]), oz_level_bits(a[3][c]));
-          const int t1 = oz_pair<8>(oz_level_bits(a[4][c]), oz_level_bits(a[5][c])) +
-                         oz_level_shr<8>(oz_level_bits(a[6][c]));
-          const long long V = ((long long)t3 << 32) + ((long long)t2 << 16) + (long long)t1;
-          const int fj = __shfl_sync(0xffffffffu, fj_lane, ch * 8 + c);
-          double* q = stg + lane * OZ_STG_LD + ch * 8 + c;
-          // entries of the stage outside the update hold stale values and are not written back
-          *q = *q - oz_i64_times_pow2(V, ei + fj - 56);
+          const int t3 = oz_pair<8>(__float_as_uint(a[0][c]), __float_as_uint(a[1][c]));
+          const int t2 = oz_pair<8>(__float_as_uint(a[2][c]), __float_as_uint(a[3][c]));
+          const int t1 = oz_pair<8>(__float_as_uint(a[4][c]), __float_as_uint(a[5][c])) +
+                         oz_level_shr<8>(__float_as_uint(a[6][c]));
+          V[q * 4 + c] = ((long long)t3 << 32) + ((long long)t2 << 16) + (long long)t1;
         }
       }
       // the accumulators have been read: the next tile's MMAs may start
@@ -246,12 +296,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar);
       acc_phase ^= 1u;
-#pragma unroll 4
-      for (int r = wr; r < 32; r += 2) {
-        if ((take >> r) & 1u) p.C[(size_t)(row0 + r) * p.ldc + j] = stg[r * OZ_STG_LD + wc];
+      int ti2, tj2;
+      const int u2 = oz_next(p, u + gridDim.x, units, ti2, tj2);
+      OzRows nxt;
+      nxt.take = 0u;
+      if (u2 < units) nxt = oz_rows(p, ti2, tj2, quarter, cg, lane);
+      cp_async_wait_group<1>();                  // this tile's first half has landed
+      unsigned bad = oz_finish<0>(cur, p.ldc, stg, V, ei_lane, fjm, lane);
+      oz_fetch<0>(nxt, p.ldc, stg_s, lane);
+      cp_async_wait_group<1>();                  // and its second half
+      bad |= oz_finish<1>(cur, p.ldc, stg, V, ei_lane, fjm, lane);
+      oz_fetch<1>(nxt, p.ldc, stg_s, lane);
+      if (__any_sync(0xffffffffu, bad != 0u)) {
+        // products outside the directly assembled exponent range (C itself is still unwritten there)
+#pragma unroll
+        for (int c = 0; c < OZ_EPI_ROWS; ++c) {
+          const int k = __shfl_sync(0xffffffffu, ei_lane, c) + fjm;
+          if ((bad >> c) & 1u) {
+            double* q = cur.at + (size_t)c * p.ldc;
+            *q = *q - oz_i64_times_pow2_slow(V[c], k);
+          }
+        }
       }
-      __syncwarp();
+      cur = nxt;
+      u = u2;
     }
+    cp_async_wait_all();
   }
   // teardown: every role has finished or given up; wait for the others before freeing TMEM
   tc_fence_before();
@@ -270,8 +340,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
 int oz_make_maps(lrs_ctx* ctx, const uint16_t* dplanes, const uint16_t* eplanes, int rows_pad, CUtensorMap* md,
                  CUtensorMap* me) {
-  LRS_TRY(make_operand_map(md, dplanes, 64, (uint64_t)OZ_PLANES * rows_pad, OZ_TM));
-  return make_operand_map(me, eplanes, 64, (uint64_t)OZ_PLANES * rows_pad, OZ_TN);
+  LRS_TRY(make_operand_map(md, dplanes, 64, (uint64_t)OZ_PLANES * rows_pad, OZ_TI));
+  return make_operand_map(me, eplanes, 64, (uint64_t)OZ_PLANES * rows_pad, OZ_TJ);
 }
 
 int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double* C, int n, int ldc,
@@ -284,18 +354,18 @@ int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double
   p.ee = ee;
   p.x0 = x0;
   p.x1 = x1;
-  p.row_tiles = (n + OZ_TM - 1) / OZ_TM;
-  p.col_tiles = (n + OZ_TN - 1) / OZ_TN;
-  p.a_plane_rows = rows_pad;
-  p.b_plane_rows = rows_pad;
+  p.ti_tiles = (n + OZ_TI - 1) / OZ_TI;
+  p.tj_tiles = (n + OZ_TJ - 1) / OZ_TJ;
+  p.d_plane_rows = rows_pad;
+  p.e_plane_rows = rows_pad;
   if (!ctx->capturing)
     LRS_CUDA_TRY(cudaFuncSetAttribute(oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  const int grid = std::min(p.row_tiles * p.col_tiles, ctx->num_sms);
+  const int grid = std::min(p.ti_tiles * p.tj_tiles, ctx->num_sms);
   oz_update_kernel<<<grid, OZ_THREADS, OZ_SMEM, stream>>>(md, me, p, ctx->ws.status.ptr + 8);
   return after_launch(ctx, "oz_update_kernel");
 }
 
-int oz_rows_pad(int n) { return (n + OZ_TM - 1) / OZ_TM * OZ_TM; }
+int oz_rows_pad(int n) { return (n + OZ_TJ - 1) / OZ_TJ * OZ_TJ; }
 size_t oz_plane_elems(int n) { return (size_t)OZ_PLANES * oz_rows_pad(n) * 64; }
 
 }  // namespace lrs

@@ -101,4 +101,33 @@ __device__ __forceinline__ double oz_i64_times_pow2(long long v, int k) {
   return oz_i64_times_pow2_slow(v, k);
 }
 
+// The same rounding without branches, for |v| < 2^63: the leading one is found on
+// 32-bit halves (a clamped funnel shift normalises both cases), the rounding bit is
+// added after the exponent is assembled (a carry out of the fraction moves into the
+// exponent, as it should), and v = 0 gives +0.  Where the result would leave the
+// range that oz_i64_times_pow2 assembles directly, `ok` is false and the result is +0;
+// the caller then takes oz_i64_times_pow2_slow.  Where both are defined the two
+// functions return the same bits.
+__device__ __forceinline__ double oz_round_pow2(long long v, int k, bool& ok) {
+  const unsigned long long sm = (unsigned long long)(v >> 63);   // all ones when v < 0
+  const unsigned long long a = ((unsigned long long)v ^ sm) - sm;
+  const unsigned ah = (unsigned)(a >> 32), al = (unsigned)a;
+  const bool big = ah != 0u;
+  const unsigned xh = big ? ah : al, xl = big ? al : 0u;
+  const unsigned s = (unsigned)__clz((int)xh);                 // 32 when a = 0
+  const unsigned mh = __funnelshift_lc(xl, xh, s);             // a shifted to put its leading one at bit 63
+  const unsigned ml = __funnelshift_lc(0u, xl, s);
+  const unsigned nh = mh >> 11;                                // 53 bits, leading one at bit 52
+  const unsigned nl = __funnelshift_r(ml, mh, 11);
+  // ties to even: the 11 dropped bits plus the kept lowest bit carry out of 0x3FF + 0x400
+  const unsigned up = ((ml & 0x7FFu) + (nl & 1u) + 0x3FFu) >> 11;
+  const int e = (big ? 63 : 31) - (int)s + k;                  // exponent of the leading one
+  const bool in_range = (unsigned)(e + 1019) <= 2040u;          // -1020 < e < 1022
+  ok = in_range || xh == 0u;
+  const unsigned hi = ((unsigned)(e + 1022) << 20) + nh;       // the leading one adds one to the field
+  unsigned long long bits = ((((unsigned long long)hi) << 32) | nl) + up;
+  bits |= sm & 0x8000000000000000ull;
+  return __longlong_as_double((xh != 0u && in_range) ? (long long)bits : 0ll);
+}
+
 }  // namespace lrs

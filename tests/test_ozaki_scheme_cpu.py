@@ -214,3 +214,74 @@ def test_level_pairs_from_biased_bit_patterns():
             pair = as_i32(((ba << w) & m32) + bb - (((bias << w) & m32) + bias))
             assert pair == (sa << w) + sb
             assert (ba >> w) - (bias >> w) == sa >> w
+
+
+def test_branch_free_rounding_on_32_bit_halves_equals_ieee():
+    """The update epilogue's branch-free rounding (oz_round_pow2): the leading one found on
+    32-bit halves (clamped funnel shifts), 53 bits kept, the tie-to-even bit added after the
+    exponent field is assembled, v = 0 giving +0, and results whose exponent leaves
+    (-1020, 1022) flagged for the out-of-line path.  Restated with explicit 32-bit words."""
+    m32 = (1 << 32) - 1
+
+    def clz32(x):
+        return 32 - x.bit_length()
+
+    def funnel_lc(lo, hi, s):          # top word of (hi:lo) << min(s, 32)
+        return ((((hi << 32) | lo) << min(s, 32)) >> 32) & m32
+
+    def funnel_r(lo, hi, s):           # low word of (hi:lo) >> (s & 31)
+        return ((((hi << 32) | lo) >> (s & 31))) & m32
+
+    def branch_free(v, k):
+        sm = m32 * 2 ** 32 + m32 if v < 0 else 0
+        a = ((v & ((1 << 64) - 1)) ^ sm) - sm & ((1 << 64) - 1)
+        ah, al = a >> 32, a & m32
+        big = ah != 0
+        xh, xl = (ah, al) if big else (al, 0)
+        s = clz32(xh)
+        mh, ml = funnel_lc(xl, xh, s), funnel_lc(0, xl, s)
+        nh, nl = mh >> 11, funnel_r(ml, mh, 11)
+        up = ((ml & 0x7FF) + (nl & 1) + 0x3FF) >> 11
+        e = (63 if big else 31) - s + k
+        in_range = 0 <= e + 1019 <= 2040
+        ok = in_range or xh == 0
+        hi = (((e + 1022) << 20) + nh) & m32
+        bits = (((hi << 32) | nl) + up) & ((1 << 64) - 1)
+        bits |= sm & (1 << 63)
+        if not (xh != 0 and in_range):
+            bits = 0
+        return np.array([bits], dtype=np.uint64).view(np.float64)[0], ok
+
+    rng = np.random.default_rng(7)
+    cases = [(0, 5), (1, 0), (-1, 0), ((1 << 62) - 1, -40), (-(1 << 62) + 1, 7), ((1 << 53) + 1, 0),
+             ((1 << 53) + 3, 0), ((1 << 32) - 1, 3), (1 << 32, -3), (0x7FF, 0), (0xFFF, 2)]
+    for _ in range(60000):
+        v = int(rng.integers(-2 ** 62, 2 ** 62)) >> int(rng.integers(0, 62))
+        if rng.random() < 0.25:   # ties and near-ties
+            v = (v >> 11 << 11) | int(rng.choice([0x400, 0x3FF, 0x401, 0xC00]))
+        cases.append((v, int(rng.integers(-400, 400))))
+    # exponents at the edges of the directly assembled range
+    cases += [(3 << 40, -1020 - 41), (3 << 40, -1020 - 42), (3 << 40, 1021 - 41), (3 << 40, 1022 - 41)]
+    for v, k in cases:
+        got, ok = branch_free(v, k)
+        if v == 0:
+            assert ok and got == 0.0 and not math.copysign(1.0, got) < 0
+        elif ok:
+            assert got == math.ldexp(float(v), k), (v, k)
+        else:
+            e = v.bit_length() - 1 + k if v > 0 else (-v).bit_length() - 1 + k
+            assert not (-1020 < e < 1022) and got == 0.0
+
+
+def test_bias_product_starts_each_level_at_the_magic_number():
+    """The update kernel starts every level accumulator with one K = 16 product of constant
+    bf16 tiles, 1.0 (bits 0x3F80) times 1.5 2^19 (bits 0x4940): sixteen exact products sum to
+    1.5 2^23, so each level then holds S + 1.5 2^23, whose fp32 bits are S + 0x4B400000."""
+    one = np.array([0x3F80 << 16], dtype=np.uint32).view(np.float32)[0]
+    c = np.array([0x4940 << 16], dtype=np.uint32).view(np.float32)[0]
+    assert one == 1.0 and c == 1.5 * 2 ** 19
+    acc = np.float32(0.0)
+    for _ in range(16):
+        acc = np.float32(acc + np.float32(one * c))
+    assert acc == np.float32(12582912.0)
+    assert int(np.array([acc], dtype=np.float32).view(np.uint32)[0]) == 0x4B400000
