@@ -47,7 +47,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one chi0 launch, from one ncu capture
 # (profiles/ncu_chi0_single-site-3520_bf16x3.md), valid only for the kernel revision named.
-CHI0_TRAFFIC = {("single-site-3520", "bf16x3", "r1"): 23.26e9, ("single-site-3520", "bf16x3", "r2"): 20.77e9}
+CHI0_TRAFFIC = {("single-site-3520", "bf16x3", "r1"): 23.26e9, ("single-site-3520", "bf16x3", "r2"): 20.77e9,
+                ("single-site-3520", "bf16x3", "r3"): 31.05e9}
 
 
 def strict_json(x):
@@ -81,11 +82,12 @@ MULTI_SITE = {"batched-64-sites", "large-cell-16-sites"}
 # (workload, dyson-gj revision) -> ncu DRAM bytes (read + write) per launch of the update kernel
 DYSON_TRAFFIC = {("single-site-3520", "r1"): 27.2e6, ("single-site-3520", "r2"): 28.5e6,
                  ("single-site-3520", "r4"): 28.52e6, ("single-site-3520", "r5"): 28.52e6,
-                 ("single-site-3520", "r6"): 28.51e6}
+                 ("single-site-3520", "r6"): 28.51e6, ("single-site-3520", "r8"): 28.54e6}
 # Multi-site workloads (launches of many sizes): DRAM bytes per rewritten element of one ncu capture
 # on the workload's largest site (r = 6768, block 100: 187.27 MB read + 119.26 MB written for
 # 22,475,160 elements), applied to the average launch; valid only for the revision named.
-DYSON_TRAFFIC_PER_ELEMENT = {("batched-64-sites", "r6"): (187.27e6 + 119.26e6) / 22475160}
+DYSON_TRAFFIC_PER_ELEMENT = {("batched-64-sites", "r6"): (187.27e6 + 119.26e6) / 22475160,
+                             ("batched-64-sites", "r8"): (187.30e6 + 118.30e6) / 22475160}
 
 
 def dyson_roofline(st, workload=None, version=None, hbm_gbs=None, bf16_tflops=None):

@@ -64,22 +64,31 @@ struct OzUpdate {
   const int* ed;        // row exponents of D (rows i of C)
   const int* ee;        // row exponents of E (columns j of C)
   int x0, x1;           // rows / columns in [x0, x1) are left to the side stream
-  int ti_tiles, tj_tiles;             // tiles of 64 rows, of 128 columns
+  int ti_tiles, tiles;                // tiles of 64 rows; tiles reaching the lower triangle
   int d_plane_rows, e_plane_rows;     // padded rows of one plane (row offset between planes)
 };
 
-__device__ __forceinline__ bool oz_decode(const OzUpdate& p, int u, int& ti, int& tj) {
-  ti = u / p.tj_tiles;
-  tj = u % p.tj_tiles;
-  return tj * OZ_TJ <= ti * OZ_TI + OZ_TI - 1;   // the tile reaches the lower triangle
+// The tiles that reach the lower triangle, numbered row by row: row tile ti holds
+// tj = 0 .. floor(ti / 2) (a tile of 64 rows and 128 columns reaches the diagonal when
+// tj 128 <= ti 64 + 63), so the rows before ti hold m (m + 1) tiles for ti = 2m and
+// (m + 1)^2 for ti = 2m + 1.  Numbering only these tiles gives every CTA of the grid
+// the same count to within one.
+__host__ __device__ inline int oz_tile_count(int ti_tiles) {
+  const int m = ti_tiles >> 1;
+  return (ti_tiles & 1) ? (m + 1) * (m + 1) : m * (m + 1);
 }
 
-// The first unit at or after u, stepping by the grid, whose tile reaches the lower
-// triangle; `units` when none is left.
-__device__ __forceinline__ int oz_next(const OzUpdate& p, int u, int units, int& ti, int& tj) {
-  for (; u < units; u += gridDim.x)
-    if (oz_decode(p, u, ti, tj)) return u;
-  return units;
+__device__ __forceinline__ void oz_tile(int L, int& ti, int& tj) {
+  int s = (int)sqrtf((float)L);
+  while (s * s > L) --s;
+  while ((s + 1) * (s + 1) <= L) ++s;
+  if (L < s * s + s) {
+    ti = 2 * s - 1;
+    tj = L - s * s;
+  } else {
+    ti = 2 * s;
+    tj = L - s * s - s;
+  }
 }
 
 // An epilogue warp's share of a tile: its lane's column j, the first of its 16 rows, and
@@ -107,33 +116,49 @@ __device__ __forceinline__ OzRows oz_rows(const OzUpdate& p, int ti, int tj, int
 }
 
 // Copies rows [8H, 8H + 8) of the warp's share of C into its stage (one copy group).
-template <int H>
+// FULL: every lane takes every row (a tile inside the lower triangle), no tests.
+template <int H, bool FULL>
 __device__ __forceinline__ void oz_fetch(const OzRows& r, int ldc, uint32_t stg_s, int lane) {
 #pragma unroll
   for (int c = H * OZ_HALF; c < (H + 1) * OZ_HALF; ++c)
-    if ((r.take >> c) & 1u) cp_async8(stg_s + (uint32_t)(c * 32 + lane) * 8u, r.at + (size_t)c * ldc);
+    if (FULL || ((r.take >> c) & 1u)) cp_async8(stg_s + (uint32_t)(c * 32 + lane) * 8u, r.at + (size_t)c * ldc);
   cp_async_commit();
+}
+
+template <int H>
+__device__ __forceinline__ void oz_fetch_any(const OzRows& r, bool full, int ldc, uint32_t stg_s, int lane) {
+  if (full) oz_fetch<H, true>(r, ldc, stg_s, lane);
+  else oz_fetch<H, false>(r, ldc, stg_s, lane);
 }
 
 // C - 2^(e_i + f_j - 56) V for rows [8H, 8H + 8): rounds each V to float64, subtracts it
 // from the staged C and writes the row back.  Returns the rows whose product leaves the
 // directly assembled exponent range (left unwritten here).
-template <int H>
+template <int H, bool FULL>
 __device__ __forceinline__ unsigned oz_finish(const OzRows& r, int ldc, const double* stg,
                                               const long long (&V)[OZ_EPI_ROWS], int ei_lane, int fjm, int lane) {
+  double x[OZ_HALF];   // the staged C (stale where this lane's element is not taken)
+#pragma unroll
+  for (int c = 0; c < OZ_HALF; ++c) x[c] = stg[(H * OZ_HALF + c) * 32 + lane];
   unsigned bad = 0u;
 #pragma unroll
   for (int c = H * OZ_HALF; c < (H + 1) * OZ_HALF; ++c) {
     const int k = __shfl_sync(0xffffffffu, ei_lane, c) + fjm;
     bool ok;
     const double prod = oz_round_pow2(V[c], k, ok);
-    const double x = stg[c * 32 + lane];   // stale where this lane's element is not taken
-    if ((r.take >> c) & 1u) {
-      if (ok) r.at[(size_t)c * ldc] = x - prod;
+    if (FULL || ((r.take >> c) & 1u)) {
+      if (ok) r.at[(size_t)c * ldc] = x[c - H * OZ_HALF] - prod;
       else bad |= 1u << c;
     }
   }
   return bad;
+}
+
+template <int H>
+__device__ __forceinline__ unsigned oz_finish_any(const OzRows& r, bool full, int ldc, const double* stg,
+                                                  const long long (&V)[OZ_EPI_ROWS], int ei_lane, int fjm, int lane) {
+  return full ? oz_finish<H, true>(r, ldc, stg, V, ei_lane, fjm, lane)
+              : oz_finish<H, false>(r, ldc, stg, V, ei_lane, fjm, lane);
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -149,7 +174,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t smem_base = (smem_u32(oz_smem_raw) + 1023u) & ~1023u;
   uint8_t* const smem = oz_smem_raw + (smem_base - smem_u32(oz_smem_raw));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int units = p.ti_tiles * p.tj_tiles;
+  const int units = p.tiles;
 
   // the constant tiles of the bias product, written once and handed to the tensor cores
   uint32_t* const bias_w = reinterpret_cast<uint32_t*>(smem + OZ_STAGE);
@@ -181,8 +206,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ------------------------------------------------ TMA producer: all slice planes of a tile
     if (lane == 0) {
       uint32_t phase = 0;
-      int ti, tj;
-      for (int u = oz_next(p, blockIdx.x, units, ti, tj); u < units; u = oz_next(p, u + gridDim.x, units, ti, tj)) {
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        int ti, tj;
+        oz_tile(u, ti, tj);
         if (!mbar_wait(&empty_bar, phase ^ 1u, &abort_flag)) {
           abort_flag = 1;
           atomicCAS(status, 0, TC_TIMEOUT_PRODUCER);
@@ -204,8 +230,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const uint32_t sa = smem_base, sb = smem_base + OZ_PLANES * OZ_A_PLANE;
       const uint64_t bias_a = sw128_desc(smem_base + OZ_STAGE), bias_b = sw128_desc(smem_base + OZ_STAGE + OZ_A_PLANE);
       uint32_t phase = 0, acc_phase = 0;
-      int ti, tj;
-      for (int u = oz_next(p, blockIdx.x, units, ti, tj); u < units; u = oz_next(p, u + gridDim.x, units, ti, tj)) {
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
         if (!mbar_wait(&acce_bar, acc_phase ^ 1u, &abort_flag) || !mbar_wait(&full_bar, phase, &abort_flag)) {
           abort_flag = 1;
           atomicCAS(status, 0, TC_TIMEOUT_MMA);
@@ -251,13 +276,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const double* stg = reinterpret_cast<const double*>(smem + OZ_STAGE + OZ_BIAS) + ew * OZ_EPI_ROWS * 32;
     const uint32_t stg_s = smem_base + OZ_STAGE + OZ_BIAS + ew * OZ_EPI_ROWS * 32 * 8;
     uint32_t acc_phase = 0;
-    int ti, tj;
-    int u = oz_next(p, blockIdx.x, units, ti, tj);
+    int u = blockIdx.x;
     OzRows cur;
     cur.take = 0u;
-    if (u < units) cur = oz_rows(p, ti, tj, quarter, cg, lane);
-    oz_fetch<0>(cur, p.ldc, stg_s, lane);
-    oz_fetch<1>(cur, p.ldc, stg_s, lane);
+    if (u < units) {
+      int ti, tj;
+      oz_tile(u, ti, tj);
+      cur = oz_rows(p, ti, tj, quarter, cg, lane);
+    }
+    bool cur_full = __all_sync(0xffffffffu, cur.take == 0xFFFFu);
+    oz_fetch_any<0>(cur, cur_full, p.ldc, stg_s, lane);
+    oz_fetch_any<1>(cur, cur_full, p.ldc, stg_s, lane);
     while (u < units) {
       // the column scale of this lane and the row scales of the warp's 16 rows
       const int fjm = (cur.j < p.n ? p.ee[cur.j] : 0) - 56;
@@ -296,17 +325,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar);
       acc_phase ^= 1u;
-      int ti2, tj2;
-      const int u2 = oz_next(p, u + gridDim.x, units, ti2, tj2);
+      const int u2 = u + gridDim.x;
       OzRows nxt;
       nxt.take = 0u;
-      if (u2 < units) nxt = oz_rows(p, ti2, tj2, quarter, cg, lane);
+      if (u2 < units) {
+        int ti2, tj2;
+        oz_tile(u2, ti2, tj2);
+        nxt = oz_rows(p, ti2, tj2, quarter, cg, lane);
+      }
+      const bool nxt_full = __all_sync(0xffffffffu, nxt.take == 0xFFFFu);
       cp_async_wait_group<1>();                  // this tile's first half has landed
-      unsigned bad = oz_finish<0>(cur, p.ldc, stg, V, ei_lane, fjm, lane);
-      oz_fetch<0>(nxt, p.ldc, stg_s, lane);
+      unsigned bad = oz_finish_any<0>(cur, cur_full, p.ldc, stg, V, ei_lane, fjm, lane);
+      oz_fetch_any<0>(nxt, nxt_full, p.ldc, stg_s, lane);
       cp_async_wait_group<1>();                  // and its second half
-      bad |= oz_finish<1>(cur, p.ldc, stg, V, ei_lane, fjm, lane);
-      oz_fetch<1>(nxt, p.ldc, stg_s, lane);
+      bad |= oz_finish_any<1>(cur, cur_full, p.ldc, stg, V, ei_lane, fjm, lane);
+      oz_fetch_any<1>(nxt, nxt_full, p.ldc, stg_s, lane);
       if (__any_sync(0xffffffffu, bad != 0u)) {
         // products outside the directly assembled exponent range (C itself is still unwritten there)
 #pragma unroll
@@ -319,6 +352,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
       }
       cur = nxt;
+      cur_full = nxt_full;
       u = u2;
     }
     cp_async_wait_all();
@@ -355,12 +389,12 @@ int oz_update(lrs_ctx* ctx, const CUtensorMap& md, const CUtensorMap& me, double
   p.x0 = x0;
   p.x1 = x1;
   p.ti_tiles = (n + OZ_TI - 1) / OZ_TI;
-  p.tj_tiles = (n + OZ_TJ - 1) / OZ_TJ;
+  p.tiles = oz_tile_count(p.ti_tiles);
   p.d_plane_rows = rows_pad;
   p.e_plane_rows = rows_pad;
   if (!ctx->capturing)
     LRS_CUDA_TRY(cudaFuncSetAttribute(oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  const int grid = std::min(p.ti_tiles * p.tj_tiles, ctx->num_sms);
+  const int grid = std::min(p.tiles, ctx->num_sms);
   oz_update_kernel<<<grid, OZ_THREADS, OZ_SMEM, stream>>>(md, me, p, ctx->ws.status.ptr + 8);
   return after_launch(ctx, "oz_update_kernel");
 }

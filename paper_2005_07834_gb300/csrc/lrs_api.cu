@@ -381,7 +381,7 @@ const char* lrs_last_error(void) { return g_last_error.c_str(); }
 
 // The chi0 tensor-core kernel revision lets measurements quote profiler
 // counters only for the kernel version they were taken on.
-const char* lrs_version(void) { return "lrs 0.6 (sm_103a) chi0-tc r3 dyson-gj r7"; }
+const char* lrs_version(void) { return "lrs 0.6 (sm_103a) chi0-tc r3 dyson-gj r8"; }
 
 int lrs_create(lrs_ctx** out, int device, int precision, void* stream) {
   clear_error();
