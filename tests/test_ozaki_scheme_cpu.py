@@ -285,3 +285,64 @@ def test_bias_product_starts_each_level_at_the_magic_number():
         acc = np.float32(acc + np.float32(one * c))
     assert acc == np.float32(12582912.0)
     assert int(np.array([acc], dtype=np.float32).view(np.uint32)[0]) == 0x4B400000
+
+
+def _update_tile(L):
+    """The update kernel's numbering of the tiles that reach the lower triangle (oz_tile)."""
+    s = int(math.sqrt(L))
+    while s * s > L:
+        s -= 1
+    while (s + 1) * (s + 1) <= L:
+        s += 1
+    return (2 * s - 1, L - s * s) if L < s * s + s else (2 * s, L - s * s - s)
+
+
+def _update_tile_count(ti_tiles):
+    m = ti_tiles >> 1
+    return (m + 1) * (m + 1) if ti_tiles & 1 else m * (m + 1)
+
+
+def test_update_tiles_numbered_directly_are_the_lower_triangle_tiles():
+    """Tiles of 64 rows x 128 columns: the direct numbering lists, in row order, exactly the tiles
+    with tj 128 <= ti 64 + 63, and no column tile beyond ceil(n / 128)."""
+    for n in list(range(1, 700)) + [2592, 3889, 6768, 9312]:
+        ti_tiles, tj_tiles = -(-n // 64), -(-n // 128)
+        want = [(ti, tj) for ti in range(ti_tiles) for tj in range(tj_tiles) if tj * 128 <= ti * 64 + 63]
+        got = [_update_tile(L) for L in range(_update_tile_count(ti_tiles))]
+        assert got == want, n
+
+
+@pytest.mark.parametrize("n,x0,x1,grid", [(100, 0, 64, 152), (130, 32, 96, 152), (257, 224, 257, 7),
+                                          (700, 320, 384, 152), (1000, 0, 0, 3), (64, 0, 32, 152), (1, 0, 0, 152)])
+def test_update_tile_walk_rewrites_each_lower_element_once(n, x0, x1, grid):
+    """The update's epilogue walk (16 warps, each 32 columns of its TMEM lane quarter x 16 rows, the
+    per-lane row masks): every element on or below the diagonal outside the rows and columns
+    [x0, x1) is rewritten exactly once, nothing else is touched, and stage indices stay in range."""
+    ti_tiles = -(-n // 64)
+    tiles = _update_tile_count(ti_tiles)
+    hits = np.zeros((n, n), np.int32)
+    g = min(tiles, grid)
+    for b in range(g):
+        for L in range(b, tiles, g):
+            ti, tj = _update_tile(L)
+            for ew in range(16):
+                quarter, cg = (ew + 2) & 3, ew >> 2
+                i0 = ti * 64 + cg * 16
+                rows_in = 0
+                for lane in range(16):
+                    i = i0 + lane
+                    if i < n and not (x0 <= i < x1):
+                        rows_in |= 1 << lane
+                for lane in range(32):
+                    j = tj * 128 + quarter * 32 + lane
+                    rmin = j - i0
+                    lower = 0xFFFF if rmin <= 0 else (0 if rmin >= 16 else (0xFFFF << rmin) & 0xFFFF)
+                    take = (rows_in & lower) if (j < n and not (x0 <= j < x1)) else 0
+                    for c in range(16):
+                        if take >> c & 1:
+                            assert ew * 16 * 32 + c * 32 + lane < 16 * 16 * 32
+                            hits[i0 + c, j] += 1
+    want = np.tril(np.ones((n, n), np.int32))
+    want[x0:x1, :] = 0
+    want[:, x0:x1] = 0
+    assert np.array_equal(hits, want)
