@@ -359,6 +359,7 @@ static void free_workspace(lrs_ctx* ctx) {
   release(ctx, w.planes_a); release(ctx, w.planes_b); release(ctx, w.slab); release(ctx, w.denom32); release(ctx, w.phase_tab32); release(ctx, w.tc_scratch); release(ctx, w.slab64);
   release(ctx, w.site_tiles);
   release(ctx, w.planes_t); release(ctx, w.planes_h); release(ctx, w.g32); release(ctx, w.yz32); release(ctx, w.psi32);
+  release(ctx, w.gamma_chk);
   release(ctx, w.adj_tiles);
   release(ctx, w.gj);
   release(ctx, w.gjb);
@@ -580,13 +581,13 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
   LRS_TRY(ensure(ctx, ctx->d_col_o, Ko)); LRS_TRY(ensure(ctx, ctx->d_col_u, Ku));
   LRS_CUDA_TRY(cudaMemcpyAsync(ctx->coeff.ptr, coeff, ncoef * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
   if (gamma_candidate) {
-    // scratch: partner [ng] ints, then the max bits and the flag
-    DevBuf<int> tmp;
+    // scratch (kept in the workspace: freeing device memory waits for the whole device, which
+    // would stall other contexts' work on every load): partner [ng] ints, the max bits, the flag
     const size_t words = (size_t)ng + 6;
-    LRS_TRY(ensure(ctx, tmp, words));
-    int* d_partner = tmp.ptr;
-    unsigned long long* d_max = reinterpret_cast<unsigned long long*>(tmp.ptr + ((ng + 1) & ~1));
-    int* d_bad = tmp.ptr + ((ng + 1) & ~1) + 2;
+    LRS_TRY(ensure(ctx, ctx->ws.gamma_chk, words));
+    int* d_partner = ctx->ws.gamma_chk.ptr;
+    unsigned long long* d_max = reinterpret_cast<unsigned long long*>(d_partner + ((ng + 1) & ~1));
+    int* d_bad = d_partner + ((ng + 1) & ~1) + 2;
     int rc = LRS_OK;
     int bad = 1;
     cudaError_t e = cudaMemcpyAsync(d_partner, partner.data(), ng * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
@@ -600,7 +601,6 @@ int lrs_load_orbitals(lrs_ctx* ctx, const double* cell, int nk, const double* kp
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) rc = set_error(LRS_ERR_CUDA, "Gamma-point check: %s", cudaGetErrorString(e));
-    dev_free_temp(ctx, tmp.ptr, words * sizeof(int));
     if (rc != LRS_OK) return rc;
     ctx->real_orbitals = bad == 0;
   }

@@ -177,6 +177,7 @@ struct Workspace {
   DevBuf<float2> g32;                   // Go, Gu^T of one frequency
   DevBuf<float2> yz32;                  // Yo, Zo, Yu, Zu of one frequency
   DevBuf<float2> psi32;                 // the site's orbitals in fp32 (mixed adjoint)
+  DevBuf<int> gamma_chk;                // Gamma-point check at load: G partners, max bits, flag
   DevBuf<SiteTile> adj_tiles;           // unit table of the adjoint launches
   DevBuf<double> gj;                    // SPD inverse: column block, signed copy, D, pivot inverse
   DevBuf<double> gjb;                   // blocked SPD inverse: C, E, D [n][128] and the pivot block
