@@ -689,6 +689,9 @@ def multisite_measure(args, lrs, wl, stream, steps, warmup, peaks, compare=True,
                             peaks["hbm_gbs"], peaks["bf16_tflops"])
     if roof_w is not None:
         roof_w["timed_with_lanes"] = 1
+        # the W stage of that solve (wall time on one lane) against the updates' share of it
+        roof_w["w_stage_ms_one_lane"] = st_w["ms_w"]
+        roof_w["update_ms_one_lane"] = st_w["ms_w_main"]
     dominant_w = roof_w is not None and st_w["ms_w_main"] > main_ms
     out = {"value": len(wl.sites) * 1e3 / ms, "unit": "site builds/s", "ms_per_step": ms, "steps": steps,
            "warmup": warmup, "tflops": flop_all / (ms * 1e-3) / 1e12, "autotuned": tuned,
