@@ -406,9 +406,13 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
                                 ((long long)tb << 14) + (long long)tc;
             const int j = col0 + ch * 8 + c;
             const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
+            // branch-free rounding; the out-of-line path only where the exponent leaves its range
+            bool ok;
+            double prod = oz_round_pow2(V, ei + fj - 56, ok);
+            if (!ok) prod = oz_i64_times_pow2_slow(V, ei + fj - 56);
             stg[c * OG_STG_LD + lane] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
                                             ? __longlong_as_double(0x7ff8000000000000ll)   // NaN, as in float64
-                                            : oz_i64_times_pow2(V, ei + fj - 56);
+                                            : prod;
           }
           __syncwarp();
 #pragma unroll
