@@ -222,6 +222,49 @@ __device__ __forceinline__ int og_b_batch(const OgGemm& p, int b) {
 
 // ROWWISE: C is row-major (cs == 1) and a warp stores 4 rows x 8 columns per step; otherwise each
 // lane stores its own row (consecutive words when rs == 1).
+// One 64-bit integer per element from the eight level sums of an epilogue step, in units of
+// 2^-56 of the scaled product: V = sum_L S_L 2^(42 - 7 L) with floor(S_7 / 2^7) (|V| < 2^62; the
+// floor drops less than 2^-56 of the row scales' product).
+__device__ __forceinline__ long long og_level_value(const float (&a)[OG_LEVELS][8], int c) {
+  const int ta = oz_pair<7>(oz_level_bits(a[1][c]), oz_level_bits(a[2][c]));
+  const int tb = oz_pair<7>(oz_level_bits(a[3][c]), oz_level_bits(a[4][c]));
+  const int tc = oz_pair<7>(oz_level_bits(a[5][c]), oz_level_bits(a[6][c])) + oz_level_shr<7>(oz_level_bits(a[7][c]));
+  return ((long long)oz_level_int(a[0][c]) << 42) + ((long long)ta << 28) + ((long long)tb << 14) + (long long)tc;
+}
+
+// Writes one staged step of 8 columns into C (alpha times the product, plus beta C, plus the
+// diagonal term), with the launch's uniform options as template arguments so that the loop over
+// the elements tests none of them.  neg flips the sign (alpha = -1) with an integer instruction.
+template <bool ROWWISE, bool READ_C, bool GEN_ALPHA, bool DIAG>
+__device__ __forceinline__ void og_write_step(const OgGemm& p, double* C, const double* stg, int row0, int colc,
+                                              int lane, long long neg, double cscale, int b) {
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int r = ROWWISE ? it * 4 + (lane >> 3) : lane, c = ROWWISE ? lane & 7 : it;
+    const int i = row0 + r, j = colc + c;
+    if (i < p.m && j < p.n) {
+      double v = __longlong_as_double(__double_as_longlong(stg[c * OG_STG_LD + r]) ^ neg);
+      if (GEN_ALPHA) v *= p.alpha;
+      if (READ_C) v = fma(cscale, C[i * p.rs + j * p.cs], v);
+      if (DIAG && i * p.dI + j * p.dJ + b * p.dB == 0) v += p.dadd;
+      C[i * p.rs + j * p.cs] = v;
+    }
+  }
+}
+
+template <bool ROWWISE, bool READ_C>
+__device__ __forceinline__ void og_write_step_any(const OgGemm& p, double* C, const double* stg, int row0, int colc,
+                                                  int lane, long long neg, bool gen_alpha, bool diag, double cscale,
+                                                  int b) {
+  if (gen_alpha) {
+    if (diag) og_write_step<ROWWISE, READ_C, true, true>(p, C, stg, row0, colc, lane, neg, cscale, b);
+    else og_write_step<ROWWISE, READ_C, true, false>(p, C, stg, row0, colc, lane, neg, cscale, b);
+  } else {
+    if (diag) og_write_step<ROWWISE, READ_C, false, true>(p, C, stg, row0, colc, lane, neg, cscale, b);
+    else og_write_step<ROWWISE, READ_C, false, false>(p, C, stg, row0, colc, lane, neg, cscale, b);
+  }
+}
+
 template <bool ROWWISE>
 __global__ void __launch_bounds__(OG_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -383,6 +426,8 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
         tc_fence_after();
         const bool read_c = sg > 0 || !p.beta_zero;
         const double cscale = sg > 0 ? 1.0 : p.beta;
+        const bool gen_alpha = p.alpha_mode == 2, diag = p.has_diag && sg == 0;
+        const long long neg = p.alpha_mode == 1 ? (long long)0x8000000000000000ull : 0ll;
         constexpr bool rowwise = ROWWISE;
 #pragma unroll 1
         for (int ch = 0; ch < OG_EPI_COLS / 8; ++ch) {
@@ -392,42 +437,39 @@ __global__ void __launch_bounds__(OG_THREADS, 1)
           for (int lv = 0; lv < OG_LEVELS; ++lv)
             tmem_ld8(tbase + lane_off + lv * OG_TN + cg * OG_EPI_COLS + ch * 8, a[lv]);
           tmem_ld_wait();
+          unsigned badm = 0u;   // columns whose product leaves the directly assembled exponent range
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            // one 64-bit integer in units of 2^-56 of the scaled product,
-            // V = sum_L S_L 2^(42 - 7 L) with floor(S_7 / 2^7) (|V| < 2^62; the floor drops
-            // less than 2^-56 of the row scales' product), rounded to float64 with integer
-            // instructions
-            const int ta = oz_pair<7>(oz_level_bits(a[1][c]), oz_level_bits(a[2][c]));
-            const int tb = oz_pair<7>(oz_level_bits(a[3][c]), oz_level_bits(a[4][c]));
-            const int tc = oz_pair<7>(oz_level_bits(a[5][c]), oz_level_bits(a[6][c])) +
-                           oz_level_shr<7>(oz_level_bits(a[7][c]));
-            const long long V = ((long long)oz_level_int(a[0][c]) << 42) + ((long long)ta << 28) +
-                                ((long long)tb << 14) + (long long)tc;
+            const long long V = og_level_value(a, c);
             const int j = col0 + ch * 8 + c;
             const int fj = p.eb[(size_t)bb * p.b_rows_pad + j];   // padded rows hold 0
-            // branch-free rounding; the out-of-line path only where the exponent leaves its range
             bool ok;
-            double prod = oz_round_pow2(V, ei + fj - 56, ok);
-            if (!ok) prod = oz_i64_times_pow2_slow(V, ei + fj - 56);
+            const double prod = oz_round_pow2(V, ei + fj - 56, ok);
+            badm |= ok ? 0u : (1u << c);
             stg[c * OG_STG_LD + lane] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
                                             ? __longlong_as_double(0x7ff8000000000000ll)   // NaN, as in float64
                                             : prod;
           }
-          __syncwarp();
+          if (__any_sync(0xffffffffu, badm != 0u)) {
+            // rare: those products again from the levels (still in TMEM), through float64
+            float a2[OG_LEVELS][8];
 #pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            const int r = rowwise ? it * 4 + (lane >> 3) : lane, c = rowwise ? lane & 7 : it;
-            const int i = row0 + r, j = col0 + ch * 8 + c;
-            if (i < p.m && j < p.n) {
-              double v = stg[c * OG_STG_LD + r];
-              if (p.alpha_mode == 1) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
-              else if (p.alpha_mode == 2) v *= p.alpha;
-              if (read_c) v = fma(cscale, C[i * p.rs + j * p.cs], v);
-              if (p.has_diag && sg == 0 && i * p.dI + j * p.dJ + b * p.dB == 0) v += p.dadd;
-              C[i * p.rs + j * p.cs] = v;
+            for (int lv = 0; lv < OG_LEVELS; ++lv)
+              tmem_ld8(tbase + lane_off + lv * OG_TN + cg * OG_EPI_COLS + ch * 8, a2[lv]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              if ((badm >> c) & 1u) {
+                const int fj = p.eb[(size_t)bb * p.b_rows_pad + col0 + ch * 8 + c];
+                stg[c * OG_STG_LD + lane] = (ei == OG_BAD_EXP || fj == OG_BAD_EXP)
+                                                ? __longlong_as_double(0x7ff8000000000000ll)
+                                                : oz_i64_times_pow2_slow(og_level_value(a2, c), ei + fj - 56);
+              }
             }
           }
+          __syncwarp();
+          if (read_c) og_write_step_any<rowwise, true>(p, C, stg, row0, col0 + ch * 8, lane, neg, gen_alpha, diag, cscale, b);
+          else og_write_step_any<rowwise, false>(p, C, stg, row0, col0 + ch * 8, lane, neg, gen_alpha, diag, cscale, b);
           __syncwarp();
         }
         tc_fence_before();
