@@ -75,39 +75,18 @@ __device__ __forceinline__ int oz_level_shr(unsigned b) {
   return (int)(b >> W) - (int)(OZ_LEVEL_BIAS >> W);
 }
 
-// Out-of-range results of oz_i64_times_pow2, kept out of line so that its float64
-// instructions are not issued (predicated off) on the common path.
+// v 2^k rounded to float64 through the float64 pipe, for the results that oz_round_pow2
+// does not assemble (subnormal or beyond the normal range): kept out of line so that its
+// float64 instructions stay off the common path.
 static __device__ __noinline__ double oz_i64_times_pow2_slow(long long v, int k) { return ldexp((double)v, k); }
 
-// v 2^k rounded to the nearest float64 (ties to even) from the bits of v:
-// find the leading one, keep 53 bits, round on the 11 dropped bits and add
-// the exponent.  Results outside the normal range take a float64 path
-// (ldexp), which the slice scaling makes rare.
-__device__ __forceinline__ double oz_i64_times_pow2(long long v, int k) {
-  if (v == 0) return 0.0;
-  const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
-  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  const unsigned long long m = a << lz;                 // leading one at bit 63
-  unsigned long long mant = m >> 11;                    // 53 bits, leading one at bit 52
-  const unsigned int rem = (unsigned int)(m & 0x7FFull);
-  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
-  const int e = 63 - lz + k;                            // exponent of the leading one
-  if (e > -1020 && e < 1022) {
-    // the leading one of mant adds one to the biased exponent field; a rounding carry
-    // to 2^53 adds another and leaves a zero fraction, as it should
-    return __longlong_as_double((long long)(sign | ((((unsigned long long)(e + 1022)) << 52) + mant)));
-  }
-  return oz_i64_times_pow2_slow(v, k);
-}
-
-// The same rounding without branches, for |v| < 2^63: the leading one is found on
-// 32-bit halves (a clamped funnel shift normalises both cases), the rounding bit is
-// added after the exponent is assembled (a carry out of the fraction moves into the
-// exponent, as it should), and v = 0 gives +0.  Where the result would leave the
-// range that oz_i64_times_pow2 assembles directly, `ok` is false and the result is +0;
-// the caller then takes oz_i64_times_pow2_slow.  Where both are defined the two
-// functions return the same bits.
+// v 2^k rounded to the nearest float64 (ties to even) from the bits of v, without
+// branches, for |v| < 2^63: the leading one is found on 32-bit halves (a clamped
+// funnel shift normalises both cases), 53 bits are kept, the rounding bit is added
+// after the exponent is assembled (a carry out of the fraction moves into the
+// exponent, as it should), and v = 0 gives +0.  Where the exponent of the leading
+// one leaves (-1020, 1022), `ok` is false and the result is +0; the caller then takes
+// oz_i64_times_pow2_slow, which the slice scaling makes rare.
 __device__ __forceinline__ double oz_round_pow2(long long v, int k, bool& ok) {
   const unsigned long long sm = (unsigned long long)(v >> 63);   // all ones when v < 0
   const unsigned long long a = ((unsigned long long)v ^ sm) - sm;

@@ -120,8 +120,9 @@ def test_magic_number_reads_level_sums_exactly():
 
 
 def test_integer_rounding_equals_ieee_round_to_nearest_even():
-    """The kernels' rounding of a 64-bit integer (leading one, 53 bits, ties to even on the 11
-    dropped bits, exponent added) equals float(v) 2^k."""
+    """The rounding of a 64-bit integer (leading one, 53 bits, ties to even on the 11 dropped bits,
+    exponent added), written on whole 64-bit words, equals float(v) 2^k; the kernels compute the
+    same steps on 32-bit halves without branches (pinned in the next test)."""
     rng = np.random.default_rng(3)
 
     def by_bits(v, k):
