@@ -165,7 +165,7 @@ struct Workspace {
   DevBuf<double> tmp_nn;              // [n][n]
   // mixed precision (bf16 hi/lo operand planes)
   DevBuf<uint16_t> planes_a, planes_b;  // chi0: per-frequency A, frequency-independent B
-  DevBuf<float> slab;                   // chi0: [nf][Np][Np] fp32 Re[Go o Gu^T] per frequency
+  DevBuf<float> slab;                   // chi0: nf slabs of Np^2 fp32 Re[Go o Gu^T] (layout of slab_index)
   DevBuf<float2> denom32;               // chi0: [nf][Kp] scaled fp32 denominators of the A planes
   DevBuf<float2> phase_tab32;           // projection: fp32 copy of the phase tables
   DevBuf<float> tc_scratch;             // chi0: per-CTA parked occupied sums
